@@ -1,0 +1,258 @@
+"""Pins of the oracle's EM weights, SIRT update, NCC/registration and metrics
+against facts fixed by statistics and algebra (not by re-typing formulas):
+
+* EM on residuals drawn from a known Gaussian + uniform mixture recovers
+  sigma and the inlier proportion c within sampling error;
+* degenerate cases: constant residuals -> m = 0 -> p = 1; p lies in [0, 1] and
+  decreases with |e|;
+* patch potentials: all-inlier patches have p-bar = 1 exactly when m = 0;
+  planted outlier patches (a heavy-tailed residual population) are masked;
+* SIRT on a consistent system (y = A x*) reduces the data residual
+  monotonically and keeps x >= 0;
+* NCC: self-similarity 1, invariance to positive affine intensity changes,
+  sign flip for negative scaling; gradient = central finite differences;
+* noiseless registration recovers a known rigid transform;
+* PSNR of a known MSE, CC/SSIM of identical images.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import pvr_oracle as O
+from paper_1611_07289_b300 import synth
+
+
+def _one_patch_desc(P, n):
+    return np.array([[0, 0, 0, 0, n, 1, p * n, 0] for p in range(P)], dtype=np.int32)
+
+
+def test_em_recovers_mixture_parameters():
+    rng = np.random.default_rng(0)
+    n = 200_000
+    sigma_t, c_t, lo, hi = 7.0, 0.8, -400.0, 400.0
+    inl = rng.uniform(size=n) < c_t
+    e = np.where(inl, rng.normal(0, sigma_t, n), rng.uniform(lo, hi, n))
+    e[0], e[1] = lo, hi  # pin the range so m = 1 / (hi - lo)
+    desc = _one_patch_desc(1, n)
+    y = e.astype(np.float32)
+    sim = np.zeros(n)
+    valid = np.ones(n, dtype=np.uint8)
+    st = O.new_state()
+    ep = O.em_params(c0=0.5)
+    for _ in range(60):
+        O.em_weights(y, sim, valid, desc, ep, st)
+    sigma = math.sqrt(st[O.ST["SIGMA2"]])
+    c = st[O.ST["C"]]
+    assert abs(st[O.ST["M"]] - 1.0 / (hi - lo)) < 1e-12
+    assert abs(sigma - sigma_t) < 0.05 * sigma_t
+    assert abs(c - c_t) < 0.01
+
+
+def test_em_degenerate_and_monotone():
+    n = 64
+    desc = _one_patch_desc(1, n)
+    valid = np.ones(n, dtype=np.uint8)
+    st = O.new_state()
+    p, wp, pbar, mask = O.em_weights(np.full(n, 3.0, np.float32), np.zeros(n), valid, desc,
+                                     O.em_params(), st)
+    assert st[O.ST["M"]] == 0.0 and np.all(p == 1.0) and pbar[0] == 1.0
+    e = np.linspace(-50, 50, n)
+    st = O.new_state()
+    p, _, _, _ = O.em_weights(e.astype(np.float32), np.zeros(n), valid, desc, O.em_params(), st)
+    assert np.all((p >= 0) & (p <= 1))
+    a = np.abs(e)
+    order = np.argsort(a)
+    assert np.all(np.diff(p[order]) <= 1e-15)
+    # invalid pixels get p = 0 and do not enter the statistics
+    valid2 = valid.copy()
+    valid2[:8] = 0
+    st2 = O.new_state()
+    p2, _, _, _ = O.em_weights(e.astype(np.float32), np.zeros(n), valid2, desc, O.em_params(), st2)
+    assert np.all(p2[:8] == 0) and st2[O.ST["N_PART"]] == n - 8
+
+
+def test_planted_outlier_patches_are_masked():
+    rng = np.random.default_rng(1)
+    P, n = 60, 400
+    bad = set(rng.choice(P, 6, replace=False).tolist())
+    e = np.empty(P * n)
+    for s in range(P):
+        if s in bad:
+            e[s * n:(s + 1) * n] = rng.normal(0, 150.0, n)   # misregistered / corrupted
+        else:
+            e[s * n:(s + 1) * n] = rng.normal(0, 10.0, n)
+    desc = _one_patch_desc(P, n)
+    st = O.new_state()
+    mask = None
+    for _ in range(5):
+        p, wp, pbar, mask = O.em_weights(e.astype(np.float32), np.zeros(P * n),
+                                         np.ones(P * n, np.uint8), desc, O.em_params(), st, mask)
+    got_bad = {s for s in range(P) if mask[s] == 0}
+    assert got_bad == bad
+    assert all(pbar[s] < min(pbar[t] for t in range(P) if t not in bad) for s in bad)
+    # threshold rule: same classification with a threshold between the groups
+    thr = 0.5 * (max(pbar[s] for s in bad) + min(pbar[t] for t in range(P) if t not in bad))
+    st1 = O.new_state()
+    _, w1, pb1, m1 = O.em_weights(e.astype(np.float32), np.zeros(P * n), np.ones(P * n, np.uint8),
+                                  desc, O.em_params(patch_rule=1, patch_threshold=thr), st1, mask)
+    assert {s for s in range(P) if m1[s] == 0} == bad
+
+
+def test_patch_with_few_valid_pixels_is_excluded():
+    P, n = 4, 100
+    desc = _one_patch_desc(P, n)
+    valid = np.ones(P * n, np.uint8)
+    valid[0:95] = 0  # patch 0: 5 % valid (< 10 %)
+    rng = np.random.default_rng(2)
+    e = rng.normal(0, 5, P * n).astype(np.float32)
+    st = O.new_state()
+    _, wp, _, mask = O.em_weights(e, np.zeros(P * n), valid, desc, O.em_params(), st)
+    assert mask[0] == 0 and wp[0] == 0.0 and st[O.ST["N_ELIG"]] == 3
+
+
+def test_sirt_reduces_residual_on_consistent_data():
+    rng = np.random.default_rng(7)
+    geom = synth.random_geometry(rng, n=12, n_stacks=3, W=10, H=10, K=6, thick=2.0)
+    desc, npix = synth.all_patches(geom, 5, 5)
+    poses = synth.random_poses(rng, desc.shape[0], rot=3.0, trans=0.5)
+    G = O.geom(geom)
+    ps = O.psf(1.2, 1, 2, 1.0)
+    fix = O.pose_fixed(G, ps, desc, poses)
+    xt = rng.uniform(0, 100, geom.n_vox).astype(np.float32)
+    y, valid, _ = O.simulate(G, ps, xt, desc, fix, npix)
+    x = O.volume_init(G, ps, desc, fix, y)
+    prev = None
+    for _ in range(8):
+        s, _, _ = O.simulate(G, ps, x.astype(np.float32), desc, fix, npix)
+        res = np.linalg.norm((y - s)[valid > 0])
+        if prev is not None:
+            assert res < prev
+        prev = res
+        addon, conf = O.adjoint(G, ps, desc, fix, r=np.where(valid > 0, y - s, 0.0), w=None)
+        x = O.volume_update(x, addon, conf, 1.0)
+        assert np.all(x >= 0)
+
+
+def test_sirt_step_maps_constant_data_to_the_constant():
+    """Rows of A sum to one, so for y = c on every valid pixel one SIRT step
+    from x = 0 gives x = c exactly on every voxel a sample reached."""
+    rng = np.random.default_rng(8)
+    geom = synth.random_geometry(rng, n=10, n_stacks=3, W=8, H=8, K=4, thick=2.0)
+    desc, npix = synth.all_patches(geom, 4, 2)
+    poses = synth.random_poses(rng, desc.shape[0], rot=10.0, trans=1.0)
+    G = O.geom(geom)
+    ps = O.psf(1.2, 1, 2, 1.0)
+    fix = O.pose_fixed(G, ps, desc, poses)
+    _, valid, _ = O.simulate(G, ps, np.zeros(geom.n_vox, np.float32), desc, fix, npix)
+    r = np.where(valid > 0, 250.0, 0.0)
+    w = rng.uniform(0.2, 1.0, npix)
+    addon, conf = O.adjoint(G, ps, desc, fix, r=r, w=w)
+    x1 = O.volume_update(np.zeros(geom.n_vox), addon, conf, 1.0, 1e-6)
+    reached = conf > 1e-6
+    assert reached.sum() > 100
+    np.testing.assert_allclose(x1[reached], 250.0, rtol=1e-12)
+    assert np.all(x1[~reached] == 0.0)
+
+
+def _reg_case(seed=0):
+    cfg = synth.config_tiny(seed=1611, noise=False)
+    geom = cfg["geom"]
+    x = cfg["gt"].reshape(-1)
+    rng = np.random.default_rng(seed)
+    desc, npix = synth.all_patches(geom, 32, 16)
+    # central patches: their PSF samples stay inside the volume for the poses
+    # used here, where NCC is a smooth function of the pose (a sample leaving
+    # the volume changes the normalisation discontinuously)
+    central = np.flatnonzero((desc[:, 2] == 16) & (desc[:, 3] == 16) & (desc[:, 1] >= 5)
+                             & (desc[:, 1] <= 14))
+    sel = rng.choice(central, 6, replace=False)
+    d = desc[sel].copy()
+    off = 0
+    for r in d:
+        r[6] = off
+        off += int(r[4] * r[5])
+    return geom, x, d, off
+
+
+def test_ncc_identities():
+    geom, x, d, npix = _reg_case()
+    G = O.geom(geom)
+    ps = O.psf(1.2, 1, 3, 1.0)
+    th = np.zeros((d.shape[0], 6))
+    th[:, 3:] = 2.0
+    fix = O.pose_fixed(G, ps, d, th)
+    y, valid, _ = O.simulate(G, ps, x, d, fix, npix)
+    for s in range(d.shape[0]):
+        off = int(d[s, 6])
+        ys = y[off:off + 1024]
+        for scale, shift, expect in ((1.0, 0.0, 1.0), (2.5, 40.0, 1.0), (-1.0, 500.0, -1.0)):
+            yy = np.zeros(npix, np.float32)
+            yy[off:off + 1024] = (scale * ys + shift).astype(np.float32)
+            v, _ = O.ncc_grad(G, ps, x, yy, d[s], th[s])
+            assert abs(v - expect) < 1e-6, (s, scale, v)
+
+
+def test_ncc_gradient_matches_finite_differences():
+    geom, x, d, npix = _reg_case(1)
+    G = O.geom(geom)
+    ps = O.psf(1.2, 1, 3, 1.0)
+    th_true = np.zeros((d.shape[0], 6))
+    fix = O.pose_fixed(G, ps, d, th_true)
+    y, _, _ = O.simulate(G, ps, x, d, fix, npix)
+    y = y.astype(np.float32)
+    rng = np.random.default_rng(3)
+    h = 1e-4
+    for s in range(3):
+        th = th_true[s] + np.concatenate([rng.uniform(-2, 2, 3), rng.uniform(-3, 3, 3)])
+        _, g = O.ncc_grad(G, ps, x, y, d[s], th, exact=False)
+        fd = np.zeros(6)
+        for k in range(6):
+            tp, tm = th.copy(), th.copy()
+            tp[k] += h
+            tm[k] -= h
+            fd[k] = (O.ncc_grad(G, ps, x, y, d[s], tp, exact=False)[0]
+                     - O.ncc_grad(G, ps, x, y, d[s], tm, exact=False)[0]) / (2 * h)
+        assert np.linalg.norm(g - fd) <= 2e-3 * np.linalg.norm(fd) + 1e-9, (g, fd)
+        # the fixed-point (exact) gradient is the same quantity up to 2^-20 voxel
+        _, ge = O.ncc_grad(G, ps, x, y, d[s], th, exact=True)
+        assert np.linalg.norm(ge - g) <= 1e-3 * np.linalg.norm(g)
+
+
+def test_noiseless_registration_recovers_known_transform():
+    from scipy.ndimage import gaussian_filter
+    geom, _, d, npix = _reg_case(2)
+    # a textured volume makes every pose direction observable from a patch
+    tex = gaussian_filter(np.random.default_rng(8).normal(size=(64, 64, 64)), 2.5)
+    x = (500 + 400 * tex / tex.std()).astype(np.float32).reshape(-1)
+    G = O.geom(geom)
+    ps = O.psf(1.2, 1, 3, 1.0)
+    rng = np.random.default_rng(4)
+    th_true = np.concatenate([rng.uniform(-1, 1, (d.shape[0], 3)), rng.uniform(-2, 2, (d.shape[0], 3))], 1)
+    fix = O.pose_fixed(G, ps, d, th_true)
+    y, _, _ = O.simulate(G, ps, x, d, fix, npix)
+    start = th_true + np.concatenate([rng.uniform(-3, 3, (d.shape[0], 3)),
+                                      rng.uniform(-5, 5, (d.shape[0], 3))], 1)
+    rp = O.reg_params(n_eval=200, delta0=2.0, delta_min=1e-4)
+    got, ncc = O.register(G, ps, rp, x, y.astype(np.float32), d, start)
+    err_t = np.abs(got[:, :3] - th_true[:, :3]).max()
+    err_r = np.abs(got[:, 3:] - th_true[:, 3:]).max()
+    assert np.all(ncc > 0.999)
+    assert err_t < 0.1 and err_r < 0.1, (err_t, err_r)
+
+
+def test_metrics_closed_forms():
+    rng = np.random.default_rng(0)
+    ref = rng.uniform(0, 1000, 5000)
+    ref[0] = 1000.0
+    m = O.metrics(ref, ref + 10.0)
+    assert abs(m["mse"] - 100.0) < 1e-9
+    assert abs(m["psnr"] - 40.0) < 1e-9
+    assert abs(m["cc"] - 1.0) < 1e-12
+    s = O.metrics(ref, ref)
+    assert abs(s["ssim"] - 1.0) < 1e-12 and abs(s["dssim"]) < 1e-12 and s["cc"] > 1 - 1e-12
+    neg = O.metrics(ref, 2000.0 - ref)
+    assert abs(neg["cc"] + 1.0) < 1e-12
+    # SSIM drops below 1 for a noisy copy and DSSIM = (1 - SSIM) / 2
+    n = O.metrics(ref, ref + rng.normal(0, 100, ref.size))
+    assert 0 < n["ssim"] < 1 and abs(n["dssim"] - (1 - n["ssim"]) / 2) < 1e-15
