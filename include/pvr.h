@@ -1,0 +1,295 @@
+/*
+ * pvr.h -- C ABI of the B300 (sm_103a) PVR hot-path library, libpvr.so.
+ *
+ * PVR (patch-to-volume reconstruction, Alansary et al., arXiv:1611.07289)
+ * reconstructs a high-resolution volume x from many small 2-D patches y_s of
+ * motion-corrupted slice stacks (Sec. II, Eq. patch), each patch with its own
+ * rigid pose, by alternating patch-to-volume registration with NCC (Sec. II),
+ * super-resolution through the PSF forward model x_i = W_i y + n_i,
+ * W_i = D B T_i (Eq. 1) and its adjoint, and EM outlier rejection at pixel
+ * and patch level (Sec. II, Eqs. m, p, p-bar).
+ *
+ * Conventions (all entry points):
+ *  - Every array argument is a DEVICE pointer owned by the caller, unless the
+ *    argument is documented as host.  The library never frees or keeps them.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL = the legacy default stream), except where "synchronises" is
+ *    stated.  No call allocates memory: the scratch a call needs was
+ *    allocated by pvr_ctx_create, sized by pvr_params.max_patches /
+ *    max_pixels.
+ *  - Return value: PVR_OK (0) or a negative pvr_status.  Arguments are
+ *    checked on the host before anything is launched; on error nothing is
+ *    enqueued and pvr_last_error(ctx) gives a one-line message.  Problems
+ *    only the device can see (a patch row outside its stack, a non-finite
+ *    pose) set a device error word instead: the offending patch is treated
+ *    as empty and pvr_device_status() reports the error later.
+ *  - Layouts: volume [nz][ny][nx] float32, x fastest.  Stacks: one packed
+ *    float32 buffer, stack after stack, each [K][H][W].  Patch table:
+ *    int32 [n][8] rows {stack, slice, x0, y0, w, h, pix_off, 0}: the patch
+ *    covers columns x0..x0+w-1, rows y0..y0+h-1 of the slice; its pixels are
+ *    stored row-major at pix_off .. pix_off + w*h - 1 of every per-pixel
+ *    array.  Poses: float64 [n][6] = (tx, ty, tz in mm, rx, ry, rz in
+ *    degrees), transform T(w) = R (w - c) + c + t, R = Rz Ry Rx, c = world
+ *    centre of the patch rectangle; T maps an acquired sample position
+ *    (scanner world) to the reconstruction's world frame.
+ *  - Geometry: 3x4 row-major affine matrices (implied last row 0 0 0 1):
+ *    world_to_voxel maps mm to voxel index (voxel centres at integers);
+ *    pixel_to_world[s] maps (column, row, slice) of stack s to mm.
+ *
+ * Thread safety: one pvr_ctx may be used from one host thread at a time;
+ * calls on one context that overlap on the GPU (different streams) race on
+ * its scratch.  Separate contexts are independent.
+ */
+#ifndef PVR_H
+#define PVR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define PVR_API __attribute__((visibility("default")))
+#else
+#define PVR_API
+#endif
+
+#define PVR_MAX_STACKS 16
+#define PVR_MAX_KXY 3
+#define PVR_MAX_KZ 8
+#define PVR_EM_STATE_LEN 16
+
+typedef enum pvr_status {
+    PVR_OK = 0,
+    PVR_ERR_INVALID_ARG = -1, /* bad argument or capacity exceeded (host check) */
+    PVR_ERR_CUDA = -2,        /* a CUDA runtime call failed */
+    PVR_ERR_NUMERIC = -3,     /* non-finite pose or state seen on the device */
+    PVR_ERR_BOUNDS = -4,      /* a patch row outside its stack / pixel range */
+    PVR_ERR_TIMEOUT = -5,     /* reserved: a bounded device wait gave up */
+    PVR_ERR_UNSUPPORTED = -6  /* valid request this build does not implement */
+} pvr_status;
+
+/* EM state vector (float64, device, PVR_EM_STATE_LEN entries).  Zero it
+ * before the first pvr_em_weights / pvr_reconstruct_iter call. */
+enum pvr_em_state_index {
+    PVR_ST_INIT = 0,      /* 0 until the first EM call has initialised it */
+    PVR_ST_SIGMA2 = 1,    /* inlier residual variance sigma^2 (Sec. II) */
+    PVR_ST_C = 2,         /* inlier proportion c */
+    PVR_ST_M = 3,         /* outlier density m = 1/(max e - min e) of the last call */
+    PVR_ST_MU_P = 4,      /* patch-level inlier mean of p-bar */
+    PVR_ST_SIGMA2_P = 5,  /* patch-level inlier variance */
+    PVR_ST_C_P = 6,       /* patch-level inlier proportion */
+    PVR_ST_M_P = 7,       /* patch-level outlier density */
+    PVR_ST_N_PART = 8,    /* participating pixels of the last call */
+    PVR_ST_SUM_P = 9,     /* sum p over them */
+    PVR_ST_SUM_PE2 = 10,  /* sum p e^2 over them */
+    PVR_ST_EMIN = 11,     /* min e */
+    PVR_ST_EMAX = 12,     /* max e */
+    PVR_ST_N_ELIG = 13,   /* patches eligible for classification */
+    PVR_ST_N_IN = 14,     /* patches classified inlier */
+    PVR_ST_SIGMA2_USED = 15 /* sigma^2 used by the E-step of the last call */
+};
+
+typedef struct pvr_geometry {
+    int32_t nx, ny, nz;                             /* volume size, each >= 2 */
+    int32_t n_stacks;                               /* 1..PVR_MAX_STACKS */
+    int32_t stack_w[PVR_MAX_STACKS];                /* columns */
+    int32_t stack_h[PVR_MAX_STACKS];                /* rows */
+    int32_t stack_k[PVR_MAX_STACKS];                /* slices */
+    double world_to_voxel[12];                      /* 3x4, mm -> voxel index */
+    double pixel_to_world[PVR_MAX_STACKS][12];      /* 3x4, (col,row,slice) -> mm */
+    double thickness[PVR_MAX_STACKS];               /* slice thickness = through-plane FWHM, mm */
+} pvr_geometry;
+
+typedef struct pvr_params {
+    /* Gaussian PSF (Sec. II; the Gaussian approximation of the cited prior
+     * work).  In-plane taps at pixel offsets -kxy..kxy with weight
+     * exp(-d^2 / 2 sigma_xy^2), sigma_xy = fwhm_xy / (2 sqrt(2 ln 2)) px;
+     * through-plane samples at zeta * dz mm, zeta = -kz..kz, weight
+     * exp(-(zeta dz)^2 / 2 sigma_z^2), sigma_z = thickness / (2 sqrt(2 ln 2)). */
+    double psf_fwhm_xy;     /* pixels (default 1.2) */
+    int32_t psf_kxy;        /* 0..PVR_MAX_KXY (default 1) */
+    int32_t psf_kz;         /* 0..PVR_MAX_KZ (default 3) */
+    double psf_dz;          /* mm, > 0 (default 1.0; use the voxel size) */
+    /* super-resolution (weighted SIRT) */
+    double alpha;           /* step, 0 < alpha < 2 (default 1) */
+    double conf_eps;        /* voxels with A^T w <= conf_eps are not updated (1e-6) */
+    /* EM outlier model */
+    double em_c0;           /* initial inlier proportion (0.9) */
+    double em_sigma_floor_rel; /* sigma^2 >= (rel * range e)^2 (1e-3) */
+    double em_min_valid_frac;  /* patches with fewer valid pixels are excluded (0.1) */
+    int32_t patch_rule;     /* 0: Gaussian/uniform patch model, 1: threshold */
+    double patch_threshold; /* rule 1 threshold on p-bar (0.5) */
+    int32_t patch_em_iters; /* patch-level EM iterations per call (5) */
+    /* registration */
+    int32_t n_params;       /* 6 = rigid (only value this build supports) */
+    int32_t reg_evals;      /* NCC evaluations per registration round (40) */
+    double reg_delta0;      /* initial step in scaled units (2) */
+    double reg_delta_min;   /* stop below this step (0.01) */
+    double reg_grow;        /* step factor after an accepted trial (1) */
+    int32_t reg_fixed_step; /* 1: always accept, constant step */
+    int32_t reg_min_valid;  /* fewer valid pixels: NCC = 0, no update (16) */
+    /* outer iteration */
+    int32_t n_sr;           /* SR passes per pvr_reconstruct_iter (1) */
+    /* capacity of the context's scratch */
+    int32_t max_patches;    /* largest patch count of any call */
+    int64_t max_pixels;     /* largest total pixel count of any call */
+    int32_t max_patch_side; /* largest patch width or height (1..256) */
+} pvr_params;
+
+/* Patch table handed to every per-patch call (host struct, device table). */
+typedef struct pvr_patches {
+    const int32_t *desc;    /* device int32 [n][8], see layout above */
+    int32_t n;              /* number of patches, 0..max_patches */
+    int32_t max_side;       /* largest w or h in the table (0: max_patch_side) */
+    int64_t n_pix;          /* pixels: every pix_off + w*h <= n_pix <= max_pixels */
+} pvr_patches;
+
+typedef struct pvr_ctx pvr_ctx;
+
+/* Fill *p with the defaults listed above (max_patches 65536,
+ * max_pixels 2^27, max_patch_side 128). */
+PVR_API void pvr_params_default(pvr_params *p);
+
+/* Create a context on the current CUDA device: copies the geometry and the
+ * parameters, derives the PSF tables and allocates all scratch (the only
+ * allocation the library makes).  Synchronises.  Errors:
+ * PVR_ERR_INVALID_ARG for a bad geometry/parameter, PVR_ERR_CUDA when an
+ * allocation fails (*out is then NULL). */
+PVR_API int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *geom, const pvr_params *params);
+
+/* Free the context and its scratch (synchronises the device).  NULL is a no-op. */
+PVR_API int pvr_ctx_destroy(pvr_ctx *ctx);
+
+/* Last host-side error message of this context ("" if none). */
+PVR_API const char *pvr_last_error(const pvr_ctx *ctx);
+
+/* Synchronise `stream`, read and clear the device error word: PVR_OK,
+ * PVR_ERR_BOUNDS or PVR_ERR_NUMERIC. */
+PVR_API int pvr_device_status(pvr_ctx *ctx, void *stream);
+
+/* Number of kernel launches this context has enqueued since creation
+ * (host counter; for launch accounting). */
+PVR_API int64_t pvr_launch_count(const pvr_ctx *ctx);
+
+/* Square patch table (Sec. II "Patch Extraction": size a, stride `stride`).
+ * Candidates x0, y0 = 0, stride, 2 stride, ... with x0 + a <= W, y0 + a <= H,
+ * on every slice of every stack, ordered by stack, slice, y0, x0.  A
+ * candidate is kept when at least keep_frac * a^2 of its pixels exceed
+ * fg_frac * I_max (I_max = largest stack pixel; level and comparisons in
+ * float32, count test in float64).  stacks: device float32, packed.
+ * desc_out: device int32 [max_out][8].  n_out, n_pix_out: HOST pointers;
+ * the call synchronises `stream` to return them.  If more than max_out
+ * patches are kept, *n_out is the full count and only max_out rows are
+ * written.  The fixed-point lattice and every later step take the table as
+ * is, so caller-made tables (uneven patch sizes) are equally valid. */
+PVR_API int pvr_patches_build(pvr_ctx *ctx, const float *stacks, int32_t a, int32_t stride,
+                      double fg_frac, double keep_frac, int32_t *desc_out, int32_t max_out,
+                      int32_t *n_out, int64_t *n_pix_out, void *stream);
+
+/* Copy every patch's pixels out of the packed stacks into y (float32
+ * [n_pix], patch after patch, row-major). */
+PVR_API int pvr_patches_gather(pvr_ctx *ctx, const float *stacks, const pvr_patches *patches, float *y,
+                       void *stream);
+
+/* Pose -> fixed-point sample lattice (Eq. 1, the motion part T_i of W_i).
+ * For each patch, M = world_to_voxel . T(theta) . pixel_to_world[stack]
+ * evaluated in float64 with a fixed operation order (no FMA; sine and
+ * cosine from their Taylor series after reduction to +-45 degrees), then
+ * quantised to Q11.20 (round half to even): fix int32 [n][16] =
+ * {o(3), e_col(3), e_row(3), e_zeta(3), ok, 0, 0, 0}; o = voxel position of
+ * patch pixel (0,0), e_col / e_row = one pixel step, e_zeta = one PSF step
+ * of psf_dz mm along the slice normal.  ok = 0 when the patch's sample box
+ * leaves +-1024 voxels or a value does not fit (the patch is then empty). */
+PVR_API int pvr_pose_to_fixed(pvr_ctx *ctx, const pvr_patches *patches, const double *poses,
+                      int32_t *fix, void *stream);
+
+/* Forward model simulate_patches (Eq. 1; Sec. II super-resolution): every
+ * patch pixel is the PSF-weighted mean of trilinear samples of x at its
+ * transformed sample positions (samples outside the volume carry no
+ * weight).  sim: float32 [n_pix]; valid: uint8 [n_pix], 0 where no sample
+ * fell inside (sim = 0 there). */
+PVR_API int pvr_simulate(pvr_ctx *ctx, const float *x, const pvr_patches *patches, const double *poses,
+                 float *sim, uint8_t *valid, void *stream);
+
+/* Adjoint of pvr_simulate (the super-resolution update's back-projection):
+ * addon = A^T (w .* r), conf = A^T w, A the matrix of pvr_simulate at these
+ * poses.  r, w: float32 [n_pix] or NULL (= all ones).  addon, conf: float32
+ * [nx*ny*nz], either may be NULL (skipped).  accumulate = 0 zeroes them
+ * first, 1 adds.  Summation order on the device is not fixed (float atomics). */
+PVR_API int pvr_adjoint(pvr_ctx *ctx, const pvr_patches *patches, const double *poses, const float *r,
+                const float *w, float *addon, float *conf, int32_t accumulate, void *stream);
+
+/* EM outlier weights (Sec. II "EM-Based Outlier Removal", Eqs. m, p, p-bar).
+ * e = y - sim on valid pixels (sim == NULL: y already holds e).
+ * Participating pixels = valid pixels of patches with mask_in = 1
+ * (mask_in == NULL: all).  First call (state[INIT] == 0): sigma^2 = mean e^2,
+ * c = em_c0.  m = 1/(max e - min e) over participating pixels (0 if the range
+ * is < 1e-12).  E-step on every valid pixel: p = G c / (G c + m (1 - c)),
+ * G = N(e; 0, sigma^2), p = 1 if m = 0, p = 0 on invalid pixels.  M-step
+ * over participating pixels: sigma^2 = sum p e^2 / sum p (floored), c =
+ * sum p / N.  Patch potential p-bar = sqrt(sum p^2 / N_valid) per patch;
+ * patches with N_valid < em_min_valid_frac * w * h are excluded; the rest are
+ * classified by patch_rule (0: one-sided Gaussian inlier vs uniform outlier
+ * model on p-bar, patch_em_iters EM iterations, w_patch = inlier posterior,
+ * mask = w_patch >= 0.5; 1: w_patch = p-bar, mask = p-bar >= threshold).
+ * state: float64 device [PVR_EM_STATE_LEN], in/out.  p: float32 [n_pix];
+ * w_patch, pbar: float32 [n] (pbar may be NULL); mask_out: uint8 [n]
+ * (must not alias mask_in). */
+PVR_API int pvr_em_weights(pvr_ctx *ctx, const float *y, const float *sim, const uint8_t *valid,
+                   const pvr_patches *patches, double *state, const uint8_t *mask_in,
+                   uint8_t *mask_out, float *p, float *w_patch, float *pbar, void *stream);
+
+/* Weighted SIRT step of the super-resolution update (rows of A sum to one):
+ * where conf > conf_eps, x = max(x + alpha * addon / conf, 0).  If
+ * clear_accumulators, addon and conf are zeroed in the same pass. */
+PVR_API int pvr_volume_update(pvr_ctx *ctx, float *x, float *addon, float *conf, int32_t clear_accumulators,
+                      void *stream);
+
+/* Initial volume x = A^T y / A^T 1 (0 where A^T 1 <= conf_eps) at `poses`. */
+PVR_API int pvr_volume_init(pvr_ctx *ctx, float *x, const float *y, const pvr_patches *patches,
+                    const double *poses, void *stream);
+
+/* NCC of every patch against the volume simulated at its pose, and its
+ * gradient with respect to the 6 pose parameters (Sec. II: CC similarity,
+ * Eq. cross_corr with population deviations, over valid pixels; the PSF
+ * normalisation is held constant in the derivative).  Fewer than
+ * reg_min_valid valid pixels or a constant patch: NCC = 0, gradient 0.
+ * ncc: float64 [n]; grad: float64 [n][6] (may be NULL). */
+PVR_API int pvr_ncc_grad(pvr_ctx *ctx, const float *x, const float *y, const pvr_patches *patches,
+                 const double *poses, double *ncc, double *grad, void *stream);
+
+/* Patch-wise gradient ascent on NCC (Sec. II; Sec. III "patch-wise gradient
+ * descent"): n_evals NCC evaluations per patch, the first at the current
+ * pose, then trials best + delta * g/|g| in scaled units (translations in
+ * mm, angles x patch half-diagonal in radians); a trial that strictly
+ * improves NCC is kept (delta *= reg_grow), otherwise delta halves; a patch
+ * stops when delta < reg_delta_min.  reg_fixed_step: always accept.
+ * poses: float64 [n][6] in/out; ncc: float64 [n] best NCC (may be NULL). */
+PVR_API int pvr_register(pvr_ctx *ctx, const float *x, const float *y, const pvr_patches *patches,
+                 double *poses, int32_t n_evals, double *ncc, void *stream);
+
+/* One outer PVR iteration (Sec. II loop): pvr_register with reg_evals
+ * evaluations, then n_sr super-resolution passes, each: simulate, residual
+ * e = y - sim, EM weights (mask carried from pass to pass), weighted adjoint
+ * of e with pixel weight mask_patch * p, SIRT update of x.  x: in/out;
+ * poses: in/out; state: EM state in/out; mask: uint8 [n] in/out (set to 1
+ * before the first call); p (float32 [n_pix]) and w_patch (float32 [n])
+ * receive the last pass's weights (either may be NULL). */
+PVR_API int pvr_reconstruct_iter(pvr_ctx *ctx, float *x, const float *y, const pvr_patches *patches,
+                         double *poses, double *state, uint8_t *mask, float *p, float *w_patch,
+                         void *stream);
+
+/* Evaluation metrics (Sec. IV-A) of img against ref over n values (mask
+ * NULL: all): out float64 device [5] = {PSNR = 10 log10(I_max^2/MSE),
+ * CC (Eq. cross_corr), SSIM (single global window, Eq. SSIM with the
+ * denominator's first factor mu_I^2 + mu_J^2 + c1), DSSIM = (1-SSIM)/2, MSE}. */
+PVR_API int pvr_metrics(pvr_ctx *ctx, const float *ref, const float *img, const uint8_t *mask, int64_t n,
+                double *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PVR_H */

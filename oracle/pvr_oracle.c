@@ -633,22 +633,19 @@ void or_volume_update(double *x, const double *addon, const double *conf, size_t
 
 /* -------------------------------------------------------- registration -- */
 
-/* Derivative of the transformed world point with respect to pose parameter k
- * at world point w (before the transform), for T(w) = L (w - c) + c + t.
- * Rigid angles are in degrees. */
-static void or_dT_dtheta(const double *th, int n_params, int k, const double c[3], const double w[3],
-                         double out[3])
+/* Derivatives of the linear part of the transform with respect to each pose
+ * parameter (3x3 each, dL[k - 3] for k = 3..n_params-1).  Rigid: d(Rz Ry
+ * Rx)/d angle per degree (libm trigonometry: the gradient is not part of
+ * the bit-exact integer path); affine: the unit matrix E_rc. */
+static void or_dlinear(const double *th, int n_params, double dL[9][9])
 {
-    double u[3] = {w[0] - c[0], w[1] - c[1], w[2] - c[2]};
-    memset(out, 0, 3 * sizeof(double));
-    if (k < 3) { out[k] = 1.0; return; }
     if (n_params == 12) {
-        int r = (k - 3) / 3, col = (k - 3) % 3;
-        out[r] = u[col];
+        for (int k = 0; k < 9; ++k) {
+            memset(dL[k], 0, 9 * sizeof(double));
+            dL[k][k] = 1.0;
+        }
         return;
     }
-    /* rigid: d/dangle of Rz Ry Rx, computed with libm trigonometry (the
-     * gradient is not part of the bit-exact integer path) */
     double ax = th[3] * M_PI / 180.0, ay = th[4] * M_PI / 180.0, az = th[5] * M_PI / 180.0;
     double Rx[9] = {1, 0, 0, 0, cos(ax), -sin(ax), 0, sin(ax), cos(ax)};
     double Ry[9] = {cos(ay), 0, sin(ay), 0, 1, 0, -sin(ay), 0, cos(ay)};
@@ -656,22 +653,35 @@ static void or_dT_dtheta(const double *th, int n_params, int k, const double c[3
     double dRx[9] = {0, 0, 0, 0, -sin(ax), -cos(ax), 0, cos(ax), -sin(ax)};
     double dRy[9] = {-sin(ay), 0, cos(ay), 0, 0, 0, -cos(ay), 0, -sin(ay)};
     double dRz[9] = {-sin(az), -cos(az), 0, cos(az), -sin(az), 0, 0, 0, 0};
-    const double *A = (k == 5) ? dRz : Rz;
-    const double *B = (k == 4) ? dRy : Ry;
-    const double *C = (k == 3) ? dRx : Rx;
-    double AB[9], ABC[9];
-    for (int r = 0; r < 3; ++r)
-        for (int cc = 0; cc < 3; ++cc) {
-            AB[r * 3 + cc] = 0.0;
-            for (int t = 0; t < 3; ++t) AB[r * 3 + cc] += A[r * 3 + t] * B[t * 3 + cc];
-        }
-    for (int r = 0; r < 3; ++r)
-        for (int cc = 0; cc < 3; ++cc) {
-            ABC[r * 3 + cc] = 0.0;
-            for (int t = 0; t < 3; ++t) ABC[r * 3 + cc] += AB[r * 3 + t] * C[t * 3 + cc];
-        }
-    for (int r = 0; r < 3; ++r)
-        out[r] = (ABC[r * 3 + 0] * u[0] + ABC[r * 3 + 1] * u[1] + ABC[r * 3 + 2] * u[2]) * (M_PI / 180.0);
+    for (int k = 3; k < 6; ++k) {
+        const double *A = (k == 5) ? dRz : Rz;
+        const double *B = (k == 4) ? dRy : Ry;
+        const double *Cm = (k == 3) ? dRx : Rx;
+        double AB[9];
+        for (int r = 0; r < 3; ++r)
+            for (int cc = 0; cc < 3; ++cc) {
+                AB[r * 3 + cc] = 0.0;
+                for (int t = 0; t < 3; ++t) AB[r * 3 + cc] += A[r * 3 + t] * B[t * 3 + cc];
+            }
+        for (int r = 0; r < 3; ++r)
+            for (int cc = 0; cc < 3; ++cc) {
+                double v = 0.0;
+                for (int t = 0; t < 3; ++t) v += AB[r * 3 + t] * Cm[t * 3 + cc];
+                dL[k - 3][r * 3 + cc] = v * (M_PI / 180.0);
+            }
+    }
+}
+
+/* Derivative of the transformed world point T(w) = L (w - c) + c + t with
+ * respect to pose parameter k at world point w (before the transform). */
+static void or_dT_dtheta(const double dL[9][9], int k, const double c[3], const double w[3],
+                         double out[3])
+{
+    double u[3] = {w[0] - c[0], w[1] - c[1], w[2] - c[2]};
+    memset(out, 0, 3 * sizeof(double));
+    if (k < 3) { out[k] = 1.0; return; }
+    const double *D = dL[k - 3];
+    for (int r = 0; r < 3; ++r) out[r] = D[r * 3 + 0] * u[0] + D[r * 3 + 1] * u[1] + D[r * 3 + 2] * u[2];
 }
 
 /* Sample position for the registration evaluation.  With exact = 1 the
@@ -745,6 +755,8 @@ double or_ncc_grad(const or_geom *g, const or_psf *psf, const float *x, const fl
     or_patch_centre(g, d, c);
     const double *S = g->p2w[d[0]];
     const double *W = g->w2v;
+    double dL[9][9];
+    or_dlinear(th, n_params, dL);
     for (int k = 0; k < n_params; ++k) grad[k] = 0.0;
     if (exact && !f[12]) return 0.0;
 
@@ -769,7 +781,7 @@ double or_ncc_grad(const or_geom *g, const or_psf *psf, const float *x, const fl
                             wp[r] = S[r * 4 + 0] * px + S[r * 4 + 1] * py + S[r * 4 + 2] * pk + S[r * 4 + 3];
                         for (int k = 0; k < n_params; ++k) {
                             double dT[3], dq[3];
-                            or_dT_dtheta(th, n_params, k, c, wp, dT);
+                            or_dT_dtheta(dL, k, c, wp, dT);
                             for (int r = 0; r < 3; ++r)
                                 dq[r] = W[r * 4 + 0] * dT[0] + W[r * 4 + 1] * dT[1] + W[r * 4 + 2] * dT[2];
                             jac[k] += wt * (gr[0] * dq[0] + gr[1] * dq[1] + gr[2] * dq[2]);

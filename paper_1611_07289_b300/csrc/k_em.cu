@@ -1,0 +1,559 @@
+// EM robust statistics (Sec. II "EM-Based Outlier Removal", Eqs. m, p,
+// p-bar), the weighted SIRT volume update and the per-patch registration
+// optimiser step.
+//
+// Pixel work (residual statistics, E-step) runs on the same (patch, tile)
+// grid as the forward model and leaves float64 partial sums per tile, so
+// every reduction is deterministic: single-CTA kernels fold the partials in
+// a fixed order in float64 (the M-step and the patch-level model, whose
+// stability needs it).
+#include <math.h>
+
+#include "pvr_internal.h"
+
+namespace pvr {
+namespace {
+
+constexpr int kRedThreads = 1024;
+
+// Pixel range of block's (patch, tile).
+struct TileRange {
+    int p, t, off, w, i0, j0, tw, th;
+};
+
+// Returns false for an empty tile or a descriptor whose pixel range is not
+// inside [0, n_pix) (then err gets bit 1 and nothing is touched).
+__device__ __forceinline__ bool tile_range(const int32_t *__restrict__ desc, const Tiling &tl,
+                                           long long n_pix, int32_t *err, TileRange &r)
+{
+    r.p = blockIdx.x / tl.tpp;
+    r.t = blockIdx.x % tl.tpp;
+    const int32_t *d = desc + 8 * (size_t)r.p;
+    r.w = d[4];
+    int h = d[5];
+    r.off = d[6];
+    if (r.w < 1 || h < 1 || r.off < 0 || (long long)r.off + (long long)r.w * h > n_pix) {
+        if (threadIdx.x == 0 && r.t == 0) atomicOr(err, 1);
+        return false;
+    }
+    r.i0 = (r.t % tl.tiles_x) * tl.T;
+    r.j0 = (r.t / tl.tiles_x) * tl.T;
+    if (r.i0 >= r.w || r.j0 >= h) return false;
+    r.tw = min(tl.T, r.w - r.i0);
+    r.th = min(tl.T, h - r.j0);
+    return true;
+}
+
+// Block sum / min / max of NV doubles; every thread gets the result.
+template <int NV>
+__device__ void block_reduce(double *v, double *sh, int op /*0 sum, 1 min, 2 max*/)
+{
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = op == 0 ? x + y : (op == 1 ? fmin(x, y) : fmax(x, y));
+        }
+        v[k] = x;
+    }
+    __syncthreads();
+    if (lane == 0)
+        for (int k = 0; k < NV; ++k) sh[wid * NV + k] = v[k];
+    __syncthreads();
+    for (int k = 0; k < NV; ++k) {
+        double x = sh[k];
+        for (int w = 1; w < nw; ++w) {
+            double y = sh[w * NV + k];
+            x = op == 0 ? x + y : (op == 1 ? fmin(x, y) : fmax(x, y));
+        }
+        v[k] = x;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double clampd(double v, double lo, double hi)
+{
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// Residual statistics of a tile for a standalone EM call:
+// part[0..3] = {N_valid, sum e^2, min e, max e}, e = y - sim (sim null: e = y).
+__global__ void __launch_bounds__(256) k_em_stats(const float *__restrict__ y,
+                                                  const float *__restrict__ sim,
+                                                  const uint8_t *__restrict__ valid,
+                                                  const int32_t *__restrict__ desc, Tiling tl,
+                                                  long long n_pix, int32_t *__restrict__ err,
+                                                  double *__restrict__ part)
+{
+    __shared__ double sh[32 * 2];
+    TileRange r;
+    double *pt = part + (size_t)blockIdx.x * kPartStride;
+    if (!tile_range(desc, tl, n_pix, err, r)) {
+        if (threadIdx.x < 4) pt[threadIdx.x] = 0.0;
+        return;
+    }
+    double a[2] = {0.0, 0.0};
+    double mn[1] = {INFINITY}, mx[1] = {-INFINITY};
+    for (int pp = threadIdx.x; pp < r.tw * r.th; pp += blockDim.x) {
+        size_t o = (size_t)r.off + (size_t)(r.j0 + pp / r.tw) * r.w + r.i0 + pp % r.tw;
+        if (!valid[o]) continue;
+        float e = sim ? y[o] - sim[o] : y[o];
+        a[0] += 1.0;
+        a[1] += (double)(e * e);
+        mn[0] = fmin(mn[0], (double)e);
+        mx[0] = fmax(mx[0], (double)e);
+    }
+    block_reduce<2>(a, sh, 0);
+    block_reduce<1>(mn, sh, 1);
+    block_reduce<1>(mx, sh, 2);
+    if (threadIdx.x == 0) {
+        pt[0] = a[0];
+        pt[1] = a[1];
+        pt[2] = mn[0];
+        pt[3] = mx[0];
+    }
+}
+
+// Step 1-3: participating-pixel statistics -> initial sigma^2, c (first
+// call), outlier density m, E-step constants.
+// pstat: [0] sigma^2 floor, [1] first call, [2] m, [3] 1/(2 sigma^2),
+//        [4] m (1-c) sqrt(2 pi) sigma / c.
+__global__ void __launch_bounds__(kRedThreads) k_em_prepare(int n, int tpp,
+                                                            const uint8_t *__restrict__ mask_in,
+                                                            const double *__restrict__ part,
+                                                            double *__restrict__ state,
+                                                            double *__restrict__ pstat, double c0,
+                                                            double floor_rel)
+{
+    __shared__ double sh[32 * 2];
+    double a[2] = {0.0, 0.0}, mn[1] = {INFINITY}, mx[1] = {-INFINITY};
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        if (mask_in && !mask_in[p]) continue;
+        for (int t = 0; t < tpp; ++t) {
+            const double *pt = part + ((size_t)p * tpp + t) * kPartStride;
+            if (pt[0] > 0.0) {
+                a[0] += pt[0];
+                a[1] += pt[1];
+                mn[0] = fmin(mn[0], pt[2]);
+                mx[0] = fmax(mx[0], pt[3]);
+            }
+        }
+    }
+    block_reduce<2>(a, sh, 0);
+    block_reduce<1>(mn, sh, 1);
+    block_reduce<1>(mx, sh, 2);
+    if (threadIdx.x == 0) {
+        double npart = a[0];
+        double range = npart > 0.0 ? mx[0] - mn[0] : 0.0;
+        double sfloor = (floor_rel * range) * (floor_rel * range);
+        if (sfloor < 1e-12) sfloor = 1e-12;
+        bool first = state[PVR_ST_INIT] == 0.0;
+        if (first) {
+            double s2 = npart > 0.0 ? a[1] / npart : 1.0;
+            state[PVR_ST_SIGMA2] = s2 < sfloor ? sfloor : s2;
+            state[PVR_ST_C] = clampd(c0, 1e-3, 1.0 - 1e-3);
+        }
+        double m = range >= 1e-12 ? 1.0 / range : 0.0;
+        double s2 = state[PVR_ST_SIGMA2], c = state[PVR_ST_C];
+        state[PVR_ST_M] = m;
+        state[PVR_ST_SIGMA2_USED] = s2;
+        state[PVR_ST_EMIN] = mn[0];
+        state[PVR_ST_EMAX] = mx[0];
+        state[PVR_ST_N_PART] = npart;
+        pstat[0] = sfloor;
+        pstat[1] = first ? 1.0 : 0.0;
+        pstat[2] = m;
+        pstat[3] = 1.0 / (2.0 * s2);
+        pstat[4] = m * (1.0 - c) * sqrt(2.0 * 3.14159265358979323846) * sqrt(s2) / c;
+    }
+}
+
+// Step 4: E-step p = G c / (G c + m (1 - c)) = 1 / (1 + K exp(e^2 / 2 sigma^2)),
+// K = m (1 - c) sqrt(2 pi) sigma / c; p = 1 if m = 0; p = 0 on invalid pixels.
+// part[4..7] = {sum p, sum p e^2 (participating), sum p^2, N_valid}.
+__global__ void __launch_bounds__(256) k_em_estep(const float *__restrict__ y,
+                                                  const float *__restrict__ sim,
+                                                  const uint8_t *__restrict__ valid,
+                                                  const int32_t *__restrict__ desc, Tiling tl,
+                                                  long long n_pix, int32_t *__restrict__ err,
+                                                  const uint8_t *__restrict__ mask_in,
+                                                  const double *__restrict__ pstat,
+                                                  float *__restrict__ p_out,
+                                                  double *__restrict__ part)
+{
+    __shared__ double sh[32 * 4];
+    TileRange r;
+    double *pt = part + (size_t)blockIdx.x * kPartStride;
+    if (!tile_range(desc, tl, n_pix, err, r)) {
+        if (threadIdx.x < 4) pt[4 + threadIdx.x] = 0.0;
+        return;
+    }
+    const bool m_zero = pstat[2] == 0.0;
+    const float inv2s2 = (float)pstat[3], K = (float)pstat[4];
+    const bool part_in = !mask_in || mask_in[r.p];
+    float sp = 0.f, spe2 = 0.f, sp2 = 0.f, nv = 0.f;
+    for (int pp = threadIdx.x; pp < r.tw * r.th; pp += blockDim.x) {
+        size_t o = (size_t)r.off + (size_t)(r.j0 + pp / r.tw) * r.w + r.i0 + pp % r.tw;
+        float pv = 0.f;
+        if (valid[o]) {
+            float e = sim ? y[o] - sim[o] : y[o];
+            pv = m_zero ? 1.f : 1.f / (1.f + K * expf(e * e * inv2s2));
+            if (part_in) {
+                sp += pv;
+                spe2 = fmaf(pv * e, e, spe2);
+            }
+            sp2 = fmaf(pv, pv, sp2);
+            nv += 1.f;
+        }
+        p_out[o] = pv;
+    }
+    double a[4] = {(double)sp, (double)spe2, (double)sp2, (double)nv};
+    block_reduce<4>(a, sh, 0);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) pt[4 + k] = a[k];
+}
+
+// Steps 5-7: M-step, patch potentials, patch classification (one CTA).
+// scratch: pbar (float64 [n]), w (float64 [n]), elig (uint8 [n]).
+__global__ void __launch_bounds__(kRedThreads) k_em_mstep(
+    const int32_t *__restrict__ desc, int n, int tpp, const uint8_t *__restrict__ mask_in,
+    const double *__restrict__ part, double *__restrict__ state, const double *__restrict__ pstat,
+    double c0, double min_valid_frac, int rule, double threshold, int iters,
+    double *__restrict__ pbar, double *__restrict__ wsc, uint8_t *__restrict__ elig,
+    uint8_t *__restrict__ mask_out, float *__restrict__ w_patch, float *__restrict__ pbar_out)
+{
+    __shared__ double sh[32 * 4];
+    __shared__ double bc[4];
+    // 5: M-step
+    double a[2] = {0.0, 0.0};
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        if (mask_in && !mask_in[p]) continue;
+        for (int t = 0; t < tpp; ++t) {
+            const double *pt = part + ((size_t)p * tpp + t) * kPartStride;
+            a[0] += pt[4];
+            a[1] += pt[5];
+        }
+    }
+    block_reduce<2>(a, sh, 0);
+    const bool first = pstat[1] != 0.0;
+    if (threadIdx.x == 0) {
+        double sfloor = pstat[0], npart = state[PVR_ST_N_PART];
+        if (a[0] > 0.0) {
+            double s2 = a[1] / a[0];
+            state[PVR_ST_SIGMA2] = s2 < sfloor ? sfloor : s2;
+        }
+        if (npart > 0.0) state[PVR_ST_C] = clampd(a[0] / npart, 1e-3, 1.0 - 1e-3);
+        state[PVR_ST_SUM_P] = a[0];
+        state[PVR_ST_SUM_PE2] = a[1];
+    }
+    // 6: patch potentials
+    double mm[1] = {INFINITY}, mxx[1] = {-INFINITY}, s[2] = {0.0, 0.0};
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        double sp2 = 0.0, nv = 0.0;
+        for (int t = 0; t < tpp; ++t) {
+            const double *pt = part + ((size_t)p * tpp + t) * kPartStride;
+            sp2 += pt[6];
+            nv += pt[7];
+        }
+        const int32_t *d = desc + 8 * (size_t)p;
+        double npx = (double)d[4] * (double)d[5];
+        double pb = nv > 0.0 ? sqrt(sp2 / nv) : 0.0;
+        bool el = nv > 0.0 && nv >= min_valid_frac * npx;
+        pbar[p] = pb;
+        elig[p] = el ? 1 : 0;
+        if (el) {
+            mm[0] = fmin(mm[0], pb);
+            mxx[0] = fmax(mxx[0], pb);
+            s[0] += pb;
+            s[1] += 1.0;
+        }
+    }
+    block_reduce<1>(mm, sh, 1);
+    block_reduce<1>(mxx, sh, 2);
+    block_reduce<2>(s, sh, 0);
+    const double nelig = s[1];
+    // 7: classification
+    if (rule == 1) {
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            wsc[p] = elig[p] ? pbar[p] : 0.0;
+            mask_out[p] = (elig[p] && pbar[p] >= threshold) ? 1 : 0;
+        }
+    } else {
+        const double mp = (nelig > 0.0 && mxx[0] - mm[0] >= 1e-12) ? 1.0 / (mxx[0] - mm[0]) : 0.0;
+        if (first) {
+            double mu = nelig > 0.0 ? s[0] / nelig : 0.0;
+            double v[1] = {0.0};
+            for (int p = threadIdx.x; p < n; p += blockDim.x)
+                if (elig[p]) v[0] += (pbar[p] - mu) * (pbar[p] - mu);
+            block_reduce<1>(v, sh, 0);
+            if (threadIdx.x == 0) {
+                double var = nelig > 0.0 ? v[0] / nelig : 0.0;
+                state[PVR_ST_MU_P] = mu;
+                state[PVR_ST_SIGMA2_P] = var < 1e-4 ? 1e-4 : var;
+                state[PVR_ST_C_P] = clampd(c0, 1e-3, 1.0 - 1e-3);
+            }
+            __syncthreads();
+        }
+        for (int it = 0; it <= iters; ++it) {
+            if (threadIdx.x == 0) {
+                bc[0] = state[PVR_ST_MU_P];
+                bc[1] = state[PVR_ST_SIGMA2_P];
+                bc[2] = state[PVR_ST_C_P];
+            }
+            __syncthreads();
+            const double mu = bc[0], v2 = bc[1], cp = bc[2];
+            const double gnorm = 1.0 / (sqrt(2.0 * 3.14159265358979323846) * sqrt(v2));
+            double acc[2] = {0.0, 0.0};
+            for (int p = threadIdx.x; p < n; p += blockDim.x) {
+                double wv;
+                if (!elig[p]) wv = 0.0;
+                else if (mp == 0.0) wv = 1.0;
+                else {
+                    double dl = pbar[p] >= mu ? 0.0 : pbar[p] - mu;
+                    double G = exp(-(dl * dl) / (2.0 * v2)) * gnorm;
+                    wv = (G * cp) / (G * cp + mp * (1.0 - cp));
+                }
+                wsc[p] = wv;
+                if (elig[p]) {
+                    acc[0] += wv;
+                    acc[1] += wv * pbar[p];
+                }
+            }
+            if (it == iters || mp == 0.0) break;
+            block_reduce<2>(acc, sh, 0);
+            if (!(acc[0] > 0.0)) break;
+            const double mu_n = acc[1] / acc[0];
+            double v[1] = {0.0};
+            for (int p = threadIdx.x; p < n; p += blockDim.x)
+                if (elig[p]) v[0] += wsc[p] * ((pbar[p] - mu_n) * (pbar[p] - mu_n));
+            block_reduce<1>(v, sh, 0);
+            if (threadIdx.x == 0) {
+                double v2n = v[0] / acc[0];
+                state[PVR_ST_MU_P] = mu_n;
+                state[PVR_ST_SIGMA2_P] = v2n < 1e-4 ? 1e-4 : v2n;
+                state[PVR_ST_C_P] = clampd(acc[0] / nelig, 1e-3, 1.0 - 1e-3);
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) state[PVR_ST_M_P] = mp;
+        for (int p = threadIdx.x; p < n; p += blockDim.x)
+            mask_out[p] = (elig[p] && wsc[p] >= 0.5) ? 1 : 0;
+    }
+    __syncthreads();
+    double nin[1] = {0.0};
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        nin[0] += mask_out[p];
+        if (w_patch) w_patch[p] = (float)wsc[p];
+        if (pbar_out) pbar_out[p] = (float)pbar[p];
+    }
+    block_reduce<1>(nin, sh, 0);
+    if (threadIdx.x == 0) {
+        state[PVR_ST_N_ELIG] = nelig;
+        state[PVR_ST_N_IN] = nin[0];
+        state[PVR_ST_INIT] = 1.0;
+    }
+}
+
+// Weighted SIRT step (rows of A sum to one): x <- max(x + alpha addon / conf, 0)
+// where conf > eps; init_mode: x <- conf > eps ? addon / conf : 0.  Optionally
+// zeroes the accumulators for the next pass.  Vectorised by 4.
+__global__ void __launch_bounds__(256) k_volume_update(float *__restrict__ x,
+                                                       float *__restrict__ addon,
+                                                       float *__restrict__ conf, long long n,
+                                                       float alpha, float eps, int clear,
+                                                       int init_mode)
+{
+    long long n4 = n >> 2;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    float4 *x4 = reinterpret_cast<float4 *>(x);
+    float4 *a4 = reinterpret_cast<float4 *>(addon);
+    float4 *c4 = reinterpret_cast<float4 *>(conf);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += stride) {
+        float4 a = a4[i], c = c4[i], v = init_mode ? z4 : x4[i];
+        float *vp = &v.x;
+        const float *ap = &a.x, *cp = &c.x;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (cp[k] > eps) {
+                if (init_mode) vp[k] = ap[k] / cp[k];
+                else vp[k] = fmaxf(vp[k] + alpha * ap[k] / cp[k], 0.f);
+            }
+        }
+        x4[i] = v;
+        if (clear) {
+            a4[i] = z4;
+            c4[i] = z4;
+        }
+    }
+    for (long long i = (n4 << 2) + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        float a = addon[i], c = conf[i];
+        float v = init_mode ? 0.f : x[i];
+        if (c > eps) v = init_mode ? a / c : fmaxf(v + alpha * a / c, 0.f);
+        x[i] = v;
+        if (clear) addon[i] = conf[i] = 0.f;
+    }
+}
+
+// ---------------------------------------------------------- registration --
+
+__global__ void k_reg_init(const double *__restrict__ poses, int n, double *__restrict__ best,
+                           double *__restrict__ trial, double *__restrict__ delta,
+                           int32_t *__restrict__ active, double delta0)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    for (int k = 0; k < 6; ++k) {
+        double v = poses[6 * (size_t)p + k];
+        best[kRegStride * (size_t)p + k] = v;
+        trial[6 * (size_t)p + k] = v;
+    }
+    delta[p] = delta0;
+    active[p] = 1;
+}
+
+// Judge evaluation `eval` (NCC and gradient at the trial pose) and propose
+// the next trial: best + delta (g/s) / |g/s| / s, s = per-parameter scale.
+__global__ void k_reg_step(const DevGeom *__restrict__ g, const int32_t *__restrict__ desc, int n,
+                           int eval, int last, const double *__restrict__ ncc,
+                           const double *__restrict__ grad, double *__restrict__ best,
+                           double *__restrict__ gbest, double *__restrict__ nbest,
+                           double *__restrict__ trial, double *__restrict__ delta,
+                           int32_t *__restrict__ active, double delta_min, double grow, int fixed)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n || !active[p]) return;
+    double *b = best + kRegStride * (size_t)p;
+    double *gb = gbest + kRegStride * (size_t)p;
+    double *tr = trial + 6 * (size_t)p;
+    const double *gr = grad + 6 * (size_t)p;
+    double v = ncc[p];
+    if (eval == 0) {
+        nbest[p] = v;
+        for (int k = 0; k < 6; ++k) gb[k] = gr[k];
+        if (v == 0.0) {
+            active[p] = 0;
+            return;
+        }
+    } else if (fixed || v > nbest[p]) {
+        for (int k = 0; k < 6; ++k) {
+            b[k] = tr[k];
+            gb[k] = gr[k];
+        }
+        nbest[p] = v;
+        if (!fixed) delta[p] = __dmul_rn(delta[p], grow);
+    } else {
+        delta[p] = __dmul_rn(delta[p], 0.5);
+        if (delta[p] < delta_min) {
+            active[p] = 0;
+            return;
+        }
+    }
+    if (last) return;
+    const int32_t *d = desc + 8 * (size_t)p;
+    const double *S = g->p2w[d[0]];
+    double cw = sqrt(S[0] * S[0] + S[4] * S[4] + S[8] * S[8]) * (double)d[4];
+    double ch = sqrt(S[1] * S[1] + S[5] * S[5] + S[9] * S[9]) * (double)d[5];
+    double hd = 0.5 * sqrt(cw * cw + ch * ch);
+    double sc[6] = {1.0, 1.0, 1.0, hd * (3.14159265358979323846 / 180.0),
+                    hd * (3.14159265358979323846 / 180.0), hd * (3.14159265358979323846 / 180.0)};
+    double gn = 0.0;
+    for (int k = 0; k < 6; ++k) gn = __dadd_rn(gn, __dmul_rn(__ddiv_rn(gb[k], sc[k]), __ddiv_rn(gb[k], sc[k])));
+    gn = __dsqrt_rn(gn);
+    if (!(gn > 0.0)) {
+        active[p] = 0;
+        return;
+    }
+    for (int k = 0; k < 6; ++k)
+        tr[k] = __dadd_rn(b[k], __ddiv_rn(__ddiv_rn(__dmul_rn(delta[p], __ddiv_rn(gb[k], sc[k])), gn), sc[k]));
+}
+
+__global__ void k_reg_finish(const double *__restrict__ best, const double *__restrict__ nbest,
+                             int n, double *__restrict__ poses, double *__restrict__ ncc_out)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    for (int k = 0; k < 6; ++k) poses[6 * (size_t)p + k] = best[kRegStride * (size_t)p + k];
+    if (ncc_out) ncc_out[p] = nbest[p];
+}
+
+}  // namespace
+
+cudaError_t launch_em_stats(const float *y, const float *sim, const uint8_t *valid,
+                            const int32_t *desc, int n, int64_t n_pix, const Tiling &tl,
+                            int32_t *err, double *part, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_em_stats<<<(unsigned)n * tl.tpp, 256, 0, st>>>(y, sim, valid, desc, tl, (long long)n_pix,
+                                                     err, part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_em(const float *y, const float *sim, const uint8_t *valid, const int32_t *desc,
+                      int n, int64_t n_pix, const Tiling &tl, int32_t *err, double *state,
+                      const uint8_t *mask_in, uint8_t *mask_out, float *p, float *w_patch,
+                      float *pbar_out, double *part, double *pstat, double *pbar, double *wsc,
+                      uint8_t *elig, const pvr_params &prm, cudaStream_t st)
+{
+    k_em_prepare<<<1, kRedThreads, 0, st>>>(n, tl.tpp, mask_in, part, state, pstat, prm.em_c0,
+                                            prm.em_sigma_floor_rel);
+    if (n > 0)
+        k_em_estep<<<(unsigned)n * tl.tpp, 256, 0, st>>>(y, sim, valid, desc, tl, (long long)n_pix,
+                                                         err, mask_in, pstat, p, part);
+    k_em_mstep<<<1, kRedThreads, 0, st>>>(desc, n, tl.tpp, mask_in, part, state, pstat, prm.em_c0,
+                                          prm.em_min_valid_frac, prm.patch_rule,
+                                          prm.patch_threshold, prm.patch_em_iters, pbar, wsc, elig,
+                                          mask_out, w_patch, pbar_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_volume_update(float *x, float *addon, float *conf, int64_t nvox, float alpha,
+                                 float conf_eps, int clear, int init_mode, cudaStream_t st)
+{
+    if (nvox <= 0) return cudaSuccess;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long n4 = (nvox + 3) / 4;
+    long long blocks = (n4 + 255) / 256;
+    long long cap = (long long)sms * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_volume_update<<<(unsigned)blocks, 256, 0, st>>>(x, addon, conf, (long long)nvox, alpha,
+                                                      conf_eps, clear, init_mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reg_init(const double *poses, int n, double *best, double *trial, double *delta,
+                            int32_t *active, double delta0, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_reg_init<<<(n + 127) / 128, 128, 0, st>>>(poses, n, best, trial, delta, active, delta0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reg_step(const DevGeom *g, const int32_t *desc, int n, int eval, int last,
+                            const double *ncc, const double *grad, double *best, double *gbest,
+                            double *nbest, double *trial, double *delta, int32_t *active,
+                            const pvr_params &prm, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_reg_step<<<(n + 127) / 128, 128, 0, st>>>(g, desc, n, eval, last, ncc, grad, best, gbest,
+                                                nbest, trial, delta, active, prm.reg_delta_min,
+                                                prm.reg_grow, prm.reg_fixed_step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reg_finish(const double *best, const double *nbest, int n, double *poses,
+                              double *ncc_out, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_reg_finish<<<(n + 127) / 128, 128, 0, st>>>(best, nbest, n, poses, ncc_out);
+    return cudaGetLastError();
+}
+
+}  // namespace pvr

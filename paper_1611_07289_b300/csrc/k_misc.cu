@@ -1,0 +1,340 @@
+// Patch table construction (Sec. II "Patch Extraction"), patch pixel
+// gather, and the evaluation metrics of Sec. IV-A.
+#include <math.h>
+
+#include "pvr_internal.h"
+
+namespace pvr {
+namespace {
+
+// Monotone map float -> unsigned so that unsigned max = float max.
+__device__ __forceinline__ unsigned float_key(float f)
+{
+    unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float key_float(unsigned k)
+{
+    unsigned u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    return __uint_as_float(u);
+}
+
+__global__ void k_stack_max(const float *__restrict__ s, long long total, unsigned *__restrict__ out)
+{
+    __shared__ unsigned sh[32];
+    unsigned m = 0u;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x)
+        m = max(m, float_key(s[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, sh[w]);
+        atomicMax(out, m);
+    }
+}
+
+struct CandTable {
+    int n_stacks;
+    long long cand_off[PVR_MAX_STACKS + 1];   // first candidate index of each stack
+    int ncx[PVR_MAX_STACKS], ncy[PVR_MAX_STACKS];
+};
+
+// One CTA per candidate patch: keep iff #pixels > fg level >= keep_frac a^2.
+__global__ void __launch_bounds__(256) k_patch_keep(const DevGeom *__restrict__ g,
+                                                    const float *__restrict__ stacks, CandTable ct,
+                                                    int a, int stride, double fg_frac,
+                                                    double keep_frac,
+                                                    const unsigned *__restrict__ imax_key,
+                                                    int32_t *__restrict__ keep)
+{
+    long long c = blockIdx.x;
+    int s = 0;
+    while (s + 1 < ct.n_stacks && c >= ct.cand_off[s + 1]) ++s;
+    long long r = c - ct.cand_off[s];
+    int per_slice = ct.ncx[s] * ct.ncy[s];
+    int k = (int)(r / per_slice), rr = (int)(r % per_slice);
+    int y0 = (rr / ct.ncx[s]) * stride, x0 = (rr % ct.ncx[s]) * stride;
+    int W = g->sw[s], H = g->sh[s];
+    const float *base = stacks + g->stack_off[s] + ((size_t)k * H + y0) * W + x0;
+    float thr = __fmul_rn((float)fg_frac, key_float(*imax_key));
+    int cnt = 0;
+    for (int t = threadIdx.x; t < a * a; t += blockDim.x) cnt += base[(size_t)(t / a) * W + t % a] > thr;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    __shared__ int sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
+        keep[c] = (double)tot >= __dmul_rn(__dmul_rn(keep_frac, (double)a), (double)a) ? 1 : 0;
+    }
+}
+
+// Single-CTA ordered compaction of the kept candidates into the table.
+// counts[0] = kept patches; counts[1..2] = total pixels (int64, split).
+__global__ void __launch_bounds__(1024) k_patch_compact(const int32_t *__restrict__ keep,
+                                                        long long n_cand, CandTable ct, int a,
+                                                        int stride, int32_t *__restrict__ desc,
+                                                        int max_out, int32_t *__restrict__ counts)
+{
+    __shared__ int warp_tot[32];
+    __shared__ long long base_sh;
+    if (threadIdx.x == 0) base_sh = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (long long c0 = 0; c0 < n_cand; c0 += blockDim.x) {
+        long long c = c0 + threadIdx.x;
+        int f = (c < n_cand) ? keep[c] : 0;
+        unsigned bal = __ballot_sync(0xffffffffu, f);
+        int pre = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) warp_tot[wid] = __popc(bal);
+        __syncthreads();
+        int woff = 0;
+        for (int w = 0; w < wid; ++w) woff += warp_tot[w];
+        int tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += warp_tot[w];
+        long long idx = base_sh + woff + pre;
+        if (f && idx < max_out) {
+            int s = 0;
+            while (s + 1 < ct.n_stacks && c >= ct.cand_off[s + 1]) ++s;
+            long long r = c - ct.cand_off[s];
+            int per_slice = ct.ncx[s] * ct.ncy[s];
+            int k = (int)(r / per_slice), rr = (int)(r % per_slice);
+            int32_t *d = desc + 8 * (size_t)idx;
+            d[0] = s;
+            d[1] = k;
+            d[2] = (rr % ct.ncx[s]) * stride;
+            d[3] = (rr / ct.ncx[s]) * stride;
+            d[4] = a;
+            d[5] = a;
+            d[6] = (int32_t)(idx * (long long)a * a);
+            d[7] = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) base_sh += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        long long npix = base_sh * (long long)a * a;
+        counts[0] = (int32_t)base_sh;
+        counts[1] = (int32_t)(npix & 0xffffffffLL);
+        counts[2] = (int32_t)(npix >> 32);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_patch_gather(const DevGeom *__restrict__ g,
+                                                      const float *__restrict__ stacks,
+                                                      const int32_t *__restrict__ desc,
+                                                      long long n_pix, int32_t *__restrict__ err,
+                                                      float *__restrict__ y)
+{
+    const int32_t *d = desc + 8 * (size_t)blockIdx.x;
+    int s = d[0], k = d[1], x0 = d[2], y0 = d[3], w = d[4], h = d[5], off = d[6];
+    if (s < 0 || s >= g->n_stacks || k < 0 || k >= g->sk[s] || x0 < 0 || y0 < 0 || w < 1 ||
+        h < 1 || x0 + w > g->sw[s] || y0 + h > g->sh[s] || off < 0 ||
+        (long long)off + (long long)w * h > n_pix) {
+        if (threadIdx.x == 0) atomicOr(err, 1);
+        return;
+    }
+    int W = g->sw[s], H = g->sh[s];
+    const float *base = stacks + g->stack_off[s] + ((size_t)k * H + y0) * W + x0;
+    float *dst = y + d[6];
+    for (int t = threadIdx.x; t < w * h; t += blockDim.x) dst[t] = base[(size_t)(t / w) * W + t % w];
+}
+
+// ---------------------------------------------------------------- metrics --
+
+__device__ __forceinline__ double wsum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int NV>
+__device__ void block_sums(double *v, double *sh)
+{
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = 0; k < NV; ++k) v[k] = wsum(v[k]);
+    __syncthreads();
+    if (lane == 0)
+        for (int k = 0; k < NV; ++k) sh[wid * NV + k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += sh[w * NV + k];
+            v[k] = s;
+        }
+}
+
+// pass 1: count, sum ref, sum img, max ref, min ref per block
+__global__ void __launch_bounds__(256) k_metrics1(const float *__restrict__ ref,
+                                                  const float *__restrict__ img,
+                                                  const uint8_t *__restrict__ mask, long long n,
+                                                  double *__restrict__ scr)
+{
+    __shared__ double sh[32 * 3];
+    __shared__ float mx[32], mn[32];
+    double v[3] = {0.0, 0.0, 0.0};
+    float a = -INFINITY, b = INFINITY;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (mask && !mask[i]) continue;
+        float r = ref[i];
+        v[0] += 1.0;
+        v[1] += r;
+        v[2] += img[i];
+        a = fmaxf(a, r);
+        b = fminf(b, r);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = fminf(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        mx[threadIdx.x >> 5] = a;
+        mn[threadIdx.x >> 5] = b;
+    }
+    block_sums<3>(v, sh);
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            a = fmaxf(a, mx[w]);
+            b = fminf(b, mn[w]);
+        }
+        double *o = scr + 8 * (size_t)blockIdx.x;
+        o[0] = v[0];
+        o[1] = v[1];
+        o[2] = v[2];
+        o[3] = a;
+        o[4] = b;
+    }
+}
+
+// pass 2: centred sums with the means of pass 1 (folded here per block)
+__global__ void __launch_bounds__(256) k_metrics2(const float *__restrict__ ref,
+                                                  const float *__restrict__ img,
+                                                  const uint8_t *__restrict__ mask, long long n,
+                                                  const double *__restrict__ scr1, int nb,
+                                                  double *__restrict__ scr2)
+{
+    __shared__ double sh[32 * 4];
+    __shared__ double means[2];
+    if (threadIdx.x == 0) {
+        double c = 0, sr = 0, si = 0;
+        for (int b = 0; b < nb; ++b) {
+            c += scr1[8 * b];
+            sr += scr1[8 * b + 1];
+            si += scr1[8 * b + 2];
+        }
+        means[0] = c > 0 ? sr / c : 0.0;
+        means[1] = c > 0 ? si / c : 0.0;
+    }
+    __syncthreads();
+    const double mr = means[0], mi = means[1];
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (mask && !mask[i]) continue;
+        double a = (double)ref[i] - mr, b = (double)img[i] - mi, d = (double)img[i] - (double)ref[i];
+        v[0] += a * a;
+        v[1] += b * b;
+        v[2] += a * b;
+        v[3] += d * d;
+    }
+    block_sums<4>(v, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) scr2[8 * (size_t)blockIdx.x + k] = v[k];
+}
+
+__global__ void k_metrics3(const double *__restrict__ scr1, const double *__restrict__ scr2, int nb,
+                           double *__restrict__ out)
+{
+    double c = 0, sr = 0, si = 0, rmax = -INFINITY, rmin = INFINITY, vr = 0, vi = 0, cv = 0, se = 0;
+    for (int b = 0; b < nb; ++b) {
+        c += scr1[8 * b];
+        sr += scr1[8 * b + 1];
+        si += scr1[8 * b + 2];
+        if (scr1[8 * b] > 0) {
+            rmax = fmax(rmax, scr1[8 * b + 3]);
+            rmin = fmin(rmin, scr1[8 * b + 4]);
+        }
+        vr += scr2[8 * b];
+        vi += scr2[8 * b + 1];
+        cv += scr2[8 * b + 2];
+        se += scr2[8 * b + 3];
+    }
+    for (int k = 0; k < 5; ++k) out[k] = 0.0;
+    if (c == 0) return;
+    double mr = sr / c, mi = si / c;
+    vr /= c;
+    vi /= c;
+    cv /= c;
+    double mse = se / c;
+    out[0] = mse > 0 ? 10.0 * log10(rmax * rmax / mse) : INFINITY;
+    out[1] = (vr > 0 && vi > 0) ? cv / sqrt(vr * vi) : 0.0;
+    double L = rmax - rmin, c1 = (0.01 * L) * (0.01 * L), c2 = (0.03 * L) * (0.03 * L);
+    double ssim = ((2 * mr * mi + c1) * (2 * cv + c2)) / ((mr * mr + mi * mi + c1) * (vr + vi + c2));
+    out[2] = ssim;
+    out[3] = (1.0 - ssim) / 2.0;
+    out[4] = mse;
+}
+
+}  // namespace
+
+constexpr int kMetricBlocks = 296;
+
+cudaError_t launch_patches_build(const DevGeom *g, const pvr_geometry &hg, const float *stacks,
+                                 int64_t total, int a, int stride, double fg_frac,
+                                 double keep_frac, int32_t *desc_out, int max_out, int32_t *keep,
+                                 int64_t *n_cand_out, unsigned *imax_key, int32_t *counts,
+                                 cudaStream_t st)
+{
+    CandTable ct;
+    ct.n_stacks = hg.n_stacks;
+    long long nc = 0;
+    for (int s = 0; s < hg.n_stacks; ++s) {
+        ct.cand_off[s] = nc;
+        int W = hg.stack_w[s], H = hg.stack_h[s];
+        ct.ncx[s] = W >= a ? (W - a) / stride + 1 : 0;
+        ct.ncy[s] = H >= a ? (H - a) / stride + 1 : 0;
+        nc += (long long)hg.stack_k[s] * ct.ncx[s] * ct.ncy[s];
+    }
+    ct.cand_off[hg.n_stacks] = nc;
+    *n_cand_out = nc;
+    cudaMemsetAsync(imax_key, 0, sizeof(unsigned), st);
+    cudaMemsetAsync(counts, 0, 4 * sizeof(int32_t), st);
+    if (total > 0) k_stack_max<<<296, 256, 0, st>>>(stacks, (long long)total, imax_key);
+    if (nc > 0) {
+        k_patch_keep<<<(unsigned)nc, 256, 0, st>>>(g, stacks, ct, a, stride, fg_frac, keep_frac,
+                                                   imax_key, keep);
+        k_patch_compact<<<1, 1024, 0, st>>>(keep, nc, ct, a, stride, desc_out, max_out, counts);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_patches_gather(const DevGeom *g, const float *stacks, const int32_t *desc,
+                                  int n, int64_t n_pix, int32_t *err, float *y, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_patch_gather<<<(unsigned)n, 256, 0, st>>>(g, stacks, desc, (long long)n_pix, err, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_metrics(const float *ref, const float *img, const uint8_t *mask, int64_t n,
+                           double *scratch, double *out, cudaStream_t st)
+{
+    double *s1 = scratch, *s2 = scratch + 8 * kMetricBlocks;
+    k_metrics1<<<kMetricBlocks, 256, 0, st>>>(ref, img, mask, (long long)n, s1);
+    k_metrics2<<<kMetricBlocks, 256, 0, st>>>(ref, img, mask, (long long)n, s1, kMetricBlocks, s2);
+    k_metrics3<<<1, 1, 0, st>>>(s1, s2, kMetricBlocks, out);
+    return cudaGetLastError();
+}
+
+}  // namespace pvr

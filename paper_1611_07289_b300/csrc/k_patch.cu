@@ -1,0 +1,819 @@
+// Per-patch kernels of the PVR hot path: forward model (K2), adjoint (K4)
+// and NCC with pose gradient (K6a/K6b).
+//
+// Decomposition (Sec. III, patch-level and voxel-level parallelism, redone
+// for sm_103a): one CTA per (patch, tile of at most T x T output pixels).
+// The CTA first evaluates the through-plane PSF sum at every in-plane
+// lattice point of its tile plus a kxy halo -- the lattice point (i, j)
+// holds sum_zeta g_z(zeta) trilinear(x, q(i, j, zeta)) and sum_zeta g_z over
+// in-volume samples -- into shared memory, then applies the separable
+// in-plane Gaussian taps from shared memory.  Each trilinear sample is thus
+// gathered once per tile instead of (2 kxy + 1)^2 times per pixel.  The
+// adjoint runs the same steps transposed: per-pixel coefficients, the
+// transposed in-plane taps into lattice weights, then a scatter of every
+// in-volume sample into its 8 voxels.
+//
+// Sample positions are Q11.20 fixed point: q = o + i e_col + j e_row +
+// zeta e_zeta in 32-bit two's-complement arithmetic (exact whenever the
+// result is in range, which the pose kernel guarantees for the whole sample
+// box), so in-volume tests and voxel indices are exact integers.
+#include "pvr_internal.h"
+
+namespace pvr {
+namespace {
+
+constexpr unsigned kFracMask = (1u << kFracBits) - 1u;
+constexpr float kFracScale = 1.0f / (float)(1u << kFracBits);
+
+struct TileInfo {
+    int p, t;                // patch, tile index
+    int stack, w, h, off;    // patch
+    int i0, j0, tw, th;      // tile pixel origin (patch-relative) and size
+    int Lw, Lh, L;           // lattice of the tile incl. halo
+    unsigned o[3], ei[3], ej[3], ez[3];
+    bool ok;
+};
+
+// Decode block -> (patch, tile); returns false for an empty tile or a
+// patch whose descriptor row failed validation in the pose kernel.
+__device__ __forceinline__ bool tile_setup(const int32_t *__restrict__ desc,
+                                           const int32_t *__restrict__ fix, const Tiling &tl,
+                                           int kxy, TileInfo &ti)
+{
+    ti.p = blockIdx.x / tl.tpp;
+    ti.t = blockIdx.x % tl.tpp;
+    const int32_t *d = desc + 8 * (size_t)ti.p;
+    ti.stack = d[0];
+    ti.w = d[4];
+    ti.h = d[5];
+    ti.off = d[6];
+    int tx = ti.t % tl.tiles_x, ty = ti.t / tl.tiles_x;
+    ti.i0 = tx * tl.T;
+    ti.j0 = ty * tl.T;
+    const int32_t *f = fix + kFixStride * (size_t)ti.p;
+    ti.ok = f[12] != 0;
+    // f[13] = 0: the descriptor row failed validation -- touch nothing
+    if (f[13] == 0 || ti.i0 >= ti.w || ti.j0 >= ti.h) return false;
+    ti.tw = min(tl.T, ti.w - ti.i0);
+    ti.th = min(tl.T, ti.h - ti.j0);
+    ti.Lw = ti.tw + 2 * kxy;
+    ti.Lh = ti.th + 2 * kxy;
+    ti.L = ti.Lw * ti.Lh;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        ti.o[r] = (unsigned)f[r];
+        ti.ei[r] = (unsigned)f[3 + r];
+        ti.ej[r] = (unsigned)f[6 + r];
+        ti.ez[r] = (unsigned)f[9 + r];
+    }
+    return true;
+}
+
+struct VolDims {
+    int nx, ny, nz;
+    unsigned ux, uy, uz;     // (n - 1) << 20: largest in-volume coordinate
+};
+
+__host__ __device__ __forceinline__ VolDims vol_dims(int nx, int ny, int nz)
+{
+    VolDims v;
+    v.nx = nx;
+    v.ny = ny;
+    v.nz = nz;
+    v.ux = (unsigned)(nx - 1) << kFracBits;
+    v.uy = (unsigned)(ny - 1) << kFracBits;
+    v.uz = (unsigned)(nz - 1) << kFracBits;
+    return v;
+}
+
+// Split an in-volume fixed-point coordinate into base voxel and fraction;
+// the last plane is addressed as cell n-2 with fraction 1.
+__device__ __forceinline__ void split(unsigned q, int n, int &b, float &f)
+{
+    b = (int)(q >> kFracBits);
+    f = (float)(q & kFracMask) * kFracScale;
+    if (b == n - 1) {
+        b = n - 2;
+        f = 1.0f;
+    }
+}
+
+// Lattice position (tile-lattice index lp) at zeta = 0.
+__device__ __forceinline__ void lattice_q0(const TileInfo &ti, int kxy, int lp, unsigned q[3])
+{
+    int li = ti.i0 - kxy + lp % ti.Lw;
+    int lj = ti.j0 - kxy + lp / ti.Lw;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) q[r] = ti.o[r] + (unsigned)li * ti.ei[r] + (unsigned)lj * ti.ej[r];
+}
+
+__device__ __forceinline__ float trilinear(const float *__restrict__ x, const VolDims &vd,
+                                           unsigned qx, unsigned qy, unsigned qz)
+{
+    int bx, by, bz;
+    float fx, fy, fz;
+    split(qx, vd.nx, bx, fx);
+    split(qy, vd.ny, by, fy);
+    split(qz, vd.nz, bz, fz);
+    size_t nxy = (size_t)vd.nx * vd.ny;
+    const float *b = x + (size_t)bz * nxy + (size_t)by * vd.nx + bx;
+    float v000 = __ldg(b), v100 = __ldg(b + 1);
+    float v010 = __ldg(b + vd.nx), v110 = __ldg(b + vd.nx + 1);
+    float v001 = __ldg(b + nxy), v101 = __ldg(b + nxy + 1);
+    float v011 = __ldg(b + nxy + vd.nx), v111 = __ldg(b + nxy + vd.nx + 1);
+    float c00 = fmaf(fx, v100 - v000, v000);
+    float c10 = fmaf(fx, v110 - v010, v010);
+    float c01 = fmaf(fx, v101 - v001, v001);
+    float c11 = fmaf(fx, v111 - v011, v011);
+    float c0 = fmaf(fy, c10 - c00, c00);
+    float c1 = fmaf(fy, c11 - c01, c01);
+    return fmaf(fz, c1 - c0, c0);
+}
+
+__device__ __forceinline__ bool inside(const VolDims &vd, unsigned qx, unsigned qy, unsigned qz)
+{
+    return qx <= vd.ux && qy <= vd.uy && qz <= vd.uz;
+}
+
+// Phase 1 of the forward model: through-plane PSF sums at every lattice
+// point of the tile.  A (may be null) <- sum g_z trilinear, B <- sum g_z.
+template <int KZ>
+__device__ __forceinline__ void lattice_forward(const float *__restrict__ x, const VolDims &vd,
+                                                const TileInfo &ti, int kxy, int kz_rt,
+                                                const float *__restrict__ gz, float *A, float *B)
+{
+    const int kz = KZ >= 0 ? KZ : kz_rt;
+    for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) {
+        unsigned q0[3];
+        lattice_q0(ti, kxy, lp, q0);
+        float acc = 0.f, den = 0.f;
+#pragma unroll
+        for (int z = -kz; z <= kz; ++z) {
+            unsigned qx = q0[0] + (unsigned)z * ti.ez[0];
+            unsigned qy = q0[1] + (unsigned)z * ti.ez[1];
+            unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
+            if (inside(vd, qx, qy, qz)) {
+                float g = gz[z + kz];
+                if (A) acc = fmaf(g, trilinear(x, vd, qx, qy, qz), acc);
+                den += g;
+            }
+        }
+        if (A) A[lp] = acc;
+        B[lp] = den;
+    }
+}
+
+// In-plane taps at tile pixel (ci, cj) from lattice array V.
+__device__ __forceinline__ float inplane(const float *V, int Lw, int kxy, const float *gxy, int ci,
+                                         int cj)
+{
+    float s = 0.f;
+    for (int dj = -kxy; dj <= kxy; ++dj) {
+        const float *row = V + (cj + kxy + dj) * Lw + ci + kxy;
+        float r = 0.f;
+        for (int di = -kxy; di <= kxy; ++di) r = fmaf(gxy[di + kxy], row[di], r);
+        s = fmaf(gxy[dj + kxy], r, s);
+    }
+    return s;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_min(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_max(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sums of NV doubles (block size multiple of 32, <= 1024);
+// result valid in thread 0.  red: shared scratch of 32 * NV doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum(double *v, double *red)
+{
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+    __syncthreads();
+    if (lane == 0)
+        for (int k = 0; k < NV; ++k) red[wid * NV + k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += red[w * NV + k];
+            v[k] = s;
+        }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ K2 --
+// Forward model.  y == null: write sim, valid.  y != null: write the
+// residual e = y - sim (0 where invalid) and valid, plus per-tile partials
+// {N_valid, sum e^2, min e, max e} for the EM step.
+template <int KXY, int KZ>
+__global__ void __launch_bounds__(256) k_simulate(const float *__restrict__ x, VolDims vd,
+                                                  const int32_t *__restrict__ desc,
+                                                  const int32_t *__restrict__ fix, PsfTab psf,
+                                                  Tiling tl, const float *__restrict__ y,
+                                                  float *__restrict__ out,
+                                                  uint8_t *__restrict__ valid,
+                                                  double *__restrict__ part)
+{
+    extern __shared__ float sm[];
+    __shared__ double red[32 * 4];
+    const int kxy = KXY >= 0 ? KXY : psf.kxy;
+    TileInfo ti;
+    bool has = tile_setup(desc, fix, tl, kxy, ti);
+    if (!has) {
+        if (part && threadIdx.x < kPartStride)
+            part[(size_t)blockIdx.x * kPartStride + threadIdx.x] = 0.0;
+        return;
+    }
+    float *A = sm, *B = sm + ti.L;
+    if (ti.ok) {
+        lattice_forward<KZ>(x, vd, ti, kxy, psf.kz, psf.gz[ti.stack], A, B);
+    } else {
+        for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) A[lp] = B[lp] = 0.f;
+    }
+    __syncthreads();
+    float se2 = 0.f, emin = INFINITY, emax = -INFINITY;
+    int nval = 0;
+    const int np = ti.tw * ti.th;
+    for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
+        int ci = pp % ti.tw, cj = pp / ti.tw;
+        float num = inplane(A, ti.Lw, kxy, psf.gxy, ci, cj);
+        float den = inplane(B, ti.Lw, kxy, psf.gxy, ci, cj);
+        bool v = den > 0.f;
+        float s = v ? num / den : 0.f;
+        size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
+        if (y) {
+            float e = v ? __ldg(y + o) - s : 0.f;
+            out[o] = e;
+            if (v) {
+                se2 = fmaf(e, e, se2);
+                emin = fminf(emin, e);
+                emax = fmaxf(emax, e);
+                ++nval;
+            }
+        } else {
+            out[o] = s;
+        }
+        valid[o] = v ? 1 : 0;
+    }
+    if (part) {
+        double acc[2] = {(double)nval, (double)se2};
+        float mn = warp_min(emin), mx = warp_max(emax);
+        __shared__ float rmn[32], rmx[32];
+        int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) {
+            rmn[wid] = mn;
+            rmx[wid] = mx;
+        }
+        block_sum<2>(acc, red);
+        if (threadIdx.x == 0) {
+            float a = INFINITY, b = -INFINITY;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                a = fminf(a, rmn[w]);
+                b = fmaxf(b, rmx[w]);
+            }
+            double *pt = part + (size_t)blockIdx.x * kPartStride;
+            pt[0] = acc[0];
+            pt[1] = acc[1];
+            pt[2] = (double)a;
+            pt[3] = (double)b;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ K4 --
+// Adjoint.  Pixel coefficients cr = w r / den, cw = w / den (valid pixels),
+// transposed in-plane taps into lattice weights U, U', then every in-volume
+// sample adds U g_z tri and U' g_z tri to its 8 voxels (float atomics).
+template <int KXY, int KZ>
+__global__ void __launch_bounds__(256) k_adjoint(VolDims vd, const int32_t *__restrict__ desc,
+                                                 const int32_t *__restrict__ fix, PsfTab psf,
+                                                 Tiling tl, const float *__restrict__ r,
+                                                 const float *__restrict__ w,
+                                                 const uint8_t *__restrict__ pmask,
+                                                 float *__restrict__ addon,
+                                                 float *__restrict__ conf)
+{
+    extern __shared__ float sm[];
+    const int kxy = KXY >= 0 ? KXY : psf.kxy;
+    const int kz = KZ >= 0 ? KZ : psf.kz;
+    TileInfo ti;
+    if (!tile_setup(desc, fix, tl, kxy, ti) || !ti.ok) return;
+    if (pmask && pmask[ti.p] == 0) return;
+    const int np = ti.tw * ti.th;
+    float *U = sm, *Uw = sm + ti.L, *CR = sm + 2 * ti.L, *CW = CR + np;
+    const float *gz = psf.gz[ti.stack];
+    // phase 0: in-volume PSF weight per lattice point (no gathers)
+    lattice_forward<KZ>(nullptr, vd, ti, kxy, kz, gz, nullptr, U);
+    __syncthreads();
+    // phase 1: pixel coefficients
+    for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
+        int ci = pp % ti.tw, cj = pp / ti.tw;
+        float den = inplane(U, ti.Lw, kxy, psf.gxy, ci, cj);
+        size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
+        float cr = 0.f, cw = 0.f;
+        if (den > 0.f) {
+            float ww = w ? __ldg(w + o) : 1.f;
+            float rr = r ? __ldg(r + o) : 1.f;
+            cw = ww / den;
+            cr = cw * rr;
+        }
+        CR[pp] = cr;
+        CW[pp] = cw;
+    }
+    __syncthreads();
+    // phase 2: transposed in-plane taps into lattice weights
+    for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) {
+        int li = lp % ti.Lw, lj = lp / ti.Lw;   // lattice point = pixel (li - kxy, lj - kxy) of the tile
+        float ur = 0.f, uw = 0.f;
+        for (int dj = -kxy; dj <= kxy; ++dj) {
+            int cj = lj - kxy - dj;
+            if (cj < 0 || cj >= ti.th) continue;
+            float rr = 0.f, rw = 0.f;
+            for (int di = -kxy; di <= kxy; ++di) {
+                int ci = li - kxy - di;
+                if (ci < 0 || ci >= ti.tw) continue;
+                float g = psf.gxy[di + kxy];
+                rr = fmaf(g, CR[cj * ti.tw + ci], rr);
+                rw = fmaf(g, CW[cj * ti.tw + ci], rw);
+            }
+            float g = psf.gxy[dj + kxy];
+            ur = fmaf(g, rr, ur);
+            uw = fmaf(g, rw, uw);
+        }
+        // written after every thread has read phase-0 data? U is overwritten
+        // only at lp, which no other thread reads in this phase.
+        U[lp] = ur;
+        Uw[lp] = uw;
+    }
+    __syncthreads();
+    // phase 3: scatter
+    const size_t nxy = (size_t)vd.nx * vd.ny;
+    for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) {
+        float ur = U[lp], uw = Uw[lp];
+        if (ur == 0.f && uw == 0.f) continue;
+        unsigned q0[3];
+        lattice_q0(ti, kxy, lp, q0);
+#pragma unroll
+        for (int z = -kz; z <= kz; ++z) {
+            unsigned qx = q0[0] + (unsigned)z * ti.ez[0];
+            unsigned qy = q0[1] + (unsigned)z * ti.ez[1];
+            unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
+            if (!inside(vd, qx, qy, qz)) continue;
+            int bx, by, bz;
+            float fx, fy, fz;
+            split(qx, vd.nx, bx, fx);
+            split(qy, vd.ny, by, fy);
+            split(qz, vd.nz, bz, fz);
+            float g = gz[z + kz];
+            float ar = g * ur, aw = g * uw;
+            size_t base = (size_t)bz * nxy + (size_t)by * vd.nx + bx;
+            float wx[2] = {1.f - fx, fx}, wy[2] = {1.f - fy, fy}, wz[2] = {1.f - fz, fz};
+#pragma unroll
+            for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+                for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+                    for (int cx = 0; cx < 2; ++cx) {
+                        float t = wx[cx] * wy[cy] * wz[cz];
+                        size_t idx = base + cz * nxy + cy * vd.nx + cx;
+                        if (addon) atomicAdd(addon + idx, ar * t);
+                        if (conf) atomicAdd(conf + idx, aw * t);
+                    }
+        }
+    }
+}
+
+// ----------------------------------------------------------------- K6a --
+// NCC moments: simulated pixel values (kept for K6b) and per-tile sums
+// {N, sum a, sum b, sum a^2, sum b^2, sum a b} with a = y - y_ref,
+// b = s - y_ref, y_ref = the patch's first acquired pixel (a shift that
+// keeps the float32 moments free of cancellation).
+template <int KXY, int KZ>
+__global__ void __launch_bounds__(256) k_ncc_moments(const float *__restrict__ x, VolDims vd,
+                                                     const int32_t *__restrict__ desc,
+                                                     const int32_t *__restrict__ fix, PsfTab psf,
+                                                     Tiling tl, const float *__restrict__ y,
+                                                     const int32_t *__restrict__ active,
+                                                     float *__restrict__ s_buf,
+                                                     uint8_t *__restrict__ v_buf,
+                                                     double *__restrict__ part)
+{
+    extern __shared__ float sm[];
+    __shared__ double red[32 * 6];
+    const int kxy = KXY >= 0 ? KXY : psf.kxy;
+    TileInfo ti;
+    bool has = tile_setup(desc, fix, tl, kxy, ti);
+    double *pt = part + (size_t)blockIdx.x * kPartStride;
+    if (!has || (active && !active[ti.p])) {
+        if (threadIdx.x < kPartStride) pt[threadIdx.x] = 0.0;
+        return;
+    }
+    float *A = sm, *B = sm + ti.L;
+    if (ti.ok) {
+        lattice_forward<KZ>(x, vd, ti, kxy, psf.kz, psf.gz[ti.stack], A, B);
+    } else {
+        for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) A[lp] = B[lp] = 0.f;
+    }
+    __syncthreads();
+    const float yref = __ldg(y + ti.off);
+    float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int np = ti.tw * ti.th;
+    for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
+        int ci = pp % ti.tw, cj = pp / ti.tw;
+        float num = inplane(A, ti.Lw, kxy, psf.gxy, ci, cj);
+        float den = inplane(B, ti.Lw, kxy, psf.gxy, ci, cj);
+        bool v = den > 0.f;
+        float s = v ? num / den : 0.f;
+        size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
+        s_buf[o] = s;
+        v_buf[o] = v ? 1 : 0;
+        if (v) {
+            float a = __ldg(y + o) - yref, b = s - yref;
+            m[0] += 1.f;
+            m[1] += a;
+            m[2] += b;
+            m[3] = fmaf(a, a, m[3]);
+            m[4] = fmaf(b, b, m[4]);
+            m[5] = fmaf(a, b, m[5]);
+        }
+    }
+    double acc[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] = (double)m[k];
+    block_sum<6>(acc, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) pt[k] = acc[k];
+        pt[6] = pt[7] = 0.0;
+    }
+}
+
+// NCC of a patch from its tile moments (float64).  Returns false when
+// degenerate (fewer than min_valid pixels or a constant patch).
+// Means are returned relative to yref (the shift used by K6a).
+__device__ bool ncc_from_moments(const double *part, int p, int tpp, int min_valid, double yref,
+                                 double &ncc, double &my, double &ms, double &sd, double &vs,
+                                 double &n)
+{
+    double m[6] = {0, 0, 0, 0, 0, 0};
+    for (int t = 0; t < tpp; ++t)
+        for (int k = 0; k < 6; ++k) m[k] += part[((size_t)p * tpp + t) * kPartStride + k];
+    n = m[0];
+    ncc = 0.0;
+    if (n < (double)min_valid || n <= 0.0) return false;
+    my = m[1] / n;
+    ms = m[2] / n;
+    double vy = m[3] / n - my * my;
+    vs = m[4] / n - ms * ms;
+    double cv = m[5] / n - my * ms;
+    double muy = my + yref, mus = ms + yref;
+    if (!(vy > 1e-12 * (muy * muy + 1.0)) || !(vs > 1e-12 * (mus * mus + 1.0))) return false;
+    sd = sqrt(vy * vs);
+    ncc = cv / sd;
+    return true;
+}
+
+// ----------------------------------------------------------------- K6b --
+// Pose gradient of NCC.  dNCC/ds_i = ((y_i - my)/sd - ncc (s_i - ms)/vs)/N;
+// pixel coefficient c_i = dNCC/ds_i / den_i; transposed in-plane taps give
+// lattice weights U; every in-volume sample adds U g_z (grad_tri . dq/dtheta_k).
+// dq/dtheta: translations = columns of the linear part of world_to_voxel;
+// rotation k: W R_k' S_lin [i - (w-1)/2, j - (h-1)/2, zeta zs] * pi/180 with
+// R_k' = d(Rz Ry Rx)/d angle_k (radians).
+template <int KXY, int KZ>
+__global__ void __launch_bounds__(256) k_ncc_grad(const float *__restrict__ x, VolDims vd,
+                                                  const DevGeom *__restrict__ g,
+                                                  const int32_t *__restrict__ desc,
+                                                  const int32_t *__restrict__ fix, PsfTab psf,
+                                                  Tiling tl, const float *__restrict__ y,
+                                                  const double *__restrict__ poses,
+                                                  const int32_t *__restrict__ active,
+                                                  const float *__restrict__ s_buf,
+                                                  const uint8_t *__restrict__ v_buf,
+                                                  const double *__restrict__ part,
+                                                  double *__restrict__ gpart, int min_valid)
+{
+    extern __shared__ float sm[];
+    __shared__ double red[32 * 6];
+    __shared__ float jc[6][12];   // per parameter: a(3), b(3), z(3), o(3): dq = a li + b lj + z zeta + o
+    __shared__ double sh_stats[4];
+    __shared__ int sh_ok;
+    const int kxy = KXY >= 0 ? KXY : psf.kxy;
+    const int kz = KZ >= 0 ? KZ : psf.kz;
+    TileInfo ti;
+    bool has = tile_setup(desc, fix, tl, kxy, ti);
+    double *gp = gpart + (size_t)blockIdx.x * kPartStride;
+    if (!has || !ti.ok || (active && !active[ti.p])) {
+        if (threadIdx.x < kPartStride) gp[threadIdx.x] = 0.0;
+        return;
+    }
+    if (threadIdx.x == 0) {
+        double ncc, my, ms, sd, vs, n;
+        const float yref = y[ti.off];
+        bool ok = ncc_from_moments(part, ti.p, tl.tpp, min_valid, (double)yref, ncc, my, ms, sd, vs, n);
+        sh_ok = ok;
+        sh_stats[0] = ncc;
+        sh_stats[1] = my + yref;   // back from the shifted means
+        sh_stats[2] = ms + yref;
+        sh_stats[3] = 0.0;
+        if (ok) {
+            const int32_t *d = desc + 8 * (size_t)ti.p;
+            const double *S = g->p2w[d[0]];
+            const double *W = g->w2v;
+            const double *th = poses + 6 * (size_t)ti.p;
+            const double dg = 3.14159265358979323846 / 180.0;
+            double ax = th[3] * dg, ay = th[4] * dg, az = th[5] * dg;
+            double sx = sin(ax), cx = cos(ax), sy = sin(ay), cy = cos(ay), sz = sin(az), cz = cos(az);
+            double Rx[9] = {1, 0, 0, 0, cx, -sx, 0, sx, cx};
+            double Ry[9] = {cy, 0, sy, 0, 1, 0, -sy, 0, cy};
+            double Rz[9] = {cz, -sz, 0, sz, cz, 0, 0, 0, 1};
+            double dRx[9] = {0, 0, 0, 0, -sx, -cx, 0, cx, -sx};
+            double dRy[9] = {-sy, 0, cy, 0, 0, 0, -cy, 0, -sy};
+            double dRz[9] = {-sz, -cz, 0, cz, -sz, 0, 0, 0, 0};
+            double n2 = S[2] * S[2] + S[6] * S[6] + S[10] * S[10];
+            double zs = g->dz / sqrt(n2);
+            double cu = 0.5 * (d[4] - 1), cv = 0.5 * (d[5] - 1);
+            for (int k = 0; k < 6; ++k) {
+                double Q[9];
+                if (k < 3) {
+                    for (int r = 0; r < 3; ++r) {
+                        jc[k][r] = 0.f;
+                        jc[k][3 + r] = 0.f;
+                        jc[k][6 + r] = 0.f;
+                        jc[k][9 + r] = (float)W[4 * r + k];
+                    }
+                    continue;
+                }
+                const double *Am = (k == 5) ? dRz : Rz;
+                const double *Bm = (k == 4) ? dRy : Ry;
+                const double *Cm = (k == 3) ? dRx : Rx;
+                double AB[9], ABC[9], WA[9];
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c) {
+                        AB[3 * r + c] = 0.0;
+                        for (int t = 0; t < 3; ++t) AB[3 * r + c] += Am[3 * r + t] * Bm[3 * t + c];
+                    }
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c) {
+                        ABC[3 * r + c] = 0.0;
+                        for (int t = 0; t < 3; ++t) ABC[3 * r + c] += AB[3 * r + t] * Cm[3 * t + c];
+                    }
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c) {
+                        WA[3 * r + c] = 0.0;
+                        for (int t = 0; t < 3; ++t) WA[3 * r + c] += W[4 * r + t] * ABC[3 * t + c];
+                    }
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c) {
+                        Q[3 * r + c] = 0.0;
+                        for (int t = 0; t < 3; ++t) Q[3 * r + c] += WA[3 * r + t] * S[4 * t + c];
+                        Q[3 * r + c] *= dg;
+                    }
+                for (int r = 0; r < 3; ++r) {
+                    jc[k][r] = (float)Q[3 * r + 0];
+                    jc[k][3 + r] = (float)Q[3 * r + 1];
+                    jc[k][6 + r] = (float)(Q[3 * r + 2] * zs);
+                    jc[k][9 + r] = (float)(-Q[3 * r + 0] * cu - Q[3 * r + 1] * cv);
+                }
+            }
+            // coefficient scale: 1/(N sd), ncc/(N vs)
+            sh_stats[3] = 1.0 / (n * sd);
+            sh_stats[0] = ncc / (n * vs);
+        }
+    }
+    __syncthreads();
+    if (!sh_ok) {
+        if (threadIdx.x < kPartStride) gp[threadIdx.x] = 0.0;
+        return;
+    }
+    const int np = ti.tw * ti.th;
+    float *U = sm, *C = sm + ti.L;
+    const float *gzp = psf.gz[ti.stack];
+    lattice_forward<KZ>(nullptr, vd, ti, kxy, kz, gzp, nullptr, U);
+    __syncthreads();
+    const float a_sc = (float)sh_stats[3], b_sc = (float)sh_stats[0];
+    const float my = (float)sh_stats[1], ms = (float)sh_stats[2];
+    for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
+        int ci = pp % ti.tw, cj = pp / ti.tw;
+        size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
+        float c = 0.f;
+        if (v_buf[o]) {
+            float den = inplane(U, ti.Lw, kxy, psf.gxy, ci, cj);
+            float dn = a_sc * (__ldg(y + o) - my) - b_sc * (s_buf[o] - ms);
+            c = dn / den;
+        }
+        C[pp] = c;
+    }
+    __syncthreads();
+    for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) {
+        int li = lp % ti.Lw, lj = lp / ti.Lw;
+        float u = 0.f;
+        for (int dj = -kxy; dj <= kxy; ++dj) {
+            int cj = lj - kxy - dj;
+            if (cj < 0 || cj >= ti.th) continue;
+            float rr = 0.f;
+            for (int di = -kxy; di <= kxy; ++di) {
+                int ci = li - kxy - di;
+                if (ci < 0 || ci >= ti.tw) continue;
+                rr = fmaf(psf.gxy[di + kxy], C[cj * ti.tw + ci], rr);
+            }
+            u = fmaf(psf.gxy[dj + kxy], rr, u);
+        }
+        U[lp] = u;   // each lp written by its own thread; phase-0 data no longer read
+    }
+    __syncthreads();
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const size_t nxy = (size_t)vd.nx * vd.ny;
+    for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) {
+        float u = U[lp];
+        if (u == 0.f) continue;
+        unsigned q0[3];
+        lattice_q0(ti, kxy, lp, q0);
+        float li = (float)(ti.i0 - kxy + lp % ti.Lw), lj = (float)(ti.j0 - kxy + lp / ti.Lw);
+#pragma unroll
+        for (int z = -kz; z <= kz; ++z) {
+            unsigned qx = q0[0] + (unsigned)z * ti.ez[0];
+            unsigned qy = q0[1] + (unsigned)z * ti.ez[1];
+            unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
+            if (!inside(vd, qx, qy, qz)) continue;
+            int bx, by, bz;
+            float fx, fy, fz;
+            split(qx, vd.nx, bx, fx);
+            split(qy, vd.ny, by, fy);
+            split(qz, vd.nz, bz, fz);
+            const float *b = x + (size_t)bz * nxy + (size_t)by * vd.nx + bx;
+            float v000 = __ldg(b), v100 = __ldg(b + 1);
+            float v010 = __ldg(b + vd.nx), v110 = __ldg(b + vd.nx + 1);
+            float v001 = __ldg(b + nxy), v101 = __ldg(b + nxy + 1);
+            float v011 = __ldg(b + nxy + vd.nx), v111 = __ldg(b + nxy + vd.nx + 1);
+            float gx = (1.f - fy) * (1.f - fz) * (v100 - v000) + fy * (1.f - fz) * (v110 - v010) +
+                       (1.f - fy) * fz * (v101 - v001) + fy * fz * (v111 - v011);
+            float gy = (1.f - fx) * (1.f - fz) * (v010 - v000) + fx * (1.f - fz) * (v110 - v100) +
+                       (1.f - fx) * fz * (v011 - v001) + fx * fz * (v111 - v101);
+            float gzv = (1.f - fx) * (1.f - fy) * (v001 - v000) + fx * (1.f - fy) * (v101 - v100) +
+                        (1.f - fx) * fy * (v011 - v010) + fx * fy * (v111 - v110);
+            float wgt = u * gzp[z + kz];
+            float fzeta = (float)z;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                float dqx = jc[k][0] * li + jc[k][3] * lj + jc[k][6] * fzeta + jc[k][9];
+                float dqy = jc[k][1] * li + jc[k][4] * lj + jc[k][7] * fzeta + jc[k][10];
+                float dqz = jc[k][2] * li + jc[k][5] * lj + jc[k][8] * fzeta + jc[k][11];
+                acc[k] = fmaf(wgt, gx * dqx + gy * dqy + gzv * dqz, acc[k]);
+            }
+        }
+    }
+    double dacc[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) dacc[k] = (double)acc[k];
+    block_sum<6>(dacc, red);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 6; ++k) gp[k] = dacc[k];
+        gp[6] = gp[7] = 0.0;
+    }
+}
+
+__global__ void k_ncc_finish(int n, int tpp, const int32_t *__restrict__ desc,
+                             const float *__restrict__ y, const double *__restrict__ part,
+                             const double *__restrict__ gpart, int min_valid,
+                             double *__restrict__ ncc, double *__restrict__ grad)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    double v, my, ms, sd, vs, nn;
+    double yref = (double)y[desc[8 * (size_t)p + 6]];
+    bool ok = ncc_from_moments(part, p, tpp, min_valid, yref, v, my, ms, sd, vs, nn);
+    ncc[p] = ok ? v : 0.0;
+    if (grad) {
+        for (int k = 0; k < 6; ++k) {
+            double s = 0.0;
+            if (ok)
+                for (int t = 0; t < tpp; ++t) s += gpart[((size_t)p * tpp + t) * kPartStride + k];
+            grad[6 * (size_t)p + k] = s;
+        }
+    }
+}
+
+size_t smem_forward(const Tiling &tl, int kxy)
+{
+    size_t L = (size_t)(tl.T + 2 * kxy) * (tl.T + 2 * kxy);
+    return 2 * L * sizeof(float);
+}
+
+size_t smem_adjoint(const Tiling &tl, int kxy)
+{
+    size_t L = (size_t)(tl.T + 2 * kxy) * (tl.T + 2 * kxy);
+    return (2 * L + 2 * (size_t)tl.T * tl.T) * sizeof(float);
+}
+
+template <typename K>
+cudaError_t prep(K kern, size_t smem)
+{
+    if (smem > 48 * 1024) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaSuccess;
+}
+
+}  // namespace
+
+// Launchers: the (kxy, kz) = (1, 3) specialisation serves the default PSF;
+// every other setting takes the runtime-loop instantiation.
+
+cudaError_t launch_simulate(const DevGeom *, const PsfTab &psf, const Tiling &tl, int nx, int ny,
+                            int nz, const float *x, const int32_t *desc, const int32_t *fix, int n,
+                            const float *y, float *out, uint8_t *valid, double *part,
+                            cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    VolDims vd = vol_dims(nx, ny, nz);
+    size_t smem = smem_forward(tl, psf.kxy);
+    dim3 grid((unsigned)n * tl.tpp), block(256);
+    cudaError_t e;
+    if (psf.kxy == 1 && psf.kz == 3) {
+        if ((e = prep(k_simulate<1, 3>, smem)) != cudaSuccess) return e;
+        k_simulate<1, 3><<<grid, block, smem, st>>>(x, vd, desc, fix, psf, tl, y, out, valid, part);
+    } else {
+        if ((e = prep(k_simulate<-1, -1>, smem)) != cudaSuccess) return e;
+        k_simulate<-1, -1><<<grid, block, smem, st>>>(x, vd, desc, fix, psf, tl, y, out, valid, part);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const PsfTab &psf, const Tiling &tl, int nx, int ny, int nz,
+                           const int32_t *desc, const int32_t *fix, int n, const float *r,
+                           const float *w, const uint8_t *pmask, float *addon, float *conf,
+                           cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    VolDims vd = vol_dims(nx, ny, nz);
+    size_t smem = smem_adjoint(tl, psf.kxy);
+    dim3 grid((unsigned)n * tl.tpp), block(256);
+    cudaError_t e;
+    if (psf.kxy == 1 && psf.kz == 3) {
+        if ((e = prep(k_adjoint<1, 3>, smem)) != cudaSuccess) return e;
+        k_adjoint<1, 3><<<grid, block, smem, st>>>(vd, desc, fix, psf, tl, r, w, pmask, addon, conf);
+    } else {
+        if ((e = prep(k_adjoint<-1, -1>, smem)) != cudaSuccess) return e;
+        k_adjoint<-1, -1><<<grid, block, smem, st>>>(vd, desc, fix, psf, tl, r, w, pmask, addon, conf);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &tl, int nx, int ny,
+                            int nz, const float *x, const float *y, const int32_t *desc,
+                            const int32_t *fix, const double *poses, int n, float *s_buf,
+                            uint8_t *v_buf, double *part, double *gpart, const int32_t *active,
+                            int min_valid, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    VolDims vd = vol_dims(nx, ny, nz);
+    size_t smem = smem_forward(tl, psf.kxy);
+    size_t smem2 = (size_t)((tl.T + 2 * psf.kxy) * (tl.T + 2 * psf.kxy) + tl.T * tl.T) * sizeof(float);
+    dim3 grid((unsigned)n * tl.tpp), block(256);
+    cudaError_t e;
+    if (psf.kxy == 1 && psf.kz == 3) {
+        if ((e = prep(k_ncc_moments<1, 3>, smem)) != cudaSuccess) return e;
+        if ((e = prep(k_ncc_grad<1, 3>, smem2)) != cudaSuccess) return e;
+        k_ncc_moments<1, 3><<<grid, block, smem, st>>>(x, vd, desc, fix, psf, tl, y, active, s_buf, v_buf, part);
+        if (gpart)
+            k_ncc_grad<1, 3><<<grid, block, smem2, st>>>(x, vd, g, desc, fix, psf, tl, y, poses, active,
+                                                         s_buf, v_buf, part, gpart, min_valid);
+    } else {
+        if ((e = prep(k_ncc_moments<-1, -1>, smem)) != cudaSuccess) return e;
+        if ((e = prep(k_ncc_grad<-1, -1>, smem2)) != cudaSuccess) return e;
+        k_ncc_moments<-1, -1><<<grid, block, smem, st>>>(x, vd, desc, fix, psf, tl, y, active, s_buf, v_buf, part);
+        if (gpart)
+            k_ncc_grad<-1, -1><<<grid, block, smem2, st>>>(x, vd, g, desc, fix, psf, tl, y, poses, active,
+                                                           s_buf, v_buf, part, gpart, min_valid);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ncc_finish(const int32_t *desc, const float *y, int n, const Tiling &tl,
+                              const double *part, const double *gpart, int min_valid, double *ncc,
+                              double *grad, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_ncc_finish<<<(n + 127) / 128, 128, 0, st>>>(n, tl.tpp, desc, y, part, gpart, min_valid, ncc, grad);
+    return cudaGetLastError();
+}
+
+}  // namespace pvr

@@ -1,0 +1,614 @@
+// C ABI of libpvr: context, argument checks, scratch, call sequencing.
+// Every compute step runs in this library's kernels; the host only checks
+// arguments, derives constants and enqueues launches.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "pvr_internal.h"
+
+namespace pvr {
+cudaError_t launch_em_stats(const float *y, const float *sim, const uint8_t *valid,
+                            const int32_t *desc, int n, int64_t n_pix, const Tiling &tl,
+                            int32_t *err, double *part, cudaStream_t st);
+cudaError_t launch_em(const float *y, const float *sim, const uint8_t *valid, const int32_t *desc,
+                      int n, int64_t n_pix, const Tiling &tl, int32_t *err, double *state,
+                      const uint8_t *mask_in, uint8_t *mask_out, float *p, float *w_patch,
+                      float *pbar_out, double *part, double *pstat, double *pbar, double *wsc,
+                      uint8_t *elig, const pvr_params &prm, cudaStream_t st);
+cudaError_t launch_patches_build(const DevGeom *g, const pvr_geometry &hg, const float *stacks,
+                                 int64_t total, int a, int stride, double fg_frac,
+                                 double keep_frac, int32_t *desc_out, int max_out, int32_t *keep,
+                                 int64_t *n_cand_out, unsigned *imax_key, int32_t *counts,
+                                 cudaStream_t st);
+}  // namespace pvr
+
+using namespace pvr;
+
+namespace {
+constexpr int kMaxTile = 64;
+constexpr int kMetricScratch = 2 * 8 * 296;
+constexpr int kMaxSideLimit = 256;
+}  // namespace
+
+struct pvr_ctx {
+    pvr_geometry geom;
+    pvr_params prm;
+    DevGeom hgeom;
+    PsfTab psf;
+    int device = 0;
+    int64_t nvox = 0;
+    int64_t stack_total = 0;
+    int tpp_cap = 1;
+    // device scratch
+    DevGeom *d_geom = nullptr;
+    int32_t *fix = nullptr;
+    double *part = nullptr, *gpart = nullptr, *pstat = nullptr;
+    double *pbar = nullptr, *wsc = nullptr;
+    uint8_t *elig = nullptr;
+    int32_t *err = nullptr;
+    double *best = nullptr, *gbest = nullptr, *nbest = nullptr, *trial = nullptr, *delta = nullptr;
+    double *ncc_tmp = nullptr, *grad_tmp = nullptr;
+    int32_t *active = nullptr;
+    float *s_buf = nullptr, *e_buf = nullptr, *p_buf = nullptr;
+    uint8_t *v_buf = nullptr, *valid_buf = nullptr, *mask_tmp = nullptr;
+    float *addon = nullptr, *conf = nullptr;
+    int32_t *keep = nullptr;
+    int64_t keep_cap = 0;
+    unsigned *imax_key = nullptr;
+    int32_t *counts = nullptr;
+    double *metric_scr = nullptr;
+    std::string last_error;
+    int64_t launches = 0;
+};
+
+namespace {
+
+int fail(pvr_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->last_error = buf;
+    return code;
+}
+
+int cuda_check(pvr_ctx *c, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return PVR_OK;
+    return fail(c, PVR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+Tiling make_tiling(int max_side)
+{
+    Tiling t;
+    t.T = max_side <= kMaxTile ? max_side : kMaxTile;
+    if (t.T < 1) t.T = 1;
+    t.tiles_x = (max_side + t.T - 1) / t.T;
+    t.tiles_y = t.tiles_x;
+    t.tpp = t.tiles_x * t.tiles_y;
+    return t;
+}
+
+int check_patches(pvr_ctx *c, const pvr_patches *pp, int *max_side)
+{
+    if (!pp) return fail(c, PVR_ERR_INVALID_ARG, "patches is NULL");
+    if (pp->n < 0 || pp->n > c->prm.max_patches)
+        return fail(c, PVR_ERR_INVALID_ARG, "patch count %d outside 0..%d", pp->n, c->prm.max_patches);
+    if (pp->n > 0 && !pp->desc) return fail(c, PVR_ERR_INVALID_ARG, "patch table is NULL");
+    if (pp->n_pix < 0 || pp->n_pix > c->prm.max_pixels)
+        return fail(c, PVR_ERR_INVALID_ARG, "pixel count %lld outside 0..%lld", (long long)pp->n_pix,
+                    (long long)c->prm.max_pixels);
+    int ms = pp->max_side > 0 ? pp->max_side : c->prm.max_patch_side;
+    if (ms > c->prm.max_patch_side)
+        return fail(c, PVR_ERR_INVALID_ARG, "max_side %d above the context's %d", ms,
+                    c->prm.max_patch_side);
+    *max_side = ms;
+    return PVR_OK;
+}
+
+#define REQUIRE(cond, ...)                                          \
+    do {                                                            \
+        if (!(cond)) return fail(c, PVR_ERR_INVALID_ARG, __VA_ARGS__); \
+    } while (0)
+
+#define CUDA_TRY(expr, what)                                  \
+    do {                                                      \
+        int _rc = cuda_check(c, (expr), what);                \
+        if (_rc != PVR_OK) return _rc;                        \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n)
+{
+    return cudaMalloc((void **)p, (n > 0 ? n : 1) * sizeof(T));
+}
+
+void free_all(pvr_ctx *c)
+{
+    void *ptrs[] = {c->d_geom, c->fix, c->part, c->gpart, c->pstat, c->pbar, c->wsc, c->elig,
+                    c->err, c->best, c->gbest, c->nbest, c->trial, c->delta, c->ncc_tmp,
+                    c->grad_tmp, c->active, c->s_buf, c->e_buf, c->p_buf, c->v_buf,
+                    c->valid_buf, c->mask_tmp, c->addon, c->conf, c->keep, c->imax_key,
+                    c->counts, c->metric_scr};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+// K1 for a patch table at `poses` into the context's fixed table.
+int pose_fixed(pvr_ctx *c, const pvr_patches *pp, int max_side, const double *poses, cudaStream_t st)
+{
+    CUDA_TRY(launch_pose_to_fixed(c->d_geom, pp->desc, poses, pp->n, pp->n_pix, max_side,
+                                  c->psf.kxy, c->psf.kz, c->fix, c->err, st),
+             "pose_to_fixed");
+    c->launches += pp->n > 0;
+    return PVR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pvr_params_default(pvr_params *p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->psf_fwhm_xy = 1.2;
+    p->psf_kxy = 1;
+    p->psf_kz = 3;
+    p->psf_dz = 1.0;
+    p->alpha = 1.0;
+    p->conf_eps = 1e-6;
+    p->em_c0 = 0.9;
+    p->em_sigma_floor_rel = 1e-3;
+    p->em_min_valid_frac = 0.1;
+    p->patch_rule = 0;
+    p->patch_threshold = 0.5;
+    p->patch_em_iters = 5;
+    p->n_params = 6;
+    p->reg_evals = 40;
+    p->reg_delta0 = 2.0;
+    p->reg_delta_min = 0.01;
+    p->reg_grow = 1.0;
+    p->reg_fixed_step = 0;
+    p->reg_min_valid = 16;
+    p->n_sr = 1;
+    p->max_patches = 65536;
+    p->max_pixels = (int64_t)1 << 27;
+    p->max_patch_side = 128;
+}
+
+int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
+{
+    if (!out) return PVR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!g || !prm) return PVR_ERR_INVALID_ARG;
+    pvr_ctx *c = new pvr_ctx();
+    auto bad = [&](const char *msg) {
+        fprintf(stderr, "pvr_ctx_create: %s\n", msg);
+        delete c;
+        return PVR_ERR_INVALID_ARG;
+    };
+    if (g->nx < 2 || g->ny < 2 || g->nz < 2 || g->nx > 2048 || g->ny > 2048 || g->nz > 2048)
+        return bad("volume sizes must be 2..2048");
+    if (g->n_stacks < 1 || g->n_stacks > PVR_MAX_STACKS) return bad("n_stacks outside 1..16");
+    for (int s = 0; s < g->n_stacks; ++s) {
+        if (g->stack_w[s] < 1 || g->stack_h[s] < 1 || g->stack_k[s] < 1) return bad("empty stack");
+        if (!(g->thickness[s] >= 0.0) || !isfinite(g->thickness[s])) return bad("bad slice thickness");
+        for (int i = 0; i < 12; ++i)
+            if (!isfinite(g->pixel_to_world[s][i])) return bad("non-finite pixel_to_world");
+        const double *S = g->pixel_to_world[s];
+        if (!(S[2] * S[2] + S[6] * S[6] + S[10] * S[10] > 0.0)) return bad("zero slice axis");
+    }
+    for (int i = 0; i < 12; ++i)
+        if (!isfinite(g->world_to_voxel[i])) return bad("non-finite world_to_voxel");
+    if (prm->psf_kxy < 0 || prm->psf_kxy > PVR_MAX_KXY) return bad("psf_kxy outside 0..3");
+    if (prm->psf_kz < 0 || prm->psf_kz > PVR_MAX_KZ) return bad("psf_kz outside 0..8");
+    if (!(prm->psf_dz > 0.0) || !(prm->psf_fwhm_xy >= 0.0)) return bad("bad PSF size");
+    if (prm->n_params != 6) return bad("only rigid (6-parameter) poses are supported");
+    if (prm->max_patches < 1 || prm->max_pixels < 1) return bad("capacity must be positive");
+    if (prm->max_patch_side < 1 || prm->max_patch_side > kMaxSideLimit)
+        return bad("max_patch_side outside 1..256");
+    if (prm->patch_em_iters < 0 || prm->reg_evals < 0 || prm->n_sr < 0) return bad("negative count");
+    c->geom = *g;
+    c->prm = *prm;
+    cudaGetDevice(&c->device);
+
+    // device geometry
+    DevGeom &hg = c->hgeom;
+    memset(&hg, 0, sizeof hg);
+    hg.nx = g->nx;
+    hg.ny = g->ny;
+    hg.nz = g->nz;
+    hg.n_stacks = g->n_stacks;
+    long long off = 0;
+    for (int s = 0; s < g->n_stacks; ++s) {
+        hg.sw[s] = g->stack_w[s];
+        hg.sh[s] = g->stack_h[s];
+        hg.sk[s] = g->stack_k[s];
+        hg.stack_off[s] = off;
+        off += (long long)g->stack_w[s] * g->stack_h[s] * g->stack_k[s];
+        memcpy(hg.p2w[s], g->pixel_to_world[s], 12 * sizeof(double));
+    }
+    memcpy(hg.w2v, g->world_to_voxel, 12 * sizeof(double));
+    hg.dz = prm->psf_dz;
+    c->stack_total = off;
+    c->nvox = (int64_t)g->nx * g->ny * g->nz;
+
+    // PSF tables: float64 Gaussian weights rounded to float32
+    PsfTab &t = c->psf;
+    memset(&t, 0, sizeof t);
+    t.kxy = prm->psf_kxy;
+    t.kz = prm->psf_kz;
+    const double to_sigma = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
+    double sxy = prm->psf_fwhm_xy * to_sigma;
+    for (int d = -t.kxy; d <= t.kxy; ++d)
+        t.gxy[d + t.kxy] = (float)(sxy > 0.0 ? exp(-(double)(d * d) / (2.0 * sxy * sxy)) : (d == 0));
+    for (int s = 0; s < g->n_stacks; ++s) {
+        double sz = g->thickness[s] * to_sigma;
+        for (int z = -t.kz; z <= t.kz; ++z) {
+            double o = z * prm->psf_dz;
+            t.gz[s][z + t.kz] = (float)(sz > 0.0 ? exp(-(o * o) / (2.0 * sz * sz)) : (z == 0));
+        }
+    }
+
+    // scratch
+    Tiling tl = make_tiling(prm->max_patch_side);
+    c->tpp_cap = tl.tpp;
+    size_t P = (size_t)prm->max_patches, NP = (size_t)prm->max_pixels;
+    size_t slots = P * (size_t)tl.tpp * kPartStride;
+    c->keep_cap = (int64_t)(P * 4 > (1u << 20) ? P * 4 : (1u << 20));
+    cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, n) if (e == cudaSuccess) e = dalloc(&(ptr), (n))
+    ALLOC(c->d_geom, 1);
+    ALLOC(c->fix, P * kFixStride);
+    ALLOC(c->part, slots);
+    ALLOC(c->gpart, slots);
+    ALLOC(c->pstat, 8);
+    ALLOC(c->pbar, P);
+    ALLOC(c->wsc, P);
+    ALLOC(c->elig, P);
+    ALLOC(c->err, 1);
+    ALLOC(c->best, P * kRegStride);
+    ALLOC(c->gbest, P * kRegStride);
+    ALLOC(c->nbest, P);
+    ALLOC(c->trial, P * 6);
+    ALLOC(c->delta, P);
+    ALLOC(c->ncc_tmp, P);
+    ALLOC(c->grad_tmp, P * 6);
+    ALLOC(c->active, P);
+    ALLOC(c->s_buf, NP);
+    ALLOC(c->e_buf, NP);
+    ALLOC(c->p_buf, NP);
+    ALLOC(c->v_buf, NP);
+    ALLOC(c->valid_buf, NP);
+    ALLOC(c->mask_tmp, P);
+    ALLOC(c->addon, (size_t)c->nvox);
+    ALLOC(c->conf, (size_t)c->nvox);
+    ALLOC(c->keep, (size_t)c->keep_cap);
+    ALLOC(c->imax_key, 1);
+    ALLOC(c->counts, 4);
+    ALLOC(c->metric_scr, kMetricScratch);
+#undef ALLOC
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_geom, &hg, sizeof hg, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(c->addon, 0, (size_t)c->nvox * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(c->conf, 0, (size_t)c->nvox * sizeof(float));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "pvr_ctx_create: %s\n", cudaGetErrorString(e));
+        free_all(c);
+        delete c;
+        return PVR_ERR_CUDA;
+    }
+    *out = c;
+    return PVR_OK;
+}
+
+int pvr_ctx_destroy(pvr_ctx *c)
+{
+    if (!c) return PVR_OK;
+    cudaDeviceSynchronize();
+    free_all(c);
+    delete c;
+    return PVR_OK;
+}
+
+const char *pvr_last_error(const pvr_ctx *c) { return c ? c->last_error.c_str() : "null context"; }
+
+int64_t pvr_launch_count(const pvr_ctx *c) { return c ? c->launches : 0; }
+
+int pvr_device_status(pvr_ctx *c, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t h = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h, c->err, sizeof h, cudaMemcpyDeviceToHost, st), "read error word");
+    CUDA_TRY(cudaStreamSynchronize(st), "synchronise");
+    CUDA_TRY(cudaMemsetAsync(c->err, 0, sizeof h, st), "clear error word");
+    if (h & 1) return fail(c, PVR_ERR_BOUNDS, "a patch row lies outside its stack or pixel range");
+    if (h & 2) return fail(c, PVR_ERR_NUMERIC, "a pose produced a non-finite sample map");
+    return PVR_OK;
+}
+
+int pvr_patches_build(pvr_ctx *c, const float *stacks, int32_t a, int32_t stride, double fg_frac,
+                      double keep_frac, int32_t *desc_out, int32_t max_out, int32_t *n_out,
+                      int64_t *n_pix_out, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    REQUIRE(stacks && desc_out && n_out && n_pix_out, "NULL argument");
+    REQUIRE(a >= 1 && stride >= 1 && a <= c->prm.max_patch_side, "a must be 1..max_patch_side, stride >= 1");
+    REQUIRE(max_out >= 0, "max_out < 0");
+    REQUIRE(isfinite(fg_frac) && isfinite(keep_frac), "non-finite level");
+    int64_t n_cand = 0;
+    for (int s = 0; s < c->geom.n_stacks; ++s) {
+        int W = c->geom.stack_w[s], H = c->geom.stack_h[s];
+        int64_t nx = W >= a ? (W - a) / stride + 1 : 0, ny = H >= a ? (H - a) / stride + 1 : 0;
+        n_cand += (int64_t)c->geom.stack_k[s] * nx * ny;
+    }
+    REQUIRE(n_cand <= c->keep_cap, "%lld candidate patches exceed the scratch (%lld)",
+            (long long)n_cand, (long long)c->keep_cap);
+    REQUIRE(n_cand * (int64_t)a * a < ((int64_t)1 << 31), "pixel offsets would exceed int32");
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t nc = 0;
+    CUDA_TRY(launch_patches_build(c->d_geom, c->geom, stacks, c->stack_total, a, stride, fg_frac,
+                                  keep_frac, desc_out, max_out, c->keep, &nc, c->imax_key,
+                                  c->counts, st),
+             "patches_build");
+    c->launches += nc > 0 ? 3 : 1;
+    int32_t h[4];
+    CUDA_TRY(cudaMemcpyAsync(h, c->counts, sizeof h, cudaMemcpyDeviceToHost, st), "read counts");
+    CUDA_TRY(cudaStreamSynchronize(st), "synchronise");
+    *n_out = h[0];
+    *n_pix_out = ((int64_t)(uint32_t)h[1]) | ((int64_t)h[2] << 32);
+    return PVR_OK;
+}
+
+int pvr_patches_gather(pvr_ctx *c, const float *stacks, const pvr_patches *pp, float *y, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    int ms;
+    int rc = check_patches(c, pp, &ms);
+    if (rc) return rc;
+    REQUIRE(stacks && y, "NULL argument");
+    CUDA_TRY(launch_patches_gather(c->d_geom, stacks, pp->desc, pp->n, pp->n_pix, c->err, y,
+                                   (cudaStream_t)stream),
+             "patches_gather");
+    c->launches += pp->n > 0;
+    return PVR_OK;
+}
+
+int pvr_pose_to_fixed(pvr_ctx *c, const pvr_patches *pp, const double *poses, int32_t *fix,
+                      void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    int ms;
+    int rc = check_patches(c, pp, &ms);
+    if (rc) return rc;
+    REQUIRE(pp->n == 0 || (poses && fix), "NULL argument");
+    CUDA_TRY(launch_pose_to_fixed(c->d_geom, pp->desc, poses, pp->n, pp->n_pix, ms, c->psf.kxy,
+                                  c->psf.kz, fix, c->err, (cudaStream_t)stream),
+             "pose_to_fixed");
+    c->launches += pp->n > 0;
+    return PVR_OK;
+}
+
+int pvr_simulate(pvr_ctx *c, const float *x, const pvr_patches *pp, const double *poses, float *sim,
+                 uint8_t *valid, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    int ms;
+    int rc = check_patches(c, pp, &ms);
+    if (rc) return rc;
+    REQUIRE(pp->n == 0 || (x && poses && sim && valid), "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
+    Tiling tl = make_tiling(ms);
+    CUDA_TRY(launch_simulate(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, pp->desc,
+                             c->fix, pp->n, nullptr, sim, valid, nullptr, st),
+             "simulate");
+    c->launches += pp->n > 0;
+    return PVR_OK;
+}
+
+int pvr_adjoint(pvr_ctx *c, const pvr_patches *pp, const double *poses, const float *r,
+                const float *w, float *addon, float *conf, int32_t accumulate, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    int ms;
+    int rc = check_patches(c, pp, &ms);
+    if (rc) return rc;
+    REQUIRE(addon || conf, "addon and conf are both NULL");
+    REQUIRE(pp->n == 0 || poses, "NULL poses");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t vb = (size_t)c->nvox * sizeof(float);
+    if (!accumulate) {
+        if (addon) CUDA_TRY(cudaMemsetAsync(addon, 0, vb, st), "clear addon");
+        if (conf) CUDA_TRY(cudaMemsetAsync(conf, 0, vb, st), "clear conf");
+    }
+    if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
+    Tiling tl = make_tiling(ms);
+    CUDA_TRY(launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix, pp->n,
+                            r, w, nullptr, addon, conf, st),
+             "adjoint");
+    c->launches += pp->n > 0;
+    return PVR_OK;
+}
+
+int pvr_em_weights(pvr_ctx *c, const float *y, const float *sim, const uint8_t *valid,
+                   const pvr_patches *pp, double *state, const uint8_t *mask_in, uint8_t *mask_out,
+                   float *p, float *w_patch, float *pbar, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    int ms;
+    int rc = check_patches(c, pp, &ms);
+    if (rc) return rc;
+    REQUIRE(y && valid && state && mask_out && p, "NULL argument");
+    REQUIRE(mask_in != mask_out, "mask_in and mask_out must not alias");
+    cudaStream_t st = (cudaStream_t)stream;
+    Tiling tl = make_tiling(ms);
+    CUDA_TRY(launch_em_stats(y, sim, valid, pp->desc, pp->n, pp->n_pix, tl, c->err, c->part, st),
+             "em_stats");
+    CUDA_TRY(launch_em(y, sim, valid, pp->desc, pp->n, pp->n_pix, tl, c->err, state, mask_in,
+                       mask_out, p, w_patch, pbar, c->part, c->pstat, c->pbar, c->wsc, c->elig,
+                       c->prm, st),
+             "em");
+    c->launches += pp->n > 0 ? 4 : 2;
+    return PVR_OK;
+}
+
+int pvr_volume_update(pvr_ctx *c, float *x, float *addon, float *conf, int32_t clear, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    REQUIRE(x && addon && conf, "NULL argument");
+    CUDA_TRY(launch_volume_update(x, addon, conf, c->nvox, (float)c->prm.alpha,
+                                  (float)c->prm.conf_eps, clear, 0, (cudaStream_t)stream),
+             "volume_update");
+    c->launches += 1;
+    return PVR_OK;
+}
+
+int pvr_volume_init(pvr_ctx *c, float *x, const float *y, const pvr_patches *pp,
+                    const double *poses, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    int ms;
+    int rc = check_patches(c, pp, &ms);
+    if (rc) return rc;
+    REQUIRE(x && y && (pp->n == 0 || poses), "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t vb = (size_t)c->nvox * sizeof(float);
+    CUDA_TRY(cudaMemsetAsync(c->addon, 0, vb, st), "clear");
+    CUDA_TRY(cudaMemsetAsync(c->conf, 0, vb, st), "clear");
+    if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
+    Tiling tl = make_tiling(ms);
+    CUDA_TRY(launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix, pp->n,
+                            y, nullptr, nullptr, c->addon, c->conf, st),
+             "adjoint");
+    CUDA_TRY(launch_volume_update(x, c->addon, c->conf, c->nvox, 1.0f, (float)c->prm.conf_eps, 1, 1,
+                                  st),
+             "volume_init");
+    c->launches += (pp->n > 0) + 1;
+    return PVR_OK;
+}
+
+int pvr_ncc_grad(pvr_ctx *c, const float *x, const float *y, const pvr_patches *pp,
+                 const double *poses, double *ncc, double *grad, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    int ms;
+    int rc = check_patches(c, pp, &ms);
+    if (rc) return rc;
+    REQUIRE(pp->n == 0 || (x && y && poses && ncc), "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
+    Tiling tl = make_tiling(ms);
+    CUDA_TRY(launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, y,
+                             pp->desc, c->fix, poses, pp->n, c->s_buf, c->v_buf, c->part,
+                             grad ? c->gpart : nullptr, nullptr, c->prm.reg_min_valid, st),
+             "ncc_grad");
+    CUDA_TRY(launch_ncc_finish(pp->desc, y, pp->n, tl, c->part, c->gpart, c->prm.reg_min_valid, ncc,
+                               grad, st),
+             "ncc_finish");
+    c->launches += pp->n > 0 ? (grad ? 3 : 2) : 0;
+    return PVR_OK;
+}
+
+static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_patches *pp, int ms,
+                         double *poses, int n_evals, double *ncc_out, cudaStream_t st)
+{
+    int n = pp->n;
+    if (n == 0 || n_evals <= 0) return PVR_OK;
+    Tiling tl = make_tiling(ms);
+    CUDA_TRY(launch_reg_init(poses, n, c->best, c->trial, c->delta, c->active, c->prm.reg_delta0, st),
+             "reg_init");
+    c->launches += 1;
+    for (int ev = 0; ev < n_evals; ++ev) {
+        int rc = pose_fixed(c, pp, ms, c->trial, st);
+        if (rc) return rc;
+        CUDA_TRY(launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, y,
+                                 pp->desc, c->fix, c->trial, n, c->s_buf, c->v_buf, c->part,
+                                 c->gpart, c->active, c->prm.reg_min_valid, st),
+                 "ncc_grad");
+        CUDA_TRY(launch_ncc_finish(pp->desc, y, n, tl, c->part, c->gpart, c->prm.reg_min_valid,
+                                   c->ncc_tmp, c->grad_tmp, st),
+                 "ncc_finish");
+        CUDA_TRY(launch_reg_step(c->d_geom, pp->desc, n, ev, ev == n_evals - 1, c->ncc_tmp,
+                                 c->grad_tmp, c->best, c->gbest, c->nbest, c->trial, c->delta,
+                                 c->active, c->prm, st),
+                 "reg_step");
+        c->launches += 4;
+    }
+    CUDA_TRY(launch_reg_finish(c->best, c->nbest, n, poses, ncc_out, st), "reg_finish");
+    c->launches += 1;
+    return PVR_OK;
+}
+
+int pvr_register(pvr_ctx *c, const float *x, const float *y, const pvr_patches *pp, double *poses,
+                 int32_t n_evals, double *ncc, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    int ms;
+    int rc = check_patches(c, pp, &ms);
+    if (rc) return rc;
+    REQUIRE(n_evals >= 0, "n_evals < 0");
+    REQUIRE(pp->n == 0 || (x && y && poses), "NULL argument");
+    return register_impl(c, x, y, pp, ms, poses, n_evals, ncc, (cudaStream_t)stream);
+}
+
+int pvr_reconstruct_iter(pvr_ctx *c, float *x, const float *y, const pvr_patches *pp, double *poses,
+                         double *state, uint8_t *mask, float *p, float *w_patch, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    int ms;
+    int rc = check_patches(c, pp, &ms);
+    if (rc) return rc;
+    REQUIRE(x && y && state && mask && (pp->n == 0 || poses), "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = register_impl(c, x, y, pp, ms, poses, c->prm.reg_evals, nullptr, st))) return rc;
+    if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
+    Tiling tl = make_tiling(ms);
+    size_t vb = (size_t)c->nvox * sizeof(float);
+    CUDA_TRY(cudaMemsetAsync(c->addon, 0, vb, st), "clear");
+    CUDA_TRY(cudaMemsetAsync(c->conf, 0, vb, st), "clear");
+    for (int it = 0; it < c->prm.n_sr; ++it) {
+        CUDA_TRY(launch_simulate(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x,
+                                 pp->desc, c->fix, pp->n, y, c->e_buf, c->valid_buf, c->part, st),
+                 "simulate");
+        CUDA_TRY(launch_em(c->e_buf, nullptr, c->valid_buf, pp->desc, pp->n, pp->n_pix, tl, c->err,
+                           state, mask, c->mask_tmp, c->p_buf, w_patch, nullptr, c->part, c->pstat,
+                           c->pbar, c->wsc, c->elig, c->prm, st),
+                 "em");
+        CUDA_TRY(cudaMemcpyAsync(mask, c->mask_tmp, (size_t)pp->n, cudaMemcpyDeviceToDevice, st),
+                 "mask copy");
+        CUDA_TRY(launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix,
+                                pp->n, c->e_buf, c->p_buf, mask, c->addon, c->conf, st),
+                 "adjoint");
+        CUDA_TRY(launch_volume_update(x, c->addon, c->conf, c->nvox, (float)c->prm.alpha,
+                                      (float)c->prm.conf_eps, 1, 0, st),
+                 "volume_update");
+        c->launches += pp->n > 0 ? 6 : 3;
+    }
+    if (p && pp->n_pix > 0)
+        CUDA_TRY(cudaMemcpyAsync(p, c->p_buf, (size_t)pp->n_pix * sizeof(float),
+                                 cudaMemcpyDeviceToDevice, st),
+                 "p copy");
+    return PVR_OK;
+}
+
+int pvr_metrics(pvr_ctx *c, const float *ref, const float *img, const uint8_t *mask, int64_t n,
+                double *out, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    REQUIRE(ref && img && out && n >= 0, "bad argument");
+    CUDA_TRY(launch_metrics(ref, img, mask, n, c->metric_scr, out, (cudaStream_t)stream), "metrics");
+    c->launches += 3;
+    return PVR_OK;
+}
+
+}  // extern "C"

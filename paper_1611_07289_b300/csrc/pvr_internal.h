@@ -1,0 +1,88 @@
+// Internal declarations of libpvr (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pvr.h"
+
+namespace pvr {
+
+constexpr int kFracBits = 20;              // Q11.20 sample coordinates
+constexpr int kFixStride = 16;             // int32 per patch in the fixed table
+constexpr int kPartStride = 8;             // float64 per (patch, tile) partial slot
+constexpr int kRegStride = 12;             // float64 per patch pose slot
+
+// Geometry as the kernels read it (device memory, copied at context creation).
+struct DevGeom {
+    int nx, ny, nz, n_stacks;
+    int sw[PVR_MAX_STACKS], sh[PVR_MAX_STACKS], sk[PVR_MAX_STACKS];
+    long long stack_off[PVR_MAX_STACKS];   // element offset of stack s in the packed buffer
+    double w2v[12];
+    double p2w[PVR_MAX_STACKS][12];
+    double dz;                             // through-plane PSF step, mm
+};
+
+// PSF weight tables (float32), passed to kernels by value.
+struct PsfTab {
+    int kxy, kz;
+    float gxy[2 * PVR_MAX_KXY + 1];
+    float gz[PVR_MAX_STACKS][2 * PVR_MAX_KZ + 1];
+};
+
+// Patch-tile decomposition shared by the per-patch kernels: tile side T
+// pixels, tiles_x * tiles_y tiles per patch (the largest patch's count);
+// block b works on patch b / tpp, tile b % tpp.
+struct Tiling {
+    int T;
+    int tiles_x, tiles_y, tpp;
+};
+
+// Launchers (each returns cudaGetLastError() of its launches).
+cudaError_t launch_pose_to_fixed(const DevGeom *g, const int32_t *desc, const double *poses,
+                                 int n, int64_t n_pix, int max_side, int kxy, int kz,
+                                 int32_t *fix, int32_t *err, cudaStream_t st);
+
+cudaError_t launch_simulate(const DevGeom *g, const PsfTab &psf, const Tiling &tl, int nx, int ny,
+                            int nz, const float *x, const int32_t *desc, const int32_t *fix, int n,
+                            const float *y, float *sim_or_e, uint8_t *valid, double *part,
+                            cudaStream_t st);
+
+cudaError_t launch_adjoint(const PsfTab &psf, const Tiling &tl, int nx, int ny, int nz,
+                           const int32_t *desc, const int32_t *fix, int n, const float *r,
+                           const float *w, const uint8_t *patch_mask, float *addon, float *conf,
+                           cudaStream_t st);
+
+cudaError_t launch_volume_update(float *x, float *addon, float *conf, int64_t nvox, float alpha,
+                                 float conf_eps, int clear, int init_mode, cudaStream_t st);
+
+
+cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &tl, int nx, int ny,
+                            int nz, const float *x, const float *y, const int32_t *desc,
+                            const int32_t *fix, const double *poses, int n, float *s_buf,
+                            uint8_t *v_buf, double *part, double *gpart, const int32_t *active,
+                            int min_valid, cudaStream_t st);
+
+cudaError_t launch_ncc_finish(const int32_t *desc, const float *y, int n, const Tiling &tl,
+                              const double *part, const double *gpart, int min_valid, double *ncc,
+                              double *grad, cudaStream_t st);
+
+cudaError_t launch_reg_init(const double *poses, int n, double *best, double *trial,
+                            double *delta, int32_t *active, double delta0, cudaStream_t st);
+
+cudaError_t launch_reg_step(const DevGeom *g, const int32_t *desc, int n, int eval, int last,
+                            const double *ncc, const double *grad, double *best, double *gbest,
+                            double *nbest, double *trial, double *delta, int32_t *active,
+                            const pvr_params &prm, cudaStream_t st);
+
+cudaError_t launch_reg_finish(const double *best, const double *nbest, int n, double *poses,
+                              double *ncc_out, cudaStream_t st);
+
+
+cudaError_t launch_patches_gather(const DevGeom *g, const float *stacks, const int32_t *desc,
+                                  int n, int64_t n_pix, int32_t *err, float *y, cudaStream_t st);
+
+cudaError_t launch_metrics(const float *ref, const float *img, const uint8_t *mask, int64_t n,
+                           double *scratch, double *out, cudaStream_t st);
+
+}  // namespace pvr
