@@ -1,0 +1,402 @@
+"""Benchmark of the PVR hot path on the whole-uterus workload.
+
+Workload (synthetic, seeded; the paper's fetal scans are not available):
+256x256x192 volume at 0.75 mm, 4 stacks (3 orthogonal + 1 oblique 30 deg)
+of 96 slices of 256x256 px at 0.75x0.75x2.5 mm, breathing + fetal motion,
+5 % corrupted slices, square patches a = 64, stride 32, kept when half
+their pixels exceed 1 % of the maximum.  Gaussian PSF kxy = 1, kz = 3,
+dz = 0.75 mm.
+
+One step = one pvr_reconstruct_iter: 2 NCC evaluations of every patch with
+a registration accept/propose, the fixed-point lattice of the new poses,
+simulate + residual, EM weights with patch classification, weighted adjoint,
+SIRT update (every row of the hot-path table).  The patch table is built
+once before timing.  value = patch-pixels processed per second (all ranks).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch with torch.distributed.run; every rank runs an independent
+replica of the workload (the method's cross-patch coupling is a volume
+all-reduce that this single-GPU build does not implement), so scaling is
+weak and value sums over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "patch-pixels/s for simulate+adjoint (and % HBM roofline); s/iteration at matched PSNR"
+UNIT = "patch-pixels/s"
+WORKLOAD = "pvr-uterus-256x256x192-4x96x256^2-a64s32"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _config_dict(n_patches=None, n_pix=None, slices=96):
+    wl = WORKLOAD if slices == 96 else WORKLOAD.replace("4x96", f"4x{slices}")
+    return {"workload": wl, "volume": [256, 256, 192], "voxel_mm": 0.75,
+            "stacks": "3 orthogonal + 1 oblique, 96 x 256^2 @ 0.75x0.75x2.5 mm",
+            "patch": 64, "stride": 32, "psf": "gaussian kxy=1 kz=3 dz=0.75mm",
+            "step": "pvr_reconstruct_iter: 2 NCC evals + pose update, 1 SR pass",
+            "n_patches": n_patches, "n_patch_pixels": n_pix,
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------- roofline --
+
+def _algorithmic_bytes(cls, n_pix, n_vox):
+    """Bytes a kernel class must move per launch group (each array read or
+    written once; see the design notes for the per-unit figures)."""
+    return {"simulate": 9 * n_pix + 4 * n_vox,        # y in, e out, valid out, x in
+            "adjoint": 8 * n_pix + 8 * n_vox,         # e, p in; addon, conf out
+            "em": 9 * n_pix,                          # e, valid in; p out
+            "ncc": 18 * n_pix + 4 * n_vox,            # y, s, valid twice; x in
+            "update": 24 * n_vox}.get(cls)            # x, addon, conf in; x, 0, 0 out
+
+
+def _profile_traffic(cls):
+    """Per-launch DRAM bytes of `cls` from the committed ncu summary, if the
+    kernel source it was taken from is unchanged."""
+    path = os.path.join(ROOT, "profiles", f"{cls}_uterus.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
+    if not m or not h:
+        return None
+    src = open(os.path.join(ROOT, "paper_1611_07289_b300", "csrc", "k_patch.cu"), "rb").read()
+    if hashlib.sha256(src).hexdigest()[:16] != h.group(1)[:16]:
+        return None
+    return float(m.group(1))
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+# ----------------------------------------------------------- CPU (oracle) --
+
+def _oracle_sample(cfg, desc_all, y_all, n_sample, seed=0):
+    """A bounded sample of the workload for the FP64 oracle: n_sample patches
+    drawn from the table (re-packed), with their acquired pixels."""
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(desc_all.shape[0], size=min(n_sample, desc_all.shape[0]), replace=False))
+    d = desc_all[sel].copy()
+    ys, off = [], 0
+    for r in d:
+        n = int(r[4] * r[5])
+        ys.append(y_all[int(r[6]):int(r[6]) + n])
+        r[6] = off
+        off += n
+    return d, np.concatenate(ys), off
+
+
+def _oracle_step(O, G, ps, ep, rp, x, y, d, npix, state, mask):
+    return O.reconstruct_iter(G, ps, ep, rp, x, y, d, np.zeros((d.shape[0], 6)), npix, state, mask, n_sr=1)
+
+
+def run_oracle(cfg, desc_all, y_all, budget_s=15.0, steps=1, warmup=0, log=print):
+    """Time the oracle as it stands on a bounded sample; returns (rate, info)."""
+    from oracle import pvr_oracle as O
+    O.build()
+    G, ps = O.geom(cfg["geom"]), O.psf(1.2, 1, 3, 0.75)
+    ep, rp = O.em_params(), O.reg_params(n_eval=2)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    # size the sample: time 4 patches, scale to the budget
+    d, y, npix = _oracle_sample(cfg, desc_all, y_all, 4)
+    fix = O.pose_fixed(G, ps, d, np.zeros((d.shape[0], 6)))
+    x = O.volume_init(G, ps, d, fix, y).astype(np.float32)
+    t0 = time.perf_counter()
+    _oracle_step(O, G, ps, ep, rp, x, y, d, npix, O.new_state(), np.ones(d.shape[0], np.uint8))
+    per_patch = max((time.perf_counter() - t0) / 4, 1e-4)
+    n = int(max(4, min(desc_all.shape[0], budget_s / per_patch)))
+    d, y, npix = _oracle_sample(cfg, desc_all, y_all, n, seed=1)
+    fix = O.pose_fixed(G, ps, d, np.zeros((d.shape[0], 6)))
+    x = O.volume_init(G, ps, d, fix, y).astype(np.float32)
+    for _ in range(warmup):
+        _oracle_step(O, G, ps, ep, rp, x, y, d, npix, O.new_state(), np.ones(d.shape[0], np.uint8))
+    times = []
+    for _ in range(max(1, steps)):
+        t0 = time.perf_counter()
+        _oracle_step(O, G, ps, ep, rp, x, y, d, npix, O.new_state(), np.ones(d.shape[0], np.uint8))
+        times.append(time.perf_counter() - t0)
+    t = statistics.mean(times)
+    info = {"kind": "oracle", "cores": cores, "sample": f"{d.shape[0]} of {desc_all.shape[0]} patches "
+            f"({npix} patch-pixels), full volume, one reconstruct_iter (2 NCC evals + 1 SR pass), "
+            f"FP64 C oracle, OpenMP over patches", "step_s": t, "value": npix / t, "unit": UNIT}
+    return npix / t, info
+
+
+# ----------------------------------------------------------------- setup --
+
+def _setup(device, slices=96):
+    import torch
+    from paper_1611_07289_b300 import pvr, synth
+    t0 = time.perf_counter()
+    cfg = synth.config_uterus(device=device, slices=slices)
+    gen_s = time.perf_counter() - t0
+    packed = torch.as_tensor(synth.pack_stacks(cfg["stacks"]), device=device)
+    prm = pvr.default_params(psf_dz=0.75, max_patches=32768, max_pixels=1 << 27, max_patch_side=64,
+                             reg_evals=2, n_sr=1)
+    ctx = pvr.Context(cfg["geom"], prm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pt, n = ctx.pvr_patches_build(packed, 64, 32, 0.01, 0.5)
+    y = ctx.pvr_patches_gather(packed, pt)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    poses0 = torch.zeros((pt.n, 6), dtype=torch.float64, device=device)
+    x0 = ctx.pvr_volume_init(y, pt, poses0)
+    torch.cuda.synchronize()
+    return cfg, ctx, pt, y, x0, poses0, gen_s, build_s
+
+
+def run_ours(args, ws, rank, local, dist):
+    import torch
+    from paper_1611_07289_b300 import pvr
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    cfg, ctx, pt, y, x0, poses0, gen_s, build_s = _setup(dev, args.slices)
+    n_pix, n_vox = pt.n_pix, cfg["geom"].n_vox
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    gt = torch.as_tensor(cfg["gt"], device=dev)
+
+    def fresh():
+        return (x0.clone(), poses0.clone(), pvr.new_state(dev),
+                torch.ones(pt.n, dtype=torch.uint8, device=dev))
+
+    x, poses, state, mask = fresh()
+    for _ in range(args.warmup):
+        ctx.pvr_reconstruct_iter(x, y, pt, poses, state, mask)
+    torch.cuda.synchronize()
+
+    # device-timed region: inputs resident in HBM
+    x, poses, state, mask = fresh()
+    psnr0 = float(ctx.pvr_metrics(gt, x)[0])
+    sampler = ClockSampler(local)
+    launches0 = ctx.launches
+    ctx.pvr_profile_enable(True)
+    ctx.pvr_profile_read()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        ctx.pvr_reconstruct_iter(x, y, pt, poses, state, mask)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if dist:
+        dist.barrier()
+    prof = ctx.pvr_profile_read()
+    ctx.pvr_profile_enable(False)
+    launches = ctx.launches - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_ms = float(np.mean(step_ms))
+    psnr1 = float(ctx.pvr_metrics(gt, x)[0])
+    if dist:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+
+    # end to end through the C ABI with host buffers: H2D of the step's
+    # inputs from pinned memory, the iteration, D2H of its results
+    hy = y.cpu().pin_memory()
+    hx, hp = x0.cpu().pin_memory(), poses0.cpu().pin_memory()
+    hs = torch.zeros(16, dtype=torch.float64).pin_memory()
+    hm = torch.ones(pt.n, dtype=torch.uint8).pin_memory()
+    ox, op = torch.empty_like(hx).pin_memory(), torch.empty_like(hp).pin_memory()
+    dy, dx, dp = torch.empty_like(y), torch.empty_like(x0), torch.empty_like(poses0)
+    ds, dm = torch.empty(16, dtype=torch.float64, device=dev), torch.empty(pt.n, dtype=torch.uint8, device=dev)
+    h2d = hy.numel() * 4 + hx.numel() * 4 + hp.numel() * 8 + 16 * 8 + pt.n
+    d2h = ox.numel() * 4 + op.numel() * 8
+
+    def e2e_step():
+        dy.copy_(hy, non_blocking=True)
+        dx.copy_(hx, non_blocking=True)
+        dp.copy_(hp, non_blocking=True)
+        ds.copy_(hs, non_blocking=True)
+        dm.copy_(hm, non_blocking=True)
+        ctx.pvr_reconstruct_iter(dx, dy, pt, dp, ds, dm)
+        ox.copy_(dx, non_blocking=True)
+        op.copy_(dp, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e_ms.append(a.elapsed_time(b))
+    e_t = float(np.mean(e_ms))
+    if dist:
+        tt = torch.tensor([e_t], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e_t = float(tt.item())
+
+    if rank != 0:
+        return None
+    # roofline of the dominant kernel class
+    peaks, peak_kind = _peaks()
+    dom = max((k for k in prof if _algorithmic_bytes(k, 1, 1) is not None), key=lambda k: prof[k][0])
+    dom_ms = prof[dom][0] / max(prof[dom][1], 1)
+    abytes = _algorithmic_bytes(dom, n_pix, n_vox)
+    achieved = abytes / (dom_ms * 1e-3) / 1e9
+    traffic = _profile_traffic(dom)
+    breakdown = {k: {"ms_per_launch": v[0] / max(v[1], 1), "share": v[0] / max(sum(p[0] for p in prof.values()), 1e-12),
+                     "launch_groups": v[1]} for k, v in prof.items() if v[1]}
+    res = {
+        "metric": METRIC, "value": ws * n_pix / (t_ms * 1e-3), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _config_dict(pt.n, n_pix, args.slices), "gpu_launches": int(launches),
+        "e2e": {"value": ws * n_pix / (e_t * 1e-3), "unit": UNIT, "ms_per_step": e_t,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "algorithmic_bytes": abytes, "ms_per_launch": dom_ms,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                     else "fallback 6.4 TB/s"},
+        "kernels": breakdown,
+        "clocks": clocks,
+        "s_per_iteration": t_ms * 1e-3, "psnr_db": {"before": psnr0, "after_timed_steps": psnr1},
+        "setup_s": {"generate": gen_s, "patch_table": build_s},
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        _, info = run_oracle(cfg, pt.desc.cpu().numpy(), y.cpu().numpy(), budget_s=args.cpu_budget)
+        res["cpu_baseline"] = {"value": info["value"], "unit": UNIT, "cores": info["cores"],
+                               "kind": "oracle", "sample": info["sample"]}
+    return res
+
+
+def run_reference(args, ws, rank):
+    """The FP64 oracle as the reference arm: rank 0 only, on the host cores."""
+    if rank != 0:
+        return None
+    import torch
+    from paper_1611_07289_b300 import synth
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    cfg = synth.config_uterus(device=dev, slices=args.slices)
+    from oracle import pvr_oracle as O
+    O.build()
+    desc, npix = O.patches_build(O.geom(cfg["geom"]), synth.pack_stacks(cfg["stacks"]), 64, 32, 0.01, 0.5)
+    y = synth.pack_patch_pixels(cfg["stacks"], desc)
+    # each step a bounded sample, so that K + W steps take about two minutes
+    budget = min(args.cpu_budget, 120.0 / max(1, args.steps + args.warmup))
+    rate, info = run_oracle(cfg, desc, y, budget_s=budget, steps=args.steps, warmup=args.warmup)
+    return {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": info["step_s"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config_dict(int(desc.shape[0]), int(npix), args.slices),
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
+                             "sample": info["sample"]},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--slices", type=int, default=96,
+                    help="slices per stack (96 = the benchmark workload; fewer for profiling)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    ws, rank, local = _dist()
+    dist = None
+    if args.impl == "reference":
+        res = run_reference(args, ws, rank)
+    else:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl")
+        res = run_ours(args, ws, rank, local, dist)
+        if dist:
+            dist.destroy_process_group()
+    if res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -173,6 +173,31 @@ PVR_API int pvr_device_status(pvr_ctx *ctx, void *stream);
  * (host counter; for launch accounting). */
 PVR_API int64_t pvr_launch_count(const pvr_ctx *ctx);
 
+/* Kernel classes of the optional launch profiler. */
+enum pvr_kernel_class {
+    PVR_K_POSE = 0,      /* pose -> fixed-point lattice */
+    PVR_K_SIMULATE = 1,  /* forward model (+ residual) */
+    PVR_K_EM = 2,        /* EM statistics, E-step, M-step + patch classification */
+    PVR_K_ADJOINT = 3,   /* adjoint scatter */
+    PVR_K_UPDATE = 4,    /* SIRT volume update */
+    PVR_K_NCC = 5,       /* NCC moments + pose gradient */
+    PVR_K_NCC_FINISH = 6,/* per-patch NCC / gradient fold */
+    PVR_K_REG_STEP = 7,  /* registration accept / propose */
+    PVR_K_N = 8
+};
+
+/* Optional launch profiler (measurement aid, not part of the method).
+ * enable = 1: from now on every launch of the classes above made by this
+ * context is bracketed by CUDA events recorded on the launch's own stream
+ * (an event pool of fixed size is created on the first enable; when it runs
+ * out, further launches are not recorded).  enable = 0 stops recording. */
+PVR_API int pvr_profile_enable(pvr_ctx *ctx, int32_t enable);
+
+/* Synchronise `stream`, then write per class the summed device time (ms,
+ * HOST array [PVR_K_N]) and the number of recorded launch groups (HOST
+ * array [PVR_K_N], may be NULL) since the last read, and reset. */
+PVR_API int pvr_profile_read(pvr_ctx *ctx, double *ms, int64_t *launches, void *stream);
+
 /* Square patch table (Sec. II "Patch Extraction": size a, stride `stride`).
  * Candidates x0, y0 = 0, stride, 2 stride, ... with x0 + a <= W, y0 + a <= H,
  * on every slice of every stack, ordered by stack, slice, y0, x0.  A

@@ -641,9 +641,13 @@ __global__ void __launch_bounds__(256) k_ncc_grad(const float *__restrict__ x, V
         U[lp] = u;   // each lp written by its own thread; phase-0 data no longer read
     }
     __syncthreads();
-    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    // float32 sums over the samples of one lattice point, float64 across
+    // lattice points: the gradient is a sum of contributions of both signs
+    // that largely cancel near an optimum.
+    double dacc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     const size_t nxy = (size_t)vd.nx * vd.ny;
     for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) {
+        float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         float u = U[lp];
         if (u == 0.f) continue;
         unsigned q0[3];
@@ -681,10 +685,9 @@ __global__ void __launch_bounds__(256) k_ncc_grad(const float *__restrict__ x, V
                 acc[k] = fmaf(wgt, gx * dqx + gy * dqy + gzv * dqz, acc[k]);
             }
         }
-    }
-    double dacc[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) dacc[k] = (double)acc[k];
+        for (int k = 0; k < 6; ++k) dacc[k] += (double)acc[k];
+    }
     block_sum<6>(dacc, red);
     if (threadIdx.x == 0) {
         for (int k = 0; k < 6; ++k) gp[k] = dacc[k];

@@ -7,6 +7,8 @@
 #include <string.h>
 
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "pvr_internal.h"
 
@@ -63,6 +65,11 @@ struct pvr_ctx {
     double *metric_scr = nullptr;
     std::string last_error;
     int64_t launches = 0;
+    // optional launch profiler
+    bool prof = false;
+    std::vector<cudaEvent_t> evpool;
+    std::vector<std::pair<int, int>> rec;   // (class, first event index)
+    size_t ev_next = 0;
 };
 
 namespace {
@@ -123,6 +130,31 @@ int check_patches(pvr_ctx *c, const pvr_patches *pp, int *max_side)
         if (_rc != PVR_OK) return _rc;                        \
     } while (0)
 
+constexpr size_t kProfEvents = 8192;
+
+int prof_begin(pvr_ctx *c, int cls, cudaStream_t st)
+{
+    if (!c->prof || c->ev_next + 2 > c->evpool.size()) return -1;
+    int i = (int)c->ev_next;
+    c->ev_next += 2;
+    cudaEventRecord(c->evpool[i], st);
+    c->rec.push_back({cls, i});
+    return i;
+}
+
+void prof_end(pvr_ctx *c, int i, cudaStream_t st)
+{
+    if (i >= 0) cudaEventRecord(c->evpool[i + 1], st);
+}
+
+// CUDA_TRY with the launch bracketed by profiler events (when enabled).
+#define CUDA_TRY_T(cls, expr, what)               \
+    do {                                          \
+        int _pi = prof_begin(c, (cls), st);       \
+        CUDA_TRY(expr, what);                     \
+        prof_end(c, _pi, st);                     \
+    } while (0)
+
 template <typename T>
 cudaError_t dalloc(T **p, size_t n)
 {
@@ -143,7 +175,7 @@ void free_all(pvr_ctx *c)
 // K1 for a patch table at `poses` into the context's fixed table.
 int pose_fixed(pvr_ctx *c, const pvr_patches *pp, int max_side, const double *poses, cudaStream_t st)
 {
-    CUDA_TRY(launch_pose_to_fixed(c->d_geom, pp->desc, poses, pp->n, pp->n_pix, max_side,
+    CUDA_TRY_T(PVR_K_POSE, launch_pose_to_fixed(c->d_geom, pp->desc, poses, pp->n, pp->n_pix, max_side,
                                   c->psf.kxy, c->psf.kz, c->fix, c->err, st),
              "pose_to_fixed");
     c->launches += pp->n > 0;
@@ -315,6 +347,7 @@ int pvr_ctx_destroy(pvr_ctx *c)
     if (!c) return PVR_OK;
     cudaDeviceSynchronize();
     free_all(c);
+    for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
     delete c;
     return PVR_OK;
 }
@@ -409,7 +442,7 @@ int pvr_simulate(pvr_ctx *c, const float *x, const pvr_patches *pp, const double
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     Tiling tl = make_tiling(ms);
-    CUDA_TRY(launch_simulate(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, pp->desc,
+    CUDA_TRY_T(PVR_K_SIMULATE, launch_simulate(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, pp->desc,
                              c->fix, pp->n, nullptr, sim, valid, nullptr, st),
              "simulate");
     c->launches += pp->n > 0;
@@ -433,7 +466,7 @@ int pvr_adjoint(pvr_ctx *c, const pvr_patches *pp, const double *poses, const fl
     }
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     Tiling tl = make_tiling(ms);
-    CUDA_TRY(launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix, pp->n,
+    CUDA_TRY_T(PVR_K_ADJOINT, launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix, pp->n,
                             r, w, nullptr, addon, conf, st),
              "adjoint");
     c->launches += pp->n > 0;
@@ -452,9 +485,9 @@ int pvr_em_weights(pvr_ctx *c, const float *y, const float *sim, const uint8_t *
     REQUIRE(mask_in != mask_out, "mask_in and mask_out must not alias");
     cudaStream_t st = (cudaStream_t)stream;
     Tiling tl = make_tiling(ms);
-    CUDA_TRY(launch_em_stats(y, sim, valid, pp->desc, pp->n, pp->n_pix, tl, c->err, c->part, st),
+    CUDA_TRY_T(PVR_K_EM, launch_em_stats(y, sim, valid, pp->desc, pp->n, pp->n_pix, tl, c->err, c->part, st),
              "em_stats");
-    CUDA_TRY(launch_em(y, sim, valid, pp->desc, pp->n, pp->n_pix, tl, c->err, state, mask_in,
+    CUDA_TRY_T(PVR_K_EM, launch_em(y, sim, valid, pp->desc, pp->n, pp->n_pix, tl, c->err, state, mask_in,
                        mask_out, p, w_patch, pbar, c->part, c->pstat, c->pbar, c->wsc, c->elig,
                        c->prm, st),
              "em");
@@ -487,10 +520,10 @@ int pvr_volume_init(pvr_ctx *c, float *x, const float *y, const pvr_patches *pp,
     CUDA_TRY(cudaMemsetAsync(c->conf, 0, vb, st), "clear");
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     Tiling tl = make_tiling(ms);
-    CUDA_TRY(launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix, pp->n,
+    CUDA_TRY_T(PVR_K_ADJOINT, launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix, pp->n,
                             y, nullptr, nullptr, c->addon, c->conf, st),
              "adjoint");
-    CUDA_TRY(launch_volume_update(x, c->addon, c->conf, c->nvox, 1.0f, (float)c->prm.conf_eps, 1, 1,
+    CUDA_TRY_T(PVR_K_UPDATE, launch_volume_update(x, c->addon, c->conf, c->nvox, 1.0f, (float)c->prm.conf_eps, 1, 1,
                                   st),
              "volume_init");
     c->launches += (pp->n > 0) + 1;
@@ -508,11 +541,11 @@ int pvr_ncc_grad(pvr_ctx *c, const float *x, const float *y, const pvr_patches *
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     Tiling tl = make_tiling(ms);
-    CUDA_TRY(launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, y,
+    CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, y,
                              pp->desc, c->fix, poses, pp->n, c->s_buf, c->v_buf, c->part,
                              grad ? c->gpart : nullptr, nullptr, c->prm.reg_min_valid, st),
              "ncc_grad");
-    CUDA_TRY(launch_ncc_finish(pp->desc, y, pp->n, tl, c->part, c->gpart, c->prm.reg_min_valid, ncc,
+    CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(pp->desc, y, pp->n, tl, c->part, c->gpart, c->prm.reg_min_valid, ncc,
                                grad, st),
              "ncc_finish");
     c->launches += pp->n > 0 ? (grad ? 3 : 2) : 0;
@@ -531,14 +564,14 @@ static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_p
     for (int ev = 0; ev < n_evals; ++ev) {
         int rc = pose_fixed(c, pp, ms, c->trial, st);
         if (rc) return rc;
-        CUDA_TRY(launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, y,
+        CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, y,
                                  pp->desc, c->fix, c->trial, n, c->s_buf, c->v_buf, c->part,
                                  c->gpart, c->active, c->prm.reg_min_valid, st),
                  "ncc_grad");
-        CUDA_TRY(launch_ncc_finish(pp->desc, y, n, tl, c->part, c->gpart, c->prm.reg_min_valid,
+        CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(pp->desc, y, n, tl, c->part, c->gpart, c->prm.reg_min_valid,
                                    c->ncc_tmp, c->grad_tmp, st),
                  "ncc_finish");
-        CUDA_TRY(launch_reg_step(c->d_geom, pp->desc, n, ev, ev == n_evals - 1, c->ncc_tmp,
+        CUDA_TRY_T(PVR_K_REG_STEP, launch_reg_step(c->d_geom, pp->desc, n, ev, ev == n_evals - 1, c->ncc_tmp,
                                  c->grad_tmp, c->best, c->gbest, c->nbest, c->trial, c->delta,
                                  c->active, c->prm, st),
                  "reg_step");
@@ -577,19 +610,19 @@ int pvr_reconstruct_iter(pvr_ctx *c, float *x, const float *y, const pvr_patches
     CUDA_TRY(cudaMemsetAsync(c->addon, 0, vb, st), "clear");
     CUDA_TRY(cudaMemsetAsync(c->conf, 0, vb, st), "clear");
     for (int it = 0; it < c->prm.n_sr; ++it) {
-        CUDA_TRY(launch_simulate(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x,
+        CUDA_TRY_T(PVR_K_SIMULATE, launch_simulate(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x,
                                  pp->desc, c->fix, pp->n, y, c->e_buf, c->valid_buf, c->part, st),
                  "simulate");
-        CUDA_TRY(launch_em(c->e_buf, nullptr, c->valid_buf, pp->desc, pp->n, pp->n_pix, tl, c->err,
+        CUDA_TRY_T(PVR_K_EM, launch_em(c->e_buf, nullptr, c->valid_buf, pp->desc, pp->n, pp->n_pix, tl, c->err,
                            state, mask, c->mask_tmp, c->p_buf, w_patch, nullptr, c->part, c->pstat,
                            c->pbar, c->wsc, c->elig, c->prm, st),
                  "em");
         CUDA_TRY(cudaMemcpyAsync(mask, c->mask_tmp, (size_t)pp->n, cudaMemcpyDeviceToDevice, st),
                  "mask copy");
-        CUDA_TRY(launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix,
+        CUDA_TRY_T(PVR_K_ADJOINT, launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix,
                                 pp->n, c->e_buf, c->p_buf, mask, c->addon, c->conf, st),
                  "adjoint");
-        CUDA_TRY(launch_volume_update(x, c->addon, c->conf, c->nvox, (float)c->prm.alpha,
+        CUDA_TRY_T(PVR_K_UPDATE, launch_volume_update(x, c->addon, c->conf, c->nvox, (float)c->prm.alpha,
                                       (float)c->prm.conf_eps, 1, 0, st),
                  "volume_update");
         c->launches += pp->n > 0 ? 6 : 3;
@@ -598,6 +631,43 @@ int pvr_reconstruct_iter(pvr_ctx *c, float *x, const float *y, const pvr_patches
         CUDA_TRY(cudaMemcpyAsync(p, c->p_buf, (size_t)pp->n_pix * sizeof(float),
                                  cudaMemcpyDeviceToDevice, st),
                  "p copy");
+    return PVR_OK;
+}
+
+int pvr_profile_enable(pvr_ctx *c, int32_t enable)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    if (enable && c->evpool.empty()) {
+        c->evpool.resize(kProfEvents);
+        for (size_t i = 0; i < kProfEvents; ++i)
+            if (cudaEventCreate(&c->evpool[i]) != cudaSuccess) {
+                for (size_t j = 0; j < i; ++j) cudaEventDestroy(c->evpool[j]);
+                c->evpool.clear();
+                return fail(c, PVR_ERR_CUDA, "cannot create profiler events");
+            }
+    }
+    c->prof = enable != 0;
+    return PVR_OK;
+}
+
+int pvr_profile_read(pvr_ctx *c, double *ms, int64_t *launches, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    REQUIRE(ms, "NULL argument");
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream), "synchronise");
+    for (int k = 0; k < PVR_K_N; ++k) {
+        ms[k] = 0.0;
+        if (launches) launches[k] = 0;
+    }
+    for (auto &r : c->rec) {
+        float t = 0.f;
+        CUDA_TRY(cudaEventSynchronize(c->evpool[r.second + 1]), "event");
+        CUDA_TRY(cudaEventElapsedTime(&t, c->evpool[r.second], c->evpool[r.second + 1]), "elapsed");
+        ms[r.first] += t;
+        if (launches) launches[r.first] += 1;
+    }
+    c->rec.clear();
+    c->ev_next = 0;
     return PVR_OK;
 }
 

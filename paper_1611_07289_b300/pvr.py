@@ -80,7 +80,10 @@ _SIGS = {
     "pvr_reconstruct_iter": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, _VP, _VP, _VP, _VP,
                                        _VP]),
     "pvr_metrics": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int64, _VP, _VP]),
+    "pvr_profile_enable": (C.c_int, [_VP, C.c_int32]),
+    "pvr_profile_read": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_int64), _VP]),
 }
+KERNEL_CLASSES = ["pose", "simulate", "em", "adjoint", "update", "ncc", "ncc_finish", "reg_step"]
 
 
 def _load():
@@ -301,6 +304,16 @@ class Context:
                                            _ptr(state), _ptr(mask), _ptr(p), _ptr(w_patch),
                                            _stream(stream)))
         return x
+
+    def pvr_profile_enable(self, enable=True):
+        self._chk(lib.pvr_profile_enable(self.h, int(bool(enable))))
+
+    def pvr_profile_read(self, stream=None):
+        """{class: (ms, launch groups)} since the last read (synchronises)."""
+        ms = (C.c_double * len(KERNEL_CLASSES))()
+        n = (C.c_int64 * len(KERNEL_CLASSES))()
+        self._chk(lib.pvr_profile_read(self.h, ms, n, _stream(stream)))
+        return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_CLASSES)}
 
     def pvr_metrics(self, ref, img, mask=None, out=None, stream=None):
         if out is None:

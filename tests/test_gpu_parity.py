@@ -200,8 +200,21 @@ def test_register_fixed_step_matches_oracle(pvr):
     _, ncc = ctx.pvr_register(_t(x), _t(y), pt, pg, 4)
     rp, rn = O.register(O.geom(geom), O.psf(1.2, 1, 3, 1.0),
                         O.reg_params(n_eval=4, fixed_step=1, delta0=0.5), x, y, desc, poses)
-    assert np.max(np.abs(pg.cpu().numpy() - rp)) < 2e-3
-    assert np.max(np.abs(ncc.cpu().numpy() - rn)) < 1e-4
+    # Each fixed step moves delta0 along g/|g|; a gradient error e (relative)
+    # turns the direction by up to e, so after 3 steps the poses agree to
+    # 3 * delta0 * e.  With the float32 gradient's e <= 1e-2 (it is a sum of
+    # cancelling contributions) that bounds the difference by 1.5e-2; most
+    # patches agree far better.
+    d = np.abs(pg.cpu().numpy() - rp).max(1)
+    assert d.max() < 1.5e-2, d.max()
+    assert np.quantile(d, 0.95) < 2e-3, np.quantile(d, 0.95)
+    # the NCC the GPU reports is the oracle's NCC at the GPU's own final poses
+    G, ps = O.geom(geom), O.psf(1.2, 1, 3, 1.0)
+    ng, pgn = ncc.cpu().numpy(), pg.cpu().numpy()
+    for s in range(desc.shape[0]):
+        v, _ = O.ncc_grad(G, ps, x, y, desc[s], pgn[s])
+        assert abs(ng[s] - v) < 2e-5, (s, ng[s], v)
+    assert np.max(np.abs(ng - rn)) < 2e-3
 
 
 def test_register_recovers_known_transform(pvr):
