@@ -404,9 +404,9 @@ __global__ void __launch_bounds__(256) k_adjoint(VolDims vd, const int32_t *__re
 
 // ----------------------------------------------------------------- K6a --
 // NCC moments: simulated pixel values (kept for K6b) and per-tile sums
-// {N, sum a, sum b, sum a^2, sum b^2, sum a b} with a = y - y_ref,
-// b = s - y_ref, y_ref = the patch's first acquired pixel (a shift that
-// keeps the float32 moments free of cancellation).
+// {N, sum y, sum s, sum y^2, sum s^2, sum y s} accumulated in float64 per
+// thread (the variances are differences of these sums, and a constant patch
+// must come out with a variance that the degeneracy test recognises).
 template <int KXY, int KZ>
 __global__ void __launch_bounds__(256) k_ncc_moments(const float *__restrict__ x, VolDims vd,
                                                      const int32_t *__restrict__ desc,
@@ -434,8 +434,7 @@ __global__ void __launch_bounds__(256) k_ncc_moments(const float *__restrict__ x
         for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) A[lp] = B[lp] = 0.f;
     }
     __syncthreads();
-    const float yref = __ldg(y + ti.off);
-    float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    double m[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     const int np = ti.tw * ti.th;
     for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
         int ci = pp % ti.tw, cj = pp / ti.tw;
@@ -447,18 +446,16 @@ __global__ void __launch_bounds__(256) k_ncc_moments(const float *__restrict__ x
         s_buf[o] = s;
         v_buf[o] = v ? 1 : 0;
         if (v) {
-            float a = __ldg(y + o) - yref, b = s - yref;
-            m[0] += 1.f;
+            double a = (double)__ldg(y + o), b = (double)s;
+            m[0] += 1.0;
             m[1] += a;
             m[2] += b;
-            m[3] = fmaf(a, a, m[3]);
-            m[4] = fmaf(b, b, m[4]);
-            m[5] = fmaf(a, b, m[5]);
+            m[3] = fma(a, a, m[3]);
+            m[4] = fma(b, b, m[4]);
+            m[5] = fma(a, b, m[5]);
         }
     }
-    double acc[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) acc[k] = (double)m[k];
+    double *acc = m;
     block_sum<6>(acc, red);
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -469,10 +466,8 @@ __global__ void __launch_bounds__(256) k_ncc_moments(const float *__restrict__ x
 
 // NCC of a patch from its tile moments (float64).  Returns false when
 // degenerate (fewer than min_valid pixels or a constant patch).
-// Means are returned relative to yref (the shift used by K6a).
-__device__ bool ncc_from_moments(const double *part, int p, int tpp, int min_valid, double yref,
-                                 double &ncc, double &my, double &ms, double &sd, double &vs,
-                                 double &n)
+__device__ bool ncc_from_moments(const double *part, int p, int tpp, int min_valid, double &ncc,
+                                 double &my, double &ms, double &sd, double &vs, double &n)
 {
     double m[6] = {0, 0, 0, 0, 0, 0};
     for (int t = 0; t < tpp; ++t)
@@ -485,8 +480,7 @@ __device__ bool ncc_from_moments(const double *part, int p, int tpp, int min_val
     double vy = m[3] / n - my * my;
     vs = m[4] / n - ms * ms;
     double cv = m[5] / n - my * ms;
-    double muy = my + yref, mus = ms + yref;
-    if (!(vy > 1e-12 * (muy * muy + 1.0)) || !(vs > 1e-12 * (mus * mus + 1.0))) return false;
+    if (!(vy > 1e-12 * (my * my + 1.0)) || !(vs > 1e-12 * (ms * ms + 1.0))) return false;
     sd = sqrt(vy * vs);
     ncc = cv / sd;
     return true;
@@ -528,12 +522,11 @@ __global__ void __launch_bounds__(256) k_ncc_grad(const float *__restrict__ x, V
     }
     if (threadIdx.x == 0) {
         double ncc, my, ms, sd, vs, n;
-        const float yref = y[ti.off];
-        bool ok = ncc_from_moments(part, ti.p, tl.tpp, min_valid, (double)yref, ncc, my, ms, sd, vs, n);
+        bool ok = ncc_from_moments(part, ti.p, tl.tpp, min_valid, ncc, my, ms, sd, vs, n);
         sh_ok = ok;
         sh_stats[0] = ncc;
-        sh_stats[1] = my + yref;   // back from the shifted means
-        sh_stats[2] = ms + yref;
+        sh_stats[1] = my;
+        sh_stats[2] = ms;
         sh_stats[3] = 0.0;
         if (ok) {
             const int32_t *d = desc + 8 * (size_t)ti.p;
@@ -703,8 +696,7 @@ __global__ void k_ncc_finish(int n, int tpp, const int32_t *__restrict__ desc,
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     double v, my, ms, sd, vs, nn;
-    double yref = (double)y[desc[8 * (size_t)p + 6]];
-    bool ok = ncc_from_moments(part, p, tpp, min_valid, yref, v, my, ms, sd, vs, nn);
+    bool ok = ncc_from_moments(part, p, tpp, min_valid, v, my, ms, sd, vs, nn);
     ncc[p] = ok ? v : 0.0;
     if (grad) {
         for (int k = 0; k < 6; ++k) {
