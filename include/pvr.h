@@ -238,6 +238,26 @@ PVR_API int pvr_pose_to_fixed(pvr_ctx *ctx, const pvr_patches *patches, const do
 PVR_API int pvr_simulate(pvr_ctx *ctx, const float *x, const pvr_patches *patches, const double *poses,
                  float *sim, uint8_t *valid, void *stream);
 
+/* pvr_simulate without a context and without any device allocation.  (The
+ * paper has no counterpart: this is a deployment variant.)  For callers
+ * that cannot call cudaMalloc -- e.g. a host application whose own pool
+ * allocator owns the device memory and forbids other allocations, or a
+ * latency-bound loop that must not allocate (allocation can synchronise the
+ * device) once it is running.  Same inputs and outputs as pvr_simulate, with
+ * the geometry and parameters passed per call; the scratch it needs (device
+ * copy of the geometry, per-patch fixed-point table, error word) lives in a
+ * fixed device array inside the library that every GPU loading the library
+ * keeps until the process exits.  Limits: patches->n <= 8192 (more:
+ * PVR_ERR_INVALID_ARG, nothing enqueued); n_pix < 2^31; max_side <= 256.
+ * The first call on a device looks the array up with that device current;
+ * make that first call before any stream capture begins.  All calls share
+ * the one array: calls that overlap on the GPU race, so serialise them.
+ * Malformed patch rows are skipped (their pixels are not written); there is
+ * no context, so no error message and no pvr_device_status for this call. */
+PVR_API int pvr_simulate_noalloc(const pvr_geometry *geom, const pvr_params *params, const float *x,
+                                 const pvr_patches *patches, const double *poses, float *sim,
+                                 uint8_t *valid, void *stream);
+
 /* Adjoint of pvr_simulate (the super-resolution update's back-projection):
  * addon = A^T (w .* r), conf = A^T w, A the matrix of pvr_simulate at these
  * poses.  r, w: float32 [n_pix] or NULL (= all ones).  addon, conf: float32

@@ -80,6 +80,8 @@ _SIGS = {
     "pvr_reconstruct_iter": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, _VP, _VP, _VP, _VP,
                                        _VP]),
     "pvr_metrics": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int64, _VP, _VP]),
+    "pvr_simulate_noalloc": (C.c_int, [C.POINTER(Geometry), C.POINTER(Params), _VP,
+                                       C.POINTER(Patches), _VP, _VP, _VP, _VP]),
     "pvr_profile_enable": (C.c_int, [_VP, C.c_int32]),
     "pvr_profile_read": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_int64), _VP]),
 }
@@ -321,6 +323,15 @@ class Context:
         self._chk(lib.pvr_metrics(self.h, _ptr(ref), _ptr(img), _ptr(mask), int(ref.numel()), _ptr(out),
                                   _stream(stream)))
         return out
+
+
+def pvr_simulate_noalloc(geom, params: Params, x, pt: PatchTable, poses, sim, valid, stream=None):
+    """Context-free pvr_simulate that allocates nothing (see include/pvr.h):
+    for callers that cannot allocate device memory.  sim and valid must be
+    caller-provided tensors; returns the pvr_status code."""
+    g = geometry(geom) if not isinstance(geom, Geometry) else geom
+    return int(lib.pvr_simulate_noalloc(C.byref(g), C.byref(params), _ptr(x), C.byref(pt.c),
+                                        _ptr(poses), _ptr(sim), _ptr(valid), _stream(stream)))
 
 
 def new_state(device="cuda"):
