@@ -79,30 +79,36 @@ class ClockSampler:
 
     def start(self):
         try:
+            import ctypes
             import threading
-
-            import pynvml
-            pynvml.nvmlInit()
-            h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
-            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM)
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit failed")
+            h = ctypes.c_void_p()
+            if nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(h)) != 0:
+                raise OSError("no NVML handle")
+            mx = ctypes.c_uint()
+            nv.nvmlDeviceGetMaxClockInfo(h, ctypes.c_int(1), ctypes.byref(mx))   # 1 = SM clock
+            self.max_mhz = mx.value
+            reasons_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
             self.stop_flag = threading.Event()
-            get_reasons = getattr(pynvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
-                pynvml.nvmlDeviceGetCurrentClocksThrottleReasons
 
             def run():
+                mhz, rs = ctypes.c_uint(), ctypes.c_ulonglong()
                 while not self.stop_flag.is_set():
-                    try:
-                        mhz = pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)
-                        rs = get_reasons(h)
-                    except Exception:
+                    if nv.nvmlDeviceGetClockInfo(h, ctypes.c_int(1), ctypes.byref(mhz)) != 0:
                         break
-                    self.samples.append((mhz, rs))
+                    if reasons_fn(h, ctypes.byref(rs)) != 0:
+                        break
+                    self.samples.append((mhz.value, rs.value))
                     self.stop_flag.wait(0.02)
 
             self.thread = threading.Thread(target=run, daemon=True)
             self.thread.start()
             return
-        except Exception:
+        except Exception as exc:  # no NVML: fall back to nvidia-smi sampling
+            print(f"clock sampler: NVML unavailable ({exc!r}); using nvidia-smi", file=sys.stderr)
             self.thread = None
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)

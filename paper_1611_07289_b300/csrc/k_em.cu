@@ -216,47 +216,43 @@ __global__ void __launch_bounds__(256) k_em_estep(const float *__restrict__ y,
         for (int k = 0; k < 4; ++k) pt[4 + k] = a[k];
 }
 
-// Steps 5-7: M-step, patch potentials, patch classification (one CTA).
-// scratch: pbar (float64 [n]), w (float64 [n]), elig (uint8 [n]).
-__global__ void __launch_bounds__(kRedThreads) k_em_mstep(
-    const int32_t *__restrict__ desc, int n, int tpp, const uint8_t *__restrict__ mask_in,
-    const double *__restrict__ part, double *__restrict__ state, const double *__restrict__ pstat,
-    double c0, double min_valid_frac, int rule, double threshold, int iters,
-    double *__restrict__ pbar, double *__restrict__ wsc, uint8_t *__restrict__ elig,
-    uint8_t *__restrict__ mask_out, float *__restrict__ w_patch, float *__restrict__ pbar_out)
+// Steps 5-7: M-step, patch potentials and patch classification, spread over
+// the grid (one thread per patch) with single-block folds of the per-block
+// partial sums in between -- the patch-level model evaluates a float64
+// exponential per patch and EM iteration.
+// pstat: [5] patch outlier density m_p, [6] stop flag of the patch EM loop,
+// [7] number of eligible patches.  bpart: kEmBlockMax x 8 float64.
+constexpr int kEmBlockMax = 512;
+
+__device__ __forceinline__ void store_block(double *bpart, const double *v, int nv)
 {
-    __shared__ double sh[32 * 4];
-    __shared__ double bc[4];
-    // 5: M-step
-    double a[2] = {0.0, 0.0};
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        if (mask_in && !mask_in[p]) continue;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < nv; ++k) bpart[(size_t)blockIdx.x * 8 + k] = v[k];
+}
+
+// 5 + 6: M-step sums of the participating patches, potentials, eligibility.
+// bpart = {sum p, sum p e^2, sum pbar, sum pbar^2, n_elig, min pbar, max pbar}
+__global__ void __launch_bounds__(256) k_em_patch_pot(const int32_t *__restrict__ desc, int n, int tpp,
+                                                      const uint8_t *__restrict__ mask_in,
+                                                      const double *__restrict__ part,
+                                                      double min_valid_frac, double *__restrict__ pbar,
+                                                      uint8_t *__restrict__ elig,
+                                                      double *__restrict__ bpart)
+{
+    __shared__ double sh[32 * 5];
+    double a[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, mn[1] = {INFINITY}, mx[1] = {-INFINITY};
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        double sp = 0.0, spe2 = 0.0, sp2 = 0.0, nv = 0.0;
         for (int t = 0; t < tpp; ++t) {
             const double *pt = part + ((size_t)p * tpp + t) * kPartStride;
-            a[0] += pt[4];
-            a[1] += pt[5];
-        }
-    }
-    block_reduce<2>(a, sh, 0);
-    const bool first = pstat[1] != 0.0;
-    if (threadIdx.x == 0) {
-        double sfloor = pstat[0], npart = state[PVR_ST_N_PART];
-        if (a[0] > 0.0) {
-            double s2 = a[1] / a[0];
-            state[PVR_ST_SIGMA2] = s2 < sfloor ? sfloor : s2;
-        }
-        if (npart > 0.0) state[PVR_ST_C] = clampd(a[0] / npart, 1e-3, 1.0 - 1e-3);
-        state[PVR_ST_SUM_P] = a[0];
-        state[PVR_ST_SUM_PE2] = a[1];
-    }
-    // 6: patch potentials
-    double mm[1] = {INFINITY}, mxx[1] = {-INFINITY}, s[2] = {0.0, 0.0};
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        double sp2 = 0.0, nv = 0.0;
-        for (int t = 0; t < tpp; ++t) {
-            const double *pt = part + ((size_t)p * tpp + t) * kPartStride;
+            sp += pt[4];
+            spe2 += pt[5];
             sp2 += pt[6];
             nv += pt[7];
+        }
+        if (!mask_in || mask_in[p]) {
+            a[0] += sp;
+            a[1] += spe2;
         }
         const int32_t *d = desc + 8 * (size_t)p;
         double npx = (double)d[4] * (double)d[5];
@@ -265,97 +261,156 @@ __global__ void __launch_bounds__(kRedThreads) k_em_mstep(
         pbar[p] = pb;
         elig[p] = el ? 1 : 0;
         if (el) {
-            mm[0] = fmin(mm[0], pb);
-            mxx[0] = fmax(mxx[0], pb);
-            s[0] += pb;
-            s[1] += 1.0;
+            a[2] += pb;
+            a[3] += pb * pb;
+            a[4] += 1.0;
+            mn[0] = fmin(mn[0], pb);
+            mx[0] = fmax(mx[0], pb);
         }
     }
-    block_reduce<1>(mm, sh, 1);
-    block_reduce<1>(mxx, sh, 2);
-    block_reduce<2>(s, sh, 0);
-    const double nelig = s[1];
-    // 7: classification
-    if (rule == 1) {
-        for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            wsc[p] = elig[p] ? pbar[p] : 0.0;
-            mask_out[p] = (elig[p] && pbar[p] >= threshold) ? 1 : 0;
-        }
-    } else {
-        const double mp = (nelig > 0.0 && mxx[0] - mm[0] >= 1e-12) ? 1.0 / (mxx[0] - mm[0]) : 0.0;
-        if (first) {
-            double mu = nelig > 0.0 ? s[0] / nelig : 0.0;
-            double v[1] = {0.0};
-            for (int p = threadIdx.x; p < n; p += blockDim.x)
-                if (elig[p]) v[0] += (pbar[p] - mu) * (pbar[p] - mu);
-            block_reduce<1>(v, sh, 0);
-            if (threadIdx.x == 0) {
-                double var = nelig > 0.0 ? v[0] / nelig : 0.0;
-                state[PVR_ST_MU_P] = mu;
-                state[PVR_ST_SIGMA2_P] = var < 1e-4 ? 1e-4 : var;
-                state[PVR_ST_C_P] = clampd(c0, 1e-3, 1.0 - 1e-3);
-            }
-            __syncthreads();
-        }
-        for (int it = 0; it <= iters; ++it) {
-            if (threadIdx.x == 0) {
-                bc[0] = state[PVR_ST_MU_P];
-                bc[1] = state[PVR_ST_SIGMA2_P];
-                bc[2] = state[PVR_ST_C_P];
-            }
-            __syncthreads();
-            const double mu = bc[0], v2 = bc[1], cp = bc[2];
-            const double gnorm = 1.0 / (sqrt(2.0 * 3.14159265358979323846) * sqrt(v2));
-            double acc[2] = {0.0, 0.0};
-            for (int p = threadIdx.x; p < n; p += blockDim.x) {
-                double wv;
-                if (!elig[p]) wv = 0.0;
-                else if (mp == 0.0) wv = 1.0;
-                else {
-                    double dl = pbar[p] >= mu ? 0.0 : pbar[p] - mu;
-                    double G = exp(-(dl * dl) / (2.0 * v2)) * gnorm;
-                    wv = (G * cp) / (G * cp + mp * (1.0 - cp));
-                }
-                wsc[p] = wv;
-                if (elig[p]) {
-                    acc[0] += wv;
-                    acc[1] += wv * pbar[p];
-                }
-            }
-            if (it == iters || mp == 0.0) break;
-            block_reduce<2>(acc, sh, 0);
-            if (!(acc[0] > 0.0)) break;
-            const double mu_n = acc[1] / acc[0];
-            double v[1] = {0.0};
-            for (int p = threadIdx.x; p < n; p += blockDim.x)
-                if (elig[p]) v[0] += wsc[p] * ((pbar[p] - mu_n) * (pbar[p] - mu_n));
-            block_reduce<1>(v, sh, 0);
-            if (threadIdx.x == 0) {
-                double v2n = v[0] / acc[0];
-                state[PVR_ST_MU_P] = mu_n;
-                state[PVR_ST_SIGMA2_P] = v2n < 1e-4 ? 1e-4 : v2n;
-                state[PVR_ST_C_P] = clampd(acc[0] / nelig, 1e-3, 1.0 - 1e-3);
-            }
-            __syncthreads();
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) state[PVR_ST_M_P] = mp;
-        for (int p = threadIdx.x; p < n; p += blockDim.x)
-            mask_out[p] = (elig[p] && wsc[p] >= 0.5) ? 1 : 0;
+    block_reduce<5>(a, sh, 0);
+    block_reduce<1>(mn, sh, 1);
+    block_reduce<1>(mx, sh, 2);
+    double v[7] = {a[0], a[1], a[2], a[3], a[4], mn[0], mx[0]};
+    store_block(bpart, v, 7);
+}
+
+// Fold of k_em_patch_pot: pixel-level M-step, patch outlier density, first-
+// call initialisation of the patch-level model.
+__global__ void k_em_patch_head(int nb, const double *__restrict__ bpart, double *__restrict__ state,
+                                double *__restrict__ pstat, double c0, int rule)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double sp = 0, spe2 = 0, ps = 0, ps2 = 0, ne = 0, mn = INFINITY, mx = -INFINITY;
+    for (int b = 0; b < nb; ++b) {
+        const double *v = bpart + 8 * (size_t)b;
+        sp += v[0];
+        spe2 += v[1];
+        ps += v[2];
+        ps2 += v[3];
+        ne += v[4];
+        mn = fmin(mn, v[5]);
+        mx = fmax(mx, v[6]);
     }
-    __syncthreads();
-    double nin[1] = {0.0};
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        nin[0] += mask_out[p];
-        if (w_patch) w_patch[p] = (float)wsc[p];
+    double sfloor = pstat[0], npart = state[PVR_ST_N_PART];
+    if (sp > 0.0) {
+        double s2 = spe2 / sp;
+        state[PVR_ST_SIGMA2] = s2 < sfloor ? sfloor : s2;
+    }
+    if (npart > 0.0) state[PVR_ST_C] = clampd(sp / npart, 1e-3, 1.0 - 1e-3);
+    state[PVR_ST_SUM_P] = sp;
+    state[PVR_ST_SUM_PE2] = spe2;
+    double mp = (ne > 0.0 && mx - mn >= 1e-12) ? 1.0 / (mx - mn) : 0.0;
+    pstat[5] = mp;
+    pstat[6] = rule == 1 ? 1.0 : 0.0;
+    pstat[7] = ne;
+    if (rule == 0 && pstat[1] != 0.0) {
+        double mu = ne > 0.0 ? ps / ne : 0.0;
+        double var = ne > 0.0 ? ps2 / ne - mu * mu : 0.0;
+        state[PVR_ST_MU_P] = mu;
+        state[PVR_ST_SIGMA2_P] = var < 1e-4 ? 1e-4 : var;
+        state[PVR_ST_C_P] = clampd(c0, 1e-3, 1.0 - 1e-3);
+    }
+}
+
+// E-step of the patch-level model: w = G c_p / (G c_p + m_p (1 - c_p)),
+// G the one-sided Gaussian density of pbar; w = 1 if m_p = 0; 0 if not
+// eligible.  bpart = {sum w, sum w pbar, sum w pbar^2} over eligible patches.
+__global__ void __launch_bounds__(256) k_em_patch_estep(int n, const uint8_t *__restrict__ elig,
+                                                        const double *__restrict__ pbar,
+                                                        const double *__restrict__ state,
+                                                        const double *__restrict__ pstat,
+                                                        double *__restrict__ wsc,
+                                                        double *__restrict__ bpart)
+{
+    __shared__ double sh[32 * 3];
+    if (pstat[6] != 0.0) return;   // the loop has stopped: keep the last weights
+    const double mu = state[PVR_ST_MU_P], v2 = state[PVR_ST_SIGMA2_P], cp = state[PVR_ST_C_P];
+    const double mp = pstat[5];
+    const double gnorm = 1.0 / (sqrt(2.0 * 3.14159265358979323846) * sqrt(v2));
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        double wv;
+        if (!elig[p]) {
+            wv = 0.0;
+        } else if (mp == 0.0) {
+            wv = 1.0;
+        } else {
+            double dl = pbar[p] >= mu ? 0.0 : pbar[p] - mu;
+            double G = exp(-(dl * dl) / (2.0 * v2)) * gnorm;
+            wv = (G * cp) / (G * cp + mp * (1.0 - cp));
+        }
+        wsc[p] = wv;
+        if (elig[p]) {
+            a[0] += wv;
+            a[1] += wv * pbar[p];
+            a[2] += wv * pbar[p] * pbar[p];
+        }
+    }
+    block_reduce<3>(a, sh, 0);
+    store_block(bpart, a, 3);
+}
+
+// M-step of the patch-level model; stops the loop when m_p = 0 or no weight.
+__global__ void k_em_patch_mstep(int nb, const double *__restrict__ bpart, double *__restrict__ state,
+                                 double *__restrict__ pstat)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0 || pstat[6] != 0.0) return;
+    if (pstat[5] == 0.0) {
+        pstat[6] = 1.0;
+        return;
+    }
+    double sw = 0, swp = 0, swp2 = 0;
+    for (int b = 0; b < nb; ++b) {
+        sw += bpart[8 * (size_t)b];
+        swp += bpart[8 * (size_t)b + 1];
+        swp2 += bpart[8 * (size_t)b + 2];
+    }
+    if (!(sw > 0.0)) {
+        pstat[6] = 1.0;
+        return;
+    }
+    double mu = swp / sw;
+    double v2 = swp2 / sw - mu * mu;
+    state[PVR_ST_MU_P] = mu;
+    state[PVR_ST_SIGMA2_P] = v2 < 1e-4 ? 1e-4 : v2;
+    state[PVR_ST_C_P] = clampd(sw / pstat[7], 1e-3, 1.0 - 1e-3);
+}
+
+// Masks and outputs; bpart[0] = number of inlier patches of the block.
+__global__ void __launch_bounds__(256) k_em_patch_final(int n, const uint8_t *__restrict__ elig,
+                                                        const double *__restrict__ pbar,
+                                                        const double *__restrict__ wsc, int rule,
+                                                        double threshold,
+                                                        uint8_t *__restrict__ mask_out,
+                                                        float *__restrict__ w_patch,
+                                                        float *__restrict__ pbar_out,
+                                                        double *__restrict__ bpart)
+{
+    __shared__ double sh[32];
+    double cnt[1] = {0.0};
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        double wv = rule == 1 ? (elig[p] ? pbar[p] : 0.0) : wsc[p];
+        uint8_t m = rule == 1 ? (elig[p] && pbar[p] >= threshold) : (elig[p] && wsc[p] >= 0.5);
+        mask_out[p] = m;
+        cnt[0] += m;
+        if (w_patch) w_patch[p] = (float)wv;
         if (pbar_out) pbar_out[p] = (float)pbar[p];
     }
-    block_reduce<1>(nin, sh, 0);
-    if (threadIdx.x == 0) {
-        state[PVR_ST_N_ELIG] = nelig;
-        state[PVR_ST_N_IN] = nin[0];
-        state[PVR_ST_INIT] = 1.0;
-    }
+    block_reduce<1>(cnt, sh, 0);
+    store_block(bpart, cnt, 1);
+}
+
+__global__ void k_em_patch_tail(int nb, const double *__restrict__ bpart, double *__restrict__ state,
+                                const double *__restrict__ pstat, int rule)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double nin = 0.0;
+    for (int b = 0; b < nb; ++b) nin += bpart[8 * (size_t)b];
+    state[PVR_ST_N_ELIG] = pstat[7];
+    state[PVR_ST_N_IN] = nin;
+    if (rule == 0) state[PVR_ST_M_P] = pstat[5];
+    state[PVR_ST_INIT] = 1.0;
 }
 
 // Weighted SIRT step (rows of A sum to one): x <- max(x + alpha addon / conf, 0)
@@ -396,6 +451,48 @@ __global__ void __launch_bounds__(256) k_volume_update(float *__restrict__ x,
         if (c > eps) v = init_mode ? a / c : fmaxf(v + alpha * a / c, 0.f);
         x[i] = v;
         if (clear) addon[i] = conf[i] = 0.f;
+    }
+}
+
+// The same step on interleaved (addon, conf) pairs (the adjoint's own
+// accumulator layout: one vector reduction per voxel and sample corner).
+__global__ void __launch_bounds__(256) k_volume_update_pairs(float *__restrict__ x,
+                                                             float2 *__restrict__ acc, long long n,
+                                                             float alpha, float eps, int clear,
+                                                             int init_mode)
+{
+    long long stride = (long long)gridDim.x * blockDim.x;
+    long long n2 = n >> 1;
+    float2 *x2 = reinterpret_cast<float2 *>(x);
+    float4 *a4 = reinterpret_cast<float4 *>(acc);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += stride) {
+        float4 a = a4[i];   // (addon, conf) of voxels 2i and 2i+1
+        float2 v = init_mode ? make_float2(0.f, 0.f) : x2[i];
+        if (a.y > eps) v.x = init_mode ? a.x / a.y : fmaxf(v.x + alpha * a.x / a.y, 0.f);
+        if (a.w > eps) v.y = init_mode ? a.z / a.w : fmaxf(v.y + alpha * a.z / a.w, 0.f);
+        x2[i] = v;
+        if (clear) a4[i] = z4;
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        long long i = n - 1;
+        float2 a = acc[i];
+        float v = init_mode ? 0.f : x[i];
+        if (a.y > eps) v = init_mode ? a.x / a.y : fmaxf(v + alpha * a.x / a.y, 0.f);
+        x[i] = v;
+        if (clear) acc[i] = make_float2(0.f, 0.f);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_split_pairs(const float2 *__restrict__ acc, long long n,
+                                                     float *__restrict__ addon,
+                                                     float *__restrict__ conf, int accumulate)
+{
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        float2 a = acc[i];
+        if (addon) addon[i] = accumulate ? addon[i] + a.x : a.x;
+        if (conf) conf[i] = accumulate ? conf[i] + a.y : a.y;
     }
 }
 
@@ -497,18 +594,37 @@ cudaError_t launch_em(const float *y, const float *sim, const uint8_t *valid, co
                       int n, int64_t n_pix, const Tiling &tl, int32_t *err, double *state,
                       const uint8_t *mask_in, uint8_t *mask_out, float *p, float *w_patch,
                       float *pbar_out, double *part, double *pstat, double *pbar, double *wsc,
-                      uint8_t *elig, const pvr_params &prm, cudaStream_t st)
+                      uint8_t *elig, double *bpart, const pvr_params &prm, cudaStream_t st)
 {
     k_em_prepare<<<1, kRedThreads, 0, st>>>(n, tl.tpp, mask_in, part, state, pstat, prm.em_c0,
                                             prm.em_sigma_floor_rel);
     if (n > 0)
         k_em_estep<<<(unsigned)n * tl.tpp, 256, 0, st>>>(y, sim, valid, desc, tl, (long long)n_pix,
                                                          err, mask_in, pstat, p, part);
-    k_em_mstep<<<1, kRedThreads, 0, st>>>(desc, n, tl.tpp, mask_in, part, state, pstat, prm.em_c0,
-                                          prm.em_min_valid_frac, prm.patch_rule,
-                                          prm.patch_threshold, prm.patch_em_iters, pbar, wsc, elig,
-                                          mask_out, w_patch, pbar_out);
+    int nb = (n + 255) / 256;
+    if (nb > kEmBlockMax) nb = kEmBlockMax;
+    if (nb < 1) nb = 1;
+    const int rule = prm.patch_rule == 1 ? 1 : 0;
+    k_em_patch_pot<<<nb, 256, 0, st>>>(desc, n, tl.tpp, mask_in, part, prm.em_min_valid_frac, pbar,
+                                       elig, bpart);
+    k_em_patch_head<<<1, 32, 0, st>>>(nb, bpart, state, pstat, prm.em_c0, rule);
+    if (rule == 0) {
+        for (int it = 0; it < prm.patch_em_iters; ++it) {
+            k_em_patch_estep<<<nb, 256, 0, st>>>(n, elig, pbar, state, pstat, wsc, bpart);
+            k_em_patch_mstep<<<1, 32, 0, st>>>(nb, bpart, state, pstat);
+        }
+        k_em_patch_estep<<<nb, 256, 0, st>>>(n, elig, pbar, state, pstat, wsc, bpart);
+    }
+    k_em_patch_final<<<nb, 256, 0, st>>>(n, elig, pbar, wsc, rule, prm.patch_threshold, mask_out,
+                                         w_patch, pbar_out, bpart);
+    k_em_patch_tail<<<1, 32, 0, st>>>(nb, bpart, state, pstat, rule);
     return cudaGetLastError();
+}
+
+// Number of kernel launches launch_em makes.
+int em_launch_count(int n, const pvr_params &prm)
+{
+    return (n > 0 ? 2 : 1) + 2 + (prm.patch_rule == 1 ? 0 : 2 * prm.patch_em_iters + 1) + 2;
 }
 
 cudaError_t launch_volume_update(float *x, float *addon, float *conf, int64_t nvox, float alpha,
@@ -525,6 +641,34 @@ cudaError_t launch_volume_update(float *x, float *addon, float *conf, int64_t nv
     if (blocks < 1) blocks = 1;
     k_volume_update<<<(unsigned)blocks, 256, 0, st>>>(x, addon, conf, (long long)nvox, alpha,
                                                       conf_eps, clear, init_mode);
+    return cudaGetLastError();
+}
+
+static unsigned elementwise_blocks(long long work)
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long blocks = (work + 255) / 256, cap = (long long)sms * 8;
+    if (blocks > cap) blocks = cap;
+    return (unsigned)(blocks < 1 ? 1 : blocks);
+}
+
+cudaError_t launch_volume_update_pairs(float *x, float2 *acc, int64_t nvox, float alpha,
+                                       float conf_eps, int clear, int init_mode, cudaStream_t st)
+{
+    if (nvox <= 0) return cudaSuccess;
+    k_volume_update_pairs<<<elementwise_blocks(nvox / 2 + 1), 256, 0, st>>>(
+        x, acc, (long long)nvox, alpha, conf_eps, clear, init_mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_pairs(const float2 *acc, int64_t nvox, float *addon, float *conf,
+                               int accumulate, cudaStream_t st)
+{
+    if (nvox <= 0) return cudaSuccess;
+    k_split_pairs<<<elementwise_blocks(nvox), 256, 0, st>>>(acc, (long long)nvox, addon, conf,
+                                                            accumulate);
     return cudaGetLastError();
 }
 

@@ -98,13 +98,46 @@ __device__ __forceinline__ void split(unsigned q, int n, int &b, float &f)
     }
 }
 
-// Lattice position (tile-lattice index lp) at zeta = 0.
-__device__ __forceinline__ void lattice_q0(const TileInfo &ti, int kxy, int lp, unsigned q[3])
+// Traversal order of a tile's lattice, chosen per patch so that neighbouring
+// lanes touch neighbouring voxels in memory (x fastest): lanes step along the
+// patch columns, along the patch rows, or -- when the slice normal is the
+// direction closest to the volume's x axis (e.g. sagittal slices) -- eight
+// lanes share a lattice point, one per through-plane sample (needs
+// 2 kz + 1 <= 8).  The order changes only the float32 summation order.
+enum { kAlongCol = 0, kAlongRow = 1, kAlongZeta = 2 };
+
+__device__ __forceinline__ float x_share(const unsigned e[3])
 {
-    int li = ti.i0 - kxy + lp % ti.Lw;
-    int lj = ti.j0 - kxy + lp / ti.Lw;
+    float a = (float)(int)e[0], b = (float)(int)e[1], c = (float)(int)e[2];
+    float n2 = a * a + b * b + c * c;
+    return n2 > 0.f ? fabsf(a) * rsqrtf(n2) : 0.f;
+}
+
+__device__ __forceinline__ int pick_order(const TileInfo &ti, int kz)
+{
+    float ci = x_share(ti.ei), cj = x_share(ti.ej), cz = x_share(ti.ez);
+    if (kz > 0 && 2 * kz + 1 <= 8 && cz > ci && cz > cj) return kAlongZeta;
+    return cj > ci ? kAlongRow : kAlongCol;
+}
+
+// Tile-lattice coordinates (li, lj) (0-based, halo included) of item it.
+__device__ __forceinline__ void lattice_coords(const TileInfo &ti, int order, int it, int &li, int &lj)
+{
+    if (order == kAlongRow) {
+        li = it / ti.Lh;
+        lj = it % ti.Lh;
+    } else {
+        li = it % ti.Lw;
+        lj = it / ti.Lw;
+    }
+}
+
+// Fixed-point position of tile-lattice point (li, lj) at zeta = 0.
+__device__ __forceinline__ void lattice_pos(const TileInfo &ti, int kxy, int li, int lj, unsigned q[3])
+{
+    int pi = ti.i0 - kxy + li, pj = ti.j0 - kxy + lj;
 #pragma unroll
-    for (int r = 0; r < 3; ++r) q[r] = ti.o[r] + (unsigned)li * ti.ei[r] + (unsigned)lj * ti.ej[r];
+    for (int r = 0; r < 3; ++r) q[r] = ti.o[r] + (unsigned)pi * ti.ei[r] + (unsigned)pj * ti.ej[r];
 }
 
 __device__ __forceinline__ float trilinear(const float *__restrict__ x, const VolDims &vd,
@@ -136,32 +169,83 @@ __device__ __forceinline__ bool inside(const VolDims &vd, unsigned qx, unsigned 
 }
 
 // Phase 1 of the forward model: through-plane PSF sums at every lattice
-// point of the tile.  A (may be null) <- sum g_z trilinear, B <- sum g_z.
+// point of the tile (stored row-major).  A (may be null) <- sum g_z
+// trilinear, B <- sum g_z over in-volume samples.
 template <int KZ>
 __device__ __forceinline__ void lattice_forward(const float *__restrict__ x, const VolDims &vd,
                                                 const TileInfo &ti, int kxy, int kz_rt,
-                                                const float *__restrict__ gz, float *A, float *B)
+                                                const float *__restrict__ gz, int order, float *A,
+                                                float *B)
 {
     const int kz = KZ >= 0 ? KZ : kz_rt;
-    for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) {
-        unsigned q0[3];
-        lattice_q0(ti, kxy, lp, q0);
-        float acc = 0.f, den = 0.f;
+    if (order != kAlongZeta) {
+        for (int it = threadIdx.x; it < ti.L; it += blockDim.x) {
+            int li, lj;
+            lattice_coords(ti, order, it, li, lj);
+            unsigned q0[3];
+            lattice_pos(ti, kxy, li, lj, q0);
+            float acc = 0.f, den = 0.f;
 #pragma unroll
-        for (int z = -kz; z <= kz; ++z) {
-            unsigned qx = q0[0] + (unsigned)z * ti.ez[0];
-            unsigned qy = q0[1] + (unsigned)z * ti.ez[1];
-            unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
+            for (int z = -kz; z <= kz; ++z) {
+                unsigned qx = q0[0] + (unsigned)z * ti.ez[0];
+                unsigned qy = q0[1] + (unsigned)z * ti.ez[1];
+                unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
+                if (inside(vd, qx, qy, qz)) {
+                    float g = gz[z + kz];
+                    if (A) acc = fmaf(g, trilinear(x, vd, qx, qy, qz), acc);
+                    den += g;
+                }
+            }
+            int sidx = lj * ti.Lw + li;
+            if (A) A[sidx] = acc;
+            B[sidx] = den;
+        }
+        return;
+    }
+    const int zl = threadIdx.x & 7;
+    const bool zon = zl <= 2 * kz;
+    const int zeta = zl - kz;
+    const float g = zon ? gz[zl] : 0.f;
+    const int ngrp = blockDim.x >> 3;
+    for (int base = 0; base < ti.L; base += ngrp) {
+        int lp = base + (threadIdx.x >> 3);
+        float a = 0.f, b = 0.f;
+        if (zon && lp < ti.L) {
+            unsigned q[3];
+            lattice_pos(ti, kxy, lp % ti.Lw, lp / ti.Lw, q);
+            unsigned qx = q[0] + (unsigned)zeta * ti.ez[0];
+            unsigned qy = q[1] + (unsigned)zeta * ti.ez[1];
+            unsigned qz = q[2] + (unsigned)zeta * ti.ez[2];
             if (inside(vd, qx, qy, qz)) {
-                float g = gz[z + kz];
-                if (A) acc = fmaf(g, trilinear(x, vd, qx, qy, qz), acc);
-                den += g;
+                if (A) a = g * trilinear(x, vd, qx, qy, qz);
+                b = g;
             }
         }
-        if (A) A[lp] = acc;
-        B[lp] = den;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (zl == 0 && lp < ti.L) {
+            if (A) A[lp] = a;
+            B[lp] = b;
+        }
     }
 }
+
+// Kahan-compensated float32 sum (the pose gradient is a sum of terms of
+// both signs that largely cancel near an optimum).
+struct KahanSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v)
+    {
+        float yv = v - c;
+        float t = s + yv;
+        c = (t - s) - yv;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
 
 // In-plane taps at tile pixel (ci, cj) from lattice array V.
 __device__ __forceinline__ float inplane(const float *V, int Lw, int kxy, const float *gxy, int ci,
@@ -245,7 +329,8 @@ __global__ void __launch_bounds__(256) k_simulate(const float *__restrict__ x, V
     }
     float *A = sm, *B = sm + ti.L;
     if (ti.ok) {
-        lattice_forward<KZ>(x, vd, ti, kxy, psf.kz, psf.gz[ti.stack], A, B);
+        lattice_forward<KZ>(x, vd, ti, kxy, psf.kz, psf.gz[ti.stack],
+                            pick_order(ti, KZ >= 0 ? KZ : psf.kz), A, B);
     } else {
         for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) A[lp] = B[lp] = 0.f;
     }
@@ -303,7 +388,40 @@ __global__ void __launch_bounds__(256) k_simulate(const float *__restrict__ x, V
 // Adjoint.  Pixel coefficients cr = w r / den, cw = w / den (valid pixels),
 // transposed in-plane taps into lattice weights U, U', then every in-volume
 // sample adds U g_z tri and U' g_z tri to its 8 voxels (float atomics).
-template <int KXY, int KZ>
+// Add one in-volume sample's contributions ar, aw (already times g_z) to the
+// 8 voxels of its cell: PAIR = interleaved (addon, conf) float2 pairs with one
+// vector reduction per voxel, otherwise two separate arrays.
+template <bool PAIR>
+__device__ __forceinline__ void scatter_sample(const VolDims &vd, unsigned qx, unsigned qy,
+                                               unsigned qz, float ar, float aw, float *addon,
+                                               float *conf)
+{
+    int bx, by, bz;
+    float fx, fy, fz;
+    split(qx, vd.nx, bx, fx);
+    split(qy, vd.ny, by, fy);
+    split(qz, vd.nz, bz, fz);
+    const size_t nxy = (size_t)vd.nx * vd.ny;
+    size_t base = (size_t)bz * nxy + (size_t)by * vd.nx + bx;
+    float wx[2] = {1.f - fx, fx}, wy[2] = {1.f - fy, fy}, wz[2] = {1.f - fz, fz};
+#pragma unroll
+    for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+        for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+            for (int cx = 0; cx < 2; ++cx) {
+                float t = wx[cx] * wy[cy] * wz[cz];
+                size_t idx = base + cz * nxy + cy * vd.nx + cx;
+                if (PAIR) {
+                    atomicAdd(reinterpret_cast<float2 *>(addon) + idx, make_float2(ar * t, aw * t));
+                } else {
+                    if (addon) atomicAdd(addon + idx, ar * t);
+                    if (conf) atomicAdd(conf + idx, aw * t);
+                }
+            }
+}
+
+template <int KXY, int KZ, bool PAIR>
 __global__ void __launch_bounds__(256) k_adjoint(VolDims vd, const int32_t *__restrict__ desc,
                                                  const int32_t *__restrict__ fix, PsfTab psf,
                                                  Tiling tl, const float *__restrict__ r,
@@ -322,7 +440,7 @@ __global__ void __launch_bounds__(256) k_adjoint(VolDims vd, const int32_t *__re
     float *U = sm, *Uw = sm + ti.L, *CR = sm + 2 * ti.L, *CW = CR + np;
     const float *gz = psf.gz[ti.stack];
     // phase 0: in-volume PSF weight per lattice point (no gathers)
-    lattice_forward<KZ>(nullptr, vd, ti, kxy, kz, gz, nullptr, U);
+    lattice_forward<KZ>(nullptr, vd, ti, kxy, kz, gz, kAlongCol, nullptr, U);
     __syncthreads();
     // phase 1: pixel coefficients
     for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
@@ -365,39 +483,41 @@ __global__ void __launch_bounds__(256) k_adjoint(VolDims vd, const int32_t *__re
         Uw[lp] = uw;
     }
     __syncthreads();
-    // phase 3: scatter
-    const size_t nxy = (size_t)vd.nx * vd.ny;
-    for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) {
-        float ur = U[lp], uw = Uw[lp];
-        if (ur == 0.f && uw == 0.f) continue;
-        unsigned q0[3];
-        lattice_q0(ti, kxy, lp, q0);
+    // phase 3: scatter, in the tile's traversal order
+    const int order = pick_order(ti, kz);
+    if (order != kAlongZeta) {
+        for (int it = threadIdx.x; it < ti.L; it += blockDim.x) {
+            int li, lj;
+            lattice_coords(ti, order, it, li, lj);
+            const int sidx = lj * ti.Lw + li;
+            float ur = U[sidx], uw = Uw[sidx];
+            if (ur == 0.f && uw == 0.f) continue;
+            unsigned q0[3];
+            lattice_pos(ti, kxy, li, lj, q0);
 #pragma unroll
-        for (int z = -kz; z <= kz; ++z) {
-            unsigned qx = q0[0] + (unsigned)z * ti.ez[0];
-            unsigned qy = q0[1] + (unsigned)z * ti.ez[1];
-            unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
-            if (!inside(vd, qx, qy, qz)) continue;
-            int bx, by, bz;
-            float fx, fy, fz;
-            split(qx, vd.nx, bx, fx);
-            split(qy, vd.ny, by, fy);
-            split(qz, vd.nz, bz, fz);
-            float g = gz[z + kz];
-            float ar = g * ur, aw = g * uw;
-            size_t base = (size_t)bz * nxy + (size_t)by * vd.nx + bx;
-            float wx[2] = {1.f - fx, fx}, wy[2] = {1.f - fy, fy}, wz[2] = {1.f - fz, fz};
-#pragma unroll
-            for (int cz = 0; cz < 2; ++cz)
-#pragma unroll
-                for (int cy = 0; cy < 2; ++cy)
-#pragma unroll
-                    for (int cx = 0; cx < 2; ++cx) {
-                        float t = wx[cx] * wy[cy] * wz[cz];
-                        size_t idx = base + cz * nxy + cy * vd.nx + cx;
-                        if (addon) atomicAdd(addon + idx, ar * t);
-                        if (conf) atomicAdd(conf + idx, aw * t);
-                    }
+            for (int z = -kz; z <= kz; ++z) {
+                unsigned qx = q0[0] + (unsigned)z * ti.ez[0];
+                unsigned qy = q0[1] + (unsigned)z * ti.ez[1];
+                unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
+                if (!inside(vd, qx, qy, qz)) continue;
+                float g = gz[z + kz];
+                scatter_sample<PAIR>(vd, qx, qy, qz, g * ur, g * uw, addon, conf);
+            }
+        }
+    } else {
+        const int zl = threadIdx.x & 7, zeta = zl - kz;
+        if (zl <= 2 * kz) {
+            const float g = gz[zl];
+            for (int lp = threadIdx.x >> 3; lp < ti.L; lp += blockDim.x >> 3) {
+                float ur = U[lp], uw = Uw[lp];
+                if (ur == 0.f && uw == 0.f) continue;
+                unsigned q[3];
+                lattice_pos(ti, kxy, lp % ti.Lw, lp / ti.Lw, q);
+                unsigned qx = q[0] + (unsigned)zeta * ti.ez[0];
+                unsigned qy = q[1] + (unsigned)zeta * ti.ez[1];
+                unsigned qz = q[2] + (unsigned)zeta * ti.ez[2];
+                if (inside(vd, qx, qy, qz)) scatter_sample<PAIR>(vd, qx, qy, qz, g * ur, g * uw, addon, conf);
+            }
         }
     }
 }
@@ -429,7 +549,8 @@ __global__ void __launch_bounds__(256) k_ncc_moments(const float *__restrict__ x
     }
     float *A = sm, *B = sm + ti.L;
     if (ti.ok) {
-        lattice_forward<KZ>(x, vd, ti, kxy, psf.kz, psf.gz[ti.stack], A, B);
+        lattice_forward<KZ>(x, vd, ti, kxy, psf.kz, psf.gz[ti.stack],
+                            pick_order(ti, KZ >= 0 ? KZ : psf.kz), A, B);
     } else {
         for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) A[lp] = B[lp] = 0.f;
     }
@@ -486,6 +607,73 @@ __device__ bool ncc_from_moments(const double *part, int p, int tpp, int min_val
     return true;
 }
 
+// Pose Jacobian of the sample positions (voxel units per parameter unit):
+// dq/dtheta_k = J1 (i - cu) + J2 (j - cv) + J4 zeta + J3 with (i, j) the patch
+// pixel, (cu, cv) its centre; jc[k] = {J1(3), J2(3), J4(3), J3(3)}.
+// Translations: J3 = columns of world_to_voxel.  Rotation k: J = W R_k' S per
+// degree, R_k' = d(Rz Ry Rx)/d angle_k (float64, math-library trigonometry:
+// the gradient is not part of the integer-exact path).
+__device__ void pose_jacobian(const DevGeom *__restrict__ g, const int32_t *d, const double *th,
+                              double jc[6][12])
+{
+    const double *S = g->p2w[d[0]];
+    const double *W = g->w2v;
+    const double dg = 3.14159265358979323846 / 180.0;
+    double ax = th[3] * dg, ay = th[4] * dg, az = th[5] * dg;
+    double sx = sin(ax), cx = cos(ax), sy = sin(ay), cy = cos(ay), sz = sin(az), cz = cos(az);
+    double Rx[9] = {1, 0, 0, 0, cx, -sx, 0, sx, cx};
+    double Ry[9] = {cy, 0, sy, 0, 1, 0, -sy, 0, cy};
+    double Rz[9] = {cz, -sz, 0, sz, cz, 0, 0, 0, 1};
+    double dRx[9] = {0, 0, 0, 0, -sx, -cx, 0, cx, -sx};
+    double dRy[9] = {-sy, 0, cy, 0, 0, 0, -cy, 0, -sy};
+    double dRz[9] = {-sz, -cz, 0, cz, -sz, 0, 0, 0, 0};
+    double n2 = S[2] * S[2] + S[6] * S[6] + S[10] * S[10];
+    double zs = g->dz / sqrt(n2);
+    for (int k = 0; k < 6; ++k) {
+        double Q[9];
+        if (k < 3) {
+            for (int r = 0; r < 3; ++r) {
+                jc[k][r] = 0.0;
+                jc[k][3 + r] = 0.0;
+                jc[k][6 + r] = 0.0;
+                jc[k][9 + r] = W[4 * r + k];
+            }
+            continue;
+        }
+        const double *Am = (k == 5) ? dRz : Rz;
+        const double *Bm = (k == 4) ? dRy : Ry;
+        const double *Cm = (k == 3) ? dRx : Rx;
+        double AB[9], ABC[9], WA[9];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                AB[3 * r + c] = 0.0;
+                for (int t = 0; t < 3; ++t) AB[3 * r + c] += Am[3 * r + t] * Bm[3 * t + c];
+            }
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                ABC[3 * r + c] = 0.0;
+                for (int t = 0; t < 3; ++t) ABC[3 * r + c] += AB[3 * r + t] * Cm[3 * t + c];
+            }
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                WA[3 * r + c] = 0.0;
+                for (int t = 0; t < 3; ++t) WA[3 * r + c] += W[4 * r + t] * ABC[3 * t + c];
+            }
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                Q[3 * r + c] = 0.0;
+                for (int t = 0; t < 3; ++t) Q[3 * r + c] += WA[3 * r + t] * S[4 * t + c];
+                Q[3 * r + c] *= dg;
+            }
+        for (int r = 0; r < 3; ++r) {
+            jc[k][r] = Q[3 * r + 0];
+            jc[k][3 + r] = Q[3 * r + 1];
+            jc[k][6 + r] = Q[3 * r + 2] * zs;
+            jc[k][9 + r] = 0.0;
+        }
+    }
+}
+
 // ----------------------------------------------------------------- K6b --
 // Pose gradient of NCC.  dNCC/ds_i = ((y_i - my)/sd - ncc (s_i - ms)/vs)/N;
 // pixel coefficient c_i = dNCC/ds_i / den_i; transposed in-plane taps give
@@ -507,8 +695,10 @@ __global__ void __launch_bounds__(256) k_ncc_grad(const float *__restrict__ x, V
                                                   double *__restrict__ gpart, int min_valid)
 {
     extern __shared__ float sm[];
-    __shared__ double red[32 * 6];
-    __shared__ float jc[6][12];   // per parameter: a(3), b(3), z(3), o(3): dq = a li + b lj + z zeta + o
+    __shared__ double red[32 * 12];
+    // per parameter k: dq/dtheta_k = J1 (i - cu) + J2 (j - cv) + J4 zeta + J3 (voxel units),
+    // stored as jc[k] = {J1(3), J2(3), J4(3), J3(3)}; (i, j) patch pixel, (cu, cv) its centre
+    __shared__ double jc[6][12];
     __shared__ double sh_stats[4];
     __shared__ int sh_ok;
     const int kxy = KXY >= 0 ? KXY : psf.kxy;
@@ -529,65 +719,7 @@ __global__ void __launch_bounds__(256) k_ncc_grad(const float *__restrict__ x, V
         sh_stats[2] = ms;
         sh_stats[3] = 0.0;
         if (ok) {
-            const int32_t *d = desc + 8 * (size_t)ti.p;
-            const double *S = g->p2w[d[0]];
-            const double *W = g->w2v;
-            const double *th = poses + 6 * (size_t)ti.p;
-            const double dg = 3.14159265358979323846 / 180.0;
-            double ax = th[3] * dg, ay = th[4] * dg, az = th[5] * dg;
-            double sx = sin(ax), cx = cos(ax), sy = sin(ay), cy = cos(ay), sz = sin(az), cz = cos(az);
-            double Rx[9] = {1, 0, 0, 0, cx, -sx, 0, sx, cx};
-            double Ry[9] = {cy, 0, sy, 0, 1, 0, -sy, 0, cy};
-            double Rz[9] = {cz, -sz, 0, sz, cz, 0, 0, 0, 1};
-            double dRx[9] = {0, 0, 0, 0, -sx, -cx, 0, cx, -sx};
-            double dRy[9] = {-sy, 0, cy, 0, 0, 0, -cy, 0, -sy};
-            double dRz[9] = {-sz, -cz, 0, cz, -sz, 0, 0, 0, 0};
-            double n2 = S[2] * S[2] + S[6] * S[6] + S[10] * S[10];
-            double zs = g->dz / sqrt(n2);
-            double cu = 0.5 * (d[4] - 1), cv = 0.5 * (d[5] - 1);
-            for (int k = 0; k < 6; ++k) {
-                double Q[9];
-                if (k < 3) {
-                    for (int r = 0; r < 3; ++r) {
-                        jc[k][r] = 0.f;
-                        jc[k][3 + r] = 0.f;
-                        jc[k][6 + r] = 0.f;
-                        jc[k][9 + r] = (float)W[4 * r + k];
-                    }
-                    continue;
-                }
-                const double *Am = (k == 5) ? dRz : Rz;
-                const double *Bm = (k == 4) ? dRy : Ry;
-                const double *Cm = (k == 3) ? dRx : Rx;
-                double AB[9], ABC[9], WA[9];
-                for (int r = 0; r < 3; ++r)
-                    for (int c = 0; c < 3; ++c) {
-                        AB[3 * r + c] = 0.0;
-                        for (int t = 0; t < 3; ++t) AB[3 * r + c] += Am[3 * r + t] * Bm[3 * t + c];
-                    }
-                for (int r = 0; r < 3; ++r)
-                    for (int c = 0; c < 3; ++c) {
-                        ABC[3 * r + c] = 0.0;
-                        for (int t = 0; t < 3; ++t) ABC[3 * r + c] += AB[3 * r + t] * Cm[3 * t + c];
-                    }
-                for (int r = 0; r < 3; ++r)
-                    for (int c = 0; c < 3; ++c) {
-                        WA[3 * r + c] = 0.0;
-                        for (int t = 0; t < 3; ++t) WA[3 * r + c] += W[4 * r + t] * ABC[3 * t + c];
-                    }
-                for (int r = 0; r < 3; ++r)
-                    for (int c = 0; c < 3; ++c) {
-                        Q[3 * r + c] = 0.0;
-                        for (int t = 0; t < 3; ++t) Q[3 * r + c] += WA[3 * r + t] * S[4 * t + c];
-                        Q[3 * r + c] *= dg;
-                    }
-                for (int r = 0; r < 3; ++r) {
-                    jc[k][r] = (float)Q[3 * r + 0];
-                    jc[k][3 + r] = (float)Q[3 * r + 1];
-                    jc[k][6 + r] = (float)(Q[3 * r + 2] * zs);
-                    jc[k][9 + r] = (float)(-Q[3 * r + 0] * cu - Q[3 * r + 1] * cv);
-                }
-            }
+            pose_jacobian(g, desc + 8 * (size_t)ti.p, poses + 6 * (size_t)ti.p, jc);
             // coefficient scale: 1/(N sd), ncc/(N vs)
             sh_stats[3] = 1.0 / (n * sd);
             sh_stats[0] = ncc / (n * vs);
@@ -601,7 +733,7 @@ __global__ void __launch_bounds__(256) k_ncc_grad(const float *__restrict__ x, V
     const int np = ti.tw * ti.th;
     float *U = sm, *C = sm + ti.L;
     const float *gzp = psf.gz[ti.stack];
-    lattice_forward<KZ>(nullptr, vd, ti, kxy, kz, gzp, nullptr, U);
+    lattice_forward<KZ>(nullptr, vd, ti, kxy, kz, gzp, kAlongCol, nullptr, U);
     __syncthreads();
     const float a_sc = (float)sh_stats[3], b_sc = (float)sh_stats[0];
     const float my = (float)sh_stats[1], ms = (float)sh_stats[2];
@@ -634,54 +766,107 @@ __global__ void __launch_bounds__(256) k_ncc_grad(const float *__restrict__ x, V
         U[lp] = u;   // each lp written by its own thread; phase-0 data no longer read
     }
     __syncthreads();
-    // float32 sums over the samples of one lattice point, float64 across
-    // lattice points: the gradient is a sum of contributions of both signs
-    // that largely cancel near an optimum.
-    double dacc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    // Gradient pass in the tile's traversal order.  With w = U g_z and the
+    // trilinear gradient gr of each in-volume sample, accumulate the moments
+    // M1 = sum w gr (i - cu), M2 = sum w gr (j - cv), M3 = sum w gr,
+    // M4 = sum w gr zeta (Kahan-compensated float32 per thread, float64 across
+    // threads); the gradient is their contraction with the pose Jacobian.
+    KahanSum ks[12];
     const size_t nxy = (size_t)vd.nx * vd.ny;
-    for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) {
-        float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        float u = U[lp];
-        if (u == 0.f) continue;
-        unsigned q0[3];
-        lattice_q0(ti, kxy, lp, q0);
-        float li = (float)(ti.i0 - kxy + lp % ti.Lw), lj = (float)(ti.j0 - kxy + lp / ti.Lw);
+    const float cu = 0.5f * (float)(ti.w - 1), cv = 0.5f * (float)(ti.h - 1);
+    auto grad_at = [&](unsigned qx, unsigned qy, unsigned qz, float gr[3]) {
+        int bx, by, bz;
+        float fx, fy, fz;
+        split(qx, vd.nx, bx, fx);
+        split(qy, vd.ny, by, fy);
+        split(qz, vd.nz, bz, fz);
+        const float *b = x + (size_t)bz * nxy + (size_t)by * vd.nx + bx;
+        float v000 = __ldg(b), v100 = __ldg(b + 1);
+        float v010 = __ldg(b + vd.nx), v110 = __ldg(b + vd.nx + 1);
+        float v001 = __ldg(b + nxy), v101 = __ldg(b + nxy + 1);
+        float v011 = __ldg(b + nxy + vd.nx), v111 = __ldg(b + nxy + vd.nx + 1);
+        gr[0] = (1.f - fy) * (1.f - fz) * (v100 - v000) + fy * (1.f - fz) * (v110 - v010) +
+                (1.f - fy) * fz * (v101 - v001) + fy * fz * (v111 - v011);
+        gr[1] = (1.f - fx) * (1.f - fz) * (v010 - v000) + fx * (1.f - fz) * (v110 - v100) +
+                (1.f - fx) * fz * (v011 - v001) + fx * fz * (v111 - v101);
+        gr[2] = (1.f - fx) * (1.f - fy) * (v001 - v000) + fx * (1.f - fy) * (v101 - v100) +
+                (1.f - fx) * fy * (v011 - v010) + fx * fy * (v111 - v110);
+    };
+    auto add_moments = [&](const float s0[3], const float sz[3], float di, float dj) {
 #pragma unroll
-        for (int z = -kz; z <= kz; ++z) {
-            unsigned qx = q0[0] + (unsigned)z * ti.ez[0];
-            unsigned qy = q0[1] + (unsigned)z * ti.ez[1];
-            unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
-            if (!inside(vd, qx, qy, qz)) continue;
-            int bx, by, bz;
-            float fx, fy, fz;
-            split(qx, vd.nx, bx, fx);
-            split(qy, vd.ny, by, fy);
-            split(qz, vd.nz, bz, fz);
-            const float *b = x + (size_t)bz * nxy + (size_t)by * vd.nx + bx;
-            float v000 = __ldg(b), v100 = __ldg(b + 1);
-            float v010 = __ldg(b + vd.nx), v110 = __ldg(b + vd.nx + 1);
-            float v001 = __ldg(b + nxy), v101 = __ldg(b + nxy + 1);
-            float v011 = __ldg(b + nxy + vd.nx), v111 = __ldg(b + nxy + vd.nx + 1);
-            float gx = (1.f - fy) * (1.f - fz) * (v100 - v000) + fy * (1.f - fz) * (v110 - v010) +
-                       (1.f - fy) * fz * (v101 - v001) + fy * fz * (v111 - v011);
-            float gy = (1.f - fx) * (1.f - fz) * (v010 - v000) + fx * (1.f - fz) * (v110 - v100) +
-                       (1.f - fx) * fz * (v011 - v001) + fx * fz * (v111 - v101);
-            float gzv = (1.f - fx) * (1.f - fy) * (v001 - v000) + fx * (1.f - fy) * (v101 - v100) +
-                        (1.f - fx) * fy * (v011 - v010) + fx * fy * (v111 - v110);
-            float wgt = u * gzp[z + kz];
-            float fzeta = (float)z;
+        for (int r = 0; r < 3; ++r) {
+            ks[r].add(s0[r] * di);
+            ks[3 + r].add(s0[r] * dj);
+            ks[6 + r].add(sz[r]);
+            ks[9 + r].add(s0[r]);
+        }
+    };
+    const int order = pick_order(ti, kz);
+    if (order != kAlongZeta) {
+        for (int it = threadIdx.x; it < ti.L; it += blockDim.x) {
+            int li, lj;
+            lattice_coords(ti, order, it, li, lj);
+            float u = U[lj * ti.Lw + li];
+            if (u == 0.f) continue;
+            unsigned q0[3];
+            lattice_pos(ti, kxy, li, lj, q0);
+            float s0[3] = {0.f, 0.f, 0.f}, sz[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                float dqx = jc[k][0] * li + jc[k][3] * lj + jc[k][6] * fzeta + jc[k][9];
-                float dqy = jc[k][1] * li + jc[k][4] * lj + jc[k][7] * fzeta + jc[k][10];
-                float dqz = jc[k][2] * li + jc[k][5] * lj + jc[k][8] * fzeta + jc[k][11];
-                acc[k] = fmaf(wgt, gx * dqx + gy * dqy + gzv * dqz, acc[k]);
+            for (int z = -kz; z <= kz; ++z) {
+                unsigned qx = q0[0] + (unsigned)z * ti.ez[0];
+                unsigned qy = q0[1] + (unsigned)z * ti.ez[1];
+                unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
+                const bool in = inside(vd, qx, qy, qz);
+                const float w = in ? u * gzp[z + kz] : 0.f;
+                float gr[3];
+                grad_at(in ? qx : 0u, in ? qy : 0u, in ? qz : 0u, gr);
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    s0[r] = fmaf(w, gr[r], s0[r]);
+                    sz[r] = fmaf(w * (float)z, gr[r], sz[r]);
+                }
+            }
+            add_moments(s0, sz, (float)(ti.i0 - kxy + li) - cu, (float)(ti.j0 - kxy + lj) - cv);
+        }
+    } else {
+        const int zl = threadIdx.x & 7, zeta = zl - kz;
+        if (zl <= 2 * kz) {
+            const float g = gzp[zl];
+            for (int lp = threadIdx.x >> 3; lp < ti.L; lp += blockDim.x >> 3) {
+                float u = U[lp];
+                if (u == 0.f) continue;
+                int li = lp % ti.Lw, lj = lp / ti.Lw;
+                unsigned q[3];
+                lattice_pos(ti, kxy, li, lj, q);
+                unsigned qx = q[0] + (unsigned)zeta * ti.ez[0];
+                unsigned qy = q[1] + (unsigned)zeta * ti.ez[1];
+                unsigned qz = q[2] + (unsigned)zeta * ti.ez[2];
+                if (!inside(vd, qx, qy, qz)) continue;
+                float gr[3], s0[3], sz[3];
+                grad_at(qx, qy, qz, gr);
+                const float w = u * g;
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    s0[r] = w * gr[r];
+                    sz[r] = s0[r] * (float)zeta;
+                }
+                add_moments(s0, sz, (float)(ti.i0 - kxy + li) - cu, (float)(ti.j0 - kxy + lj) - cv);
             }
         }
-#pragma unroll
-        for (int k = 0; k < 6; ++k) dacc[k] += (double)acc[k];
     }
-    block_sum<6>(dacc, red);
+    double mom[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) mom[k] = ks[k].value();
+    block_sum<12>(mom, red);
+    double dacc[6];
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 6; ++k) {
+            double gsum = 0.0;
+            for (int r = 0; r < 3; ++r)
+                gsum += jc[k][r] * mom[r] + jc[k][3 + r] * mom[3 + r] + jc[k][6 + r] * mom[6 + r] +
+                        jc[k][9 + r] * mom[9 + r];
+            dacc[k] = gsum;
+        }
     if (threadIdx.x == 0) {
         for (int k = 0; k < 6; ++k) gp[k] = dacc[k];
         gp[6] = gp[7] = 0.0;
@@ -755,20 +940,25 @@ cudaError_t launch_simulate(const DevGeom *, const PsfTab &psf, const Tiling &tl
 cudaError_t launch_adjoint(const PsfTab &psf, const Tiling &tl, int nx, int ny, int nz,
                            const int32_t *desc, const int32_t *fix, int n, const float *r,
                            const float *w, const uint8_t *pmask, float *addon, float *conf,
-                           cudaStream_t st)
+                           int pair, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     VolDims vd = vol_dims(nx, ny, nz);
     size_t smem = smem_adjoint(tl, psf.kxy);
     dim3 grid((unsigned)n * tl.tpp), block(256);
     cudaError_t e;
-    if (psf.kxy == 1 && psf.kz == 3) {
-        if ((e = prep(k_adjoint<1, 3>, smem)) != cudaSuccess) return e;
-        k_adjoint<1, 3><<<grid, block, smem, st>>>(vd, desc, fix, psf, tl, r, w, pmask, addon, conf);
-    } else {
-        if ((e = prep(k_adjoint<-1, -1>, smem)) != cudaSuccess) return e;
-        k_adjoint<-1, -1><<<grid, block, smem, st>>>(vd, desc, fix, psf, tl, r, w, pmask, addon, conf);
-    }
+#define PVR_ADJ(KX, KZv, PR)                                                                          \
+    do {                                                                                              \
+        if ((e = prep(k_adjoint<KX, KZv, PR>, smem)) != cudaSuccess) return e;                        \
+        k_adjoint<KX, KZv, PR><<<grid, block, smem, st>>>(vd, desc, fix, psf, tl, r, w, pmask, addon, \
+                                                          conf);                                      \
+    } while (0)
+    const bool fast = psf.kxy == 1 && psf.kz == 3;
+    if (fast && pair) PVR_ADJ(1, 3, true);
+    else if (fast) PVR_ADJ(1, 3, false);
+    else if (pair) PVR_ADJ(-1, -1, true);
+    else PVR_ADJ(-1, -1, false);
+#undef PVR_ADJ
     return cudaGetLastError();
 }
 

@@ -20,7 +20,8 @@ cudaError_t launch_em(const float *y, const float *sim, const uint8_t *valid, co
                       int n, int64_t n_pix, const Tiling &tl, int32_t *err, double *state,
                       const uint8_t *mask_in, uint8_t *mask_out, float *p, float *w_patch,
                       float *pbar_out, double *part, double *pstat, double *pbar, double *wsc,
-                      uint8_t *elig, const pvr_params &prm, cudaStream_t st);
+                      uint8_t *elig, double *bpart, const pvr_params &prm, cudaStream_t st);
+int em_launch_count(int n, const pvr_params &prm);
 cudaError_t launch_patches_build(const DevGeom *g, const pvr_geometry &hg, const float *stacks,
                                  int64_t total, int a, int stride, double fg_frac,
                                  double keep_frac, int32_t *desc_out, int max_out, int32_t *keep,
@@ -49,7 +50,7 @@ struct pvr_ctx {
     DevGeom *d_geom = nullptr;
     int32_t *fix = nullptr;
     double *part = nullptr, *gpart = nullptr, *pstat = nullptr;
-    double *pbar = nullptr, *wsc = nullptr;
+    double *pbar = nullptr, *wsc = nullptr, *emblk = nullptr;
     uint8_t *elig = nullptr;
     int32_t *err = nullptr;
     double *best = nullptr, *gbest = nullptr, *nbest = nullptr, *trial = nullptr, *delta = nullptr;
@@ -57,7 +58,7 @@ struct pvr_ctx {
     int32_t *active = nullptr;
     float *s_buf = nullptr, *e_buf = nullptr, *p_buf = nullptr;
     uint8_t *v_buf = nullptr, *valid_buf = nullptr, *mask_tmp = nullptr;
-    float *addon = nullptr, *conf = nullptr;
+    float2 *acc2 = nullptr;   // interleaved (addon, conf) accumulator, one pair per voxel
     int32_t *keep = nullptr;
     int64_t keep_cap = 0;
     unsigned *imax_key = nullptr;
@@ -163,10 +164,10 @@ cudaError_t dalloc(T **p, size_t n)
 
 void free_all(pvr_ctx *c)
 {
-    void *ptrs[] = {c->d_geom, c->fix, c->part, c->gpart, c->pstat, c->pbar, c->wsc, c->elig,
+    void *ptrs[] = {c->d_geom, c->fix, c->part, c->gpart, c->pstat, c->pbar, c->wsc, c->emblk, c->elig,
                     c->err, c->best, c->gbest, c->nbest, c->trial, c->delta, c->ncc_tmp,
                     c->grad_tmp, c->active, c->s_buf, c->e_buf, c->p_buf, c->v_buf,
-                    c->valid_buf, c->mask_tmp, c->addon, c->conf, c->keep, c->imax_key,
+                    c->valid_buf, c->mask_tmp, c->acc2, c->keep, c->imax_key,
                     c->counts, c->metric_scr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -304,6 +305,7 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
     ALLOC(c->pstat, 8);
     ALLOC(c->pbar, P);
     ALLOC(c->wsc, P);
+    ALLOC(c->emblk, 512 * 8);
     ALLOC(c->elig, P);
     ALLOC(c->err, 1);
     ALLOC(c->best, P * kRegStride);
@@ -320,8 +322,7 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
     ALLOC(c->v_buf, NP);
     ALLOC(c->valid_buf, NP);
     ALLOC(c->mask_tmp, P);
-    ALLOC(c->addon, (size_t)c->nvox);
-    ALLOC(c->conf, (size_t)c->nvox);
+    ALLOC(c->acc2, (size_t)c->nvox);
     ALLOC(c->keep, (size_t)c->keep_cap);
     ALLOC(c->imax_key, 1);
     ALLOC(c->counts, 4);
@@ -329,8 +330,7 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
 #undef ALLOC
     if (e == cudaSuccess) e = cudaMemcpy(c->d_geom, &hg, sizeof hg, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMemset(c->addon, 0, (size_t)c->nvox * sizeof(float));
-    if (e == cudaSuccess) e = cudaMemset(c->conf, 0, (size_t)c->nvox * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(c->acc2, 0, (size_t)c->nvox * sizeof(float2));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         fprintf(stderr, "pvr_ctx_create: %s\n", cudaGetErrorString(e));
@@ -459,17 +459,16 @@ int pvr_adjoint(pvr_ctx *c, const pvr_patches *pp, const double *poses, const fl
     REQUIRE(addon || conf, "addon and conf are both NULL");
     REQUIRE(pp->n == 0 || poses, "NULL poses");
     cudaStream_t st = (cudaStream_t)stream;
-    size_t vb = (size_t)c->nvox * sizeof(float);
-    if (!accumulate) {
-        if (addon) CUDA_TRY(cudaMemsetAsync(addon, 0, vb, st), "clear addon");
-        if (conf) CUDA_TRY(cudaMemsetAsync(conf, 0, vb, st), "clear conf");
-    }
+    // scatter into the context's interleaved pair accumulator (one vector
+    // reduction per voxel corner), then copy / add into the caller's arrays
+    CUDA_TRY(cudaMemsetAsync(c->acc2, 0, (size_t)c->nvox * sizeof(float2), st), "clear");
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     Tiling tl = make_tiling(ms);
     CUDA_TRY_T(PVR_K_ADJOINT, launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix, pp->n,
-                            r, w, nullptr, addon, conf, st),
+                            r, w, nullptr, (float *)c->acc2, nullptr, 1, st),
              "adjoint");
-    c->launches += pp->n > 0;
+    CUDA_TRY(launch_split_pairs(c->acc2, c->nvox, addon, conf, accumulate, st), "split");
+    c->launches += (pp->n > 0) + 1;
     return PVR_OK;
 }
 
@@ -489,9 +488,9 @@ int pvr_em_weights(pvr_ctx *c, const float *y, const float *sim, const uint8_t *
              "em_stats");
     CUDA_TRY_T(PVR_K_EM, launch_em(y, sim, valid, pp->desc, pp->n, pp->n_pix, tl, c->err, state, mask_in,
                        mask_out, p, w_patch, pbar, c->part, c->pstat, c->pbar, c->wsc, c->elig,
-                       c->prm, st),
+                       c->emblk, c->prm, st),
              "em");
-    c->launches += pp->n > 0 ? 4 : 2;
+    c->launches += (pp->n > 0) + em_launch_count(pp->n, c->prm);
     return PVR_OK;
 }
 
@@ -515,15 +514,13 @@ int pvr_volume_init(pvr_ctx *c, float *x, const float *y, const pvr_patches *pp,
     if (rc) return rc;
     REQUIRE(x && y && (pp->n == 0 || poses), "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
-    size_t vb = (size_t)c->nvox * sizeof(float);
-    CUDA_TRY(cudaMemsetAsync(c->addon, 0, vb, st), "clear");
-    CUDA_TRY(cudaMemsetAsync(c->conf, 0, vb, st), "clear");
+    CUDA_TRY(cudaMemsetAsync(c->acc2, 0, (size_t)c->nvox * sizeof(float2), st), "clear");
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     Tiling tl = make_tiling(ms);
     CUDA_TRY_T(PVR_K_ADJOINT, launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix, pp->n,
-                            y, nullptr, nullptr, c->addon, c->conf, st),
+                            y, nullptr, nullptr, (float *)c->acc2, nullptr, 1, st),
              "adjoint");
-    CUDA_TRY_T(PVR_K_UPDATE, launch_volume_update(x, c->addon, c->conf, c->nvox, 1.0f, (float)c->prm.conf_eps, 1, 1,
+    CUDA_TRY_T(PVR_K_UPDATE, launch_volume_update_pairs(x, c->acc2, c->nvox, 1.0f, (float)c->prm.conf_eps, 1, 1,
                                   st),
              "volume_init");
     c->launches += (pp->n > 0) + 1;
@@ -606,26 +603,24 @@ int pvr_reconstruct_iter(pvr_ctx *c, float *x, const float *y, const pvr_patches
     if ((rc = register_impl(c, x, y, pp, ms, poses, c->prm.reg_evals, nullptr, st))) return rc;
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     Tiling tl = make_tiling(ms);
-    size_t vb = (size_t)c->nvox * sizeof(float);
-    CUDA_TRY(cudaMemsetAsync(c->addon, 0, vb, st), "clear");
-    CUDA_TRY(cudaMemsetAsync(c->conf, 0, vb, st), "clear");
+    CUDA_TRY(cudaMemsetAsync(c->acc2, 0, (size_t)c->nvox * sizeof(float2), st), "clear");
     for (int it = 0; it < c->prm.n_sr; ++it) {
         CUDA_TRY_T(PVR_K_SIMULATE, launch_simulate(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x,
                                  pp->desc, c->fix, pp->n, y, c->e_buf, c->valid_buf, c->part, st),
                  "simulate");
         CUDA_TRY_T(PVR_K_EM, launch_em(c->e_buf, nullptr, c->valid_buf, pp->desc, pp->n, pp->n_pix, tl, c->err,
                            state, mask, c->mask_tmp, c->p_buf, w_patch, nullptr, c->part, c->pstat,
-                           c->pbar, c->wsc, c->elig, c->prm, st),
+                           c->pbar, c->wsc, c->elig, c->emblk, c->prm, st),
                  "em");
         CUDA_TRY(cudaMemcpyAsync(mask, c->mask_tmp, (size_t)pp->n, cudaMemcpyDeviceToDevice, st),
                  "mask copy");
         CUDA_TRY_T(PVR_K_ADJOINT, launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix,
-                                pp->n, c->e_buf, c->p_buf, mask, c->addon, c->conf, st),
+                                pp->n, c->e_buf, c->p_buf, mask, (float *)c->acc2, nullptr, 1, st),
                  "adjoint");
-        CUDA_TRY_T(PVR_K_UPDATE, launch_volume_update(x, c->addon, c->conf, c->nvox, (float)c->prm.alpha,
+        CUDA_TRY_T(PVR_K_UPDATE, launch_volume_update_pairs(x, c->acc2, c->nvox, (float)c->prm.alpha,
                                       (float)c->prm.conf_eps, 1, 0, st),
                  "volume_update");
-        c->launches += pp->n > 0 ? 6 : 3;
+        c->launches += (pp->n > 0 ? 3 : 1) + em_launch_count(pp->n, c->prm);
     }
     if (p && pp->n_pix > 0)
         CUDA_TRY(cudaMemcpyAsync(p, c->p_buf, (size_t)pp->n_pix * sizeof(float),

@@ -48,10 +48,19 @@ cudaError_t launch_simulate(const DevGeom *g, const PsfTab &psf, const Tiling &t
                             const float *y, float *sim_or_e, uint8_t *valid, double *part,
                             cudaStream_t st);
 
+// pair = 1: addon points to interleaved (addon, conf) float2 pairs, conf unused.
 cudaError_t launch_adjoint(const PsfTab &psf, const Tiling &tl, int nx, int ny, int nz,
                            const int32_t *desc, const int32_t *fix, int n, const float *r,
                            const float *w, const uint8_t *patch_mask, float *addon, float *conf,
-                           cudaStream_t st);
+                           int pair, cudaStream_t st);
+
+// Weighted SIRT step on interleaved (addon, conf) pairs; optionally clears them.
+cudaError_t launch_volume_update_pairs(float *x, float2 *acc, int64_t nvox, float alpha,
+                                       float conf_eps, int clear, int init_mode, cudaStream_t st);
+
+// Copy (or add, accumulate = 1) interleaved pairs into separate arrays (either may be null).
+cudaError_t launch_split_pairs(const float2 *acc, int64_t nvox, float *addon, float *conf,
+                               int accumulate, cudaStream_t st);
 
 cudaError_t launch_volume_update(float *x, float *addon, float *conf, int64_t nvox, float alpha,
                                  float conf_eps, int clear, int init_mode, cudaStream_t st);
