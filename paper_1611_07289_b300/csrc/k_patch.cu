@@ -36,12 +36,12 @@ struct TileInfo {
 
 // Decode block -> (patch, tile); returns false for an empty tile or a
 // patch whose descriptor row failed validation in the pose kernel.
-__device__ __forceinline__ bool tile_setup(const int32_t *__restrict__ desc,
-                                           const int32_t *__restrict__ fix, const Tiling &tl,
-                                           int kxy, TileInfo &ti)
+__device__ __forceinline__ bool tile_setup_at(long long gid, const int32_t *__restrict__ desc,
+                                              const int32_t *__restrict__ fix, const Tiling &tl,
+                                              int kxy, TileInfo &ti)
 {
-    ti.p = blockIdx.x / tl.tpp;
-    ti.t = blockIdx.x % tl.tpp;
+    ti.p = (int)(gid / tl.tpp);
+    ti.t = (int)(gid % tl.tpp);
     const int32_t *d = desc + 8 * (size_t)ti.p;
     ti.stack = d[0];
     ti.w = d[4];
@@ -67,6 +67,13 @@ __device__ __forceinline__ bool tile_setup(const int32_t *__restrict__ desc,
         ti.ez[r] = (unsigned)f[9 + r];
     }
     return true;
+}
+
+__device__ __forceinline__ bool tile_setup(const int32_t *__restrict__ desc,
+                                           const int32_t *__restrict__ fix, const Tiling &tl,
+                                           int kxy, TileInfo &ti)
+{
+    return tile_setup_at(blockIdx.x, desc, fix, tl, kxy, ti);
 }
 
 struct VolDims {
@@ -166,6 +173,133 @@ __device__ __forceinline__ float trilinear(const float *__restrict__ x, const Vo
 __device__ __forceinline__ bool inside(const VolDims &vd, unsigned qx, unsigned qy, unsigned qz)
 {
     return qx <= vd.ux && qy <= vd.uy && qz <= vd.uz;
+}
+
+// Through-plane walks with cell-face reuse.  The through-plane samples of a
+// lattice point are one PSF step apart along e_zeta.  Walking them in the
+// direction in which e_zeta's largest voxel component FA is positive, a
+// sample whose cell starts one voxel further along FA (and in the same cell
+// along the two other axes) shares its lower face with the previous
+// sample's upper face: the adjoint merges the two contributions to those 4
+// voxels before one set of reductions.  The test compares exact voxel
+// indices, so it only removes duplicate memory operations.
+struct Walk {
+    int fa, z0, dz;
+};
+
+__device__ __forceinline__ Walk zeta_walk(const TileInfo &ti, int kz)
+{
+    int c0 = abs((int)ti.ez[0]), c1 = abs((int)ti.ez[1]), c2 = abs((int)ti.ez[2]);
+    Walk w;
+    w.fa = (c2 >= c1 && c2 >= c0) ? 2 : (c1 >= c0 ? 1 : 0);
+    const bool up = (int)ti.ez[w.fa] >= 0;
+    w.dz = up ? 1 : -1;
+    w.z0 = up ? -kz : kz;
+    return w;
+}
+
+template <int FA>
+struct FaceAxes;
+template <>
+struct FaceAxes<0> {
+    static constexpr int A1 = 1, A2 = 2;
+};
+template <>
+struct FaceAxes<1> {
+    static constexpr int A1 = 0, A2 = 2;
+};
+template <>
+struct FaceAxes<2> {
+    static constexpr int A1 = 0, A2 = 1;
+};
+
+__device__ __forceinline__ size_t axis_stride(const VolDims &vd, int a)
+{
+    return a == 0 ? (size_t)1 : (a == 1 ? (size_t)vd.nx : (size_t)vd.nx * vd.ny);
+}
+
+template <bool PAIR>
+__device__ __forceinline__ void face_red(float *addon, float *conf, size_t idx, size_t s1, size_t s2,
+                                         const float r[4], const float w[4])
+{
+    const size_t o[4] = {0, s1, s2, s1 + s2};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (PAIR) {
+            atomicAdd(reinterpret_cast<float2 *>(addon) + idx + o[k], make_float2(r[k], w[k]));
+        } else {
+            if (addon) atomicAdd(addon + idx + o[k], r[k]);
+            if (conf) atomicAdd(conf + idx + o[k], w[k]);
+        }
+    }
+}
+
+// Adjoint walk of one lattice point with weights ur, uw (times g_z per sample).
+template <int FA, int KZ, bool PAIR>
+__device__ __forceinline__ void walk_scatter(const VolDims &vd, const TileInfo &ti, const unsigned q0[3],
+                                             int kz_rt, const float *__restrict__ gz, const Walk &wk,
+                                             float ur, float uw, float *addon, float *conf)
+{
+    constexpr int A1 = FaceAxes<FA>::A1, A2 = FaceAxes<FA>::A2;
+    const int kz = KZ >= 0 ? KZ : kz_rt;
+    const size_t s1 = axis_stride(vd, A1), s2 = axis_stride(vd, A2), sf = axis_stride(vd, FA);
+    const size_t nxy = (size_t)vd.nx * vd.ny;
+    float pr[4] = {0.f, 0.f, 0.f, 0.f}, pw[4] = {0.f, 0.f, 0.f, 0.f};
+    size_t pidx = 0;
+    bool have = false;
+    int pb[3] = {-2, -2, -2};
+#pragma unroll
+    for (int t = 0; t <= 2 * kz; ++t) {
+        const int z = wk.z0 + t * wk.dz;
+        unsigned q[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) q[r] = q0[r] + (unsigned)z * ti.ez[r];
+        if (!inside(vd, q[0], q[1], q[2])) {
+            if (have) face_red<PAIR>(addon, conf, pidx, s1, s2, pr, pw);
+            have = false;
+            pb[FA] = -2;
+            continue;
+        }
+        int b[3];
+        float f[3];
+        split(q[0], vd.nx, b[0], f[0]);
+        split(q[1], vd.ny, b[1], f[1]);
+        split(q[2], vd.nz, b[2], f[2]);
+        const size_t idx = (size_t)b[2] * nxy + (size_t)b[1] * vd.nx + b[0];
+        const float g = gz[z + kz];
+        const float f1 = f[A1], f2 = f[A2];
+        const float wf[4] = {(1.f - f1) * (1.f - f2), f1 * (1.f - f2), (1.f - f1) * f2, f1 * f2};
+        const float ar = g * ur, aw = g * uw;
+        const float lo = 1.f - f[FA], hi = f[FA];
+        float lr[4], lw[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            lr[k] = ar * lo * wf[k];
+            lw[k] = aw * lo * wf[k];
+        }
+        if (have && b[FA] == pb[FA] + 1 && b[A1] == pb[A1] && b[A2] == pb[A2]) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                pr[k] += lr[k];
+                pw[k] += lw[k];
+            }
+            face_red<PAIR>(addon, conf, pidx, s1, s2, pr, pw);
+        } else {
+            if (have) face_red<PAIR>(addon, conf, pidx, s1, s2, pr, pw);
+            face_red<PAIR>(addon, conf, idx, s1, s2, lr, lw);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            pr[k] = ar * hi * wf[k];
+            pw[k] = aw * hi * wf[k];
+        }
+        pidx = idx + sf;
+        have = true;
+        pb[0] = b[0];
+        pb[1] = b[1];
+        pb[2] = b[2];
+    }
+    if (have) face_red<PAIR>(addon, conf, pidx, s1, s2, pr, pw);
 }
 
 // Phase 1 of the forward model: through-plane PSF sums at every lattice
@@ -486,6 +620,7 @@ __global__ void __launch_bounds__(256) k_adjoint(VolDims vd, const int32_t *__re
     // phase 3: scatter, in the tile's traversal order
     const int order = pick_order(ti, kz);
     if (order != kAlongZeta) {
+        const Walk wk = zeta_walk(ti, kz);
         for (int it = threadIdx.x; it < ti.L; it += blockDim.x) {
             int li, lj;
             lattice_coords(ti, order, it, li, lj);
@@ -494,15 +629,9 @@ __global__ void __launch_bounds__(256) k_adjoint(VolDims vd, const int32_t *__re
             if (ur == 0.f && uw == 0.f) continue;
             unsigned q0[3];
             lattice_pos(ti, kxy, li, lj, q0);
-#pragma unroll
-            for (int z = -kz; z <= kz; ++z) {
-                unsigned qx = q0[0] + (unsigned)z * ti.ez[0];
-                unsigned qy = q0[1] + (unsigned)z * ti.ez[1];
-                unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
-                if (!inside(vd, qx, qy, qz)) continue;
-                float g = gz[z + kz];
-                scatter_sample<PAIR>(vd, qx, qy, qz, g * ur, g * uw, addon, conf);
-            }
+            if (wk.fa == 2) walk_scatter<2, KZ, PAIR>(vd, ti, q0, kz, gz, wk, ur, uw, addon, conf);
+            else if (wk.fa == 1) walk_scatter<1, KZ, PAIR>(vd, ti, q0, kz, gz, wk, ur, uw, addon, conf);
+            else walk_scatter<0, KZ, PAIR>(vd, ti, q0, kz, gz, wk, ur, uw, addon, conf);
         }
     } else {
         const int zl = threadIdx.x & 7, zeta = zl - kz;
@@ -523,36 +652,146 @@ __global__ void __launch_bounds__(256) k_adjoint(VolDims vd, const int32_t *__re
 }
 
 // ----------------------------------------------------------------- K6a --
-// NCC moments: simulated pixel values (kept for K6b) and per-tile sums
-// {N, sum y, sum s, sum y^2, sum s^2, sum y s} accumulated in float64 per
-// thread (the variances are differences of these sums, and a constant patch
-// must come out with a variance that the degeneracy test recognises).
+// Trilinear value and its gradient (voxel units) from one set of 8 loads.
+__device__ __forceinline__ float tri_grad(const float *__restrict__ x, const VolDims &vd, unsigned qx,
+                                         unsigned qy, unsigned qz, float gr[3])
+{
+    int bx, by, bz;
+    float fx, fy, fz;
+    split(qx, vd.nx, bx, fx);
+    split(qy, vd.ny, by, fy);
+    split(qz, vd.nz, bz, fz);
+    const size_t nxy = (size_t)vd.nx * vd.ny;
+    const float *b = x + (size_t)bz * nxy + (size_t)by * vd.nx + bx;
+    float v000 = __ldg(b), v100 = __ldg(b + 1);
+    float v010 = __ldg(b + vd.nx), v110 = __ldg(b + vd.nx + 1);
+    float v001 = __ldg(b + nxy), v101 = __ldg(b + nxy + 1);
+    float v011 = __ldg(b + nxy + vd.nx), v111 = __ldg(b + nxy + vd.nx + 1);
+    float dx00 = v100 - v000, dx10 = v110 - v010, dx01 = v101 - v001, dx11 = v111 - v011;
+    float c00 = fmaf(fx, dx00, v000), c10 = fmaf(fx, dx10, v010);
+    float c01 = fmaf(fx, dx01, v001), c11 = fmaf(fx, dx11, v011);
+    float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
+    float gx0 = fmaf(fy, dx10 - dx00, dx00), gx1 = fmaf(fy, dx11 - dx01, dx01);
+    gr[0] = fmaf(fz, gx1 - gx0, gx0);
+    gr[1] = fmaf(fz, (c11 - c01) - (c10 - c00), c10 - c00);
+    gr[2] = c1 - c0;
+    return fmaf(fz, c1 - c0, c0);
+}
+
+// NCC moments of a tile: simulated pixel values (kept for K6b) and the sums
+// {N, sum y, sum s, sum y^2, sum s^2, sum y s} (float64 per thread: the
+// variances are differences of these sums and a constant patch must come
+// out degenerate).  With gbuf, the same gather pass also computes the
+// trilinear gradient of every sample and streams, per lattice point,
+// GA = sum g_z grad and GB = sum g_z zeta grad (3 planes each, Lmax apart)
+// to gbuf for K6b, which therefore gathers nothing.
 template <int KXY, int KZ>
 __global__ void __launch_bounds__(256) k_ncc_moments(const float *__restrict__ x, VolDims vd,
                                                      const int32_t *__restrict__ desc,
                                                      const int32_t *__restrict__ fix, PsfTab psf,
-                                                     Tiling tl, const float *__restrict__ y,
+                                                     Tiling tl, long long tile_base,
+                                                     const float *__restrict__ y,
                                                      const int32_t *__restrict__ active,
                                                      float *__restrict__ s_buf,
                                                      uint8_t *__restrict__ v_buf,
-                                                     double *__restrict__ part)
+                                                     double *__restrict__ part,
+                                                     float *__restrict__ gbuf, int Lmax)
 {
     extern __shared__ float sm[];
     __shared__ double red[32 * 6];
     const int kxy = KXY >= 0 ? KXY : psf.kxy;
+    const int kz = KZ >= 0 ? KZ : psf.kz;
+    const long long gid = tile_base + blockIdx.x;
     TileInfo ti;
-    bool has = tile_setup(desc, fix, tl, kxy, ti);
-    double *pt = part + (size_t)blockIdx.x * kPartStride;
+    bool has = tile_setup_at(gid, desc, fix, tl, kxy, ti);
+    double *pt = part + (size_t)gid * kPartStride;
     if (!has || (active && !active[ti.p])) {
         if (threadIdx.x < kPartStride) pt[threadIdx.x] = 0.0;
         return;
     }
     float *A = sm, *B = sm + ti.L;
-    if (ti.ok) {
-        lattice_forward<KZ>(x, vd, ti, kxy, psf.kz, psf.gz[ti.stack],
-                            pick_order(ti, KZ >= 0 ? KZ : psf.kz), A, B);
+    const float *gz = psf.gz[ti.stack];
+    float *G = gbuf ? gbuf + (size_t)blockIdx.x * 6 * Lmax : nullptr;
+    const int order = ti.ok ? pick_order(ti, kz) : kAlongCol;
+    if (!G) {
+        if (ti.ok) {
+            lattice_forward<KZ>(x, vd, ti, kxy, kz, gz, order, A, B);
+        } else {
+            for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) A[lp] = B[lp] = 0.f;
+        }
+    } else if (order != kAlongZeta) {
+        for (int it = threadIdx.x; it < ti.L; it += blockDim.x) {
+            int li, lj;
+            lattice_coords(ti, order, it, li, lj);
+            float a = 0.f, b = 0.f, ga[3] = {0.f, 0.f, 0.f}, gb[3] = {0.f, 0.f, 0.f};
+            if (ti.ok) {
+                unsigned q0[3];
+                lattice_pos(ti, kxy, li, lj, q0);
+#pragma unroll
+                for (int z = -kz; z <= kz; ++z) {
+                    unsigned qx = q0[0] + (unsigned)z * ti.ez[0];
+                    unsigned qy = q0[1] + (unsigned)z * ti.ez[1];
+                    unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
+                    if (!inside(vd, qx, qy, qz)) continue;
+                    float gr[3];
+                    const float w = gz[z + kz];
+                    a = fmaf(w, tri_grad(x, vd, qx, qy, qz, gr), a);
+                    b += w;
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        ga[r] = fmaf(w, gr[r], ga[r]);
+                        gb[r] = fmaf(w * (float)z, gr[r], gb[r]);
+                    }
+                }
+            }
+            const int si = lj * ti.Lw + li;
+            A[si] = a;
+            B[si] = b;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                G[r * Lmax + si] = ga[r];
+                G[(3 + r) * Lmax + si] = gb[r];
+            }
+        }
     } else {
-        for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) A[lp] = B[lp] = 0.f;
+        const int zl = threadIdx.x & 7, zeta = zl - kz;
+        const bool zon = zl <= 2 * kz;
+        const float w = zon ? gz[zl] : 0.f;
+        const int ngrp = blockDim.x >> 3;
+        for (int base = 0; base < ti.L; base += ngrp) {
+            const int lp = base + (threadIdx.x >> 3);
+            float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (zon && lp < ti.L) {
+                unsigned q[3];
+                lattice_pos(ti, kxy, lp % ti.Lw, lp / ti.Lw, q);
+                unsigned qx = q[0] + (unsigned)zeta * ti.ez[0];
+                unsigned qy = q[1] + (unsigned)zeta * ti.ez[1];
+                unsigned qz = q[2] + (unsigned)zeta * ti.ez[2];
+                if (inside(vd, qx, qy, qz)) {
+                    float gr[3];
+                    v[0] = w * tri_grad(x, vd, qx, qy, qz, gr);
+                    v[1] = w;
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        v[2 + r] = w * gr[r];
+                        v[5 + r] = v[2 + r] * (float)zeta;
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+#pragma unroll
+                for (int o = 1; o < 8; o <<= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+            if (zl == 0 && lp < ti.L) {
+                A[lp] = v[0];
+                B[lp] = v[1];
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    G[r * Lmax + lp] = v[2 + r];
+                    G[(3 + r) * Lmax + lp] = v[5 + r];
+                }
+            }
+        }
     }
     __syncthreads();
     double m[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -562,12 +801,12 @@ __global__ void __launch_bounds__(256) k_ncc_moments(const float *__restrict__ x
         float num = inplane(A, ti.Lw, kxy, psf.gxy, ci, cj);
         float den = inplane(B, ti.Lw, kxy, psf.gxy, ci, cj);
         bool v = den > 0.f;
-        float s = v ? num / den : 0.f;
+        float sv = v ? num / den : 0.f;
         size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
-        s_buf[o] = s;
+        s_buf[o] = sv;
         v_buf[o] = v ? 1 : 0;
         if (v) {
-            double a = (double)__ldg(y + o), b = (double)s;
+            double a = (double)__ldg(y + o), b = (double)sv;
             m[0] += 1.0;
             m[1] += a;
             m[2] += b;
@@ -576,11 +815,10 @@ __global__ void __launch_bounds__(256) k_ncc_moments(const float *__restrict__ x
             m[5] = fma(a, b, m[5]);
         }
     }
-    double *acc = m;
-    block_sum<6>(acc, red);
+    block_sum<6>(m, red);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k) pt[k] = acc[k];
+        for (int k = 0; k < 6; ++k) pt[k] = m[k];
         pt[6] = pt[7] = 0.0;
     }
 }
@@ -675,37 +913,38 @@ __device__ void pose_jacobian(const DevGeom *__restrict__ g, const int32_t *d, c
 }
 
 // ----------------------------------------------------------------- K6b --
-// Pose gradient of NCC.  dNCC/ds_i = ((y_i - my)/sd - ncc (s_i - ms)/vs)/N;
-// pixel coefficient c_i = dNCC/ds_i / den_i; transposed in-plane taps give
-// lattice weights U; every in-volume sample adds U g_z (grad_tri . dq/dtheta_k).
-// dq/dtheta: translations = columns of the linear part of world_to_voxel;
-// rotation k: W R_k' S_lin [i - (w-1)/2, j - (h-1)/2, zeta zs] * pi/180 with
-// R_k' = d(Rz Ry Rx)/d angle_k (radians).
+// Pose gradient of NCC from the gradient sums K6a streamed to gbuf.
+// dNCC/ds_i = ((y_i - my)/sd - ncc (s_i - ms)/vs)/N; pixel coefficient
+// c_i = dNCC/ds_i / den_i; the transposed in-plane taps give lattice weights
+// U; the moments M1 = sum U GA (i - cu), M2 = sum U GA (j - cv),
+// M3 = sum U GA, M4 = sum U GB (Kahan-compensated float32 per thread, float64
+// across threads) contracted with the pose Jacobian give dNCC/dtheta.
 template <int KXY, int KZ>
-__global__ void __launch_bounds__(256) k_ncc_grad(const float *__restrict__ x, VolDims vd,
-                                                  const DevGeom *__restrict__ g,
+__global__ void __launch_bounds__(256) k_ncc_grad(VolDims vd, const DevGeom *__restrict__ g,
                                                   const int32_t *__restrict__ desc,
                                                   const int32_t *__restrict__ fix, PsfTab psf,
-                                                  Tiling tl, const float *__restrict__ y,
+                                                  Tiling tl, long long tile_base,
+                                                  const float *__restrict__ y,
                                                   const double *__restrict__ poses,
                                                   const int32_t *__restrict__ active,
                                                   const float *__restrict__ s_buf,
                                                   const uint8_t *__restrict__ v_buf,
                                                   const double *__restrict__ part,
-                                                  double *__restrict__ gpart, int min_valid)
+                                                  double *__restrict__ gpart,
+                                                  const float *__restrict__ gbuf, int Lmax,
+                                                  int min_valid)
 {
     extern __shared__ float sm[];
     __shared__ double red[32 * 12];
-    // per parameter k: dq/dtheta_k = J1 (i - cu) + J2 (j - cv) + J4 zeta + J3 (voxel units),
-    // stored as jc[k] = {J1(3), J2(3), J4(3), J3(3)}; (i, j) patch pixel, (cu, cv) its centre
     __shared__ double jc[6][12];
-    __shared__ double sh_stats[4];
+    __shared__ float sh_coef[4];
     __shared__ int sh_ok;
     const int kxy = KXY >= 0 ? KXY : psf.kxy;
     const int kz = KZ >= 0 ? KZ : psf.kz;
+    const long long gid = tile_base + blockIdx.x;
     TileInfo ti;
-    bool has = tile_setup(desc, fix, tl, kxy, ti);
-    double *gp = gpart + (size_t)blockIdx.x * kPartStride;
+    bool has = tile_setup_at(gid, desc, fix, tl, kxy, ti);
+    double *gp = gpart + (size_t)gid * kPartStride;
     if (!has || !ti.ok || (active && !active[ti.p])) {
         if (threadIdx.x < kPartStride) gp[threadIdx.x] = 0.0;
         return;
@@ -714,15 +953,12 @@ __global__ void __launch_bounds__(256) k_ncc_grad(const float *__restrict__ x, V
         double ncc, my, ms, sd, vs, n;
         bool ok = ncc_from_moments(part, ti.p, tl.tpp, min_valid, ncc, my, ms, sd, vs, n);
         sh_ok = ok;
-        sh_stats[0] = ncc;
-        sh_stats[1] = my;
-        sh_stats[2] = ms;
-        sh_stats[3] = 0.0;
         if (ok) {
             pose_jacobian(g, desc + 8 * (size_t)ti.p, poses + 6 * (size_t)ti.p, jc);
-            // coefficient scale: 1/(N sd), ncc/(N vs)
-            sh_stats[3] = 1.0 / (n * sd);
-            sh_stats[0] = ncc / (n * vs);
+            sh_coef[0] = (float)(1.0 / (n * sd));
+            sh_coef[1] = (float)(ncc / (n * vs));
+            sh_coef[2] = (float)my;
+            sh_coef[3] = (float)ms;
         }
     }
     __syncthreads();
@@ -732,23 +968,23 @@ __global__ void __launch_bounds__(256) k_ncc_grad(const float *__restrict__ x, V
     }
     const int np = ti.tw * ti.th;
     float *U = sm, *C = sm + ti.L;
-    const float *gzp = psf.gz[ti.stack];
-    lattice_forward<KZ>(nullptr, vd, ti, kxy, kz, gzp, kAlongCol, nullptr, U);
+    lattice_forward<KZ>(nullptr, vd, ti, kxy, kz, psf.gz[ti.stack], kAlongCol, nullptr, U);
     __syncthreads();
-    const float a_sc = (float)sh_stats[3], b_sc = (float)sh_stats[0];
-    const float my = (float)sh_stats[1], ms = (float)sh_stats[2];
+    const float a_sc = sh_coef[0], b_sc = sh_coef[1], my = sh_coef[2], ms = sh_coef[3];
     for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
         int ci = pp % ti.tw, cj = pp / ti.tw;
         size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
         float c = 0.f;
         if (v_buf[o]) {
             float den = inplane(U, ti.Lw, kxy, psf.gxy, ci, cj);
-            float dn = a_sc * (__ldg(y + o) - my) - b_sc * (s_buf[o] - ms);
-            c = dn / den;
+            c = (a_sc * (__ldg(y + o) - my) - b_sc * (s_buf[o] - ms)) / den;
         }
         C[pp] = c;
     }
     __syncthreads();
+    const float *G = gbuf + (size_t)blockIdx.x * 6 * Lmax;
+    const float cu = 0.5f * (float)(ti.w - 1), cv = 0.5f * (float)(ti.h - 1);
+    KahanSum ks[12];
     for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) {
         int li = lp % ti.Lw, lj = lp / ti.Lw;
         float u = 0.f;
@@ -763,112 +999,29 @@ __global__ void __launch_bounds__(256) k_ncc_grad(const float *__restrict__ x, V
             }
             u = fmaf(psf.gxy[dj + kxy], rr, u);
         }
-        U[lp] = u;   // each lp written by its own thread; phase-0 data no longer read
-    }
-    __syncthreads();
-    // Gradient pass in the tile's traversal order.  With w = U g_z and the
-    // trilinear gradient gr of each in-volume sample, accumulate the moments
-    // M1 = sum w gr (i - cu), M2 = sum w gr (j - cv), M3 = sum w gr,
-    // M4 = sum w gr zeta (Kahan-compensated float32 per thread, float64 across
-    // threads); the gradient is their contraction with the pose Jacobian.
-    KahanSum ks[12];
-    const size_t nxy = (size_t)vd.nx * vd.ny;
-    const float cu = 0.5f * (float)(ti.w - 1), cv = 0.5f * (float)(ti.h - 1);
-    auto grad_at = [&](unsigned qx, unsigned qy, unsigned qz, float gr[3]) {
-        int bx, by, bz;
-        float fx, fy, fz;
-        split(qx, vd.nx, bx, fx);
-        split(qy, vd.ny, by, fy);
-        split(qz, vd.nz, bz, fz);
-        const float *b = x + (size_t)bz * nxy + (size_t)by * vd.nx + bx;
-        float v000 = __ldg(b), v100 = __ldg(b + 1);
-        float v010 = __ldg(b + vd.nx), v110 = __ldg(b + vd.nx + 1);
-        float v001 = __ldg(b + nxy), v101 = __ldg(b + nxy + 1);
-        float v011 = __ldg(b + nxy + vd.nx), v111 = __ldg(b + nxy + vd.nx + 1);
-        gr[0] = (1.f - fy) * (1.f - fz) * (v100 - v000) + fy * (1.f - fz) * (v110 - v010) +
-                (1.f - fy) * fz * (v101 - v001) + fy * fz * (v111 - v011);
-        gr[1] = (1.f - fx) * (1.f - fz) * (v010 - v000) + fx * (1.f - fz) * (v110 - v100) +
-                (1.f - fx) * fz * (v011 - v001) + fx * fz * (v111 - v101);
-        gr[2] = (1.f - fx) * (1.f - fy) * (v001 - v000) + fx * (1.f - fy) * (v101 - v100) +
-                (1.f - fx) * fy * (v011 - v010) + fx * fy * (v111 - v110);
-    };
-    auto add_moments = [&](const float s0[3], const float sz[3], float di, float dj) {
+        if (u == 0.f) continue;
+        const float di = (float)(ti.i0 - kxy + li) - cu, dj = (float)(ti.j0 - kxy + lj) - cv;
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-            ks[r].add(s0[r] * di);
-            ks[3 + r].add(s0[r] * dj);
-            ks[6 + r].add(sz[r]);
-            ks[9 + r].add(s0[r]);
-        }
-    };
-    const int order = pick_order(ti, kz);
-    if (order != kAlongZeta) {
-        for (int it = threadIdx.x; it < ti.L; it += blockDim.x) {
-            int li, lj;
-            lattice_coords(ti, order, it, li, lj);
-            float u = U[lj * ti.Lw + li];
-            if (u == 0.f) continue;
-            unsigned q0[3];
-            lattice_pos(ti, kxy, li, lj, q0);
-            float s0[3] = {0.f, 0.f, 0.f}, sz[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-            for (int z = -kz; z <= kz; ++z) {
-                unsigned qx = q0[0] + (unsigned)z * ti.ez[0];
-                unsigned qy = q0[1] + (unsigned)z * ti.ez[1];
-                unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
-                const bool in = inside(vd, qx, qy, qz);
-                const float w = in ? u * gzp[z + kz] : 0.f;
-                float gr[3];
-                grad_at(in ? qx : 0u, in ? qy : 0u, in ? qz : 0u, gr);
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    s0[r] = fmaf(w, gr[r], s0[r]);
-                    sz[r] = fmaf(w * (float)z, gr[r], sz[r]);
-                }
-            }
-            add_moments(s0, sz, (float)(ti.i0 - kxy + li) - cu, (float)(ti.j0 - kxy + lj) - cv);
-        }
-    } else {
-        const int zl = threadIdx.x & 7, zeta = zl - kz;
-        if (zl <= 2 * kz) {
-            const float g = gzp[zl];
-            for (int lp = threadIdx.x >> 3; lp < ti.L; lp += blockDim.x >> 3) {
-                float u = U[lp];
-                if (u == 0.f) continue;
-                int li = lp % ti.Lw, lj = lp / ti.Lw;
-                unsigned q[3];
-                lattice_pos(ti, kxy, li, lj, q);
-                unsigned qx = q[0] + (unsigned)zeta * ti.ez[0];
-                unsigned qy = q[1] + (unsigned)zeta * ti.ez[1];
-                unsigned qz = q[2] + (unsigned)zeta * ti.ez[2];
-                if (!inside(vd, qx, qy, qz)) continue;
-                float gr[3], s0[3], sz[3];
-                grad_at(qx, qy, qz, gr);
-                const float w = u * g;
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    s0[r] = w * gr[r];
-                    sz[r] = s0[r] * (float)zeta;
-                }
-                add_moments(s0, sz, (float)(ti.i0 - kxy + li) - cu, (float)(ti.j0 - kxy + lj) - cv);
-            }
+            const float s0 = u * __ldg(G + r * Lmax + lp);
+            ks[r].add(s0 * di);
+            ks[3 + r].add(s0 * dj);
+            ks[6 + r].add(u * __ldg(G + (3 + r) * Lmax + lp));
+            ks[9 + r].add(s0);
         }
     }
     double mom[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) mom[k] = ks[k].value();
     block_sum<12>(mom, red);
-    double dacc[6];
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
         for (int k = 0; k < 6; ++k) {
             double gsum = 0.0;
             for (int r = 0; r < 3; ++r)
                 gsum += jc[k][r] * mom[r] + jc[k][3 + r] * mom[3 + r] + jc[k][6 + r] * mom[6 + r] +
                         jc[k][9 + r] * mom[9 + r];
-            dacc[k] = gsum;
+            gp[k] = gsum;
         }
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < 6; ++k) gp[k] = dacc[k];
         gp[6] = gp[7] = 0.0;
     }
 }
@@ -966,30 +1119,50 @@ cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &t
                             int nz, const float *x, const float *y, const int32_t *desc,
                             const int32_t *fix, const double *poses, int n, float *s_buf,
                             uint8_t *v_buf, double *part, double *gpart, const int32_t *active,
-                            int min_valid, cudaStream_t st)
+                            int min_valid, float *gbuf, long long gbuf_tiles, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     VolDims vd = vol_dims(nx, ny, nz);
     size_t smem = smem_forward(tl, psf.kxy);
-    size_t smem2 = (size_t)((tl.T + 2 * psf.kxy) * (tl.T + 2 * psf.kxy) + tl.T * tl.T) * sizeof(float);
-    dim3 grid((unsigned)n * tl.tpp), block(256);
+    const int Lmax = (tl.T + 2 * psf.kxy) * (tl.T + 2 * psf.kxy);
+    size_t smem2 = (size_t)(Lmax + tl.T * tl.T) * sizeof(float);
+    const long long total = (long long)n * tl.tpp;
+    // chunks of whole patches that fit the gradient scratch
+    long long chunk = gpart ? (gbuf_tiles / tl.tpp) * tl.tpp : total;
+    if (chunk <= 0) return cudaErrorInvalidValue;
+    const bool fast = psf.kxy == 1 && psf.kz == 3;
     cudaError_t e;
-    if (psf.kxy == 1 && psf.kz == 3) {
+    if (fast) {
         if ((e = prep(k_ncc_moments<1, 3>, smem)) != cudaSuccess) return e;
         if ((e = prep(k_ncc_grad<1, 3>, smem2)) != cudaSuccess) return e;
-        k_ncc_moments<1, 3><<<grid, block, smem, st>>>(x, vd, desc, fix, psf, tl, y, active, s_buf, v_buf, part);
-        if (gpart)
-            k_ncc_grad<1, 3><<<grid, block, smem2, st>>>(x, vd, g, desc, fix, psf, tl, y, poses, active,
-                                                         s_buf, v_buf, part, gpart, min_valid);
     } else {
         if ((e = prep(k_ncc_moments<-1, -1>, smem)) != cudaSuccess) return e;
         if ((e = prep(k_ncc_grad<-1, -1>, smem2)) != cudaSuccess) return e;
-        k_ncc_moments<-1, -1><<<grid, block, smem, st>>>(x, vd, desc, fix, psf, tl, y, active, s_buf, v_buf, part);
-        if (gpart)
-            k_ncc_grad<-1, -1><<<grid, block, smem2, st>>>(x, vd, g, desc, fix, psf, tl, y, poses, active,
-                                                           s_buf, v_buf, part, gpart, min_valid);
+    }
+    for (long long base = 0; base < total; base += chunk) {
+        unsigned grid = (unsigned)((total - base) < chunk ? (total - base) : chunk);
+        float *gb = gpart ? gbuf : nullptr;
+        if (fast)
+            k_ncc_moments<1, 3><<<grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, base, y, active, s_buf,
+                                                         v_buf, part, gb, Lmax);
+        else
+            k_ncc_moments<-1, -1><<<grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, base, y, active,
+                                                           s_buf, v_buf, part, gb, Lmax);
+        if (!gpart) continue;
+        if (fast)
+            k_ncc_grad<1, 3><<<grid, 256, smem2, st>>>(vd, g, desc, fix, psf, tl, base, y, poses, active,
+                                                       s_buf, v_buf, part, gpart, gbuf, Lmax, min_valid);
+        else
+            k_ncc_grad<-1, -1><<<grid, 256, smem2, st>>>(vd, g, desc, fix, psf, tl, base, y, poses, active,
+                                                         s_buf, v_buf, part, gpart, gbuf, Lmax, min_valid);
     }
     return cudaGetLastError();
+}
+
+// Tiles of gradient scratch needed per chunk (float planes of the lattice).
+size_t ncc_gbuf_floats_per_tile(const Tiling &tl, int kxy)
+{
+    return 6 * (size_t)(tl.T + 2 * kxy) * (tl.T + 2 * kxy);
 }
 
 cudaError_t launch_ncc_finish(const int32_t *desc, const float *y, int n, const Tiling &tl,

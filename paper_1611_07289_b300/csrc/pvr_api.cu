@@ -59,6 +59,8 @@ struct pvr_ctx {
     float *s_buf = nullptr, *e_buf = nullptr, *p_buf = nullptr;
     uint8_t *v_buf = nullptr, *valid_buf = nullptr, *mask_tmp = nullptr;
     float2 *acc2 = nullptr;   // interleaved (addon, conf) accumulator, one pair per voxel
+    float *gbuf = nullptr;    // NCC gradient scratch (per-lattice-point gradient sums)
+    long long gbuf_tiles = 0;
     int32_t *keep = nullptr;
     int64_t keep_cap = 0;
     unsigned *imax_key = nullptr;
@@ -167,7 +169,7 @@ void free_all(pvr_ctx *c)
     void *ptrs[] = {c->d_geom, c->fix, c->part, c->gpart, c->pstat, c->pbar, c->wsc, c->emblk, c->elig,
                     c->err, c->best, c->gbest, c->nbest, c->trial, c->delta, c->ncc_tmp,
                     c->grad_tmp, c->active, c->s_buf, c->e_buf, c->p_buf, c->v_buf,
-                    c->valid_buf, c->mask_tmp, c->acc2, c->keep, c->imax_key,
+                    c->valid_buf, c->mask_tmp, c->acc2, c->gbuf, c->keep, c->imax_key,
                     c->counts, c->metric_scr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -323,6 +325,14 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
     ALLOC(c->valid_buf, NP);
     ALLOC(c->mask_tmp, P);
     ALLOC(c->acc2, (size_t)c->nvox);
+    {
+        // gradient scratch: all tiles if they fit in 2.5 GB, else chunks of whole patches
+        size_t per = ncc_gbuf_floats_per_tile(tl, prm->psf_kxy) * sizeof(float);
+        long long want = (long long)P * tl.tpp, cap = (long long)((size_t)2560 << 20) / (long long)per;
+        if (cap < tl.tpp) cap = tl.tpp;
+        c->gbuf_tiles = want < cap ? want : cap;
+        ALLOC(c->gbuf, (size_t)c->gbuf_tiles * per / sizeof(float));
+    }
     ALLOC(c->keep, (size_t)c->keep_cap);
     ALLOC(c->imax_key, 1);
     ALLOC(c->counts, 4);
@@ -540,7 +550,8 @@ int pvr_ncc_grad(pvr_ctx *c, const float *x, const float *y, const pvr_patches *
     Tiling tl = make_tiling(ms);
     CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, y,
                              pp->desc, c->fix, poses, pp->n, c->s_buf, c->v_buf, c->part,
-                             grad ? c->gpart : nullptr, nullptr, c->prm.reg_min_valid, st),
+                             grad ? c->gpart : nullptr, nullptr, c->prm.reg_min_valid, c->gbuf,
+                             c->gbuf_tiles, st),
              "ncc_grad");
     CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(pp->desc, y, pp->n, tl, c->part, c->gpart, c->prm.reg_min_valid, ncc,
                                grad, st),
@@ -563,7 +574,8 @@ static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_p
         if (rc) return rc;
         CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, y,
                                  pp->desc, c->fix, c->trial, n, c->s_buf, c->v_buf, c->part,
-                                 c->gpart, c->active, c->prm.reg_min_valid, st),
+                                 c->gpart, c->active, c->prm.reg_min_valid, c->gbuf, c->gbuf_tiles,
+                                 st),
                  "ncc_grad");
         CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(pp->desc, y, n, tl, c->part, c->gpart, c->prm.reg_min_valid,
                                    c->ncc_tmp, c->grad_tmp, st),

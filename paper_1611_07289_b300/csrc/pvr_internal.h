@@ -66,11 +66,15 @@ cudaError_t launch_volume_update(float *x, float *addon, float *conf, int64_t nv
                                  float conf_eps, int clear, int init_mode, cudaStream_t st);
 
 
+// NCC moments (+ gradient when gpart != null) of every patch; the gradient
+// pass streams per-lattice-point gradient sums through gbuf, processed in
+// chunks of whole patches of at most gbuf_tiles tiles.
 cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &tl, int nx, int ny,
                             int nz, const float *x, const float *y, const int32_t *desc,
                             const int32_t *fix, const double *poses, int n, float *s_buf,
                             uint8_t *v_buf, double *part, double *gpart, const int32_t *active,
-                            int min_valid, cudaStream_t st);
+                            int min_valid, float *gbuf, long long gbuf_tiles, cudaStream_t st);
+size_t ncc_gbuf_floats_per_tile(const Tiling &tl, int kxy);
 
 cudaError_t launch_ncc_finish(const int32_t *desc, const float *y, int n, const Tiling &tl,
                               const double *part, const double *gpart, int min_valid, double *ncc,
