@@ -210,10 +210,23 @@ __global__ void __launch_bounds__(256) k_em_estep(const float *__restrict__ y,
         }
         p_out[o] = pv;
     }
-    double a[4] = {(double)sp, (double)spe2, (double)sp2, (double)nv};
-    block_reduce<4>(a, sh, 0);
+    // float32 tile sums (at most a 64 x 64 tile: counts exact, sums to ~1e-7)
+    float a[4] = {sp, spe2, sp2, nv};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_xor_sync(0xffffffffu, a[k], o);
+    float *fs = reinterpret_cast<float *>(sh);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+        for (int k = 0; k < 4; ++k) fs[wid * 4 + k] = a[k];
+    __syncthreads();
     if (threadIdx.x == 0)
-        for (int k = 0; k < 4; ++k) pt[4 + k] = a[k];
+        for (int k = 0; k < 4; ++k) {
+            float t = 0.f;
+            for (int w = 0; w < nw; ++w) t += fs[w * 4 + k];
+            pt[4 + k] = (double)t;
+        }
 }
 
 // Steps 5-7: M-step, patch potentials and patch classification, spread over

@@ -438,6 +438,50 @@ __device__ __forceinline__ void block_sum(double *v, double *red)
     __syncthreads();
 }
 
+// Block-wide float32 sums of NV values; result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum_f(float *v, float *red)
+{
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+    __syncthreads();
+    if (lane == 0)
+        for (int k = 0; k < NV; ++k) red[wid * NV + k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NV; ++k) {
+            float s = 0.f;
+            for (int w = 0; w < nw; ++w) s += red[w * NV + k];
+            v[k] = s;
+        }
+    __syncthreads();
+}
+
+// Float-float accumulator: an unevaluated sum hi + lo of float32s, updated
+// with error-free transformations (two-sum; exact products by fma), so sums
+// of products keep about 44 bits -- enough for variances computed as
+// differences of raw moments, at float32 speed.
+struct FFSum {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float a)
+    {
+        float s = hi + a;
+        float bb = s - hi;
+        float err = (hi - (s - bb)) + (a - bb);
+        hi = s;
+        lo += err;
+    }
+    __device__ __forceinline__ void add_prod(float a, float b)
+    {
+        float p = a * b;
+        float e = fmaf(a, b, -p);
+        add(p);
+        lo += e;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // ------------------------------------------------------------------ K2 --
 // Forward model.  y == null: write sim, valid.  y != null: write the
 // residual e = y - sim (0 where invalid) and valid, plus per-tile partials
@@ -452,7 +496,7 @@ __global__ void __launch_bounds__(256) k_simulate(const float *__restrict__ x, V
                                                   double *__restrict__ part)
 {
     extern __shared__ float sm[];
-    __shared__ double red[32 * 4];
+    __shared__ float fred[32 * 2];
     const int kxy = KXY >= 0 ? KXY : psf.kxy;
     TileInfo ti;
     bool has = tile_setup(desc, fix, tl, kxy, ti);
@@ -494,7 +538,7 @@ __global__ void __launch_bounds__(256) k_simulate(const float *__restrict__ x, V
         valid[o] = v ? 1 : 0;
     }
     if (part) {
-        double acc[2] = {(double)nval, (double)se2};
+        float acc[2] = {(float)nval, se2};
         float mn = warp_min(emin), mx = warp_max(emax);
         __shared__ float rmn[32], rmx[32];
         int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -502,7 +546,7 @@ __global__ void __launch_bounds__(256) k_simulate(const float *__restrict__ x, V
             rmn[wid] = mn;
             rmx[wid] = mx;
         }
-        block_sum<2>(acc, red);
+        block_sum_f<2>(acc, fred);
         if (threadIdx.x == 0) {
             float a = INFINITY, b = -INFINITY;
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
@@ -510,8 +554,8 @@ __global__ void __launch_bounds__(256) k_simulate(const float *__restrict__ x, V
                 b = fmaxf(b, rmx[w]);
             }
             double *pt = part + (size_t)blockIdx.x * kPartStride;
-            pt[0] = acc[0];
-            pt[1] = acc[1];
+            pt[0] = (double)acc[0];
+            pt[1] = (double)acc[1];
             pt[2] = (double)a;
             pt[3] = (double)b;
         }
@@ -794,7 +838,8 @@ __global__ void __launch_bounds__(256) k_ncc_moments(const float *__restrict__ x
         }
     }
     __syncthreads();
-    double m[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    FFSum f1, f2, f3, f4, f5;
+    int cnt = 0;
     const int np = ti.tw * ti.th;
     for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
         int ci = pp % ti.tw, cj = pp / ti.tw;
@@ -806,15 +851,16 @@ __global__ void __launch_bounds__(256) k_ncc_moments(const float *__restrict__ x
         s_buf[o] = sv;
         v_buf[o] = v ? 1 : 0;
         if (v) {
-            double a = (double)__ldg(y + o), b = (double)sv;
-            m[0] += 1.0;
-            m[1] += a;
-            m[2] += b;
-            m[3] = fma(a, a, m[3]);
-            m[4] = fma(b, b, m[4]);
-            m[5] = fma(a, b, m[5]);
+            float a = __ldg(y + o);
+            ++cnt;
+            f1.add(a);
+            f2.add(sv);
+            f3.add_prod(a, a);
+            f4.add_prod(sv, sv);
+            f5.add_prod(a, sv);
         }
     }
+    double m[6] = {(double)cnt, f1.value(), f2.value(), f3.value(), f4.value(), f5.value()};
     block_sum<6>(m, red);
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -917,8 +963,9 @@ __device__ void pose_jacobian(const DevGeom *__restrict__ g, const int32_t *d, c
 // dNCC/ds_i = ((y_i - my)/sd - ncc (s_i - ms)/vs)/N; pixel coefficient
 // c_i = dNCC/ds_i / den_i; the transposed in-plane taps give lattice weights
 // U; the moments M1 = sum U GA (i - cu), M2 = sum U GA (j - cv),
-// M3 = sum U GA, M4 = sum U GB (Kahan-compensated float32 per thread, float64
-// across threads) contracted with the pose Jacobian give dNCC/dtheta.
+// M3 = sum U GA, M4 = sum U GB (float32 per thread over its few lattice
+// points, float64 across threads), written per tile; k_ncc_finish contracts
+// them with the pose Jacobian once per patch.
 template <int KXY, int KZ>
 __global__ void __launch_bounds__(256) k_ncc_grad(VolDims vd, const DevGeom *__restrict__ g,
                                                   const int32_t *__restrict__ desc,
@@ -936,7 +983,6 @@ __global__ void __launch_bounds__(256) k_ncc_grad(VolDims vd, const DevGeom *__r
 {
     extern __shared__ float sm[];
     __shared__ double red[32 * 12];
-    __shared__ double jc[6][12];
     __shared__ float sh_coef[4];
     __shared__ int sh_ok;
     const int kxy = KXY >= 0 ? KXY : psf.kxy;
@@ -944,9 +990,9 @@ __global__ void __launch_bounds__(256) k_ncc_grad(VolDims vd, const DevGeom *__r
     const long long gid = tile_base + blockIdx.x;
     TileInfo ti;
     bool has = tile_setup_at(gid, desc, fix, tl, kxy, ti);
-    double *gp = gpart + (size_t)gid * kPartStride;
+    double *gp = gpart + (size_t)gid * kGradStride;
     if (!has || !ti.ok || (active && !active[ti.p])) {
-        if (threadIdx.x < kPartStride) gp[threadIdx.x] = 0.0;
+        if (threadIdx.x < kGradStride) gp[threadIdx.x] = 0.0;
         return;
     }
     if (threadIdx.x == 0) {
@@ -954,7 +1000,6 @@ __global__ void __launch_bounds__(256) k_ncc_grad(VolDims vd, const DevGeom *__r
         bool ok = ncc_from_moments(part, ti.p, tl.tpp, min_valid, ncc, my, ms, sd, vs, n);
         sh_ok = ok;
         if (ok) {
-            pose_jacobian(g, desc + 8 * (size_t)ti.p, poses + 6 * (size_t)ti.p, jc);
             sh_coef[0] = (float)(1.0 / (n * sd));
             sh_coef[1] = (float)(ncc / (n * vs));
             sh_coef[2] = (float)my;
@@ -963,7 +1008,7 @@ __global__ void __launch_bounds__(256) k_ncc_grad(VolDims vd, const DevGeom *__r
     }
     __syncthreads();
     if (!sh_ok) {
-        if (threadIdx.x < kPartStride) gp[threadIdx.x] = 0.0;
+        if (threadIdx.x < kGradStride) gp[threadIdx.x] = 0.0;
         return;
     }
     const int np = ti.tw * ti.th;
@@ -984,7 +1029,9 @@ __global__ void __launch_bounds__(256) k_ncc_grad(VolDims vd, const DevGeom *__r
     __syncthreads();
     const float *G = gbuf + (size_t)blockIdx.x * 6 * Lmax;
     const float cu = 0.5f * (float)(ti.w - 1), cv = 0.5f * (float)(ti.h - 1);
-    KahanSum ks[12];
+    float mo[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) mo[k] = 0.f;
     for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) {
         int li = lp % ti.Lw, lj = lp / ti.Lw;
         float u = 0.f;
@@ -1004,45 +1051,54 @@ __global__ void __launch_bounds__(256) k_ncc_grad(VolDims vd, const DevGeom *__r
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             const float s0 = u * __ldg(G + r * Lmax + lp);
-            ks[r].add(s0 * di);
-            ks[3 + r].add(s0 * dj);
-            ks[6 + r].add(u * __ldg(G + (3 + r) * Lmax + lp));
-            ks[9 + r].add(s0);
+            mo[r] = fmaf(s0, di, mo[r]);
+            mo[3 + r] = fmaf(s0, dj, mo[3 + r]);
+            mo[6 + r] = fmaf(u, __ldg(G + (3 + r) * Lmax + lp), mo[6 + r]);
+            mo[9 + r] += s0;
         }
     }
     double mom[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) mom[k] = ks[k].value();
+    for (int k = 0; k < 12; ++k) mom[k] = (double)mo[k];
     block_sum<12>(mom, red);
     if (threadIdx.x == 0) {
-        for (int k = 0; k < 6; ++k) {
-            double gsum = 0.0;
-            for (int r = 0; r < 3; ++r)
-                gsum += jc[k][r] * mom[r] + jc[k][3 + r] * mom[3 + r] + jc[k][6 + r] * mom[6 + r] +
-                        jc[k][9 + r] * mom[9 + r];
-            gp[k] = gsum;
-        }
-        gp[6] = gp[7] = 0.0;
+        for (int k = 0; k < 12; ++k) gp[k] = mom[k];
+        for (int k = 12; k < kGradStride; ++k) gp[k] = 0.0;
     }
 }
 
-__global__ void k_ncc_finish(int n, int tpp, const int32_t *__restrict__ desc,
-                             const float *__restrict__ y, const double *__restrict__ part,
-                             const double *__restrict__ gpart, int min_valid,
-                             double *__restrict__ ncc, double *__restrict__ grad)
+// Per patch: NCC from the tile moments, and the pose gradient as the
+// contraction of the summed gradient moments with the pose Jacobian.
+__global__ void k_ncc_finish(const DevGeom *__restrict__ g, int n, int tpp,
+                             const int32_t *__restrict__ desc, const double *__restrict__ poses,
+                             const double *__restrict__ part, const double *__restrict__ gpart,
+                             int min_valid, double *__restrict__ ncc, double *__restrict__ grad)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     double v, my, ms, sd, vs, nn;
     bool ok = ncc_from_moments(part, p, tpp, min_valid, v, my, ms, sd, vs, nn);
     ncc[p] = ok ? v : 0.0;
-    if (grad) {
-        for (int k = 0; k < 6; ++k) {
-            double s = 0.0;
-            if (ok)
-                for (int t = 0; t < tpp; ++t) s += gpart[((size_t)p * tpp + t) * kPartStride + k];
-            grad[6 * (size_t)p + k] = s;
-        }
+    if (!grad) return;
+    double *gr = grad + 6 * (size_t)p;
+    if (!ok) {
+        for (int k = 0; k < 6; ++k) gr[k] = 0.0;
+        return;
+    }
+    double mom[12];
+    for (int k = 0; k < 12; ++k) {
+        double s = 0.0;
+        for (int t = 0; t < tpp; ++t) s += gpart[((size_t)p * tpp + t) * kGradStride + k];
+        mom[k] = s;
+    }
+    double jc[6][12];
+    pose_jacobian(g, desc + 8 * (size_t)p, poses + 6 * (size_t)p, jc);
+    for (int k = 0; k < 6; ++k) {
+        double gsum = 0.0;
+        for (int r = 0; r < 3; ++r)
+            gsum += jc[k][r] * mom[r] + jc[k][3 + r] * mom[3 + r] + jc[k][6 + r] * mom[6 + r] +
+                    jc[k][9 + r] * mom[9 + r];
+        gr[k] = gsum;
     }
 }
 
@@ -1165,12 +1221,13 @@ size_t ncc_gbuf_floats_per_tile(const Tiling &tl, int kxy)
     return 6 * (size_t)(tl.T + 2 * kxy) * (tl.T + 2 * kxy);
 }
 
-cudaError_t launch_ncc_finish(const int32_t *desc, const float *y, int n, const Tiling &tl,
-                              const double *part, const double *gpart, int min_valid, double *ncc,
-                              double *grad, cudaStream_t st)
+cudaError_t launch_ncc_finish(const DevGeom *g, const int32_t *desc, const double *poses, int n,
+                              const Tiling &tl, const double *part, const double *gpart,
+                              int min_valid, double *ncc, double *grad, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    k_ncc_finish<<<(n + 127) / 128, 128, 0, st>>>(n, tl.tpp, desc, y, part, gpart, min_valid, ncc, grad);
+    k_ncc_finish<<<(n + 127) / 128, 128, 0, st>>>(g, n, tl.tpp, desc, poses, part, gpart, min_valid,
+                                                  ncc, grad);
     return cudaGetLastError();
 }
 

@@ -303,7 +303,7 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
     ALLOC(c->d_geom, 1);
     ALLOC(c->fix, P * kFixStride);
     ALLOC(c->part, slots);
-    ALLOC(c->gpart, slots);
+    ALLOC(c->gpart, P * (size_t)tl.tpp * kGradStride);
     ALLOC(c->pstat, 8);
     ALLOC(c->pbar, P);
     ALLOC(c->wsc, P);
@@ -553,7 +553,7 @@ int pvr_ncc_grad(pvr_ctx *c, const float *x, const float *y, const pvr_patches *
                              grad ? c->gpart : nullptr, nullptr, c->prm.reg_min_valid, c->gbuf,
                              c->gbuf_tiles, st),
              "ncc_grad");
-    CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(pp->desc, y, pp->n, tl, c->part, c->gpart, c->prm.reg_min_valid, ncc,
+    CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(c->d_geom, pp->desc, poses, pp->n, tl, c->part, c->gpart, c->prm.reg_min_valid, ncc,
                                grad, st),
              "ncc_finish");
     c->launches += pp->n > 0 ? (grad ? 3 : 2) : 0;
@@ -577,7 +577,7 @@ static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_p
                                  c->gpart, c->active, c->prm.reg_min_valid, c->gbuf, c->gbuf_tiles,
                                  st),
                  "ncc_grad");
-        CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(pp->desc, y, n, tl, c->part, c->gpart, c->prm.reg_min_valid,
+        CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(c->d_geom, pp->desc, c->trial, n, tl, c->part, c->gpart, c->prm.reg_min_valid,
                                    c->ncc_tmp, c->grad_tmp, st),
                  "ncc_finish");
         CUDA_TRY_T(PVR_K_REG_STEP, launch_reg_step(c->d_geom, pp->desc, n, ev, ev == n_evals - 1, c->ncc_tmp,

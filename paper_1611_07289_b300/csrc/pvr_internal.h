@@ -11,6 +11,7 @@ namespace pvr {
 constexpr int kFracBits = 20;              // Q11.20 sample coordinates
 constexpr int kFixStride = 16;             // int32 per patch in the fixed table
 constexpr int kPartStride = 8;             // float64 per (patch, tile) partial slot
+constexpr int kGradStride = 16;            // float64 per (patch, tile) gradient-moment slot
 constexpr int kRegStride = 12;             // float64 per patch pose slot
 
 // Geometry as the kernels read it (device memory, copied at context creation).
@@ -76,9 +77,9 @@ cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &t
                             int min_valid, float *gbuf, long long gbuf_tiles, cudaStream_t st);
 size_t ncc_gbuf_floats_per_tile(const Tiling &tl, int kxy);
 
-cudaError_t launch_ncc_finish(const int32_t *desc, const float *y, int n, const Tiling &tl,
-                              const double *part, const double *gpart, int min_valid, double *ncc,
-                              double *grad, cudaStream_t st);
+cudaError_t launch_ncc_finish(const DevGeom *g, const int32_t *desc, const double *poses, int n,
+                              const Tiling &tl, const double *part, const double *gpart,
+                              int min_valid, double *ncc, double *grad, cudaStream_t st);
 
 cudaError_t launch_reg_init(const double *poses, int n, double *best, double *trial,
                             double *delta, int32_t *active, double delta0, cudaStream_t st);
