@@ -95,11 +95,13 @@ __host__ __device__ __forceinline__ VolDims vol_dims(int nx, int ny, int nz)
 
 // Split an in-volume fixed-point coordinate into base voxel and fraction;
 // the last plane is addressed as cell n-2 with fraction 1.
+// FAST: the caller knows q < (n - 1) << 20, so no clamp is needed.
+template <bool FAST = false>
 __device__ __forceinline__ void split(unsigned q, int n, int &b, float &f)
 {
     b = (int)(q >> kFracBits);
     f = (float)(q & kFracMask) * kFracScale;
-    if (b == n - 1) {
+    if (!FAST && b == n - 1) {
         b = n - 2;
         f = 1.0f;
     }
@@ -147,14 +149,15 @@ __device__ __forceinline__ void lattice_pos(const TileInfo &ti, int kxy, int li,
     for (int r = 0; r < 3; ++r) q[r] = ti.o[r] + (unsigned)pi * ti.ei[r] + (unsigned)pj * ti.ej[r];
 }
 
+template <bool FAST = false>
 __device__ __forceinline__ float trilinear(const float *__restrict__ x, const VolDims &vd,
                                            unsigned qx, unsigned qy, unsigned qz)
 {
     int bx, by, bz;
     float fx, fy, fz;
-    split(qx, vd.nx, bx, fx);
-    split(qy, vd.ny, by, fy);
-    split(qz, vd.nz, bz, fz);
+    split<FAST>(qx, vd.nx, bx, fx);
+    split<FAST>(qy, vd.ny, by, fy);
+    split<FAST>(qz, vd.nz, bz, fz);
     size_t nxy = (size_t)vd.nx * vd.ny;
     const float *b = x + (size_t)bz * nxy + (size_t)by * vd.nx + bx;
     float v000 = __ldg(b), v100 = __ldg(b + 1);
@@ -173,6 +176,28 @@ __device__ __forceinline__ float trilinear(const float *__restrict__ x, const Vo
 __device__ __forceinline__ bool inside(const VolDims &vd, unsigned qx, unsigned qy, unsigned qz)
 {
     return qx <= vd.ux && qy <= vd.uy && qz <= vd.uz;
+}
+
+// True when every sample of the tile (lattice with halo, every zeta) lies
+// strictly inside the volume, so that loops need no in-volume test and no
+// last-plane clamp.  Sample positions are affine in (column, row, zeta): the
+// extremes sit at the 8 corners of the sample box.
+__device__ __forceinline__ bool tile_interior(const TileInfo &ti, const VolDims &vd, int kxy, int kz)
+{
+    if (!ti.ok) return false;
+    const unsigned lim[3] = {vd.ux, vd.uy, vd.uz};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        int pi = ti.i0 - kxy + ((c & 1) ? ti.Lw - 1 : 0);
+        int pj = ti.j0 - kxy + ((c & 2) ? ti.Lh - 1 : 0);
+        int z = (c & 4) ? kz : -kz;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            unsigned q = ti.o[r] + (unsigned)pi * ti.ei[r] + (unsigned)pj * ti.ej[r] + (unsigned)z * ti.ez[r];
+            if (q >= lim[r]) return false;
+        }
+    }
+    return true;
 }
 
 // Through-plane walks with cell-face reuse.  The through-plane samples of a
@@ -235,7 +260,7 @@ __device__ __forceinline__ void face_red(float *addon, float *conf, size_t idx, 
 }
 
 // Adjoint walk of one lattice point with weights ur, uw (times g_z per sample).
-template <int FA, int KZ, bool PAIR>
+template <int FA, int KZ, bool PAIR, bool FAST>
 __device__ __forceinline__ void walk_scatter(const VolDims &vd, const TileInfo &ti, const unsigned q0[3],
                                              int kz_rt, const float *__restrict__ gz, const Walk &wk,
                                              float ur, float uw, float *addon, float *conf)
@@ -254,7 +279,7 @@ __device__ __forceinline__ void walk_scatter(const VolDims &vd, const TileInfo &
         unsigned q[3];
 #pragma unroll
         for (int r = 0; r < 3; ++r) q[r] = q0[r] + (unsigned)z * ti.ez[r];
-        if (!inside(vd, q[0], q[1], q[2])) {
+        if (!FAST && !inside(vd, q[0], q[1], q[2])) {
             if (have) face_red<PAIR>(addon, conf, pidx, s1, s2, pr, pw);
             have = false;
             pb[FA] = -2;
@@ -262,9 +287,9 @@ __device__ __forceinline__ void walk_scatter(const VolDims &vd, const TileInfo &
         }
         int b[3];
         float f[3];
-        split(q[0], vd.nx, b[0], f[0]);
-        split(q[1], vd.ny, b[1], f[1]);
-        split(q[2], vd.nz, b[2], f[2]);
+        split<FAST>(q[0], vd.nx, b[0], f[0]);
+        split<FAST>(q[1], vd.ny, b[1], f[1]);
+        split<FAST>(q[2], vd.nz, b[2], f[2]);
         const size_t idx = (size_t)b[2] * nxy + (size_t)b[1] * vd.nx + b[0];
         const float g = gz[z + kz];
         const float f1 = f[A1], f2 = f[A2];
@@ -305,7 +330,7 @@ __device__ __forceinline__ void walk_scatter(const VolDims &vd, const TileInfo &
 // Phase 1 of the forward model: through-plane PSF sums at every lattice
 // point of the tile (stored row-major).  A (may be null) <- sum g_z
 // trilinear, B <- sum g_z over in-volume samples.
-template <int KZ>
+template <int KZ, bool FAST = false>
 __device__ __forceinline__ void lattice_forward(const float *__restrict__ x, const VolDims &vd,
                                                 const TileInfo &ti, int kxy, int kz_rt,
                                                 const float *__restrict__ gz, int order, float *A,
@@ -324,9 +349,9 @@ __device__ __forceinline__ void lattice_forward(const float *__restrict__ x, con
                 unsigned qx = q0[0] + (unsigned)z * ti.ez[0];
                 unsigned qy = q0[1] + (unsigned)z * ti.ez[1];
                 unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
-                if (inside(vd, qx, qy, qz)) {
+                if (FAST || inside(vd, qx, qy, qz)) {
                     float g = gz[z + kz];
-                    if (A) acc = fmaf(g, trilinear(x, vd, qx, qy, qz), acc);
+                    if (A) acc = fmaf(g, trilinear<FAST>(x, vd, qx, qy, qz), acc);
                     den += g;
                 }
             }
@@ -350,8 +375,8 @@ __device__ __forceinline__ void lattice_forward(const float *__restrict__ x, con
             unsigned qx = q[0] + (unsigned)zeta * ti.ez[0];
             unsigned qy = q[1] + (unsigned)zeta * ti.ez[1];
             unsigned qz = q[2] + (unsigned)zeta * ti.ez[2];
-            if (inside(vd, qx, qy, qz)) {
-                if (A) a = g * trilinear(x, vd, qx, qy, qz);
+            if (FAST || inside(vd, qx, qy, qz)) {
+                if (A) a = g * trilinear<FAST>(x, vd, qx, qy, qz);
                 b = g;
             }
         }
@@ -507,8 +532,12 @@ __global__ void __launch_bounds__(256) k_simulate(const float *__restrict__ x, V
     }
     float *A = sm, *B = sm + ti.L;
     if (ti.ok) {
-        lattice_forward<KZ>(x, vd, ti, kxy, psf.kz, psf.gz[ti.stack],
-                            pick_order(ti, KZ >= 0 ? KZ : psf.kz), A, B);
+        const int kz = KZ >= 0 ? KZ : psf.kz;
+        const int order = pick_order(ti, kz);
+        if (tile_interior(ti, vd, kxy, kz))
+            lattice_forward<KZ, true>(x, vd, ti, kxy, kz, psf.gz[ti.stack], order, A, B);
+        else
+            lattice_forward<KZ, false>(x, vd, ti, kxy, kz, psf.gz[ti.stack], order, A, B);
     } else {
         for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) A[lp] = B[lp] = 0.f;
     }
@@ -569,16 +598,16 @@ __global__ void __launch_bounds__(256) k_simulate(const float *__restrict__ x, V
 // Add one in-volume sample's contributions ar, aw (already times g_z) to the
 // 8 voxels of its cell: PAIR = interleaved (addon, conf) float2 pairs with one
 // vector reduction per voxel, otherwise two separate arrays.
-template <bool PAIR>
+template <bool PAIR, bool FAST = false>
 __device__ __forceinline__ void scatter_sample(const VolDims &vd, unsigned qx, unsigned qy,
                                                unsigned qz, float ar, float aw, float *addon,
                                                float *conf)
 {
     int bx, by, bz;
     float fx, fy, fz;
-    split(qx, vd.nx, bx, fx);
-    split(qy, vd.ny, by, fy);
-    split(qz, vd.nz, bz, fz);
+    split<FAST>(qx, vd.nx, bx, fx);
+    split<FAST>(qy, vd.ny, by, fy);
+    split<FAST>(qz, vd.nz, bz, fz);
     const size_t nxy = (size_t)vd.nx * vd.ny;
     size_t base = (size_t)bz * nxy + (size_t)by * vd.nx + bx;
     float wx[2] = {1.f - fx, fx}, wy[2] = {1.f - fy, fy}, wz[2] = {1.f - fz, fz};
@@ -597,6 +626,46 @@ __device__ __forceinline__ void scatter_sample(const VolDims &vd, unsigned qx, u
                     if (conf) atomicAdd(conf + idx, aw * t);
                 }
             }
+}
+
+// Phase 3 of the adjoint: scatter of every in-volume sample of the tile in
+// its traversal order (FAST: interior tile, no in-volume tests).
+template <int KZ, bool PAIR, bool FAST>
+__device__ __forceinline__ void adjoint_scatter(const VolDims &vd, const TileInfo &ti, int kxy, int kz,
+                                                const float *__restrict__ gz, const float *U,
+                                                const float *Uw, float *addon, float *conf)
+{
+    const int order = pick_order(ti, kz);
+    if (order != kAlongZeta) {
+        const Walk wk = zeta_walk(ti, kz);
+        for (int it = threadIdx.x; it < ti.L; it += blockDim.x) {
+            int li, lj;
+            lattice_coords(ti, order, it, li, lj);
+            const int sidx = lj * ti.Lw + li;
+            float ur = U[sidx], uw = Uw[sidx];
+            if (ur == 0.f && uw == 0.f) continue;
+            unsigned q0[3];
+            lattice_pos(ti, kxy, li, lj, q0);
+            if (wk.fa == 2) walk_scatter<2, KZ, PAIR, FAST>(vd, ti, q0, kz, gz, wk, ur, uw, addon, conf);
+            else if (wk.fa == 1) walk_scatter<1, KZ, PAIR, FAST>(vd, ti, q0, kz, gz, wk, ur, uw, addon, conf);
+            else walk_scatter<0, KZ, PAIR, FAST>(vd, ti, q0, kz, gz, wk, ur, uw, addon, conf);
+        }
+    } else {
+        const int zl = threadIdx.x & 7, zeta = zl - kz;
+        if (zl <= 2 * kz) {
+            const float g = gz[zl];
+            for (int lp = threadIdx.x >> 3; lp < ti.L; lp += blockDim.x >> 3) {
+                float ur = U[lp], uw = Uw[lp];
+                if (ur == 0.f && uw == 0.f) continue;
+                unsigned q[3];
+                lattice_pos(ti, kxy, lp % ti.Lw, lp / ti.Lw, q);
+                unsigned qx = q[0] + (unsigned)zeta * ti.ez[0];
+                unsigned qy = q[1] + (unsigned)zeta * ti.ez[1];
+                unsigned qz = q[2] + (unsigned)zeta * ti.ez[2];
+                if (FAST || inside(vd, qx, qy, qz)) scatter_sample<PAIR, FAST>(vd, qx, qy, qz, g * ur, g * uw, addon, conf);
+            }
+        }
+    }
 }
 
 template <int KXY, int KZ, bool PAIR>
@@ -661,50 +730,24 @@ __global__ void __launch_bounds__(256) k_adjoint(VolDims vd, const int32_t *__re
         Uw[lp] = uw;
     }
     __syncthreads();
-    // phase 3: scatter, in the tile's traversal order
-    const int order = pick_order(ti, kz);
-    if (order != kAlongZeta) {
-        const Walk wk = zeta_walk(ti, kz);
-        for (int it = threadIdx.x; it < ti.L; it += blockDim.x) {
-            int li, lj;
-            lattice_coords(ti, order, it, li, lj);
-            const int sidx = lj * ti.Lw + li;
-            float ur = U[sidx], uw = Uw[sidx];
-            if (ur == 0.f && uw == 0.f) continue;
-            unsigned q0[3];
-            lattice_pos(ti, kxy, li, lj, q0);
-            if (wk.fa == 2) walk_scatter<2, KZ, PAIR>(vd, ti, q0, kz, gz, wk, ur, uw, addon, conf);
-            else if (wk.fa == 1) walk_scatter<1, KZ, PAIR>(vd, ti, q0, kz, gz, wk, ur, uw, addon, conf);
-            else walk_scatter<0, KZ, PAIR>(vd, ti, q0, kz, gz, wk, ur, uw, addon, conf);
-        }
-    } else {
-        const int zl = threadIdx.x & 7, zeta = zl - kz;
-        if (zl <= 2 * kz) {
-            const float g = gz[zl];
-            for (int lp = threadIdx.x >> 3; lp < ti.L; lp += blockDim.x >> 3) {
-                float ur = U[lp], uw = Uw[lp];
-                if (ur == 0.f && uw == 0.f) continue;
-                unsigned q[3];
-                lattice_pos(ti, kxy, lp % ti.Lw, lp / ti.Lw, q);
-                unsigned qx = q[0] + (unsigned)zeta * ti.ez[0];
-                unsigned qy = q[1] + (unsigned)zeta * ti.ez[1];
-                unsigned qz = q[2] + (unsigned)zeta * ti.ez[2];
-                if (inside(vd, qx, qy, qz)) scatter_sample<PAIR>(vd, qx, qy, qz, g * ur, g * uw, addon, conf);
-            }
-        }
-    }
+    // phase 3: scatter
+    if (tile_interior(ti, vd, kxy, kz))
+        adjoint_scatter<KZ, PAIR, true>(vd, ti, kxy, kz, gz, U, Uw, addon, conf);
+    else
+        adjoint_scatter<KZ, PAIR, false>(vd, ti, kxy, kz, gz, U, Uw, addon, conf);
 }
 
 // ----------------------------------------------------------------- K6a --
 // Trilinear value and its gradient (voxel units) from one set of 8 loads.
+template <bool FAST>
 __device__ __forceinline__ float tri_grad(const float *__restrict__ x, const VolDims &vd, unsigned qx,
                                          unsigned qy, unsigned qz, float gr[3])
 {
     int bx, by, bz;
     float fx, fy, fz;
-    split(qx, vd.nx, bx, fx);
-    split(qy, vd.ny, by, fy);
-    split(qz, vd.nz, bz, fz);
+    split<FAST>(qx, vd.nx, bx, fx);
+    split<FAST>(qy, vd.ny, by, fy);
+    split<FAST>(qz, vd.nz, bz, fz);
     const size_t nxy = (size_t)vd.nx * vd.ny;
     const float *b = x + (size_t)bz * nxy + (size_t)by * vd.nx + bx;
     float v000 = __ldg(b), v100 = __ldg(b + 1);
@@ -720,6 +763,90 @@ __device__ __forceinline__ float tri_grad(const float *__restrict__ x, const Vol
     gr[1] = fmaf(fz, (c11 - c01) - (c10 - c00), c10 - c00);
     gr[2] = c1 - c0;
     return fmaf(fz, c1 - c0, c0);
+}
+
+// Gather pass of the NCC moments kernel: A, B into shared memory and the
+// gradient sums GA, GB into G (FAST: interior tile).
+template <int KZ, bool FAST>
+__device__ __forceinline__ void moments_gather(const float *__restrict__ x, const VolDims &vd,
+                                               const TileInfo &ti, int kxy, int kz, int order,
+                                               const float *__restrict__ gz, float *A, float *B,
+                                               float *G, int Lmax)
+{
+    if (order != kAlongZeta) {
+        for (int it = threadIdx.x; it < ti.L; it += blockDim.x) {
+            int li, lj;
+            lattice_coords(ti, order, it, li, lj);
+            float a = 0.f, b = 0.f, ga[3] = {0.f, 0.f, 0.f}, gb[3] = {0.f, 0.f, 0.f};
+            if (ti.ok) {
+                unsigned q0[3];
+                lattice_pos(ti, kxy, li, lj, q0);
+#pragma unroll
+                for (int z = -kz; z <= kz; ++z) {
+                    unsigned qx = q0[0] + (unsigned)z * ti.ez[0];
+                    unsigned qy = q0[1] + (unsigned)z * ti.ez[1];
+                    unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
+                    if (!FAST && !inside(vd, qx, qy, qz)) continue;
+                    float gr[3];
+                    const float w = gz[z + kz];
+                    a = fmaf(w, tri_grad<FAST>(x, vd, qx, qy, qz, gr), a);
+                    b += w;
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        ga[r] = fmaf(w, gr[r], ga[r]);
+                        gb[r] = fmaf(w * (float)z, gr[r], gb[r]);
+                    }
+                }
+            }
+            const int si = lj * ti.Lw + li;
+            A[si] = a;
+            B[si] = b;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                G[r * Lmax + si] = ga[r];
+                G[(3 + r) * Lmax + si] = gb[r];
+            }
+        }
+    } else {
+        const int zl = threadIdx.x & 7, zeta = zl - kz;
+        const bool zon = zl <= 2 * kz;
+        const float w = zon ? gz[zl] : 0.f;
+        const int ngrp = blockDim.x >> 3;
+        for (int base = 0; base < ti.L; base += ngrp) {
+            const int lp = base + (threadIdx.x >> 3);
+            float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (zon && lp < ti.L) {
+                unsigned q[3];
+                lattice_pos(ti, kxy, lp % ti.Lw, lp / ti.Lw, q);
+                unsigned qx = q[0] + (unsigned)zeta * ti.ez[0];
+                unsigned qy = q[1] + (unsigned)zeta * ti.ez[1];
+                unsigned qz = q[2] + (unsigned)zeta * ti.ez[2];
+                if (FAST || inside(vd, qx, qy, qz)) {
+                    float gr[3];
+                    v[0] = w * tri_grad<FAST>(x, vd, qx, qy, qz, gr);
+                    v[1] = w;
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        v[2 + r] = w * gr[r];
+                        v[5 + r] = v[2 + r] * (float)zeta;
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+#pragma unroll
+                for (int o = 1; o < 8; o <<= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+            if (zl == 0 && lp < ti.L) {
+                A[lp] = v[0];
+                B[lp] = v[1];
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    G[r * Lmax + lp] = v[2 + r];
+                    G[(3 + r) * Lmax + lp] = v[5 + r];
+                }
+            }
+        }
+    }
 }
 
 // NCC moments of a tile: simulated pixel values (kept for K6b) and the sums
@@ -763,79 +890,10 @@ __global__ void __launch_bounds__(256) k_ncc_moments(const float *__restrict__ x
         } else {
             for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) A[lp] = B[lp] = 0.f;
         }
-    } else if (order != kAlongZeta) {
-        for (int it = threadIdx.x; it < ti.L; it += blockDim.x) {
-            int li, lj;
-            lattice_coords(ti, order, it, li, lj);
-            float a = 0.f, b = 0.f, ga[3] = {0.f, 0.f, 0.f}, gb[3] = {0.f, 0.f, 0.f};
-            if (ti.ok) {
-                unsigned q0[3];
-                lattice_pos(ti, kxy, li, lj, q0);
-#pragma unroll
-                for (int z = -kz; z <= kz; ++z) {
-                    unsigned qx = q0[0] + (unsigned)z * ti.ez[0];
-                    unsigned qy = q0[1] + (unsigned)z * ti.ez[1];
-                    unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
-                    if (!inside(vd, qx, qy, qz)) continue;
-                    float gr[3];
-                    const float w = gz[z + kz];
-                    a = fmaf(w, tri_grad(x, vd, qx, qy, qz, gr), a);
-                    b += w;
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        ga[r] = fmaf(w, gr[r], ga[r]);
-                        gb[r] = fmaf(w * (float)z, gr[r], gb[r]);
-                    }
-                }
-            }
-            const int si = lj * ti.Lw + li;
-            A[si] = a;
-            B[si] = b;
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                G[r * Lmax + si] = ga[r];
-                G[(3 + r) * Lmax + si] = gb[r];
-            }
-        }
+    } else if (tile_interior(ti, vd, kxy, kz)) {
+        moments_gather<KZ, true>(x, vd, ti, kxy, kz, order, gz, A, B, G, Lmax);
     } else {
-        const int zl = threadIdx.x & 7, zeta = zl - kz;
-        const bool zon = zl <= 2 * kz;
-        const float w = zon ? gz[zl] : 0.f;
-        const int ngrp = blockDim.x >> 3;
-        for (int base = 0; base < ti.L; base += ngrp) {
-            const int lp = base + (threadIdx.x >> 3);
-            float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (zon && lp < ti.L) {
-                unsigned q[3];
-                lattice_pos(ti, kxy, lp % ti.Lw, lp / ti.Lw, q);
-                unsigned qx = q[0] + (unsigned)zeta * ti.ez[0];
-                unsigned qy = q[1] + (unsigned)zeta * ti.ez[1];
-                unsigned qz = q[2] + (unsigned)zeta * ti.ez[2];
-                if (inside(vd, qx, qy, qz)) {
-                    float gr[3];
-                    v[0] = w * tri_grad(x, vd, qx, qy, qz, gr);
-                    v[1] = w;
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        v[2 + r] = w * gr[r];
-                        v[5 + r] = v[2 + r] * (float)zeta;
-                    }
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-#pragma unroll
-                for (int o = 1; o < 8; o <<= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-            if (zl == 0 && lp < ti.L) {
-                A[lp] = v[0];
-                B[lp] = v[1];
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    G[r * Lmax + lp] = v[2 + r];
-                    G[(3 + r) * Lmax + lp] = v[5 + r];
-                }
-            }
-        }
+        moments_gather<KZ, false>(x, vd, ti, kxy, kz, order, gz, A, B, G, Lmax);
     }
     __syncthreads();
     FFSum f1, f2, f3, f4, f5;
