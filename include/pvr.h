@@ -92,7 +92,7 @@ enum pvr_em_state_index {
 };
 
 typedef struct pvr_geometry {
-    int32_t nx, ny, nz;                             /* volume size, each >= 2 */
+    int32_t nx, ny, nz;                             /* volume size, each 2..2048, nx*ny*nz < 2^31 */
     int32_t n_stacks;                               /* 1..PVR_MAX_STACKS */
     int32_t stack_w[PVR_MAX_STACKS];                /* columns */
     int32_t stack_h[PVR_MAX_STACKS];                /* rows */

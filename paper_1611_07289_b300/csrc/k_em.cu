@@ -540,11 +540,13 @@ __global__ void k_reg_step(const DevGeom *__restrict__ g, const int32_t *__restr
     double *b = best + kRegStride * (size_t)p;
     double *gb = gbest + kRegStride * (size_t)p;
     double *tr = trial + 6 * (size_t)p;
-    const double *gr = grad + 6 * (size_t)p;
+    // grad is null on the last evaluation (no further step uses it)
+    const double *gr = grad ? grad + 6 * (size_t)p : nullptr;
     double v = ncc[p];
     if (eval == 0) {
         nbest[p] = v;
-        for (int k = 0; k < 6; ++k) gb[k] = gr[k];
+        if (gr)
+            for (int k = 0; k < 6; ++k) gb[k] = gr[k];
         if (v == 0.0) {
             active[p] = 0;
             return;
@@ -552,7 +554,7 @@ __global__ void k_reg_step(const DevGeom *__restrict__ g, const int32_t *__restr
     } else if (fixed || v > nbest[p]) {
         for (int k = 0; k < 6; ++k) {
             b[k] = tr[k];
-            gb[k] = gr[k];
+            if (gr) gb[k] = gr[k];
         }
         nbest[p] = v;
         if (!fixed) delta[p] = __dmul_rn(delta[p], grow);

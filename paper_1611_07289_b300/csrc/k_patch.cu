@@ -23,16 +23,26 @@ namespace pvr {
 namespace {
 
 constexpr unsigned kFracMask = (1u << kFracBits) - 1u;
-constexpr float kFracScale = 1.0f / (float)(1u << kFracBits);
 
 struct TileInfo {
     int p, t;                // patch, tile index
     int stack, w, h, off;    // patch
     int i0, j0, tw, th;      // tile pixel origin (patch-relative) and size
     int Lw, Lh, L;           // lattice of the tile incl. halo
+    float rLw, rLh, rtw;     // 1 / Lw, 1 / Lh, 1 / tw for qdiv
     unsigned o[3], ei[3], ej[3], ez[3];
     bool ok;
 };
+
+// Integer quotient a / d for 0 <= a < 2^22 from r = 1 / d (float): the
+// exact quotient (a + 0.5) / d lies at least 0.5 / d from an integer, and
+// the two float roundings move it by at most (a + 0.5) / d * 2^-23 < 0.5 / d,
+// so truncation gives floor(a / d).  Lattice and tile indices stay far
+// below 2^22.
+__device__ __forceinline__ int qdiv(int a, float r)
+{
+    return (int)(((float)a + 0.5f) * r);
+}
 
 // Decode block -> (patch, tile); returns false for an empty tile or a
 // patch whose descriptor row failed validation in the pose kernel.
@@ -59,6 +69,9 @@ __device__ __forceinline__ bool tile_setup_at(long long gid, const int32_t *__re
     ti.Lw = ti.tw + 2 * kxy;
     ti.Lh = ti.th + 2 * kxy;
     ti.L = ti.Lw * ti.Lh;
+    ti.rLw = 1.0f / (float)ti.Lw;
+    ti.rLh = 1.0f / (float)ti.Lh;
+    ti.rtw = 1.0f / (float)ti.tw;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         ti.o[r] = (unsigned)f[r];
@@ -78,6 +91,7 @@ __device__ __forceinline__ bool tile_setup(const int32_t *__restrict__ desc,
 
 struct VolDims {
     int nx, ny, nz;
+    unsigned nxy;            // nx * ny (used where the volume has < 2^31 voxels)
     unsigned ux, uy, uz;     // (n - 1) << 20: largest in-volume coordinate
 };
 
@@ -87,6 +101,7 @@ __host__ __device__ __forceinline__ VolDims vol_dims(int nx, int ny, int nz)
     v.nx = nx;
     v.ny = ny;
     v.nz = nz;
+    v.nxy = (unsigned)nx * (unsigned)ny;
     v.ux = (unsigned)(nx - 1) << kFracBits;
     v.uy = (unsigned)(ny - 1) << kFracBits;
     v.uz = (unsigned)(nz - 1) << kFracBits;
@@ -100,7 +115,9 @@ template <bool FAST = false>
 __device__ __forceinline__ void split(unsigned q, int n, int &b, float &f)
 {
     b = (int)(q >> kFracBits);
-    f = (float)(q & kFracMask) * kFracScale;
+    // 1 + frac * 2^-20 has the fraction bits as its top mantissa bits, so
+    // subtracting 1 gives (q & mask) * 2^-20 exactly (without a conversion)
+    f = __uint_as_float(0x3f800000u | ((q & kFracMask) << (23 - kFracBits))) - 1.0f;
     if (!FAST && b == n - 1) {
         b = n - 2;
         f = 1.0f;
@@ -133,11 +150,11 @@ __device__ __forceinline__ int pick_order(const TileInfo &ti, int kz)
 __device__ __forceinline__ void lattice_coords(const TileInfo &ti, int order, int it, int &li, int &lj)
 {
     if (order == kAlongRow) {
-        li = it / ti.Lh;
-        lj = it % ti.Lh;
+        li = qdiv(it, ti.rLh);
+        lj = it - li * ti.Lh;
     } else {
-        li = it % ti.Lw;
-        lj = it / ti.Lw;
+        lj = qdiv(it, ti.rLw);
+        li = it - lj * ti.Lw;
     }
 }
 
@@ -149,25 +166,65 @@ __device__ __forceinline__ void lattice_pos(const TileInfo &ti, int kxy, int li,
     for (int r = 0; r < 3; ++r) q[r] = ti.o[r] + (unsigned)pi * ti.ei[r] + (unsigned)pj * ti.ej[r];
 }
 
-template <bool FAST = false>
-__device__ __forceinline__ float trilinear(const float *__restrict__ x, const VolDims &vd,
-                                           unsigned qx, unsigned qy, unsigned qz)
+// Volume sources of the gathers.  PlainVol reads the eight corners of a
+// trilinear cell as eight 4-byte loads (any volume size).  QuadVol reads the
+// quad copy of the volume, q[i] = (x[i], x[i + 1], x[i + nx], x[i + nx + 1])
+// for voxel i, so a cell is two 16-byte loads (its two z planes); it needs
+// fewer than 2^31 voxels.  Both give the same eight values.
+struct PlainVol {
+    const float *x;
+};
+struct QuadVol {
+    const float4 *q;
+};
+
+__device__ __forceinline__ void cell_corners(const PlainVol &src, const VolDims &vd, int bx, int by,
+                                             int bz, float v[8])
+{
+    const size_t nxy = (size_t)vd.nx * vd.ny;
+    const float *b = src.x + (size_t)bz * nxy + (size_t)by * vd.nx + bx;
+    v[0] = __ldg(b);
+    v[1] = __ldg(b + 1);
+    v[2] = __ldg(b + vd.nx);
+    v[3] = __ldg(b + vd.nx + 1);
+    v[4] = __ldg(b + nxy);
+    v[5] = __ldg(b + nxy + 1);
+    v[6] = __ldg(b + nxy + vd.nx);
+    v[7] = __ldg(b + nxy + vd.nx + 1);
+}
+
+__device__ __forceinline__ void cell_corners(const QuadVol &src, const VolDims &vd, int bx, int by,
+                                             int bz, float v[8])
+{
+    const unsigned i = ((unsigned)bz * (unsigned)vd.ny + (unsigned)by) * (unsigned)vd.nx + (unsigned)bx;
+    const float4 lo = __ldg(src.q + i), hi = __ldg(src.q + i + vd.nxy);
+    v[0] = lo.x;
+    v[1] = lo.y;
+    v[2] = lo.z;
+    v[3] = lo.w;
+    v[4] = hi.x;
+    v[5] = hi.y;
+    v[6] = hi.z;
+    v[7] = hi.w;
+}
+
+// Trilinear value at a fixed-point position inside the volume; corners v
+// ordered (x, y, z) = 000, 100, 010, 110, 001, 101, 011, 111.
+template <bool FAST = false, class SRC>
+__device__ __forceinline__ float trilinear(const SRC &src, const VolDims &vd, unsigned qx, unsigned qy,
+                                           unsigned qz)
 {
     int bx, by, bz;
     float fx, fy, fz;
     split<FAST>(qx, vd.nx, bx, fx);
     split<FAST>(qy, vd.ny, by, fy);
     split<FAST>(qz, vd.nz, bz, fz);
-    size_t nxy = (size_t)vd.nx * vd.ny;
-    const float *b = x + (size_t)bz * nxy + (size_t)by * vd.nx + bx;
-    float v000 = __ldg(b), v100 = __ldg(b + 1);
-    float v010 = __ldg(b + vd.nx), v110 = __ldg(b + vd.nx + 1);
-    float v001 = __ldg(b + nxy), v101 = __ldg(b + nxy + 1);
-    float v011 = __ldg(b + nxy + vd.nx), v111 = __ldg(b + nxy + vd.nx + 1);
-    float c00 = fmaf(fx, v100 - v000, v000);
-    float c10 = fmaf(fx, v110 - v010, v010);
-    float c01 = fmaf(fx, v101 - v001, v001);
-    float c11 = fmaf(fx, v111 - v011, v011);
+    float v[8];
+    cell_corners(src, vd, bx, by, bz, v);
+    float c00 = fmaf(fx, v[1] - v[0], v[0]);
+    float c10 = fmaf(fx, v[3] - v[2], v[2]);
+    float c01 = fmaf(fx, v[5] - v[4], v[4]);
+    float c11 = fmaf(fx, v[7] - v[6], v[6]);
     float c0 = fmaf(fy, c10 - c00, c00);
     float c1 = fmaf(fy, c11 - c01, c01);
     return fmaf(fz, c1 - c0, c0);
@@ -330,8 +387,8 @@ __device__ __forceinline__ void walk_scatter(const VolDims &vd, const TileInfo &
 // Phase 1 of the forward model: through-plane PSF sums at every lattice
 // point of the tile (stored row-major).  A (may be null) <- sum g_z
 // trilinear, B <- sum g_z over in-volume samples.
-template <int KZ, bool FAST = false>
-__device__ __forceinline__ void lattice_forward(const float *__restrict__ x, const VolDims &vd,
+template <int KZ, bool FAST = false, class SRC = PlainVol>
+__device__ __forceinline__ void lattice_forward(const SRC src, const VolDims &vd,
                                                 const TileInfo &ti, int kxy, int kz_rt,
                                                 const float *__restrict__ gz, int order, float *A,
                                                 float *B)
@@ -351,7 +408,7 @@ __device__ __forceinline__ void lattice_forward(const float *__restrict__ x, con
                 unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
                 if (FAST || inside(vd, qx, qy, qz)) {
                     float g = gz[z + kz];
-                    if (A) acc = fmaf(g, trilinear<FAST>(x, vd, qx, qy, qz), acc);
+                    if (A) acc = fmaf(g, trilinear<FAST>(src, vd, qx, qy, qz), acc);
                     den += g;
                 }
             }
@@ -371,40 +428,28 @@ __device__ __forceinline__ void lattice_forward(const float *__restrict__ x, con
         float a = 0.f, b = 0.f;
         if (zon && lp < ti.L) {
             unsigned q[3];
-            lattice_pos(ti, kxy, lp % ti.Lw, lp / ti.Lw, q);
+            const int lj = qdiv(lp, ti.rLw);
+                lattice_pos(ti, kxy, lp - lj * ti.Lw, lj, q);
             unsigned qx = q[0] + (unsigned)zeta * ti.ez[0];
             unsigned qy = q[1] + (unsigned)zeta * ti.ez[1];
             unsigned qz = q[2] + (unsigned)zeta * ti.ez[2];
             if (FAST || inside(vd, qx, qy, qz)) {
-                if (A) a = g * trilinear<FAST>(x, vd, qx, qy, qz);
+                if (A) a = g * trilinear<FAST>(src, vd, qx, qy, qz);
                 b = g;
             }
         }
-#pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            b += __shfl_xor_sync(0xffffffffu, b, o);
-        }
-        if (zl == 0 && lp < ti.L) {
-            if (A) A[lp] = a;
-            B[lp] = b;
+        // reduce-scatter over the group of 8: lanes 0-3 end with sum a,
+        // lanes 4-7 with sum b
+        const bool hi4 = zl & 4;
+        float t = (hi4 ? b : a) + __shfl_xor_sync(0xffffffffu, hi4 ? a : b, 4);
+        t += __shfl_xor_sync(0xffffffffu, t, 2);
+        t += __shfl_xor_sync(0xffffffffu, t, 1);
+        if (lp < ti.L) {
+            if (zl == 0 && A) A[lp] = t;
+            if (zl == 4) B[lp] = t;
         }
     }
 }
-
-// Kahan-compensated float32 sum (the pose gradient is a sum of terms of
-// both signs that largely cancel near an optimum).
-struct KahanSum {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float v)
-    {
-        float yv = v - c;
-        float t = s + yv;
-        c = (t - s) - yv;
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
-};
 
 // In-plane taps at tile pixel (ci, cj) from lattice array V.
 __device__ __forceinline__ float inplane(const float *V, int Lw, int kxy, const float *gxy, int ci,
@@ -511,8 +556,8 @@ struct FFSum {
 // Forward model.  y == null: write sim, valid.  y != null: write the
 // residual e = y - sim (0 where invalid) and valid, plus per-tile partials
 // {N_valid, sum e^2, min e, max e} for the EM step.
-template <int KXY, int KZ>
-__global__ void __launch_bounds__(256) k_simulate(const float *__restrict__ x, VolDims vd,
+template <int KXY, int KZ, class SRC>
+__global__ void __launch_bounds__(256) k_simulate(const SRC x, VolDims vd,
                                                   const int32_t *__restrict__ desc,
                                                   const int32_t *__restrict__ fix, PsfTab psf,
                                                   Tiling tl, const float *__restrict__ y,
@@ -535,9 +580,9 @@ __global__ void __launch_bounds__(256) k_simulate(const float *__restrict__ x, V
         const int kz = KZ >= 0 ? KZ : psf.kz;
         const int order = pick_order(ti, kz);
         if (tile_interior(ti, vd, kxy, kz))
-            lattice_forward<KZ, true>(x, vd, ti, kxy, kz, psf.gz[ti.stack], order, A, B);
+            lattice_forward<KZ, true, SRC>(x, vd, ti, kxy, kz, psf.gz[ti.stack], order, A, B);
         else
-            lattice_forward<KZ, false>(x, vd, ti, kxy, kz, psf.gz[ti.stack], order, A, B);
+            lattice_forward<KZ, false, SRC>(x, vd, ti, kxy, kz, psf.gz[ti.stack], order, A, B);
     } else {
         for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) A[lp] = B[lp] = 0.f;
     }
@@ -546,7 +591,7 @@ __global__ void __launch_bounds__(256) k_simulate(const float *__restrict__ x, V
     int nval = 0;
     const int np = ti.tw * ti.th;
     for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
-        int ci = pp % ti.tw, cj = pp / ti.tw;
+        const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
         float num = inplane(A, ti.Lw, kxy, psf.gxy, ci, cj);
         float den = inplane(B, ti.Lw, kxy, psf.gxy, ci, cj);
         bool v = den > 0.f;
@@ -658,7 +703,8 @@ __device__ __forceinline__ void adjoint_scatter(const VolDims &vd, const TileInf
                 float ur = U[lp], uw = Uw[lp];
                 if (ur == 0.f && uw == 0.f) continue;
                 unsigned q[3];
-                lattice_pos(ti, kxy, lp % ti.Lw, lp / ti.Lw, q);
+                const int lj = qdiv(lp, ti.rLw);
+                lattice_pos(ti, kxy, lp - lj * ti.Lw, lj, q);
                 unsigned qx = q[0] + (unsigned)zeta * ti.ez[0];
                 unsigned qy = q[1] + (unsigned)zeta * ti.ez[1];
                 unsigned qz = q[2] + (unsigned)zeta * ti.ez[2];
@@ -687,11 +733,11 @@ __global__ void __launch_bounds__(256) k_adjoint(VolDims vd, const int32_t *__re
     float *U = sm, *Uw = sm + ti.L, *CR = sm + 2 * ti.L, *CW = CR + np;
     const float *gz = psf.gz[ti.stack];
     // phase 0: in-volume PSF weight per lattice point (no gathers)
-    lattice_forward<KZ>(nullptr, vd, ti, kxy, kz, gz, kAlongCol, nullptr, U);
+    lattice_forward<KZ>(PlainVol{nullptr}, vd, ti, kxy, kz, gz, kAlongCol, nullptr, U);
     __syncthreads();
     // phase 1: pixel coefficients
     for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
-        int ci = pp % ti.tw, cj = pp / ti.tw;
+        const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
         float den = inplane(U, ti.Lw, kxy, psf.gxy, ci, cj);
         size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
         float cr = 0.f, cw = 0.f;
@@ -707,7 +753,7 @@ __global__ void __launch_bounds__(256) k_adjoint(VolDims vd, const int32_t *__re
     __syncthreads();
     // phase 2: transposed in-plane taps into lattice weights
     for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) {
-        int li = lp % ti.Lw, lj = lp / ti.Lw;   // lattice point = pixel (li - kxy, lj - kxy) of the tile
+        const int lj = qdiv(lp, ti.rLw), li = lp - lj * ti.Lw;   // lattice point = pixel (li - kxy, lj - kxy) of the tile
         float ur = 0.f, uw = 0.f;
         for (int dj = -kxy; dj <= kxy; ++dj) {
             int cj = lj - kxy - dj;
@@ -739,21 +785,19 @@ __global__ void __launch_bounds__(256) k_adjoint(VolDims vd, const int32_t *__re
 
 // ----------------------------------------------------------------- K6a --
 // Trilinear value and its gradient (voxel units) from one set of 8 loads.
-template <bool FAST>
-__device__ __forceinline__ float tri_grad(const float *__restrict__ x, const VolDims &vd, unsigned qx,
-                                         unsigned qy, unsigned qz, float gr[3])
+template <bool FAST, class SRC>
+__device__ __forceinline__ float tri_grad(const SRC &src, const VolDims &vd, unsigned qx, unsigned qy,
+                                         unsigned qz, float gr[3])
 {
     int bx, by, bz;
     float fx, fy, fz;
     split<FAST>(qx, vd.nx, bx, fx);
     split<FAST>(qy, vd.ny, by, fy);
     split<FAST>(qz, vd.nz, bz, fz);
-    const size_t nxy = (size_t)vd.nx * vd.ny;
-    const float *b = x + (size_t)bz * nxy + (size_t)by * vd.nx + bx;
-    float v000 = __ldg(b), v100 = __ldg(b + 1);
-    float v010 = __ldg(b + vd.nx), v110 = __ldg(b + vd.nx + 1);
-    float v001 = __ldg(b + nxy), v101 = __ldg(b + nxy + 1);
-    float v011 = __ldg(b + nxy + vd.nx), v111 = __ldg(b + nxy + vd.nx + 1);
+    float v[8];
+    cell_corners(src, vd, bx, by, bz, v);
+    const float v000 = v[0], v100 = v[1], v010 = v[2], v110 = v[3];
+    const float v001 = v[4], v101 = v[5], v011 = v[6], v111 = v[7];
     float dx00 = v100 - v000, dx10 = v110 - v010, dx01 = v101 - v001, dx11 = v111 - v011;
     float c00 = fmaf(fx, dx00, v000), c10 = fmaf(fx, dx10, v010);
     float c01 = fmaf(fx, dx01, v001), c11 = fmaf(fx, dx11, v011);
@@ -767,8 +811,8 @@ __device__ __forceinline__ float tri_grad(const float *__restrict__ x, const Vol
 
 // Gather pass of the NCC moments kernel: A, B into shared memory and the
 // gradient sums GA, GB into G (FAST: interior tile).
-template <int KZ, bool FAST>
-__device__ __forceinline__ void moments_gather(const float *__restrict__ x, const VolDims &vd,
+template <int KZ, bool FAST, class SRC>
+__device__ __forceinline__ void moments_gather(const SRC src, const VolDims &vd,
                                                const TileInfo &ti, int kxy, int kz, int order,
                                                const float *__restrict__ gz, float *A, float *B,
                                                float *G, int Lmax)
@@ -789,7 +833,7 @@ __device__ __forceinline__ void moments_gather(const float *__restrict__ x, cons
                     if (!FAST && !inside(vd, qx, qy, qz)) continue;
                     float gr[3];
                     const float w = gz[z + kz];
-                    a = fmaf(w, tri_grad<FAST>(x, vd, qx, qy, qz, gr), a);
+                    a = fmaf(w, tri_grad<FAST>(src, vd, qx, qy, qz, gr), a);
                     b += w;
 #pragma unroll
                     for (int r = 0; r < 3; ++r) {
@@ -803,8 +847,8 @@ __device__ __forceinline__ void moments_gather(const float *__restrict__ x, cons
             B[si] = b;
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
-                G[r * Lmax + si] = ga[r];
-                G[(3 + r) * Lmax + si] = gb[r];
+                __stcg(G + r * Lmax + si, ga[r]);
+                __stcg(G + (3 + r) * Lmax + si, gb[r]);
             }
         }
     } else {
@@ -817,13 +861,14 @@ __device__ __forceinline__ void moments_gather(const float *__restrict__ x, cons
             float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (zon && lp < ti.L) {
                 unsigned q[3];
-                lattice_pos(ti, kxy, lp % ti.Lw, lp / ti.Lw, q);
+                const int lj = qdiv(lp, ti.rLw);
+                lattice_pos(ti, kxy, lp - lj * ti.Lw, lj, q);
                 unsigned qx = q[0] + (unsigned)zeta * ti.ez[0];
                 unsigned qy = q[1] + (unsigned)zeta * ti.ez[1];
                 unsigned qz = q[2] + (unsigned)zeta * ti.ez[2];
                 if (FAST || inside(vd, qx, qy, qz)) {
                     float gr[3];
-                    v[0] = w * tri_grad<FAST>(x, vd, qx, qy, qz, gr);
+                    v[0] = w * tri_grad<FAST>(src, vd, qx, qy, qz, gr);
                     v[1] = w;
 #pragma unroll
                     for (int r = 0; r < 3; ++r) {
@@ -832,18 +877,21 @@ __device__ __forceinline__ void moments_gather(const float *__restrict__ x, cons
                     }
                 }
             }
+            // reduce-scatter over the group of 8 lanes: lane zl ends with the
+            // group sum of v[zl] (halving the values kept at every step)
+            const bool b2 = zl & 4, b1 = zl & 2, b0 = zl & 1;
+            float w4[4], w2[2];
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
+            for (int k = 0; k < 4; ++k)
+                w4[k] = (b2 ? v[k + 4] : v[k]) + __shfl_xor_sync(0xffffffffu, b2 ? v[k] : v[k + 4], 4);
 #pragma unroll
-                for (int o = 1; o < 8; o <<= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-            if (zl == 0 && lp < ti.L) {
-                A[lp] = v[0];
-                B[lp] = v[1];
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    G[r * Lmax + lp] = v[2 + r];
-                    G[(3 + r) * Lmax + lp] = v[5 + r];
-                }
+            for (int k = 0; k < 2; ++k)
+                w2[k] = (b1 ? w4[k + 2] : w4[k]) + __shfl_xor_sync(0xffffffffu, b1 ? w4[k] : w4[k + 2], 2);
+            const float t = (b0 ? w2[1] : w2[0]) + __shfl_xor_sync(0xffffffffu, b0 ? w2[0] : w2[1], 1);
+            if (lp < ti.L) {
+                if (zl == 0) A[lp] = t;
+                else if (zl == 1) B[lp] = t;
+                else __stcg(G + (zl - 2) * Lmax + lp, t);
             }
         }
     }
@@ -856,8 +904,8 @@ __device__ __forceinline__ void moments_gather(const float *__restrict__ x, cons
 // trilinear gradient of every sample and streams, per lattice point,
 // GA = sum g_z grad and GB = sum g_z zeta grad (3 planes each, Lmax apart)
 // to gbuf for K6b, which therefore gathers nothing.
-template <int KXY, int KZ>
-__global__ void __launch_bounds__(256) k_ncc_moments(const float *__restrict__ x, VolDims vd,
+template <int KXY, int KZ, class SRC>
+__global__ void __launch_bounds__(256, 4) k_ncc_moments(const SRC x, VolDims vd,
                                                      const int32_t *__restrict__ desc,
                                                      const int32_t *__restrict__ fix, PsfTab psf,
                                                      Tiling tl, long long tile_base,
@@ -886,28 +934,30 @@ __global__ void __launch_bounds__(256) k_ncc_moments(const float *__restrict__ x
     const int order = ti.ok ? pick_order(ti, kz) : kAlongCol;
     if (!G) {
         if (ti.ok) {
-            lattice_forward<KZ>(x, vd, ti, kxy, kz, gz, order, A, B);
+            lattice_forward<KZ, false, SRC>(x, vd, ti, kxy, kz, gz, order, A, B);
         } else {
             for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) A[lp] = B[lp] = 0.f;
         }
     } else if (tile_interior(ti, vd, kxy, kz)) {
-        moments_gather<KZ, true>(x, vd, ti, kxy, kz, order, gz, A, B, G, Lmax);
+        moments_gather<KZ, true, SRC>(x, vd, ti, kxy, kz, order, gz, A, B, G, Lmax);
     } else {
-        moments_gather<KZ, false>(x, vd, ti, kxy, kz, order, gz, A, B, G, Lmax);
+        moments_gather<KZ, false, SRC>(x, vd, ti, kxy, kz, order, gz, A, B, G, Lmax);
     }
     __syncthreads();
     FFSum f1, f2, f3, f4, f5;
     int cnt = 0;
     const int np = ti.tw * ti.th;
     for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
-        int ci = pp % ti.tw, cj = pp / ti.tw;
+        const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
         float num = inplane(A, ti.Lw, kxy, psf.gxy, ci, cj);
         float den = inplane(B, ti.Lw, kxy, psf.gxy, ci, cj);
         bool v = den > 0.f;
         float sv = v ? num / den : 0.f;
         size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
-        s_buf[o] = sv;
-        v_buf[o] = v ? 1 : 0;
+        if (s_buf) {   // kept for the separate gradient pass only
+            s_buf[o] = sv;
+            v_buf[o] = v ? 1 : 0;
+        }
         if (v) {
             float a = __ldg(y + o);
             ++cnt;
@@ -929,12 +979,9 @@ __global__ void __launch_bounds__(256) k_ncc_moments(const float *__restrict__ x
 
 // NCC of a patch from its tile moments (float64).  Returns false when
 // degenerate (fewer than min_valid pixels or a constant patch).
-__device__ bool ncc_from_moments(const double *part, int p, int tpp, int min_valid, double &ncc,
-                                 double &my, double &ms, double &sd, double &vs, double &n)
+__device__ bool ncc_of_sums(const double m[6], int min_valid, double &ncc, double &my, double &ms,
+                            double &sd, double &vs, double &n)
 {
-    double m[6] = {0, 0, 0, 0, 0, 0};
-    for (int t = 0; t < tpp; ++t)
-        for (int k = 0; k < 6; ++k) m[k] += part[((size_t)p * tpp + t) * kPartStride + k];
     n = m[0];
     ncc = 0.0;
     if (n < (double)min_valid || n <= 0.0) return false;
@@ -947,6 +994,15 @@ __device__ bool ncc_from_moments(const double *part, int p, int tpp, int min_val
     sd = sqrt(vy * vs);
     ncc = cv / sd;
     return true;
+}
+
+__device__ bool ncc_from_moments(const double *part, int p, int tpp, int min_valid, double &ncc,
+                                 double &my, double &ms, double &sd, double &vs, double &n)
+{
+    double m[6] = {0, 0, 0, 0, 0, 0};
+    for (int t = 0; t < tpp; ++t)
+        for (int k = 0; k < 6; ++k) m[k] += part[((size_t)p * tpp + t) * kPartStride + k];
+    return ncc_of_sums(m, min_valid, ncc, my, ms, sd, vs, n);
 }
 
 // Pose Jacobian of the sample positions (voxel units per parameter unit):
@@ -1016,6 +1072,46 @@ __device__ void pose_jacobian(const DevGeom *__restrict__ g, const int32_t *d, c
     }
 }
 
+// Lattice phase of the NCC gradient: the transposed in-plane taps of the
+// pixel coefficients C give the lattice weight U; with the gradient sums
+// GA, GB of the lattice point (planes of G, Lmax apart, read through L2) it
+// accumulates M1 = sum U GA (i - cu), M2 = sum U GA (j - cv), M4 = sum U GB,
+// M3 = sum U GA into mo[0..2], mo[3..5], mo[6..8], mo[9..11] (float32 per
+// thread over its few lattice points).
+__device__ __forceinline__ void grad_lattice_moments(const TileInfo &ti, int kxy, const float *gxy,
+                                                     const float *C, const float *G, int Lmax,
+                                                     float mo[12])
+{
+    const float cu = 0.5f * (float)(ti.w - 1), cv = 0.5f * (float)(ti.h - 1);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) mo[k] = 0.f;
+    for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) {
+        const int lj = qdiv(lp, ti.rLw), li = lp - lj * ti.Lw;
+        float u = 0.f;
+        for (int dj = -kxy; dj <= kxy; ++dj) {
+            int cj = lj - kxy - dj;
+            if (cj < 0 || cj >= ti.th) continue;
+            float rr = 0.f;
+            for (int di = -kxy; di <= kxy; ++di) {
+                int ci = li - kxy - di;
+                if (ci < 0 || ci >= ti.tw) continue;
+                rr = fmaf(gxy[di + kxy], C[cj * ti.tw + ci], rr);
+            }
+            u = fmaf(gxy[dj + kxy], rr, u);
+        }
+        if (u == 0.f) continue;
+        const float di = (float)(ti.i0 - kxy + li) - cu, dj = (float)(ti.j0 - kxy + lj) - cv;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const float s0 = u * __ldcg(G + r * Lmax + lp);
+            mo[r] = fmaf(s0, di, mo[r]);
+            mo[3 + r] = fmaf(s0, dj, mo[3 + r]);
+            mo[6 + r] = fmaf(u, __ldcg(G + (3 + r) * Lmax + lp), mo[6 + r]);
+            mo[9 + r] += s0;
+        }
+    }
+}
+
 // ----------------------------------------------------------------- K6b --
 // Pose gradient of NCC from the gradient sums K6a streamed to gbuf.
 // dNCC/ds_i = ((y_i - my)/sd - ncc (s_i - ms)/vs)/N; pixel coefficient
@@ -1071,11 +1167,11 @@ __global__ void __launch_bounds__(256) k_ncc_grad(VolDims vd, const DevGeom *__r
     }
     const int np = ti.tw * ti.th;
     float *U = sm, *C = sm + ti.L;
-    lattice_forward<KZ>(nullptr, vd, ti, kxy, kz, psf.gz[ti.stack], kAlongCol, nullptr, U);
+    lattice_forward<KZ>(PlainVol{nullptr}, vd, ti, kxy, kz, psf.gz[ti.stack], kAlongCol, nullptr, U);
     __syncthreads();
     const float a_sc = sh_coef[0], b_sc = sh_coef[1], my = sh_coef[2], ms = sh_coef[3];
     for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
-        int ci = pp % ti.tw, cj = pp / ti.tw;
+        const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
         size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
         float c = 0.f;
         if (v_buf[o]) {
@@ -1085,36 +1181,8 @@ __global__ void __launch_bounds__(256) k_ncc_grad(VolDims vd, const DevGeom *__r
         C[pp] = c;
     }
     __syncthreads();
-    const float *G = gbuf + (size_t)blockIdx.x * 6 * Lmax;
-    const float cu = 0.5f * (float)(ti.w - 1), cv = 0.5f * (float)(ti.h - 1);
     float mo[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) mo[k] = 0.f;
-    for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) {
-        int li = lp % ti.Lw, lj = lp / ti.Lw;
-        float u = 0.f;
-        for (int dj = -kxy; dj <= kxy; ++dj) {
-            int cj = lj - kxy - dj;
-            if (cj < 0 || cj >= ti.th) continue;
-            float rr = 0.f;
-            for (int di = -kxy; di <= kxy; ++di) {
-                int ci = li - kxy - di;
-                if (ci < 0 || ci >= ti.tw) continue;
-                rr = fmaf(psf.gxy[di + kxy], C[cj * ti.tw + ci], rr);
-            }
-            u = fmaf(psf.gxy[dj + kxy], rr, u);
-        }
-        if (u == 0.f) continue;
-        const float di = (float)(ti.i0 - kxy + li) - cu, dj = (float)(ti.j0 - kxy + lj) - cv;
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            const float s0 = u * __ldg(G + r * Lmax + lp);
-            mo[r] = fmaf(s0, di, mo[r]);
-            mo[3 + r] = fmaf(s0, dj, mo[3 + r]);
-            mo[6 + r] = fmaf(u, __ldg(G + (3 + r) * Lmax + lp), mo[6 + r]);
-            mo[9 + r] += s0;
-        }
-    }
+    grad_lattice_moments(ti, kxy, psf.gxy, C, gbuf + (size_t)blockIdx.x * 6 * Lmax, Lmax, mo);
     double mom[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) mom[k] = (double)mo[k];
@@ -1122,6 +1190,118 @@ __global__ void __launch_bounds__(256) k_ncc_grad(VolDims vd, const DevGeom *__r
     if (threadIdx.x == 0) {
         for (int k = 0; k < 12; ++k) gp[k] = mom[k];
         for (int k = 12; k < kGradStride; ++k) gp[k] = 0.0;
+    }
+}
+
+// K6a + K6b in one persistent kernel for one-tile patches (every patch side
+// <= the tile side): the CTA holds the whole patch, so once its moments are
+// reduced it knows the patch's NCC coefficients and finishes the gradient
+// moments itself.  The gradient sums GA, GB of the current tile go to the
+// CTA's own slot of the scratch (6 Lmax floats, rewritten for every tile and
+// read back by the same CTA through L2), so they never make an HBM round
+// trip, and no simulated pixel values are stored.  Grid: at most the number
+// of co-resident CTAs; CTA b takes tiles b, b + grid, ...
+template <int KXY, int KZ, class SRC>
+__global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
+                                                      const int32_t *__restrict__ desc,
+                                                      const int32_t *__restrict__ fix, PsfTab psf,
+                                                      Tiling tl, long long n_tiles,
+                                                      const float *__restrict__ y,
+                                                      const int32_t *__restrict__ active,
+                                                      double *__restrict__ part,
+                                                      double *__restrict__ gpart,
+                                                      float *__restrict__ scratch, int Lmax,
+                                                      int min_valid)
+{
+    extern __shared__ float sm[];
+    __shared__ double red[32 * 12];
+    __shared__ float sh_coef[4];
+    __shared__ int sh_ok;
+    const int kxy = KXY >= 0 ? KXY : psf.kxy;
+    const int kz = KZ >= 0 ? KZ : psf.kz;
+    float *G = scratch + (size_t)blockIdx.x * 6 * Lmax;
+    float *A = sm, *B = sm + Lmax, *C = sm + 2 * Lmax;
+    for (long long gid = blockIdx.x; gid < n_tiles; gid += gridDim.x) {
+        TileInfo ti;
+        const bool has = tile_setup_at(gid, desc, fix, tl, kxy, ti);
+        double *pt = part + (size_t)gid * kPartStride;
+        double *gp = gpart + (size_t)gid * kGradStride;
+        // outside the fixed-point range every pixel is invalid: zero moments
+        if (!has || !ti.ok || (active && !active[ti.p])) {
+            if (threadIdx.x < kPartStride) pt[threadIdx.x] = 0.0;
+            if (threadIdx.x < kGradStride) gp[threadIdx.x] = 0.0;
+            continue;
+        }
+        const float *gz = psf.gz[ti.stack];
+        const int order = pick_order(ti, kz);
+        if (tile_interior(ti, vd, kxy, kz))
+            moments_gather<KZ, true, SRC>(x, vd, ti, kxy, kz, order, gz, A, B, G, Lmax);
+        else
+            moments_gather<KZ, false, SRC>(x, vd, ti, kxy, kz, order, gz, A, B, G, Lmax);
+        __syncthreads();
+        FFSum f1, f2, f3, f4, f5;
+        int cnt = 0;
+        const int np = ti.tw * ti.th;
+        for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
+            const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
+            const float den = inplane(B, ti.Lw, kxy, psf.gxy, ci, cj);
+            if (den > 0.f) {
+                const float sv = inplane(A, ti.Lw, kxy, psf.gxy, ci, cj) / den;
+                const size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
+                const float a = __ldg(y + o);
+                ++cnt;
+                f1.add(a);
+                f2.add(sv);
+                f3.add_prod(a, a);
+                f4.add_prod(sv, sv);
+                f5.add_prod(a, sv);
+            }
+        }
+        double m[6] = {(double)cnt, f1.value(), f2.value(), f3.value(), f4.value(), f5.value()};
+        block_sum<6>(m, red);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) pt[k] = m[k];
+            pt[6] = pt[7] = 0.0;
+            double ncc, my, ms, sd, vs, n;
+            const bool ok = ncc_of_sums(m, min_valid, ncc, my, ms, sd, vs, n);
+            sh_ok = ok;
+            if (ok) {
+                sh_coef[0] = (float)(1.0 / (n * sd));
+                sh_coef[1] = (float)(ncc / (n * vs));
+                sh_coef[2] = (float)my;
+                sh_coef[3] = (float)ms;
+            }
+        }
+        __syncthreads();
+        if (!sh_ok) {
+            if (threadIdx.x < kGradStride) gp[threadIdx.x] = 0.0;
+            continue;
+        }
+        // dNCC/ds per pixel over its PSF weight (as K6b), from the same A, B
+        const float a_sc = sh_coef[0], b_sc = sh_coef[1], my = sh_coef[2], ms = sh_coef[3];
+        for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
+            const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
+            const float den = inplane(B, ti.Lw, kxy, psf.gxy, ci, cj);
+            float c = 0.f;
+            if (den > 0.f) {
+                const float sv = inplane(A, ti.Lw, kxy, psf.gxy, ci, cj) / den;
+                const size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
+                c = (a_sc * (__ldg(y + o) - my) - b_sc * (sv - ms)) / den;
+            }
+            C[pp] = c;
+        }
+        __syncthreads();
+        float mo[12];
+        grad_lattice_moments(ti, kxy, psf.gxy, C, G, Lmax, mo);
+        double mom[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) mom[k] = (double)mo[k];
+        block_sum<12>(mom, red);   // ends with a barrier: A, B, C, G free for the next tile
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < 12; ++k) gp[k] = mom[k];
+            for (int k = 12; k < kGradStride; ++k) gp[k] = 0.0;
+        }
     }
 }
 
@@ -1172,6 +1352,21 @@ size_t smem_adjoint(const Tiling &tl, int kxy)
     return (2 * L + 2 * (size_t)tl.T * tl.T) * sizeof(float);
 }
 
+// Quad copy of the volume for QuadVol gathers: q[i] = (x[i], x[i + 1],
+// x[i + nx], x[i + nx + 1]) for every voxel i with bx < nx - 1 and
+// by < ny - 1 (the cells a sample can address); the last column and row
+// are never read and hold their own voxel four times.
+__global__ void k_build_quad(const float *__restrict__ x, float4 *__restrict__ q, int nx, int ny,
+                             unsigned n)
+{
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned bx = i % (unsigned)nx, by = (i / (unsigned)nx) % (unsigned)ny;
+        const unsigned dx = bx + 1 < (unsigned)nx ? 1u : 0u;
+        const unsigned dy = by + 1 < (unsigned)ny ? (unsigned)nx : 0u;
+        q[i] = make_float4(__ldg(x + i), __ldg(x + i + dx), __ldg(x + i + dy), __ldg(x + i + dy + dx));
+    }
+}
+
 template <typename K>
 cudaError_t prep(K kern, size_t smem)
 {
@@ -1185,22 +1380,42 @@ cudaError_t prep(K kern, size_t smem)
 // every other setting takes the runtime-loop instantiation.
 
 cudaError_t launch_simulate(const DevGeom *, const PsfTab &psf, const Tiling &tl, int nx, int ny,
-                            int nz, const float *x, const int32_t *desc, const int32_t *fix, int n,
-                            const float *y, float *out, uint8_t *valid, double *part,
-                            cudaStream_t st)
+                            int nz, const float *x, const float4 *quad, const int32_t *desc,
+                            const int32_t *fix, int n, const float *y, float *out, uint8_t *valid,
+                            double *part, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     VolDims vd = vol_dims(nx, ny, nz);
     size_t smem = smem_forward(tl, psf.kxy);
     dim3 grid((unsigned)n * tl.tpp), block(256);
     cudaError_t e;
-    if (psf.kxy == 1 && psf.kz == 3) {
-        if ((e = prep(k_simulate<1, 3>, smem)) != cudaSuccess) return e;
-        k_simulate<1, 3><<<grid, block, smem, st>>>(x, vd, desc, fix, psf, tl, y, out, valid, part);
+#define PVR_SIM(KX, KZv, SRCT, src)                                                                  \
+    do {                                                                                          \
+        if ((e = prep(k_simulate<KX, KZv, SRCT>, smem)) != cudaSuccess) return e;                  \
+        k_simulate<KX, KZv, SRCT><<<grid, block, smem, st>>>(src, vd, desc, fix, psf, tl, y, out, valid, \
+                                                             part);                               \
+    } while (0)
+    const bool fast = psf.kxy == 1 && psf.kz == 3;
+    if (quad) {
+        if (fast) PVR_SIM(1, 3, QuadVol, QuadVol{quad});
+        else PVR_SIM(-1, -1, QuadVol, QuadVol{quad});
     } else {
-        if ((e = prep(k_simulate<-1, -1>, smem)) != cudaSuccess) return e;
-        k_simulate<-1, -1><<<grid, block, smem, st>>>(x, vd, desc, fix, psf, tl, y, out, valid, part);
+        if (fast) PVR_SIM(1, 3, PlainVol, PlainVol{x});
+        else PVR_SIM(-1, -1, PlainVol, PlainVol{x});
     }
+#undef PVR_SIM
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_quad(const float *x, float4 *quad, int nx, int ny, int nz, cudaStream_t st)
+{
+    const unsigned n = (unsigned)nx * (unsigned)ny * (unsigned)nz;
+    int dev = 0, nsm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    unsigned blocks = (n + 255) / 256, cap = 8u * (unsigned)nsm;
+    k_build_quad<<<blocks < cap ? blocks : cap, 256, 0, st>>>(x, quad, nx, ny, n);
     return cudaGetLastError();
 }
 
@@ -1230,37 +1445,66 @@ cudaError_t launch_adjoint(const PsfTab &psf, const Tiling &tl, int nx, int ny, 
 }
 
 cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &tl, int nx, int ny,
-                            int nz, const float *x, const float *y, const int32_t *desc,
+                            int nz, const float4 *quad, const float *y, const int32_t *desc,
                             const int32_t *fix, const double *poses, int n, float *s_buf,
                             uint8_t *v_buf, double *part, double *gpart, const int32_t *active,
                             int min_valid, float *gbuf, long long gbuf_tiles, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     VolDims vd = vol_dims(nx, ny, nz);
+    const QuadVol x{quad};
     size_t smem = smem_forward(tl, psf.kxy);
     const int Lmax = (tl.T + 2 * psf.kxy) * (tl.T + 2 * psf.kxy);
     size_t smem2 = (size_t)(Lmax + tl.T * tl.T) * sizeof(float);
     const long long total = (long long)n * tl.tpp;
+    const bool fast = psf.kxy == 1 && psf.kz == 3;
+    cudaError_t e;
+    if (gpart && tl.tpp == 1) {
+        // one-tile patches: the fused persistent kernel, one scratch slot per CTA
+        size_t smem3 = (size_t)(2 * Lmax + tl.T * tl.T) * sizeof(float);
+        int dev = 0, nsm = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if (fast) {
+            if ((e = prep(k_ncc_fused<1, 3, QuadVol>, smem3)) != cudaSuccess) return e;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ncc_fused<1, 3, QuadVol>, 256, smem3);
+        } else {
+            if ((e = prep(k_ncc_fused<-1, -1, QuadVol>, smem3)) != cudaSuccess) return e;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ncc_fused<-1, -1, QuadVol>, 256, smem3);
+        }
+        if (e != cudaSuccess) return e;
+        long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
+        if (grid > total) grid = total;
+        if (grid > gbuf_tiles) grid = gbuf_tiles;
+        if (grid <= 0) return cudaErrorInvalidValue;
+        if (fast)
+            k_ncc_fused<1, 3, QuadVol><<<(unsigned)grid, 256, smem3, st>>>(x, vd, desc, fix, psf, tl, total, y, active,
+                                                                  part, gpart, gbuf, Lmax, min_valid);
+        else
+            k_ncc_fused<-1, -1, QuadVol><<<(unsigned)grid, 256, smem3, st>>>(x, vd, desc, fix, psf, tl, total, y,
+                                                                    active, part, gpart, gbuf, Lmax,
+                                                                    min_valid);
+        return cudaGetLastError();
+    }
     // chunks of whole patches that fit the gradient scratch
     long long chunk = gpart ? (gbuf_tiles / tl.tpp) * tl.tpp : total;
     if (chunk <= 0) return cudaErrorInvalidValue;
-    const bool fast = psf.kxy == 1 && psf.kz == 3;
-    cudaError_t e;
     if (fast) {
-        if ((e = prep(k_ncc_moments<1, 3>, smem)) != cudaSuccess) return e;
+        if ((e = prep(k_ncc_moments<1, 3, QuadVol>, smem)) != cudaSuccess) return e;
         if ((e = prep(k_ncc_grad<1, 3>, smem2)) != cudaSuccess) return e;
     } else {
-        if ((e = prep(k_ncc_moments<-1, -1>, smem)) != cudaSuccess) return e;
+        if ((e = prep(k_ncc_moments<-1, -1, QuadVol>, smem)) != cudaSuccess) return e;
         if ((e = prep(k_ncc_grad<-1, -1>, smem2)) != cudaSuccess) return e;
     }
+    if (!gpart) s_buf = nullptr, v_buf = nullptr;
     for (long long base = 0; base < total; base += chunk) {
         unsigned grid = (unsigned)((total - base) < chunk ? (total - base) : chunk);
         float *gb = gpart ? gbuf : nullptr;
         if (fast)
-            k_ncc_moments<1, 3><<<grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, base, y, active, s_buf,
+            k_ncc_moments<1, 3, QuadVol><<<grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, base, y, active, s_buf,
                                                          v_buf, part, gb, Lmax);
         else
-            k_ncc_moments<-1, -1><<<grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, base, y, active,
+            k_ncc_moments<-1, -1, QuadVol><<<grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, base, y, active,
                                                            s_buf, v_buf, part, gb, Lmax);
         if (!gpart) continue;
         if (fast)
@@ -1277,6 +1521,15 @@ cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &t
 size_t ncc_gbuf_floats_per_tile(const Tiling &tl, int kxy)
 {
     return 6 * (size_t)(tl.T + 2 * kxy) * (tl.T + 2 * kxy);
+}
+
+int ncc_launch_count(const Tiling &tl, int n, bool grad, long long gbuf_tiles)
+{
+    if (n <= 0) return 0;
+    if (!grad) return 1;
+    if (tl.tpp == 1) return 1;
+    const long long total = (long long)n * tl.tpp, chunk = (gbuf_tiles / tl.tpp) * tl.tpp;
+    return chunk > 0 ? (int)(2 * ((total + chunk - 1) / chunk)) : 0;
 }
 
 cudaError_t launch_ncc_finish(const DevGeom *g, const int32_t *desc, const double *poses, int n,

@@ -59,6 +59,7 @@ struct pvr_ctx {
     float *s_buf = nullptr, *e_buf = nullptr, *p_buf = nullptr;
     uint8_t *v_buf = nullptr, *valid_buf = nullptr, *mask_tmp = nullptr;
     float2 *acc2 = nullptr;   // interleaved (addon, conf) accumulator, one pair per voxel
+    float4 *quad = nullptr;   // quad copy of the volume read by the gathers
     float *gbuf = nullptr;    // NCC gradient scratch (per-lattice-point gradient sums)
     long long gbuf_tiles = 0;
     int32_t *keep = nullptr;
@@ -169,10 +170,18 @@ void free_all(pvr_ctx *c)
     void *ptrs[] = {c->d_geom, c->fix, c->part, c->gpart, c->pstat, c->pbar, c->wsc, c->emblk, c->elig,
                     c->err, c->best, c->gbest, c->nbest, c->trial, c->delta, c->ncc_tmp,
                     c->grad_tmp, c->active, c->s_buf, c->e_buf, c->p_buf, c->v_buf,
-                    c->valid_buf, c->mask_tmp, c->acc2, c->gbuf, c->keep, c->imax_key,
+                    c->valid_buf, c->mask_tmp, c->acc2, c->quad, c->gbuf, c->keep, c->imax_key,
                     c->counts, c->metric_scr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+}
+
+// Quad copy of x for the gathers (once per call that gathers from x).
+int build_quad(pvr_ctx *c, const float *x, cudaStream_t st)
+{
+    CUDA_TRY(launch_build_quad(x, c->quad, c->geom.nx, c->geom.ny, c->geom.nz, st), "quad");
+    c->launches += 1;
+    return PVR_OK;
 }
 
 // K1 for a patch table at `poses` into the context's fixed table.
@@ -231,6 +240,8 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
     };
     if (g->nx < 2 || g->ny < 2 || g->nz < 2 || g->nx > 2048 || g->ny > 2048 || g->nz > 2048)
         return bad("volume sizes must be 2..2048");
+    if ((int64_t)g->nx * g->ny * g->nz >= ((int64_t)1 << 31))
+        return bad("the volume must have fewer than 2^31 voxels");
     if (g->n_stacks < 1 || g->n_stacks > PVR_MAX_STACKS) return bad("n_stacks outside 1..16");
     for (int s = 0; s < g->n_stacks; ++s) {
         if (g->stack_w[s] < 1 || g->stack_h[s] < 1 || g->stack_k[s] < 1) return bad("empty stack");
@@ -325,6 +336,7 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
     ALLOC(c->valid_buf, NP);
     ALLOC(c->mask_tmp, P);
     ALLOC(c->acc2, (size_t)c->nvox);
+    ALLOC(c->quad, (size_t)c->nvox);
     {
         // gradient scratch: all tiles if they fit in 2.5 GB, else chunks of whole patches
         size_t per = ncc_gbuf_floats_per_tile(tl, prm->psf_kxy) * sizeof(float);
@@ -450,10 +462,13 @@ int pvr_simulate(pvr_ctx *c, const float *x, const pvr_patches *pp, const double
     if (rc) return rc;
     REQUIRE(pp->n == 0 || (x && poses && sim && valid), "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
+    if (pp->n == 0) return PVR_OK;
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
+    if ((rc = build_quad(c, x, st))) return rc;
     Tiling tl = make_tiling(ms);
-    CUDA_TRY_T(PVR_K_SIMULATE, launch_simulate(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, pp->desc,
-                             c->fix, pp->n, nullptr, sim, valid, nullptr, st),
+    CUDA_TRY_T(PVR_K_SIMULATE, launch_simulate(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x,
+                                               c->quad, pp->desc, c->fix, pp->n, nullptr, sim, valid,
+                                               nullptr, st),
              "simulate");
     c->launches += pp->n > 0;
     return PVR_OK;
@@ -546,9 +561,11 @@ int pvr_ncc_grad(pvr_ctx *c, const float *x, const float *y, const pvr_patches *
     if (rc) return rc;
     REQUIRE(pp->n == 0 || (x && y && poses && ncc), "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
+    if (pp->n == 0) return PVR_OK;
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
+    if ((rc = build_quad(c, x, st))) return rc;
     Tiling tl = make_tiling(ms);
-    CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, y,
+    CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, c->quad, y,
                              pp->desc, c->fix, poses, pp->n, c->s_buf, c->v_buf, c->part,
                              grad ? c->gpart : nullptr, nullptr, c->prm.reg_min_valid, c->gbuf,
                              c->gbuf_tiles, st),
@@ -556,13 +573,15 @@ int pvr_ncc_grad(pvr_ctx *c, const float *x, const float *y, const pvr_patches *
     CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(c->d_geom, pp->desc, poses, pp->n, tl, c->part, c->gpart, c->prm.reg_min_valid, ncc,
                                grad, st),
              "ncc_finish");
-    c->launches += pp->n > 0 ? (grad ? 3 : 2) : 0;
+    c->launches += ncc_launch_count(tl, pp->n, grad != nullptr, c->gbuf_tiles) + (pp->n > 0);
     return PVR_OK;
 }
 
+// Registration rounds; gathers from c->quad, which the caller has built from x.
 static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_patches *pp, int ms,
                          double *poses, int n_evals, double *ncc_out, cudaStream_t st)
 {
+    (void)x;
     int n = pp->n;
     if (n == 0 || n_evals <= 0) return PVR_OK;
     Tiling tl = make_tiling(ms);
@@ -572,19 +591,23 @@ static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_p
     for (int ev = 0; ev < n_evals; ++ev) {
         int rc = pose_fixed(c, pp, ms, c->trial, st);
         if (rc) return rc;
-        CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, y,
+        // the last evaluation only decides acceptance: its gradient would
+        // never be used, so it computes the NCC alone
+        const bool need_grad = ev < n_evals - 1;
+        double *gpart = need_grad ? c->gpart : nullptr, *grad = need_grad ? c->grad_tmp : nullptr;
+        CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, c->quad, y,
                                  pp->desc, c->fix, c->trial, n, c->s_buf, c->v_buf, c->part,
-                                 c->gpart, c->active, c->prm.reg_min_valid, c->gbuf, c->gbuf_tiles,
+                                 gpart, c->active, c->prm.reg_min_valid, c->gbuf, c->gbuf_tiles,
                                  st),
                  "ncc_grad");
-        CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(c->d_geom, pp->desc, c->trial, n, tl, c->part, c->gpart, c->prm.reg_min_valid,
-                                   c->ncc_tmp, c->grad_tmp, st),
+        CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(c->d_geom, pp->desc, c->trial, n, tl, c->part, gpart, c->prm.reg_min_valid,
+                                   c->ncc_tmp, grad, st),
                  "ncc_finish");
         CUDA_TRY_T(PVR_K_REG_STEP, launch_reg_step(c->d_geom, pp->desc, n, ev, ev == n_evals - 1, c->ncc_tmp,
-                                 c->grad_tmp, c->best, c->gbest, c->nbest, c->trial, c->delta,
+                                 grad, c->best, c->gbest, c->nbest, c->trial, c->delta,
                                  c->active, c->prm, st),
                  "reg_step");
-        c->launches += 4;
+        c->launches += ncc_launch_count(tl, n, need_grad, c->gbuf_tiles) + 2;
     }
     CUDA_TRY(launch_reg_finish(c->best, c->nbest, n, poses, ncc_out, st), "reg_finish");
     c->launches += 1;
@@ -600,6 +623,8 @@ int pvr_register(pvr_ctx *c, const float *x, const float *y, const pvr_patches *
     if (rc) return rc;
     REQUIRE(n_evals >= 0, "n_evals < 0");
     REQUIRE(pp->n == 0 || (x && y && poses), "NULL argument");
+    if (pp->n == 0 || n_evals == 0) return PVR_OK;
+    if ((rc = build_quad(c, x, (cudaStream_t)stream))) return rc;
     return register_impl(c, x, y, pp, ms, poses, n_evals, ncc, (cudaStream_t)stream);
 }
 
@@ -612,13 +637,17 @@ int pvr_reconstruct_iter(pvr_ctx *c, float *x, const float *y, const pvr_patches
     if (rc) return rc;
     REQUIRE(x && y && state && mask && (pp->n == 0 || poses), "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = build_quad(c, x, st))) return rc;
     if ((rc = register_impl(c, x, y, pp, ms, poses, c->prm.reg_evals, nullptr, st))) return rc;
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     Tiling tl = make_tiling(ms);
     CUDA_TRY(cudaMemsetAsync(c->acc2, 0, (size_t)c->nvox * sizeof(float2), st), "clear");
     for (int it = 0; it < c->prm.n_sr; ++it) {
+        // x changes with every SR pass: refresh its quad copy after the first
+        if (it > 0 && (rc = build_quad(c, x, st))) return rc;
         CUDA_TRY_T(PVR_K_SIMULATE, launch_simulate(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x,
-                                 pp->desc, c->fix, pp->n, y, c->e_buf, c->valid_buf, c->part, st),
+                                                   c->quad, pp->desc, c->fix, pp->n, y, c->e_buf,
+                                                   c->valid_buf, c->part, st),
                  "simulate");
         CUDA_TRY_T(PVR_K_EM, launch_em(c->e_buf, nullptr, c->valid_buf, pp->desc, pp->n, pp->n_pix, tl, c->err,
                            state, mask, c->mask_tmp, c->p_buf, w_patch, nullptr, c->part, c->pstat,

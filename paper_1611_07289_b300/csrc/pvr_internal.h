@@ -44,10 +44,15 @@ cudaError_t launch_pose_to_fixed(const DevGeom *g, const int32_t *desc, const do
                                  int n, int64_t n_pix, int max_side, int kxy, int kz,
                                  int32_t *fix, int32_t *err, cudaStream_t st);
 
+// Forward model from x (quad == null) or from the quad copy of x.
 cudaError_t launch_simulate(const DevGeom *g, const PsfTab &psf, const Tiling &tl, int nx, int ny,
-                            int nz, const float *x, const int32_t *desc, const int32_t *fix, int n,
-                            const float *y, float *sim_or_e, uint8_t *valid, double *part,
-                            cudaStream_t st);
+                            int nz, const float *x, const float4 *quad, const int32_t *desc,
+                            const int32_t *fix, int n, const float *y, float *sim_or_e,
+                            uint8_t *valid, double *part, cudaStream_t st);
+
+// Quad copy of the volume (nx * ny * nz < 2^31): quad[i] = (x[i], x[i + 1],
+// x[i + nx], x[i + nx + 1]), read by the gathers as two 16-byte loads per cell.
+cudaError_t launch_build_quad(const float *x, float4 *quad, int nx, int ny, int nz, cudaStream_t st);
 
 // pair = 1: addon points to interleaved (addon, conf) float2 pairs, conf unused.
 cudaError_t launch_adjoint(const PsfTab &psf, const Tiling &tl, int nx, int ny, int nz,
@@ -67,15 +72,19 @@ cudaError_t launch_volume_update(float *x, float *addon, float *conf, int64_t nv
                                  float conf_eps, int clear, int init_mode, cudaStream_t st);
 
 
-// NCC moments (+ gradient when gpart != null) of every patch; the gradient
-// pass streams per-lattice-point gradient sums through gbuf, processed in
-// chunks of whole patches of at most gbuf_tiles tiles.
+// NCC moments (+ gradient when gpart != null) of every patch, gathering
+// from the quad copy of the volume.  One-tile patches run one fused
+// persistent kernel with a gbuf slot per CTA; otherwise the gradient pass
+// streams per-lattice-point gradient sums through gbuf, in chunks of whole
+// patches of at most gbuf_tiles tiles.
 cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &tl, int nx, int ny,
-                            int nz, const float *x, const float *y, const int32_t *desc,
+                            int nz, const float4 *quad, const float *y, const int32_t *desc,
                             const int32_t *fix, const double *poses, int n, float *s_buf,
                             uint8_t *v_buf, double *part, double *gpart, const int32_t *active,
                             int min_valid, float *gbuf, long long gbuf_tiles, cudaStream_t st);
 size_t ncc_gbuf_floats_per_tile(const Tiling &tl, int kxy);
+// Kernel launches launch_ncc_grad makes for these arguments.
+int ncc_launch_count(const Tiling &tl, int n, bool grad, long long gbuf_tiles);
 
 cudaError_t launch_ncc_finish(const DevGeom *g, const int32_t *desc, const double *poses, int n,
                               const Tiling &tl, const double *part, const double *gpart,
