@@ -17,6 +17,7 @@
  *                      potentials and patch classification         Outlier Removal")
  *   or_volume_update   weighted SIRT step                         (super-resolution by gradient descent, Sec. II)
  *   or_ncc_grad        NCC of a patch and d NCC / d pose          (Sec. II registration with CC; Eq. cross_corr)
+ *   or_sim_pose_vjp    d (sum r * sim) / d pose of one patch      (Eq. 1 differentiated through the sample positions)
  *   or_register        per-patch gradient ascent on NCC           (Sec. III "patch-wise gradient descent")
  *   or_metrics         PSNR, CC, SSIM, DSSIM                      (Eqs. cross_corr, PSNR, SSIM, DSSIM)
  *
@@ -733,19 +734,20 @@ static int or_reg_sample(const or_geom *g, const float *x, const int64_t *f, con
     return 1;
 }
 
-/* NCC between the acquired patch y and the patch simulated at pose th, and
- * its gradient with respect to the pose (Sec. II: registration maximises CC,
- * Eq. cross_corr with population standard deviations, over valid pixels).
- * d sim / d theta = sum_samples g * grad_trilinear . d q / d theta / den, the
- * normalisation den being treated as constant.  Fewer than min_valid valid
- * pixels or a (near-)constant patch give NCC = 0 and a zero gradient.
- * Returns the NCC; grad receives n_params values. */
-double or_ncc_grad(const or_geom *g, const or_psf *psf, const float *x, const float *y,
-                   const int *d, const double *th, int n_params, int min_valid, int exact,
-                   double *grad)
+/* Simulated value s, validity ok and pose Jacobian J = d s / d theta
+ * (n_params per pixel) of every pixel of one patch at pose th, by the
+ * definition of the forward model (Eq. 1: PSF-weighted trilinear samples
+ * over the in-volume PSF weight) differentiated through the sample
+ * positions: d s / d theta = sum_samples g * grad_trilinear . d q / d theta
+ * / den, the normalisation den treated as constant (it changes only where a
+ * sample leaves the volume).  exact selects the fixed-point lattice or plain
+ * FP64 positions (or_reg_sample).  Returns 0 when the exact lattice is out of
+ * range (every pixel invalid). */
+static int or_patch_sim_jac(const or_geom *g, const or_psf *psf, const float *x, const int *d,
+                            const double *th, int n_params, int exact, double *s, uint8_t *ok,
+                            double *J)
 {
     int K = psf->kxy, Kz = psf->kz, w = d[4], h = d[5];
-    size_t npx = (size_t)w * h, off = (size_t)d[6];
     int64_t f[16];
     double M[12], gxy[33], gzt[65], c[3];
     or_pose_fixed(g, psf, d, th, n_params, f);
@@ -757,12 +759,7 @@ double or_ncc_grad(const or_geom *g, const or_psf *psf, const float *x, const fl
     const double *W = g->w2v;
     double dL[9][9];
     or_dlinear(th, n_params, dL);
-    for (int k = 0; k < n_params; ++k) grad[k] = 0.0;
-    if (exact && !f[12]) return 0.0;
-
-    double *s = (double *)calloc(npx, sizeof(double));
-    double *J = (double *)calloc(npx * (size_t)n_params, sizeof(double));
-    uint8_t *ok = (uint8_t *)calloc(npx, 1);
+    if (exact && !f[12]) return 0;
     for (int j = 0; j < h; ++j)
         for (int i = 0; i < w; ++i) {
             double num = 0.0, dn = 0.0, jac[12] = {0};
@@ -794,6 +791,57 @@ double or_ncc_grad(const or_geom *g, const or_psf *psf, const float *x, const fl
                 for (int k = 0; k < n_params; ++k) J[o * n_params + k] = jac[k] / dn;
             }
         }
+    return 1;
+}
+
+/* Pose gradient of sum_pix r_pix s_pix for one patch (the vector-Jacobian
+ * product of the forward model with respect to the patch pose, what the
+ * backward pass of a differentiable simulate needs), with r indexed like
+ * the patch pixels (offset d[6]).  Returns sum_pix r_pix s_pix over the
+ * valid pixels; grad receives n_params values. */
+double or_sim_pose_vjp(const or_geom *g, const or_psf *psf, const float *x, const double *r,
+                       const int *d, const double *th, int n_params, int exact, double *grad)
+{
+    size_t npx = (size_t)d[4] * d[5], off = (size_t)d[6];
+    for (int k = 0; k < n_params; ++k) grad[k] = 0.0;
+    double *s = (double *)calloc(npx, sizeof(double));
+    double *J = (double *)calloc(npx * (size_t)n_params, sizeof(double));
+    uint8_t *ok = (uint8_t *)calloc(npx, 1);
+    double val = 0.0;
+    if (or_patch_sim_jac(g, psf, x, d, th, n_params, exact, s, ok, J))
+        for (size_t o = 0; o < npx; ++o)
+            if (ok[o]) {
+                val += r[off + o] * s[o];
+                for (int k = 0; k < n_params; ++k) grad[k] += r[off + o] * J[o * n_params + k];
+            }
+    free(s);
+    free(J);
+    free(ok);
+    return val;
+}
+
+/* NCC between the acquired patch y and the patch simulated at pose th, and
+ * its gradient with respect to the pose (Sec. II: registration maximises CC,
+ * Eq. cross_corr with population standard deviations, over valid pixels).
+ * d sim / d theta = sum_samples g * grad_trilinear . d q / d theta / den, the
+ * normalisation den being treated as constant.  Fewer than min_valid valid
+ * pixels or a (near-)constant patch give NCC = 0 and a zero gradient.
+ * Returns the NCC; grad receives n_params values. */
+double or_ncc_grad(const or_geom *g, const or_psf *psf, const float *x, const float *y,
+                   const int *d, const double *th, int n_params, int min_valid, int exact,
+                   double *grad)
+{
+    size_t npx = (size_t)d[4] * d[5], off = (size_t)d[6];
+    for (int k = 0; k < n_params; ++k) grad[k] = 0.0;
+    double *s = (double *)calloc(npx, sizeof(double));
+    double *J = (double *)calloc(npx * (size_t)n_params, sizeof(double));
+    uint8_t *ok = (uint8_t *)calloc(npx, 1);
+    if (!or_patch_sim_jac(g, psf, x, d, th, n_params, exact, s, ok, J)) {
+        free(s);
+        free(J);
+        free(ok);
+        return 0.0;
+    }
     double n = 0.0, my = 0.0, ms = 0.0;
     for (size_t o = 0; o < npx; ++o)
         if (ok[o]) { n += 1.0; my += y[off + o]; ms += s[o]; }

@@ -89,6 +89,9 @@ def lib():
         L.or_ncc_grad.argtypes = [P(_Geom), P(_Psf), P(C.c_float), P(C.c_float), P(C.c_int),
                                   P(C.c_double), C.c_int, C.c_int, C.c_int, P(C.c_double)]
         L.or_ncc_grad.restype = C.c_double
+        L.or_sim_pose_vjp.argtypes = [P(_Geom), P(_Psf), P(C.c_float), P(C.c_double), P(C.c_int),
+                                      P(C.c_double), C.c_int, C.c_int, P(C.c_double)]
+        L.or_sim_pose_vjp.restype = C.c_double
         L.or_register.argtypes = [P(_Geom), P(_Psf), P(_RegParams), P(C.c_float), P(C.c_float),
                                   P(C.c_int), C.c_int, P(C.c_double), P(C.c_double)]
         L.or_metrics.argtypes = [P(C.c_double), P(C.c_double), P(C.c_uint8), C.c_size_t,
@@ -237,6 +240,20 @@ def ncc_grad(G, ps, x, y, drow, theta, n_params=6, min_valid=16, exact=True):
     v = lib().or_ncc_grad(C.byref(G), C.byref(ps), _ptr(x, C.c_float), _ptr(y, C.c_float),
                           _ptr(drow, C.c_int), _ptr(th, C.c_double), int(n_params), int(min_valid),
                           int(bool(exact)), _ptr(g, C.c_double))
+    return float(v), g
+
+
+def sim_pose_vjp(G, ps, x, r, drow, theta, n_params=6, exact=True):
+    """d (sum_pix r * sim) / d pose for one patch; returns (sum r * sim, grad).
+    r is indexed like the patch pixels (offset drow[6])."""
+    x = _c(x, np.float32)
+    r = _c(r, np.float64)
+    drow = _c(drow, np.int32)
+    th = _c(theta, np.float64)
+    g = np.zeros(n_params, dtype=np.float64)
+    v = lib().or_sim_pose_vjp(C.byref(G), C.byref(ps), _ptr(x, C.c_float), _ptr(r, C.c_double),
+                              _ptr(drow, C.c_int), _ptr(th, C.c_double), int(n_params),
+                              int(bool(exact)), _ptr(g, C.c_double))
     return float(v), g
 
 
