@@ -305,6 +305,19 @@ PVR_API int pvr_volume_init(pvr_ctx *ctx, float *x, const float *y, const pvr_pa
 PVR_API int pvr_ncc_grad(pvr_ctx *ctx, const float *x, const float *y, const pvr_patches *patches,
                  const double *poses, double *ncc, double *grad, void *stream);
 
+/* Pose gradient of sum_pix r_pix sim_pix for every patch: the
+ * vector-Jacobian product of pvr_simulate with respect to the poses, the
+ * backward pass of a differentiable forward model (Eq. 1 differentiated
+ * through the sample positions; the PSF normalisation is held constant, as
+ * in pvr_ncc_grad).  Together with pvr_adjoint (the product with respect to
+ * x) it gives both gradients of any loss of the simulated patches.  The PSF
+ * weights are recomputed, nothing is stored by the forward call.
+ * x: float32 volume; r: float32 [n_pix] (dL/dsim; invalid pixels ignored);
+ * poses: float64 [n][6]; grad: float64 [n][6] out.  This entry point extends
+ * the paper's method (the paper differentiates only NCC). */
+PVR_API int pvr_pose_grad(pvr_ctx *ctx, const float *x, const float *r, const pvr_patches *patches,
+                          const double *poses, double *grad, void *stream);
+
 /* Patch-wise gradient ascent on NCC (Sec. II; Sec. III "patch-wise gradient
  * descent"): n_evals NCC evaluations per patch, the first at the current
  * pose, then trials best + delta * g/|g| in scaled units (translations in

@@ -1305,6 +1305,66 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
     }
 }
 
+// Pose vector-Jacobian product of the forward model (backward pass of a
+// differentiable simulate): per tile, the gradient moments of
+// sum_pix r_pix s_pix, i.e. the lattice phase of the NCC gradient with the
+// pixel coefficient r / den.  Tile moments add over a patch's tiles, so any
+// tiling works.  Persistent like k_ncc_fused: one scratch slot per CTA.
+template <int KXY, int KZ, class SRC>
+__global__ void __launch_bounds__(256, 4) k_pose_vjp(const SRC x, VolDims vd,
+                                                     const int32_t *__restrict__ desc,
+                                                     const int32_t *__restrict__ fix, PsfTab psf,
+                                                     Tiling tl, long long n_tiles,
+                                                     const float *__restrict__ r,
+                                                     double *__restrict__ gpart,
+                                                     float *__restrict__ scratch, int Lmax)
+{
+    extern __shared__ float sm[];
+    __shared__ double red[32 * 12];
+    const int kxy = KXY >= 0 ? KXY : psf.kxy;
+    const int kz = KZ >= 0 ? KZ : psf.kz;
+    float *G = scratch + (size_t)blockIdx.x * 6 * Lmax;
+    float *A = sm, *B = sm + Lmax, *C = sm + 2 * Lmax;
+    for (long long gid = blockIdx.x; gid < n_tiles; gid += gridDim.x) {
+        TileInfo ti;
+        const bool has = tile_setup_at(gid, desc, fix, tl, kxy, ti);
+        double *gp = gpart + (size_t)gid * kGradStride;
+        if (!has || !ti.ok) {
+            if (threadIdx.x < kGradStride) gp[threadIdx.x] = 0.0;
+            continue;
+        }
+        const float *gz = psf.gz[ti.stack];
+        const int order = pick_order(ti, kz);
+        if (tile_interior(ti, vd, kxy, kz))
+            moments_gather<KZ, true, SRC>(x, vd, ti, kxy, kz, order, gz, A, B, G, Lmax);
+        else
+            moments_gather<KZ, false, SRC>(x, vd, ti, kxy, kz, order, gz, A, B, G, Lmax);
+        __syncthreads();
+        const int np = ti.tw * ti.th;
+        for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
+            const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
+            const float den = inplane(B, ti.Lw, kxy, psf.gxy, ci, cj);
+            float c = 0.f;
+            if (den > 0.f) {
+                const size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
+                c = __ldg(r + o) / den;
+            }
+            C[pp] = c;
+        }
+        __syncthreads();
+        float mo[12];
+        grad_lattice_moments(ti, kxy, psf.gxy, C, G, Lmax, mo);
+        double mom[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) mom[k] = (double)mo[k];
+        block_sum<12>(mom, red);   // ends with a barrier: A, B, C, G free for the next tile
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < 12; ++k) gp[k] = mom[k];
+            for (int k = 12; k < kGradStride; ++k) gp[k] = 0.0;
+        }
+    }
+}
+
 // Per patch: NCC from the tile moments, and the pose gradient as the
 // contraction of the summed gradient moments with the pose Jacobian.
 __global__ void k_ncc_finish(const DevGeom *__restrict__ g, int n, int tpp,
@@ -1314,9 +1374,12 @@ __global__ void k_ncc_finish(const DevGeom *__restrict__ g, int n, int tpp,
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    double v, my, ms, sd, vs, nn;
-    bool ok = ncc_from_moments(part, p, tpp, min_valid, v, my, ms, sd, vs, nn);
-    ncc[p] = ok ? v : 0.0;
+    bool ok = true;   // part == null: gradient moments only (pose VJP)
+    if (part) {
+        double v, my, ms, sd, vs, nn;
+        ok = ncc_from_moments(part, p, tpp, min_valid, v, my, ms, sd, vs, nn);
+        ncc[p] = ok ? v : 0.0;
+    }
     if (!grad) return;
     double *gr = grad + 6 * (size_t)p;
     if (!ok) {
@@ -1514,6 +1577,43 @@ cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &t
             k_ncc_grad<-1, -1><<<grid, 256, smem2, st>>>(vd, g, desc, fix, psf, tl, base, y, poses, active,
                                                          s_buf, v_buf, part, gpart, gbuf, Lmax, min_valid);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pose_vjp(const PsfTab &psf, const Tiling &tl, int nx, int ny, int nz,
+                            const float4 *quad, const float *r, const int32_t *desc,
+                            const int32_t *fix, int n, double *gpart, float *gbuf,
+                            long long gbuf_tiles, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    VolDims vd = vol_dims(nx, ny, nz);
+    const QuadVol x{quad};
+    const int Lmax = (tl.T + 2 * psf.kxy) * (tl.T + 2 * psf.kxy);
+    const long long total = (long long)n * tl.tpp;
+    const size_t smem = (size_t)(2 * Lmax + tl.T * tl.T) * sizeof(float);
+    const bool fast = psf.kxy == 1 && psf.kz == 3;
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if (fast) {
+        if ((e = prep(k_pose_vjp<1, 3, QuadVol>, smem)) != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pose_vjp<1, 3, QuadVol>, 256, smem);
+    } else {
+        if ((e = prep(k_pose_vjp<-1, -1, QuadVol>, smem)) != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pose_vjp<-1, -1, QuadVol>, 256, smem);
+    }
+    if (e != cudaSuccess) return e;
+    long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
+    if (grid > total) grid = total;
+    if (grid > gbuf_tiles) grid = gbuf_tiles;
+    if (grid <= 0) return cudaErrorInvalidValue;
+    if (fast)
+        k_pose_vjp<1, 3, QuadVol><<<(unsigned)grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, total, r,
+                                                                     gpart, gbuf, Lmax);
+    else
+        k_pose_vjp<-1, -1, QuadVol><<<(unsigned)grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, total, r,
+                                                                       gpart, gbuf, Lmax);
     return cudaGetLastError();
 }
 

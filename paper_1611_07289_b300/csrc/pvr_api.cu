@@ -577,6 +577,29 @@ int pvr_ncc_grad(pvr_ctx *c, const float *x, const float *y, const pvr_patches *
     return PVR_OK;
 }
 
+int pvr_pose_grad(pvr_ctx *c, const float *x, const float *r, const pvr_patches *pp,
+                  const double *poses, double *grad, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    int ms;
+    int rc = check_patches(c, pp, &ms);
+    if (rc) return rc;
+    REQUIRE(pp->n == 0 || (x && r && poses && grad), "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (pp->n == 0) return PVR_OK;
+    if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
+    if ((rc = build_quad(c, x, st))) return rc;
+    Tiling tl = make_tiling(ms);
+    CUDA_TRY_T(PVR_K_NCC, launch_pose_vjp(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, c->quad, r,
+                                          pp->desc, c->fix, pp->n, c->gpart, c->gbuf, c->gbuf_tiles, st),
+               "pose_vjp");
+    CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(c->d_geom, pp->desc, poses, pp->n, tl, nullptr, c->gpart,
+                                                   c->prm.reg_min_valid, nullptr, grad, st),
+               "pose_vjp_finish");
+    c->launches += 2;
+    return PVR_OK;
+}
+
 // Registration rounds; gathers from c->quad, which the caller has built from x.
 static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_patches *pp, int ms,
                          double *poses, int n_evals, double *ncc_out, cudaStream_t st)

@@ -86,6 +86,15 @@ size_t ncc_gbuf_floats_per_tile(const Tiling &tl, int kxy);
 // Kernel launches launch_ncc_grad makes for these arguments.
 int ncc_launch_count(const Tiling &tl, int n, bool grad, long long gbuf_tiles);
 
+// Pose vector-Jacobian product of the forward model: per-tile gradient
+// moments of sum_pix r_pix sim_pix into gpart (contracted per patch by
+// launch_ncc_finish with part = null).
+cudaError_t launch_pose_vjp(const PsfTab &psf, const Tiling &tl, int nx, int ny, int nz,
+                            const float4 *quad, const float *r, const int32_t *desc,
+                            const int32_t *fix, int n, double *gpart, float *gbuf,
+                            long long gbuf_tiles, cudaStream_t st);
+
+// part == null: only the gradient (from gpart), no NCC.
 cudaError_t launch_ncc_finish(const DevGeom *g, const int32_t *desc, const double *poses, int n,
                               const Tiling &tl, const double *part, const double *gpart,
                               int min_valid, double *ncc, double *grad, cudaStream_t st);

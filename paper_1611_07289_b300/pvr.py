@@ -76,6 +76,7 @@ _SIGS = {
     "pvr_volume_update": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int32, _VP]),
     "pvr_volume_init": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, _VP]),
     "pvr_ncc_grad": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, _VP, _VP, _VP]),
+    "pvr_pose_grad": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, _VP, _VP]),
     "pvr_register": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, C.c_int32, _VP, _VP]),
     "pvr_reconstruct_iter": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, _VP, _VP, _VP, _VP,
                                        _VP]),
@@ -292,6 +293,14 @@ class Context:
         self._chk(lib.pvr_ncc_grad(self.h, _ptr(x), _ptr(y), C.byref(pt.c), _ptr(poses), _ptr(ncc),
                                    _ptr(grad), _stream(stream)))
         return ncc, grad
+
+    def pvr_pose_grad(self, x, r, pt: PatchTable, poses, grad=None, stream=None):
+        """d (sum_pix r * sim) / d pose per patch (float64 [n, 6])."""
+        if grad is None:
+            grad = torch.empty((pt.n, 6), dtype=torch.float64, device=x.device)
+        self._chk(lib.pvr_pose_grad(self.h, _ptr(x), _ptr(r), C.byref(pt.c), _ptr(poses), _ptr(grad),
+                                    _stream(stream)))
+        return grad
 
     def pvr_register(self, x, y, pt: PatchTable, poses, n_evals, ncc=None, stream=None):
         if ncc is None:

@@ -23,6 +23,10 @@ workloads here stand in for its whole-uterus scans:
   jumps (+-15 deg) of the fetus only, 5 % corrupted slices (half zeroed,
   half scaled by 0.3), patches 64 / stride 32 kept when at least half their
   pixels exceed 1 % of the maximum.
+* ``config_diff``: the differentiable-forward-model workload, 128^3 voxels
+  of 1 mm with nested ellipsoids, 3 orthogonal stacks of 86 slices of
+  128x128 pixels at 1x1x1.5 mm, all square patches 48 / stride 24 (4,128
+  patches of 48x48).
 """
 from __future__ import annotations
 
@@ -377,6 +381,26 @@ def config_uterus(seed=7289, device="cpu", slices=96, size=256):
     return dict(name="uterus-256x256x192", geom=geom, stacks=stacks, gt=gt.numpy(),
                 ellipsoids=ells, corrupt=corrupt, a=64, stride=32, fg_frac=0.01, keep_frac=0.5,
                 fwhm_xy=1.2, dz=sp, n_outer=10)
+
+
+def config_diff(seed=3, device="cpu"):
+    """128^3 workload of the differentiable forward model (module docstring):
+    geometry, ground-truth volume and the full patch table."""
+    rng = np.random.default_rng(seed)
+    dims, sp = (128, 128, 128), 1.0
+    w2v, v2w = volume_geometry(dims, sp)
+    W = H = 128
+    K = 86
+    axes = [((1, 0, 0), (0, 1, 0), (0, 0, 1)),
+            ((1, 0, 0), (0, 0, 1), (0, 1, 0)),
+            ((0, 1, 0), (0, 0, 1), (1, 0, 0))]
+    p2w = [stack_matrix(u, v, n, W, H, K, 1.0, 1.5) for (u, v, n) in axes]
+    geom = Geometry(dims, w2v, v2w, [(W, H, K)] * 3, p2w, [1.5, 1.5, 1.5])
+    ells = phantom_nested(rng, 128.0)
+    gt = ground_truth(ells, geom, device=device)
+    desc, npix = all_patches(geom, 48, 24)
+    return dict(name="diff-128", geom=geom, gt=gt.cpu().numpy(), ellipsoids=ells, desc=desc, n_pix=npix,
+                a=48, stride=24, fwhm_xy=1.2, dz=sp)
 
 
 def random_geometry(rng, n=8, n_stacks=2, W=6, H=5, K=3, spacing=1.0, pix=1.0, thick=2.0):
