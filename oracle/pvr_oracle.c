@@ -10,6 +10,7 @@
  *
  * What it computes, one function per step of the method:
  *   or_patches_build   square patches of side a and stride w      (Sec. II "Patch Extraction")
+ *   or_patches_build_sizes  the same with a side and stride per slice (multi-scale patches, Sec. II)
  *   or_pose_fixed      patch pose -> pixel-to-voxel map, Q11.20  (Eq. 1, W_i = D B T_i; Sec. II registration)
  *   or_simulate        Gaussian-PSF forward model of every patch  (Eq. 1; Sec. II "Patch to Volume Registration")
  *   or_adjoint         exact transpose of or_simulate             (super-resolution update, Sec. II)
@@ -993,9 +994,14 @@ void or_metrics(const double *ref, const double *img, const uint8_t *mask, size_
  * the level and the comparison are taken in single precision, the count
  * test in double.  desc rows: {stack, slice, x0, y0, a, a, pix_off, 0}.
  * Returns the number of patches (at most max_out rows are written);
- * *npix receives the total pixel count of the kept patches. */
-int or_patches_build(const or_geom *g, const float *stacks, int a, int stride, double fg_frac,
-                     double keep_frac, int *desc, int max_out, int64_t *npix)
+ * *npix receives the total pixel count of the kept patches.
+ * or_patches_build_sizes takes the side a and stride of every slice from
+ * slice_a[] and slice_stride[] (slices numbered over all stacks in order):
+ * patches of several scales (Sec. II builds its patch sets at several
+ * sizes); or_patches_build is the single-size case. */
+int or_patches_build_sizes(const or_geom *g, const float *stacks, const int *slice_a,
+                           const int *slice_stride, double fg_frac, double keep_frac, int *desc,
+                           int max_out, int64_t *npix)
 {
     size_t total = 0;
     for (int s = 0; s < g->n_stacks; ++s) total += (size_t)g->sw[s] * g->sh[s] * g->sk[s];
@@ -1005,9 +1011,11 @@ int or_patches_build(const or_geom *g, const float *stacks, int a, int stride, d
     int n = 0;
     int64_t off = 0;
     size_t soff = 0;
+    int gk = 0;   /* slice index over all stacks */
     for (int s = 0; s < g->n_stacks; ++s) {
         int W = g->sw[s], H = g->sh[s], Kk = g->sk[s];
-        for (int k = 0; k < Kk; ++k)
+        for (int k = 0; k < Kk; ++k, ++gk) {
+            int a = slice_a[gk], stride = slice_stride[gk];
             for (int y0 = 0; y0 + a <= H; y0 += stride)
                 for (int x0 = 0; x0 + a <= W; x0 += stride) {
                     long cnt = 0;
@@ -1023,8 +1031,23 @@ int or_patches_build(const or_geom *g, const float *stacks, int a, int stride, d
                     off += (int64_t)a * a;
                     ++n;
                 }
+        }
         soff += (size_t)W * H * Kk;
     }
     *npix = off;
+    return n;
+}
+
+int or_patches_build(const or_geom *g, const float *stacks, int a, int stride, double fg_frac,
+                     double keep_frac, int *desc, int max_out, int64_t *npix)
+{
+    int nk = 0;
+    for (int s = 0; s < g->n_stacks; ++s) nk += g->sk[s];
+    int *sa = (int *)malloc((size_t)(nk > 0 ? nk : 1) * sizeof(int));
+    int *ss = (int *)malloc((size_t)(nk > 0 ? nk : 1) * sizeof(int));
+    for (int i = 0; i < nk; ++i) { sa[i] = a; ss[i] = stride; }
+    int n = or_patches_build_sizes(g, stacks, sa, ss, fg_frac, keep_frac, desc, max_out, npix);
+    free(sa);
+    free(ss);
     return n;
 }

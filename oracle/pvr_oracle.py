@@ -99,6 +99,10 @@ def lib():
         L.or_patches_build.argtypes = [P(_Geom), P(C.c_float), C.c_int, C.c_int, C.c_double,
                                        C.c_double, P(C.c_int), C.c_int, P(C.c_int64)]
         L.or_patches_build.restype = C.c_int
+        L.or_patches_build_sizes.argtypes = [P(_Geom), P(C.c_float), P(C.c_int), P(C.c_int),
+                                             C.c_double, C.c_double, P(C.c_int), C.c_int,
+                                             P(C.c_int64)]
+        L.or_patches_build_sizes.restype = C.c_int
         L.or_psf_table.argtypes = [P(_Geom), P(_Psf), C.c_int, P(C.c_double), P(C.c_double)]
         _lib = L
     return _lib
@@ -332,3 +336,20 @@ def reconstruct_iter(G, ps, ep, rp, x, y, desc, poses, npix, state, mask, n_sr=1
                          conf_eps)
         mask = aux["mask"]
     return x, poses, mask, ncc
+
+
+def patches_build_sizes(G, stacks, slice_a, slice_stride, fg_frac=0.0, keep_frac=0.0):
+    """Patch table with a side and stride per slice (slices over all stacks
+    in order); returns (desc [P,8] int32, npix)."""
+    stacks = _c(stacks, np.float32)
+    sa = _c(slice_a, np.int32)
+    ss = _c(slice_stride, np.int32)
+    npix = C.c_int64(0)
+    n = lib().or_patches_build_sizes(C.byref(G), _ptr(stacks, C.c_float), _ptr(sa, C.c_int),
+                                     _ptr(ss, C.c_int), float(fg_frac), float(keep_frac), None, 0,
+                                     C.byref(npix))
+    desc = np.zeros((max(n, 1), 8), dtype=np.int32)
+    lib().or_patches_build_sizes(C.byref(G), _ptr(stacks, C.c_float), _ptr(sa, C.c_int),
+                                 _ptr(ss, C.c_int), float(fg_frac), float(keep_frac),
+                                 _ptr(desc, C.c_int), n, C.byref(npix))
+    return desc[:n], int(npix.value)

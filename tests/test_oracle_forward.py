@@ -270,6 +270,45 @@ def test_patch_table_enumeration_and_rejection():
     assert desc2.shape[0] == 1 and list(desc2[0, :7]) == [1, 0, 4, 4, 8, 8, 0] and npix2 == 64
 
 
+def test_multi_size_patch_table_enumeration_and_rejection():
+    """Per-slice sizes: without rejection the table is the plain enumeration
+    (written out here slice by slice); with rejection the kept rows are those
+    whose foreground count (numpy) reaches keep_frac * a^2, offsets packed."""
+    rng = np.random.default_rng(5)
+    geom = synth.random_geometry(rng, n=8, n_stacks=2, W=30, H=26, K=3)
+    offs, total = geom.stack_offsets()
+    stacks = rng.uniform(0.0, 1.0, total).astype(np.float32)
+    nk = sum(k for (_, _, k) in geom.stack_dims)
+    sa = rng.choice([4, 6, 8, 12], nk).astype(np.int32)
+    ss = (sa // 2).astype(np.int32)
+    G = O.geom(geom)
+    desc, npix = O.patches_build_sizes(G, stacks, sa, ss)
+    rows, cnts, off, gk = [], [], 0, 0
+    thr = np.float32(0.5) * stacks.max()
+    for s, (W, H, K) in enumerate(geom.stack_dims):
+        img = stacks[offs[s]:offs[s] + W * H * K].reshape(K, H, W)
+        for k in range(K):
+            a, st = int(sa[gk]), int(ss[gk])
+            for y0 in range(0, H - a + 1, st):
+                for x0 in range(0, W - a + 1, st):
+                    rows.append([s, k, x0, y0, a, a, off, 0])
+                    cnts.append(int((img[k, y0:y0 + a, x0:x0 + a] > thr).sum()))
+                    off += a * a
+            gk += 1
+    rows = np.array(rows, dtype=np.int32)
+    assert np.array_equal(desc, rows) and npix == off
+    keep = np.array([c >= 0.5 * r[4] * r[5] for c, r in zip(cnts, rows)])
+    kept = rows[keep].copy()
+    kept[:, 6] = np.concatenate([[0], np.cumsum(kept[:-1, 4] * kept[:-1, 5])])
+    desc2, npix2 = O.patches_build_sizes(G, stacks, sa, ss, fg_frac=0.5, keep_frac=0.5)
+    assert 0 < desc2.shape[0] < rows.shape[0]
+    assert np.array_equal(desc2, kept) and npix2 == int((kept[:, 4] * kept[:, 5]).sum())
+    # uniform sizes reproduce the single-size builder
+    d3, n3 = O.patches_build_sizes(G, stacks, np.full(nk, 8, np.int32), np.full(nk, 4, np.int32), 0.5, 0.5)
+    d4, n4 = O.patches_build(G, stacks, 8, 4, 0.5, 0.5)
+    assert np.array_equal(d3, d4) and n3 == n4
+
+
 def test_samples_on_the_last_voxel_plane_read_that_plane():
     """A sample exactly on the upper boundary (index N-1) is inside and takes
     the value of that plane."""
