@@ -213,6 +213,18 @@ PVR_API int pvr_patches_build(pvr_ctx *ctx, const float *stacks, int32_t a, int3
                       double fg_frac, double keep_frac, int32_t *desc_out, int32_t max_out,
                       int32_t *n_out, int64_t *n_pix_out, void *stream);
 
+/* The same with a side and stride per slice: slice_a, slice_stride are HOST
+ * int32 arrays with one entry per slice of every stack, numbered over the
+ * stacks in order (multi-scale patch sets: Sec. II extracts patches at
+ * several sizes).  Candidates of a slice use that slice's side and stride;
+ * pixel offsets are packed over the kept patches in table order.  Each side
+ * must be 1..max_patch_side and each stride >= 1; the total candidate pixel
+ * count must stay below 2^31. */
+PVR_API int pvr_patches_build_sizes(pvr_ctx *ctx, const float *stacks, const int32_t *slice_a,
+                                    const int32_t *slice_stride, double fg_frac, double keep_frac,
+                                    int32_t *desc_out, int32_t max_out, int32_t *n_out,
+                                    int64_t *n_pix_out, void *stream);
+
 /* Copy every patch's pixels out of the packed stacks into y (float32
  * [n_pix], patch after patch, row-major). */
 PVR_API int pvr_patches_gather(pvr_ctx *ctx, const float *stacks, const pvr_patches *patches, float *y,
@@ -338,6 +350,37 @@ PVR_API int pvr_register(pvr_ctx *ctx, const float *x, const float *y, const pvr
 PVR_API int pvr_reconstruct_iter(pvr_ctx *ctx, float *x, const float *y, const pvr_patches *patches,
                          double *poses, double *state, uint8_t *mask, float *p, float *w_patch,
                          void *stream);
+
+/* Work plan for one patch table (batched patches of uneven sizes): the
+ * table's non-empty (patch, tile) slots ordered largest tile first, served by
+ * persistent simulate / adjoint kernels that take tiles from an atomic work
+ * queue (mode 1), or one CTA per slot (mode 0), with tile side 64 or 32.
+ * tile: 0 = tune, 32 or 64; mode: -1 = tune, 0 or 1.  Tuning times each
+ * candidate (simulate with residual + adjoint, 3 runs after a warm-up) on
+ * x, y, poses and keeps the fastest; it synchronises `stream`.  The plan
+ * applies to later pvr_simulate, pvr_adjoint and pvr_reconstruct_iter calls
+ * with this same table (device pointer, n, n_pix); NCC and registration keep
+ * their own tiling.  Reads the table to the host and synchronises. */
+PVR_API int pvr_plan(pvr_ctx *ctx, const pvr_patches *patches, const float *x, const float *y,
+                     const double *poses, int32_t tile, int32_t mode, void *stream);
+
+/* The current plan: tile side (0 if none), mode (-1 if none), listed tiles. */
+PVR_API int pvr_plan_info(const pvr_ctx *ctx, int32_t *tile, int32_t *mode, int32_t *n_items);
+
+/* Drop the plan (later calls use one CTA per 64-pixel tile slot). */
+PVR_API int pvr_plan_clear(pvr_ctx *ctx);
+
+/* Capture one pvr_reconstruct_iter with these arguments into a CUDA graph
+ * held by the context (replacing any earlier one); nothing runs.  stream
+ * must be a non-default stream; the profiler must be off.  The graph keeps
+ * the pointers and the context's scratch, so replays read and write the
+ * same buffers. */
+PVR_API int pvr_graph_capture(pvr_ctx *ctx, float *x, const float *y, const pvr_patches *patches,
+                              double *poses, double *state, uint8_t *mask, float *p, float *w_patch,
+                              void *stream);
+
+/* Replay the captured iteration on `stream`. */
+PVR_API int pvr_graph_launch(pvr_ctx *ctx, void *stream);
 
 /* Evaluation metrics (Sec. IV-A) of img against ref over n values (mask
  * NULL: all): out float64 device [5] = {PSNR = 10 log10(I_max^2/MSE),

@@ -2,6 +2,8 @@
 // gather, and the evaluation metrics of Sec. IV-A.
 #include <math.h>
 
+#include <vector>
+
 #include "pvr_internal.h"
 
 namespace pvr {
@@ -37,30 +39,43 @@ __global__ void k_stack_max(const float *__restrict__ s, long long total, unsign
     }
 }
 
-struct CandTable {
-    int n_stacks;
-    long long cand_off[PVR_MAX_STACKS + 1];   // first candidate index of each stack
-    int ncx[PVR_MAX_STACKS], ncy[PVR_MAX_STACKS];
+// Candidate patches of one slice: corners (ix * stride, iy * stride) for
+// ix < ncx, iy < ncy; candidates of all slices are numbered consecutively
+// from cand_off.  The table has one entry per slice (over all stacks in
+// order) plus a sentinel whose cand_off is the candidate count.
+struct SliceCand {
+    long long cand_off;
+    int s, k, a, stride, ncx, ncy;
 };
+
+// Slice entry of candidate c (binary search over the cand_off prefix).
+__device__ __forceinline__ const SliceCand &slice_of(const SliceCand *__restrict__ sc, int n_slices,
+                                                     long long c)
+{
+    int lo = 0, hi = n_slices - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (sc[mid].cand_off <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return sc[lo];
+}
 
 // One CTA per candidate patch: keep iff #pixels > fg level >= keep_frac a^2.
 __global__ void __launch_bounds__(256) k_patch_keep(const DevGeom *__restrict__ g,
-                                                    const float *__restrict__ stacks, CandTable ct,
-                                                    int a, int stride, double fg_frac,
-                                                    double keep_frac,
+                                                    const float *__restrict__ stacks,
+                                                    const SliceCand *__restrict__ sc, int n_slices,
+                                                    double fg_frac, double keep_frac,
                                                     const unsigned *__restrict__ imax_key,
                                                     int32_t *__restrict__ keep)
 {
-    long long c = blockIdx.x;
-    int s = 0;
-    while (s + 1 < ct.n_stacks && c >= ct.cand_off[s + 1]) ++s;
-    long long r = c - ct.cand_off[s];
-    int per_slice = ct.ncx[s] * ct.ncy[s];
-    int k = (int)(r / per_slice), rr = (int)(r % per_slice);
-    int y0 = (rr / ct.ncx[s]) * stride, x0 = (rr % ct.ncx[s]) * stride;
-    int W = g->sw[s], H = g->sh[s];
-    const float *base = stacks + g->stack_off[s] + ((size_t)k * H + y0) * W + x0;
-    float thr = __fmul_rn((float)fg_frac, key_float(*imax_key));
+    const long long c = blockIdx.x;
+    const SliceCand e = slice_of(sc, n_slices, c);
+    const int r = (int)(c - e.cand_off), a = e.a;
+    const int y0 = (r / e.ncx) * e.stride, x0 = (r % e.ncx) * e.stride;
+    const int W = g->sw[e.s], H = g->sh[e.s];
+    const float *base = stacks + g->stack_off[e.s] + ((size_t)e.k * H + y0) * W + x0;
+    const float thr = __fmul_rn((float)fg_frac, key_float(*imax_key));
     int cnt = 0;
     for (int t = threadIdx.x; t < a * a; t += blockDim.x) cnt += base[(size_t)(t / a) * W + t % a] > thr;
 #pragma unroll
@@ -75,55 +90,75 @@ __global__ void __launch_bounds__(256) k_patch_keep(const DevGeom *__restrict__ 
     }
 }
 
-// Single-CTA ordered compaction of the kept candidates into the table.
+// Single-CTA ordered compaction of the kept candidates into the table, with
+// packed pixel offsets (exclusive prefix of a^2 over the kept candidates).
 // counts[0] = kept patches; counts[1..2] = total pixels (int64, split).
 __global__ void __launch_bounds__(1024) k_patch_compact(const int32_t *__restrict__ keep,
-                                                        long long n_cand, CandTable ct, int a,
-                                                        int stride, int32_t *__restrict__ desc,
+                                                        long long n_cand,
+                                                        const SliceCand *__restrict__ sc,
+                                                        int n_slices, int32_t *__restrict__ desc,
                                                         int max_out, int32_t *__restrict__ counts)
 {
     __shared__ int warp_tot[32];
-    __shared__ long long base_sh;
-    if (threadIdx.x == 0) base_sh = 0;
+    __shared__ long long warp_pix[32];
+    __shared__ long long base_sh, pix_sh;
+    if (threadIdx.x == 0) base_sh = pix_sh = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (long long c0 = 0; c0 < n_cand; c0 += blockDim.x) {
-        long long c = c0 + threadIdx.x;
-        int f = (c < n_cand) ? keep[c] : 0;
-        unsigned bal = __ballot_sync(0xffffffffu, f);
-        int pre = __popc(bal & ((1u << lane) - 1u));
-        if (lane == 0) warp_tot[wid] = __popc(bal);
+        const long long c = c0 + threadIdx.x;
+        const int f = (c < n_cand) ? keep[c] : 0;
+        SliceCand e;
+        e.a = 0;
+        if (f) e = slice_of(sc, n_slices, c);
+        const long long sz = f ? (long long)e.a * e.a : 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        const int pre = __popc(bal & ((1u << lane) - 1u));
+        long long v = sz;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane == 31) {
+            warp_tot[wid] = __popc(bal);
+            warp_pix[wid] = v;
+        }
         __syncthreads();
-        int woff = 0;
-        for (int w = 0; w < wid; ++w) woff += warp_tot[w];
-        int tot = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += warp_tot[w];
-        long long idx = base_sh + woff + pre;
+        int woff = 0, tot = 0;
+        long long poff = 0, ptot = 0;
+        for (int w = 0; w < nw; ++w) {
+            if (w < wid) {
+                woff += warp_tot[w];
+                poff += warp_pix[w];
+            }
+            tot += warp_tot[w];
+            ptot += warp_pix[w];
+        }
+        const long long idx = base_sh + woff + pre;
         if (f && idx < max_out) {
-            int s = 0;
-            while (s + 1 < ct.n_stacks && c >= ct.cand_off[s + 1]) ++s;
-            long long r = c - ct.cand_off[s];
-            int per_slice = ct.ncx[s] * ct.ncy[s];
-            int k = (int)(r / per_slice), rr = (int)(r % per_slice);
+            const int r = (int)(c - e.cand_off);
             int32_t *d = desc + 8 * (size_t)idx;
-            d[0] = s;
-            d[1] = k;
-            d[2] = (rr % ct.ncx[s]) * stride;
-            d[3] = (rr / ct.ncx[s]) * stride;
-            d[4] = a;
-            d[5] = a;
-            d[6] = (int32_t)(idx * (long long)a * a);
+            d[0] = e.s;
+            d[1] = e.k;
+            d[2] = (r % e.ncx) * e.stride;
+            d[3] = (r / e.ncx) * e.stride;
+            d[4] = e.a;
+            d[5] = e.a;
+            d[6] = (int32_t)(pix_sh + poff + (v - sz));
             d[7] = 0;
         }
         __syncthreads();
-        if (threadIdx.x == 0) base_sh += tot;
+        if (threadIdx.x == 0) {
+            base_sh += tot;
+            pix_sh += ptot;
+        }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        long long npix = base_sh * (long long)a * a;
         counts[0] = (int32_t)base_sh;
-        counts[1] = (int32_t)(npix & 0xffffffffLL);
-        counts[2] = (int32_t)(npix >> 32);
+        counts[1] = (int32_t)(pix_sh & 0xffffffffLL);
+        counts[2] = (int32_t)(pix_sh >> 32);
     }
 }
 
@@ -291,32 +326,51 @@ __global__ void k_metrics3(const double *__restrict__ scr1, const double *__rest
 constexpr int kMetricBlocks = 296;
 
 cudaError_t launch_patches_build(const DevGeom *g, const pvr_geometry &hg, const float *stacks,
-                                 int64_t total, int a, int stride, double fg_frac,
-                                 double keep_frac, int32_t *desc_out, int max_out, int32_t *keep,
-                                 int64_t *n_cand_out, unsigned *imax_key, int32_t *counts,
-                                 cudaStream_t st)
+                                 int64_t total, const int32_t *slice_a, const int32_t *slice_stride,
+                                 double fg_frac, double keep_frac, int32_t *desc_out, int max_out,
+                                 int32_t *keep, int64_t *n_cand_out, unsigned *imax_key,
+                                 int32_t *counts, void *slice_scratch, cudaStream_t st)
 {
-    CandTable ct;
-    ct.n_stacks = hg.n_stacks;
+    std::vector<SliceCand> sc;
     long long nc = 0;
+    int gk = 0;
     for (int s = 0; s < hg.n_stacks; ++s) {
-        ct.cand_off[s] = nc;
-        int W = hg.stack_w[s], H = hg.stack_h[s];
-        ct.ncx[s] = W >= a ? (W - a) / stride + 1 : 0;
-        ct.ncy[s] = H >= a ? (H - a) / stride + 1 : 0;
-        nc += (long long)hg.stack_k[s] * ct.ncx[s] * ct.ncy[s];
+        const int W = hg.stack_w[s], H = hg.stack_h[s];
+        for (int k = 0; k < hg.stack_k[s]; ++k, ++gk) {
+            SliceCand e;
+            e.cand_off = nc;
+            e.s = s;
+            e.k = k;
+            e.a = slice_a[gk];
+            e.stride = slice_stride[gk];
+            e.ncx = W >= e.a ? (W - e.a) / e.stride + 1 : 0;
+            e.ncy = H >= e.a ? (H - e.a) / e.stride + 1 : 0;
+            nc += (long long)e.ncx * e.ncy;
+            sc.push_back(e);
+        }
     }
-    ct.cand_off[hg.n_stacks] = nc;
     *n_cand_out = nc;
+    const int n_slices = (int)sc.size();
+    SliceCand *d_sc = (SliceCand *)slice_scratch;
+    cudaError_t e;
+    // from pageable memory: returns once the host vector has been staged
+    if ((e = cudaMemcpyAsync(d_sc, sc.data(), sc.size() * sizeof(SliceCand), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess)
+        return e;
     cudaMemsetAsync(imax_key, 0, sizeof(unsigned), st);
     cudaMemsetAsync(counts, 0, 4 * sizeof(int32_t), st);
     if (total > 0) k_stack_max<<<296, 256, 0, st>>>(stacks, (long long)total, imax_key);
     if (nc > 0) {
-        k_patch_keep<<<(unsigned)nc, 256, 0, st>>>(g, stacks, ct, a, stride, fg_frac, keep_frac,
+        k_patch_keep<<<(unsigned)nc, 256, 0, st>>>(g, stacks, d_sc, n_slices, fg_frac, keep_frac,
                                                    imax_key, keep);
-        k_patch_compact<<<1, 1024, 0, st>>>(keep, nc, ct, a, stride, desc_out, max_out, counts);
+        k_patch_compact<<<1, 1024, 0, st>>>(keep, nc, d_sc, n_slices, desc_out, max_out, counts);
     }
     return cudaGetLastError();
+}
+
+size_t patches_slice_scratch_bytes(int n_slices)
+{
+    return (size_t)(n_slices + 1) * sizeof(SliceCand);
 }
 
 cudaError_t launch_patches_gather(const DevGeom *g, const float *stacks, const int32_t *desc,

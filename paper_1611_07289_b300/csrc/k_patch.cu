@@ -82,13 +82,6 @@ __device__ __forceinline__ bool tile_setup_at(long long gid, const int32_t *__re
     return true;
 }
 
-__device__ __forceinline__ bool tile_setup(const int32_t *__restrict__ desc,
-                                           const int32_t *__restrict__ fix, const Tiling &tl,
-                                           int kxy, TileInfo &ti)
-{
-    return tile_setup_at(blockIdx.x, desc, fix, tl, kxy, ti);
-}
-
 struct VolDims {
     int nx, ny, nz;
     unsigned nxy;            // nx * ny (used where the volume has < 2^31 voxels)
@@ -556,23 +549,23 @@ struct FFSum {
 // Forward model.  y == null: write sim, valid.  y != null: write the
 // residual e = y - sim (0 where invalid) and valid, plus per-tile partials
 // {N_valid, sum e^2, min e, max e} for the EM step.
+// One (patch, tile) slot gid of the forward model; sm: dynamic shared memory.
+// Ends with every thread past its last shared-memory read.
 template <int KXY, int KZ, class SRC>
-__global__ void __launch_bounds__(256) k_simulate(const SRC x, VolDims vd,
-                                                  const int32_t *__restrict__ desc,
-                                                  const int32_t *__restrict__ fix, PsfTab psf,
-                                                  Tiling tl, const float *__restrict__ y,
-                                                  float *__restrict__ out,
-                                                  uint8_t *__restrict__ valid,
-                                                  double *__restrict__ part)
+__device__ __forceinline__ void simulate_tile(long long gid, const SRC &x, const VolDims &vd,
+                                              const int32_t *__restrict__ desc,
+                                              const int32_t *__restrict__ fix, const PsfTab &psf,
+                                              const Tiling &tl, const float *__restrict__ y,
+                                              float *__restrict__ out, uint8_t *__restrict__ valid,
+                                              double *__restrict__ part, float *sm)
 {
-    extern __shared__ float sm[];
     __shared__ float fred[32 * 2];
     const int kxy = KXY >= 0 ? KXY : psf.kxy;
     TileInfo ti;
-    bool has = tile_setup(desc, fix, tl, kxy, ti);
+    bool has = tile_setup_at(gid, desc, fix, tl, kxy, ti);
     if (!has) {
         if (part && threadIdx.x < kPartStride)
-            part[(size_t)blockIdx.x * kPartStride + threadIdx.x] = 0.0;
+            part[(size_t)gid * kPartStride + threadIdx.x] = 0.0;
         return;
     }
     float *A = sm, *B = sm + ti.L;
@@ -627,12 +620,61 @@ __global__ void __launch_bounds__(256) k_simulate(const SRC x, VolDims vd,
                 a = fminf(a, rmn[w]);
                 b = fmaxf(b, rmx[w]);
             }
-            double *pt = part + (size_t)blockIdx.x * kPartStride;
+            double *pt = part + (size_t)gid * kPartStride;
             pt[0] = (double)acc[0];
             pt[1] = (double)acc[1];
             pt[2] = (double)a;
             pt[3] = (double)b;
         }
+    } else {
+        __syncthreads();
+    }
+}
+
+// Forward model, one CTA per (patch, tile) slot.
+template <int KXY, int KZ, class SRC>
+__global__ void __launch_bounds__(256) k_simulate(const SRC x, VolDims vd,
+                                                  const int32_t *__restrict__ desc,
+                                                  const int32_t *__restrict__ fix, PsfTab psf,
+                                                  Tiling tl, const float *__restrict__ y,
+                                                  float *__restrict__ out,
+                                                  uint8_t *__restrict__ valid,
+                                                  double *__restrict__ part)
+{
+    extern __shared__ float sm[];
+    simulate_tile<KXY, KZ, SRC>(blockIdx.x, x, vd, desc, fix, psf, tl, y, out, valid, part, sm);
+}
+
+// Next work item of a persistent CTA from the queue counter (thread 0 takes
+// it, the block reads it after the barrier); >= n_items: queue empty.
+__device__ __forceinline__ int next_item(int *counter, int *slot)
+{
+    if (threadIdx.x == 0) *slot = atomicAdd(counter, 1);
+    __syncthreads();
+    return *slot;
+}
+
+// Forward model as a persistent work queue over the non-empty (patch, tile)
+// slots listed in items (largest tiles first): one launch serves patches of
+// every size, and CTAs that finish early take more tiles.
+template <int KXY, int KZ, class SRC>
+__global__ void __launch_bounds__(256) k_simulate_q(const SRC x, VolDims vd,
+                                                    const int32_t *__restrict__ desc,
+                                                    const int32_t *__restrict__ fix, PsfTab psf,
+                                                    Tiling tl, const float *__restrict__ y,
+                                                    float *__restrict__ out,
+                                                    uint8_t *__restrict__ valid,
+                                                    double *__restrict__ part,
+                                                    const int32_t *__restrict__ items, int n_items,
+                                                    int *counter)
+{
+    extern __shared__ float sm[];
+    __shared__ int cur;
+    for (;;) {
+        const int it = next_item(counter, &cur);
+        if (it >= n_items) break;
+        simulate_tile<KXY, KZ, SRC>(items[it], x, vd, desc, fix, psf, tl, y, out, valid, part, sm);
+        __syncthreads();
     }
 }
 
@@ -714,26 +756,35 @@ __device__ __forceinline__ void adjoint_scatter(const VolDims &vd, const TileInf
     }
 }
 
+// One (patch, tile) slot gid of the adjoint; sm: dynamic shared memory.
 template <int KXY, int KZ, bool PAIR>
-__global__ void __launch_bounds__(256) k_adjoint(VolDims vd, const int32_t *__restrict__ desc,
-                                                 const int32_t *__restrict__ fix, PsfTab psf,
-                                                 Tiling tl, const float *__restrict__ r,
-                                                 const float *__restrict__ w,
-                                                 const uint8_t *__restrict__ pmask,
-                                                 float *__restrict__ addon,
-                                                 float *__restrict__ conf)
+__device__ __forceinline__ void adjoint_tile(long long gid, const VolDims &vd,
+                                             const int32_t *__restrict__ desc,
+                                             const int32_t *__restrict__ fix, const PsfTab &psf,
+                                             const Tiling &tl, const float *__restrict__ r,
+                                             const float *__restrict__ w,
+                                             const uint8_t *__restrict__ pmask,
+                                             float *__restrict__ addon, float *__restrict__ conf,
+                                             float *sm)
 {
-    extern __shared__ float sm[];
     const int kxy = KXY >= 0 ? KXY : psf.kxy;
     const int kz = KZ >= 0 ? KZ : psf.kz;
     TileInfo ti;
-    if (!tile_setup(desc, fix, tl, kxy, ti) || !ti.ok) return;
+    if (!tile_setup_at(gid, desc, fix, tl, kxy, ti) || !ti.ok) return;
     if (pmask && pmask[ti.p] == 0) return;
     const int np = ti.tw * ti.th;
     float *U = sm, *Uw = sm + ti.L, *CR = sm + 2 * ti.L, *CW = CR + np;
     const float *gz = psf.gz[ti.stack];
-    // phase 0: in-volume PSF weight per lattice point (no gathers)
-    lattice_forward<KZ>(PlainVol{nullptr}, vd, ti, kxy, kz, gz, kAlongCol, nullptr, U);
+    const bool interior = tile_interior(ti, vd, kxy, kz);
+    // phase 0: in-volume PSF weight per lattice point (no gathers); inside
+    // the volume every sample counts
+    if (interior) {
+        float b = 0.f;
+        for (int z = -kz; z <= kz; ++z) b += gz[z + kz];
+        for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) U[lp] = b;
+    } else {
+        lattice_forward<KZ>(PlainVol{nullptr}, vd, ti, kxy, kz, gz, kAlongCol, nullptr, U);
+    }
     __syncthreads();
     // phase 1: pixel coefficients
     for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
@@ -777,10 +828,45 @@ __global__ void __launch_bounds__(256) k_adjoint(VolDims vd, const int32_t *__re
     }
     __syncthreads();
     // phase 3: scatter
-    if (tile_interior(ti, vd, kxy, kz))
+    if (interior)
         adjoint_scatter<KZ, PAIR, true>(vd, ti, kxy, kz, gz, U, Uw, addon, conf);
     else
         adjoint_scatter<KZ, PAIR, false>(vd, ti, kxy, kz, gz, U, Uw, addon, conf);
+}
+
+template <int KXY, int KZ, bool PAIR>
+__global__ void __launch_bounds__(256, 3) k_adjoint(VolDims vd, const int32_t *__restrict__ desc,
+                                                 const int32_t *__restrict__ fix, PsfTab psf,
+                                                 Tiling tl, const float *__restrict__ r,
+                                                 const float *__restrict__ w,
+                                                 const uint8_t *__restrict__ pmask,
+                                                 float *__restrict__ addon,
+                                                 float *__restrict__ conf)
+{
+    extern __shared__ float sm[];
+    adjoint_tile<KXY, KZ, PAIR>(blockIdx.x, vd, desc, fix, psf, tl, r, w, pmask, addon, conf, sm);
+}
+
+// The adjoint as a persistent work queue over listed (patch, tile) slots.
+template <int KXY, int KZ, bool PAIR>
+__global__ void __launch_bounds__(256, 3) k_adjoint_q(VolDims vd, const int32_t *__restrict__ desc,
+                                                   const int32_t *__restrict__ fix, PsfTab psf,
+                                                   Tiling tl, const float *__restrict__ r,
+                                                   const float *__restrict__ w,
+                                                   const uint8_t *__restrict__ pmask,
+                                                   float *__restrict__ addon,
+                                                   float *__restrict__ conf,
+                                                   const int32_t *__restrict__ items, int n_items,
+                                                   int *counter)
+{
+    extern __shared__ float sm[];
+    __shared__ int cur;
+    for (;;) {
+        const int it = next_item(counter, &cur);
+        if (it >= n_items) break;
+        adjoint_tile<KXY, KZ, PAIR>(items[it], vd, desc, fix, psf, tl, r, w, pmask, addon, conf, sm);
+        __syncthreads();
+    }
 }
 
 // ----------------------------------------------------------------- K6a --
@@ -1442,21 +1528,49 @@ cudaError_t prep(K kern, size_t smem)
 // Launchers: the (kxy, kz) = (1, 3) specialisation serves the default PSF;
 // every other setting takes the runtime-loop instantiation.
 
+// Grid of a persistent kernel: every co-resident CTA, at most n_items.
+template <typename K>
+cudaError_t persistent_grid(K kern, size_t smem, int n_items, unsigned *grid)
+{
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem)) != cudaSuccess) return e;
+    long long g = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
+    *grid = (unsigned)(g < n_items ? g : n_items);
+    return cudaSuccess;
+}
+
 cudaError_t launch_simulate(const DevGeom *, const PsfTab &psf, const Tiling &tl, int nx, int ny,
                             int nz, const float *x, const float4 *quad, const int32_t *desc,
                             const int32_t *fix, int n, const float *y, float *out, uint8_t *valid,
-                            double *part, cudaStream_t st)
+                            double *part, cudaStream_t st, const WorkQueue *wq)
 {
     if (n <= 0) return cudaSuccess;
     VolDims vd = vol_dims(nx, ny, nz);
     size_t smem = smem_forward(tl, psf.kxy);
     dim3 grid((unsigned)n * tl.tpp), block(256);
     cudaError_t e;
+    if (wq && wq->items) {
+        if (wq->n_items <= 0) return cudaSuccess;
+        if ((e = cudaMemsetAsync(wq->counter, 0, sizeof(int), st)) != cudaSuccess) return e;
+    }
 #define PVR_SIM(KX, KZv, SRCT, src)                                                                  \
     do {                                                                                          \
-        if ((e = prep(k_simulate<KX, KZv, SRCT>, smem)) != cudaSuccess) return e;                  \
-        k_simulate<KX, KZv, SRCT><<<grid, block, smem, st>>>(src, vd, desc, fix, psf, tl, y, out, valid, \
-                                                             part);                               \
+        if (wq && wq->items) {                                                                    \
+            unsigned pg;                                                                          \
+            if ((e = prep(k_simulate_q<KX, KZv, SRCT>, smem)) != cudaSuccess) return e;            \
+            if ((e = persistent_grid(k_simulate_q<KX, KZv, SRCT>, smem, wq->n_items, &pg)) != cudaSuccess) \
+                return e;                                                                         \
+            k_simulate_q<KX, KZv, SRCT><<<pg, block, smem, st>>>(src, vd, desc, fix, psf, tl, y, out, \
+                                                                 valid, part, wq->items, wq->n_items, \
+                                                                 wq->counter);                    \
+        } else {                                                                                  \
+            if ((e = prep(k_simulate<KX, KZv, SRCT>, smem)) != cudaSuccess) return e;              \
+            k_simulate<KX, KZv, SRCT><<<grid, block, smem, st>>>(src, vd, desc, fix, psf, tl, y, out, \
+                                                                 valid, part);                    \
+        }                                                                                         \
     } while (0)
     const bool fast = psf.kxy == 1 && psf.kz == 3;
     if (quad) {
@@ -1485,18 +1599,32 @@ cudaError_t launch_build_quad(const float *x, float4 *quad, int nx, int ny, int 
 cudaError_t launch_adjoint(const PsfTab &psf, const Tiling &tl, int nx, int ny, int nz,
                            const int32_t *desc, const int32_t *fix, int n, const float *r,
                            const float *w, const uint8_t *pmask, float *addon, float *conf,
-                           int pair, cudaStream_t st)
+                           int pair, cudaStream_t st, const WorkQueue *wq)
 {
     if (n <= 0) return cudaSuccess;
     VolDims vd = vol_dims(nx, ny, nz);
     size_t smem = smem_adjoint(tl, psf.kxy);
     dim3 grid((unsigned)n * tl.tpp), block(256);
     cudaError_t e;
+    if (wq && wq->items) {
+        if (wq->n_items <= 0) return cudaSuccess;
+        if ((e = cudaMemsetAsync(wq->counter, 0, sizeof(int), st)) != cudaSuccess) return e;
+    }
 #define PVR_ADJ(KX, KZv, PR)                                                                          \
     do {                                                                                              \
-        if ((e = prep(k_adjoint<KX, KZv, PR>, smem)) != cudaSuccess) return e;                        \
-        k_adjoint<KX, KZv, PR><<<grid, block, smem, st>>>(vd, desc, fix, psf, tl, r, w, pmask, addon, \
-                                                          conf);                                      \
+        if (wq && wq->items) {                                                                        \
+            unsigned pg;                                                                              \
+            if ((e = prep(k_adjoint_q<KX, KZv, PR>, smem)) != cudaSuccess) return e;                  \
+            if ((e = persistent_grid(k_adjoint_q<KX, KZv, PR>, smem, wq->n_items, &pg)) != cudaSuccess) \
+                return e;                                                                             \
+            k_adjoint_q<KX, KZv, PR><<<pg, block, smem, st>>>(vd, desc, fix, psf, tl, r, w, pmask,    \
+                                                              addon, conf, wq->items, wq->n_items,    \
+                                                              wq->counter);                           \
+        } else {                                                                                      \
+            if ((e = prep(k_adjoint<KX, KZv, PR>, smem)) != cudaSuccess) return e;                    \
+            k_adjoint<KX, KZv, PR><<<grid, block, smem, st>>>(vd, desc, fix, psf, tl, r, w, pmask,    \
+                                                              addon, conf);                           \
+        }                                                                                             \
     } while (0)
     const bool fast = psf.kxy == 1 && psf.kz == 3;
     if (fast && pair) PVR_ADJ(1, 3, true);

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <utility>
 #include <vector>
@@ -23,10 +24,11 @@ cudaError_t launch_em(const float *y, const float *sim, const uint8_t *valid, co
                       uint8_t *elig, double *bpart, const pvr_params &prm, cudaStream_t st);
 int em_launch_count(int n, const pvr_params &prm);
 cudaError_t launch_patches_build(const DevGeom *g, const pvr_geometry &hg, const float *stacks,
-                                 int64_t total, int a, int stride, double fg_frac,
-                                 double keep_frac, int32_t *desc_out, int max_out, int32_t *keep,
-                                 int64_t *n_cand_out, unsigned *imax_key, int32_t *counts,
-                                 cudaStream_t st);
+                                 int64_t total, const int32_t *slice_a, const int32_t *slice_stride,
+                                 double fg_frac, double keep_frac, int32_t *desc_out, int max_out,
+                                 int32_t *keep, int64_t *n_cand_out, unsigned *imax_key,
+                                 int32_t *counts, void *slice_scratch, cudaStream_t st);
+size_t patches_slice_scratch_bytes(int n_slices);
 }  // namespace pvr
 
 using namespace pvr;
@@ -66,6 +68,21 @@ struct pvr_ctx {
     int64_t keep_cap = 0;
     unsigned *imax_key = nullptr;
     int32_t *counts = nullptr;
+    void *slice_scr = nullptr;   // per-slice candidate table of the patch builder
+    int n_slices = 0;
+    // work plan of one patch table (pvr_plan): tiling, launch mode, tile list
+    int tpp_alloc = 1;            // slots per patch the partial buffers hold
+    int32_t *plan_items = nullptr;
+    int *plan_counter = nullptr;
+    const int32_t *plan_desc = nullptr;
+    int plan_n = -1;
+    int64_t plan_npix = -1;
+    Tiling plan_tl{};
+    int plan_mode = 0;            // 0: one CTA per slot, 1: persistent work queue
+    int plan_n_items = 0;
+    // captured reconstruct_iter (pvr_graph_capture)
+    cudaGraphExec_t graph_exec = nullptr;
+    int64_t graph_launches = 0;
     double *metric_scr = nullptr;
     std::string last_error;
     int64_t launches = 0;
@@ -104,6 +121,33 @@ Tiling make_tiling(int max_side)
     t.tiles_y = t.tiles_x;
     t.tpp = t.tiles_x * t.tiles_y;
     return t;
+}
+
+Tiling make_tiling_t(int max_side, int T)
+{
+    Tiling t;
+    t.T = max_side <= T ? max_side : T;
+    if (t.T < 1) t.T = 1;
+    t.tiles_x = (max_side + t.T - 1) / t.T;
+    t.tiles_y = t.tiles_x;
+    t.tpp = t.tiles_x * t.tiles_y;
+    return t;
+}
+
+// The plan of this exact table (same device pointer, counts and side), if
+// one was made: its tiling replaces tl and, in queue mode, its work queue is
+// returned for the simulate / adjoint launches.
+const WorkQueue *plan_for(pvr_ctx *c, const pvr_patches *pp, int max_side, Tiling *tl, WorkQueue *wq)
+{
+    if (c->plan_n < 0 || pp->desc != c->plan_desc || pp->n != c->plan_n || pp->n_pix != c->plan_npix ||
+        max_side > c->plan_tl.T * c->plan_tl.tiles_x)
+        return nullptr;
+    *tl = c->plan_tl;
+    if (c->plan_mode != 1) return nullptr;
+    wq->items = c->plan_items;
+    wq->n_items = c->plan_n_items;
+    wq->counter = c->plan_counter;
+    return wq;
 }
 
 int check_patches(pvr_ctx *c, const pvr_patches *pp, int *max_side)
@@ -171,9 +215,11 @@ void free_all(pvr_ctx *c)
                     c->err, c->best, c->gbest, c->nbest, c->trial, c->delta, c->ncc_tmp,
                     c->grad_tmp, c->active, c->s_buf, c->e_buf, c->p_buf, c->v_buf,
                     c->valid_buf, c->mask_tmp, c->acc2, c->quad, c->gbuf, c->keep, c->imax_key,
+                    c->slice_scr, c->plan_items, c->plan_counter,
                     c->counts, c->metric_scr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
 }
 
 // Quad copy of x for the gathers (once per call that gathers from x).
@@ -306,15 +352,24 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
     // scratch
     Tiling tl = make_tiling(prm->max_patch_side);
     c->tpp_cap = tl.tpp;
+    // partial-sum slots also cover the 32-pixel tiling the planner may pick
+    // (offered for patch sides up to 128)
+    c->tpp_alloc = tl.tpp;
+    if (prm->max_patch_side <= 128) {
+        int t32 = (prm->max_patch_side + 31) / 32;
+        if (t32 * t32 > c->tpp_alloc) c->tpp_alloc = t32 * t32;
+    }
     size_t P = (size_t)prm->max_patches, NP = (size_t)prm->max_pixels;
-    size_t slots = P * (size_t)tl.tpp * kPartStride;
+    size_t slots = P * (size_t)c->tpp_alloc * kPartStride;
     c->keep_cap = (int64_t)(P * 4 > (1u << 20) ? P * 4 : (1u << 20));
     cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, n) if (e == cudaSuccess) e = dalloc(&(ptr), (n))
     ALLOC(c->d_geom, 1);
     ALLOC(c->fix, P * kFixStride);
     ALLOC(c->part, slots);
-    ALLOC(c->gpart, P * (size_t)tl.tpp * kGradStride);
+    ALLOC(c->gpart, P * (size_t)c->tpp_alloc * kGradStride);
+    ALLOC(c->plan_items, P * (size_t)c->tpp_alloc);
+    ALLOC(c->plan_counter, 4);
     ALLOC(c->pstat, 8);
     ALLOC(c->pbar, P);
     ALLOC(c->wsc, P);
@@ -348,6 +403,9 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
     ALLOC(c->keep, (size_t)c->keep_cap);
     ALLOC(c->imax_key, 1);
     ALLOC(c->counts, 4);
+    c->n_slices = 0;
+    for (int s = 0; s < g->n_stacks; ++s) c->n_slices += g->stack_k[s];
+    ALLOC((char *&)c->slice_scr, patches_slice_scratch_bytes(c->n_slices));
     ALLOC(c->metric_scr, kMetricScratch);
 #undef ALLOC
     if (e == cudaSuccess) e = cudaMemcpy(c->d_geom, &hg, sizeof hg, cudaMemcpyHostToDevice);
@@ -391,29 +449,36 @@ int pvr_device_status(pvr_ctx *c, void *stream)
     return PVR_OK;
 }
 
-int pvr_patches_build(pvr_ctx *c, const float *stacks, int32_t a, int32_t stride, double fg_frac,
-                      double keep_frac, int32_t *desc_out, int32_t max_out, int32_t *n_out,
-                      int64_t *n_pix_out, void *stream)
+int pvr_patches_build_sizes(pvr_ctx *c, const float *stacks, const int32_t *slice_a,
+                            const int32_t *slice_stride, double fg_frac, double keep_frac,
+                            int32_t *desc_out, int32_t max_out, int32_t *n_out, int64_t *n_pix_out,
+                            void *stream)
 {
     if (!c) return PVR_ERR_INVALID_ARG;
-    REQUIRE(stacks && desc_out && n_out && n_pix_out, "NULL argument");
-    REQUIRE(a >= 1 && stride >= 1 && a <= c->prm.max_patch_side, "a must be 1..max_patch_side, stride >= 1");
+    REQUIRE(stacks && slice_a && slice_stride && desc_out && n_out && n_pix_out, "NULL argument");
     REQUIRE(max_out >= 0, "max_out < 0");
     REQUIRE(isfinite(fg_frac) && isfinite(keep_frac), "non-finite level");
-    int64_t n_cand = 0;
+    int64_t n_cand = 0, pix = 0;
+    int gk = 0;
     for (int s = 0; s < c->geom.n_stacks; ++s) {
-        int W = c->geom.stack_w[s], H = c->geom.stack_h[s];
-        int64_t nx = W >= a ? (W - a) / stride + 1 : 0, ny = H >= a ? (H - a) / stride + 1 : 0;
-        n_cand += (int64_t)c->geom.stack_k[s] * nx * ny;
+        const int W = c->geom.stack_w[s], H = c->geom.stack_h[s];
+        for (int k = 0; k < c->geom.stack_k[s]; ++k, ++gk) {
+            const int a = slice_a[gk], stride = slice_stride[gk];
+            REQUIRE(a >= 1 && stride >= 1 && a <= c->prm.max_patch_side,
+                    "slice %d: a must be 1..max_patch_side, stride >= 1", gk);
+            int64_t nx = W >= a ? (W - a) / stride + 1 : 0, ny = H >= a ? (H - a) / stride + 1 : 0;
+            n_cand += nx * ny;
+            pix += nx * ny * (int64_t)a * a;
+        }
     }
     REQUIRE(n_cand <= c->keep_cap, "%lld candidate patches exceed the scratch (%lld)",
             (long long)n_cand, (long long)c->keep_cap);
-    REQUIRE(n_cand * (int64_t)a * a < ((int64_t)1 << 31), "pixel offsets would exceed int32");
+    REQUIRE(pix < ((int64_t)1 << 31), "pixel offsets would exceed int32");
     cudaStream_t st = (cudaStream_t)stream;
     int64_t nc = 0;
-    CUDA_TRY(launch_patches_build(c->d_geom, c->geom, stacks, c->stack_total, a, stride, fg_frac,
-                                  keep_frac, desc_out, max_out, c->keep, &nc, c->imax_key,
-                                  c->counts, st),
+    CUDA_TRY(launch_patches_build(c->d_geom, c->geom, stacks, c->stack_total, slice_a, slice_stride,
+                                  fg_frac, keep_frac, desc_out, max_out, c->keep, &nc, c->imax_key,
+                                  c->counts, c->slice_scr, st),
              "patches_build");
     c->launches += nc > 0 ? 3 : 1;
     int32_t h[4];
@@ -422,6 +487,16 @@ int pvr_patches_build(pvr_ctx *c, const float *stacks, int32_t a, int32_t stride
     *n_out = h[0];
     *n_pix_out = ((int64_t)(uint32_t)h[1]) | ((int64_t)h[2] << 32);
     return PVR_OK;
+}
+
+int pvr_patches_build(pvr_ctx *c, const float *stacks, int32_t a, int32_t stride, double fg_frac,
+                      double keep_frac, int32_t *desc_out, int32_t max_out, int32_t *n_out,
+                      int64_t *n_pix_out, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    std::vector<int32_t> sa((size_t)c->n_slices, a), ss((size_t)c->n_slices, stride);
+    return pvr_patches_build_sizes(c, stacks, sa.data(), ss.data(), fg_frac, keep_frac, desc_out,
+                                   max_out, n_out, n_pix_out, stream);
 }
 
 int pvr_patches_gather(pvr_ctx *c, const float *stacks, const pvr_patches *pp, float *y, void *stream)
@@ -466,9 +541,11 @@ int pvr_simulate(pvr_ctx *c, const float *x, const pvr_patches *pp, const double
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     if ((rc = build_quad(c, x, st))) return rc;
     Tiling tl = make_tiling(ms);
+    WorkQueue wqs;
+    const WorkQueue *wq = plan_for(c, pp, ms, &tl, &wqs);
     CUDA_TRY_T(PVR_K_SIMULATE, launch_simulate(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x,
                                                c->quad, pp->desc, c->fix, pp->n, nullptr, sim, valid,
-                                               nullptr, st),
+                                               nullptr, st, wq),
              "simulate");
     c->launches += pp->n > 0;
     return PVR_OK;
@@ -489,8 +566,10 @@ int pvr_adjoint(pvr_ctx *c, const pvr_patches *pp, const double *poses, const fl
     CUDA_TRY(cudaMemsetAsync(c->acc2, 0, (size_t)c->nvox * sizeof(float2), st), "clear");
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     Tiling tl = make_tiling(ms);
+    WorkQueue wqs;
+    const WorkQueue *wq = plan_for(c, pp, ms, &tl, &wqs);
     CUDA_TRY_T(PVR_K_ADJOINT, launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix, pp->n,
-                            r, w, nullptr, (float *)c->acc2, nullptr, 1, st),
+                            r, w, nullptr, (float *)c->acc2, nullptr, 1, st, wq),
              "adjoint");
     CUDA_TRY(launch_split_pairs(c->acc2, c->nvox, addon, conf, accumulate, st), "split");
     c->launches += (pp->n > 0) + 1;
@@ -664,13 +743,20 @@ int pvr_reconstruct_iter(pvr_ctx *c, float *x, const float *y, const pvr_patches
     if ((rc = register_impl(c, x, y, pp, ms, poses, c->prm.reg_evals, nullptr, st))) return rc;
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     Tiling tl = make_tiling(ms);
+    WorkQueue wqs;
+    const WorkQueue *wq = plan_for(c, pp, ms, &tl, &wqs);
     CUDA_TRY(cudaMemsetAsync(c->acc2, 0, (size_t)c->nvox * sizeof(float2), st), "clear");
     for (int it = 0; it < c->prm.n_sr; ++it) {
         // x changes with every SR pass: refresh its quad copy after the first
         if (it > 0 && (rc = build_quad(c, x, st))) return rc;
+        // the work queue visits non-empty tiles only: empty slots of the EM
+        // partials must read as zero
+        if (wq)
+            CUDA_TRY(cudaMemsetAsync(c->part, 0, (size_t)pp->n * tl.tpp * kPartStride * sizeof(double), st),
+                     "clear partials");
         CUDA_TRY_T(PVR_K_SIMULATE, launch_simulate(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x,
                                                    c->quad, pp->desc, c->fix, pp->n, y, c->e_buf,
-                                                   c->valid_buf, c->part, st),
+                                                   c->valid_buf, c->part, st, wq),
                  "simulate");
         CUDA_TRY_T(PVR_K_EM, launch_em(c->e_buf, nullptr, c->valid_buf, pp->desc, pp->n, pp->n_pix, tl, c->err,
                            state, mask, c->mask_tmp, c->p_buf, w_patch, nullptr, c->part, c->pstat,
@@ -679,7 +765,7 @@ int pvr_reconstruct_iter(pvr_ctx *c, float *x, const float *y, const pvr_patches
         CUDA_TRY(cudaMemcpyAsync(mask, c->mask_tmp, (size_t)pp->n, cudaMemcpyDeviceToDevice, st),
                  "mask copy");
         CUDA_TRY_T(PVR_K_ADJOINT, launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix,
-                                pp->n, c->e_buf, c->p_buf, mask, (float *)c->acc2, nullptr, 1, st),
+                                pp->n, c->e_buf, c->p_buf, mask, (float *)c->acc2, nullptr, 1, st, wq),
                  "adjoint");
         CUDA_TRY_T(PVR_K_UPDATE, launch_volume_update_pairs(x, c->acc2, c->nvox, (float)c->prm.alpha,
                                       (float)c->prm.conf_eps, 1, 0, st),
@@ -690,6 +776,190 @@ int pvr_reconstruct_iter(pvr_ctx *c, float *x, const float *y, const pvr_patches
         CUDA_TRY(cudaMemcpyAsync(p, c->p_buf, (size_t)pp->n_pix * sizeof(float),
                                  cudaMemcpyDeviceToDevice, st),
                  "p copy");
+    return PVR_OK;
+}
+
+// ------------------------------------------------------------ work plan --
+
+namespace {
+
+// Non-empty (patch, tile) slots of the table under tiling tl, largest tiles
+// first (stable, so equal tiles keep table order).
+std::vector<int32_t> tile_items(const std::vector<int32_t> &desc, int n, const Tiling &tl)
+{
+    std::vector<std::pair<int, int32_t>> v;
+    v.reserve((size_t)n * tl.tpp);
+    for (int p = 0; p < n; ++p) {
+        const int w = desc[8 * (size_t)p + 4], h = desc[8 * (size_t)p + 5];
+        for (int t = 0; t < tl.tpp; ++t) {
+            const int i0 = (t % tl.tiles_x) * tl.T, j0 = (t / tl.tiles_x) * tl.T;
+            if (i0 >= w || j0 >= h) continue;
+            const int tw = w - i0 < tl.T ? w - i0 : tl.T, th = h - j0 < tl.T ? h - j0 : tl.T;
+            v.push_back({tw * th, (int32_t)((int64_t)p * tl.tpp + t)});
+        }
+    }
+    std::stable_sort(v.begin(), v.end(), [](const std::pair<int, int32_t> &a,
+                                            const std::pair<int, int32_t> &b) { return a.first > b.first; });
+    std::vector<int32_t> items(v.size());
+    for (size_t i = 0; i < v.size(); ++i) items[i] = v[i].second;
+    return items;
+}
+
+}  // namespace
+
+int pvr_plan(pvr_ctx *c, const pvr_patches *pp, const float *x, const float *y, const double *poses,
+             int32_t tile, int32_t mode, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    int ms;
+    int rc = check_patches(c, pp, &ms);
+    if (rc) return rc;
+    REQUIRE(tile == 0 || tile == 32 || tile == 64, "tile must be 0 (tune), 32 or 64");
+    REQUIRE(mode >= -1 && mode <= 1, "mode must be -1 (tune), 0 or 1");
+    const bool autotune = tile == 0 || mode == -1;
+    REQUIRE(!autotune || (x && y && poses), "tuning needs x, y and poses");
+    cudaStream_t st = (cudaStream_t)stream;
+    c->plan_n = -1;   // no plan while this one is being made
+    if (pp->n == 0) return PVR_OK;
+    std::vector<int32_t> desc((size_t)pp->n * 8);
+    CUDA_TRY(cudaMemcpyAsync(desc.data(), pp->desc, desc.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st),
+             "read table");
+    CUDA_TRY(cudaStreamSynchronize(st), "synchronise");
+    // candidates: tile side 64 (or the largest side below it), and 32 where
+    // the partial buffers hold its slots; each as one CTA per slot or as a
+    // persistent work queue
+    std::vector<int> sides;
+    if (tile != 32) sides.push_back(64);
+    if (tile != 64 && (int64_t)((ms + 31) / 32) * ((ms + 31) / 32) <= c->tpp_alloc) sides.push_back(32);
+    REQUIRE(!sides.empty(), "32-pixel tiles need max_patch_side <= 128");
+    struct Cand {
+        Tiling tl;
+        int mode;
+        std::vector<int32_t> items;
+    };
+    std::vector<Cand> cands;
+    for (int T : sides) {
+        Tiling tl = make_tiling_t(ms, T);
+        if (mode != 0) cands.push_back({tl, 1, tile_items(desc, pp->n, tl)});
+        if (mode != 1) cands.push_back({tl, 0, {}});
+    }
+    int best = 0;
+    if (autotune && cands.size() > 1) {
+        if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
+        if ((rc = build_quad(c, x, st))) return rc;
+        cudaEvent_t e0, e1;
+        CUDA_TRY(cudaEventCreate(&e0), "event");
+        CUDA_TRY(cudaEventCreate(&e1), "event");
+        float best_ms = 1e30f;
+        for (size_t k = 0; k < cands.size(); ++k) {
+            Cand &cd = cands[k];
+            WorkQueue wq;
+            if (cd.mode == 1) {
+                CUDA_TRY(cudaMemcpyAsync(c->plan_items, cd.items.data(), cd.items.size() * sizeof(int32_t),
+                                         cudaMemcpyHostToDevice, st),
+                         "upload items");
+                wq.items = c->plan_items;
+                wq.n_items = (int)cd.items.size();
+                wq.counter = c->plan_counter;
+            }
+            float t_sum[3];
+            for (int rep = 0; rep < 4; ++rep) {
+                CUDA_TRY(cudaEventRecord(e0, st), "event");
+                CUDA_TRY(launch_simulate(c->d_geom, c->psf, cd.tl, c->geom.nx, c->geom.ny, c->geom.nz, x,
+                                         c->quad, pp->desc, c->fix, pp->n, y, c->e_buf, c->valid_buf,
+                                         nullptr, st, cd.mode ? &wq : nullptr),
+                         "simulate");
+                CUDA_TRY(launch_adjoint(c->psf, cd.tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix,
+                                        pp->n, c->e_buf, nullptr, nullptr, (float *)c->acc2, nullptr, 1, st,
+                                        cd.mode ? &wq : nullptr),
+                         "adjoint");
+                CUDA_TRY(cudaEventRecord(e1, st), "event");
+                CUDA_TRY(cudaEventSynchronize(e1), "synchronise");
+                float ms_ = 0.f;
+                cudaEventElapsedTime(&ms_, e0, e1);
+                if (rep > 0) t_sum[rep - 1] = ms_;   // first run warms up
+            }
+            float med = t_sum[0] + t_sum[1] + t_sum[2] - fminf(t_sum[0], fminf(t_sum[1], t_sum[2])) -
+                        fmaxf(t_sum[0], fmaxf(t_sum[1], t_sum[2]));
+            if (med < best_ms) {
+                best_ms = med;
+                best = (int)k;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        CUDA_TRY(cudaMemsetAsync(c->acc2, 0, (size_t)c->nvox * sizeof(float2), st), "clear");
+    }
+    Cand &cd = cands[best];
+    if (cd.mode == 1)
+        CUDA_TRY(cudaMemcpyAsync(c->plan_items, cd.items.data(), cd.items.size() * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, st),
+                 "upload items");
+    CUDA_TRY(cudaStreamSynchronize(st), "synchronise");
+    c->plan_tl = cd.tl;
+    c->plan_mode = cd.mode;
+    c->plan_n_items = (int)cd.items.size();
+    c->plan_desc = pp->desc;
+    c->plan_n = pp->n;
+    c->plan_npix = pp->n_pix;
+    return PVR_OK;
+}
+
+int pvr_plan_info(const pvr_ctx *c, int32_t *tile, int32_t *mode, int32_t *n_items)
+{
+    if (!c || !tile || !mode || !n_items) return PVR_ERR_INVALID_ARG;
+    const bool on = c->plan_n >= 0;
+    *tile = on ? c->plan_tl.T : 0;
+    *mode = on ? c->plan_mode : -1;
+    *n_items = on ? c->plan_n_items : 0;
+    return PVR_OK;
+}
+
+int pvr_plan_clear(pvr_ctx *c)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    c->plan_n = -1;
+    return PVR_OK;
+}
+
+// ---------------------------------------------------------------- graphs --
+
+int pvr_graph_capture(pvr_ctx *c, float *x, const float *y, const pvr_patches *pp, double *poses,
+                      double *state, uint8_t *mask, float *p, float *w_patch, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    REQUIRE(stream != nullptr, "capture needs a non-default stream");
+    REQUIRE(!c->prof, "disable the profiler before capturing");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
+    const int64_t l0 = c->launches;
+    CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed), "begin capture");
+    int rc = pvr_reconstruct_iter(c, x, y, pp, poses, state, mask, p, w_patch, stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (rc != PVR_OK) {
+        if (g) cudaGraphDestroy(g);
+        c->launches = l0;
+        return rc;
+    }
+    CUDA_TRY(e, "end capture");
+    e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    CUDA_TRY(e, "instantiate");
+    c->graph_launches = c->launches - l0;
+    c->launches = l0;
+    return PVR_OK;
+}
+
+int pvr_graph_launch(pvr_ctx *c, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    REQUIRE(c->graph_exec != nullptr, "no captured graph");
+    CUDA_TRY(cudaGraphLaunch(c->graph_exec, (cudaStream_t)stream), "graph launch");
+    c->launches += c->graph_launches;
     return PVR_OK;
 }
 

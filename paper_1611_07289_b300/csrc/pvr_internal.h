@@ -39,6 +39,15 @@ struct Tiling {
     int tiles_x, tiles_y, tpp;
 };
 
+// Persistent work queue over the non-empty (patch, tile) slots of a patch
+// table: items = slot indices (patch * tpp + tile), largest tiles first;
+// counter: one device int, reset by the launcher before every launch.
+struct WorkQueue {
+    const int32_t *items = nullptr;
+    int n_items = 0;
+    int *counter = nullptr;
+};
+
 // Launchers (each returns cudaGetLastError() of its launches).
 cudaError_t launch_pose_to_fixed(const DevGeom *g, const int32_t *desc, const double *poses,
                                  int n, int64_t n_pix, int max_side, int kxy, int kz,
@@ -48,7 +57,8 @@ cudaError_t launch_pose_to_fixed(const DevGeom *g, const int32_t *desc, const do
 cudaError_t launch_simulate(const DevGeom *g, const PsfTab &psf, const Tiling &tl, int nx, int ny,
                             int nz, const float *x, const float4 *quad, const int32_t *desc,
                             const int32_t *fix, int n, const float *y, float *sim_or_e,
-                            uint8_t *valid, double *part, cudaStream_t st);
+                            uint8_t *valid, double *part, cudaStream_t st,
+                            const WorkQueue *wq = nullptr);
 
 // Quad copy of the volume (nx * ny * nz < 2^31): quad[i] = (x[i], x[i + 1],
 // x[i + nx], x[i + nx + 1]), read by the gathers as two 16-byte loads per cell.
@@ -58,7 +68,7 @@ cudaError_t launch_build_quad(const float *x, float4 *quad, int nx, int ny, int 
 cudaError_t launch_adjoint(const PsfTab &psf, const Tiling &tl, int nx, int ny, int nz,
                            const int32_t *desc, const int32_t *fix, int n, const float *r,
                            const float *w, const uint8_t *patch_mask, float *addon, float *conf,
-                           int pair, cudaStream_t st);
+                           int pair, cudaStream_t st, const WorkQueue *wq = nullptr);
 
 // Weighted SIRT step on interleaved (addon, conf) pairs; optionally clears them.
 cudaError_t launch_volume_update_pairs(float *x, float2 *acc, int64_t nvox, float alpha,

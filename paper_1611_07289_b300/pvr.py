@@ -67,6 +67,8 @@ _SIGS = {
     "pvr_launch_count": (C.c_int64, [_VP]),
     "pvr_patches_build": (C.c_int, [_VP, _VP, C.c_int32, C.c_int32, C.c_double, C.c_double, _VP,
                                     C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64), _VP]),
+    "pvr_patches_build_sizes": (C.c_int, [_VP, _VP, _VP, _VP, C.c_double, C.c_double, _VP, C.c_int32,
+                                          C.POINTER(C.c_int32), C.POINTER(C.c_int64), _VP]),
     "pvr_patches_gather": (C.c_int, [_VP, _VP, C.POINTER(Patches), _VP, _VP]),
     "pvr_pose_to_fixed": (C.c_int, [_VP, C.POINTER(Patches), _VP, _VP, _VP]),
     "pvr_simulate": (C.c_int, [_VP, _VP, C.POINTER(Patches), _VP, _VP, _VP, _VP]),
@@ -77,6 +79,11 @@ _SIGS = {
     "pvr_volume_init": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, _VP]),
     "pvr_ncc_grad": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, _VP, _VP, _VP]),
     "pvr_pose_grad": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, _VP, _VP]),
+    "pvr_plan": (C.c_int, [_VP, C.POINTER(Patches), _VP, _VP, _VP, C.c_int32, C.c_int32, _VP]),
+    "pvr_plan_info": (C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "pvr_plan_clear": (C.c_int, [_VP]),
+    "pvr_graph_capture": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, _VP, _VP, _VP, _VP, _VP]),
+    "pvr_graph_launch": (C.c_int, [_VP, _VP]),
     "pvr_register": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, C.c_int32, _VP, _VP]),
     "pvr_reconstruct_iter": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, _VP, _VP, _VP, _VP,
                                        _VP]),
@@ -222,6 +229,24 @@ class Context:
         nn = min(int(n.value), int(max_out))
         return PatchTable(desc[:nn].clone(), int(npix.value), int(a)), int(n.value)
 
+    def pvr_patches_build_sizes(self, stacks, slice_a, slice_stride, fg_frac=0.0, keep_frac=0.0,
+                                max_out=None, stream=None):
+        """Patch table with a side and stride per slice (host int arrays, one
+        entry per slice of every stack in order)."""
+        if max_out is None:
+            max_out = self.params.max_patches
+        sa = np.ascontiguousarray(slice_a, dtype=np.int32)
+        ss = np.ascontiguousarray(slice_stride, dtype=np.int32)
+        desc = torch.zeros((max(max_out, 1), 8), dtype=torch.int32, device=stacks.device)
+        n = C.c_int32(0)
+        npix = C.c_int64(0)
+        self._chk(lib.pvr_patches_build_sizes(self.h, _ptr(stacks), sa.ctypes.data, ss.ctypes.data,
+                                              float(fg_frac), float(keep_frac), _ptr(desc), int(max_out),
+                                              C.byref(n), C.byref(npix), _stream(stream)))
+        nn = min(int(n.value), int(max_out))
+        ms = int(sa.max()) if sa.size else 0
+        return PatchTable(desc[:nn].clone(), int(npix.value), ms), int(n.value)
+
     def pvr_patches_gather(self, stacks, pt: PatchTable, y=None, stream=None):
         if y is None:
             y = torch.empty(pt.n_pix, dtype=torch.float32, device=stacks.device)
@@ -301,6 +326,30 @@ class Context:
         self._chk(lib.pvr_pose_grad(self.h, _ptr(x), _ptr(r), C.byref(pt.c), _ptr(poses), _ptr(grad),
                                     _stream(stream)))
         return grad
+
+    def pvr_plan(self, pt: PatchTable, x=None, y=None, poses=None, tile=0, mode=-1, stream=None):
+        """Work plan for this table (tile 0 / mode -1: tuned on x, y, poses);
+        returns (tile, mode, n_items)."""
+        self._chk(lib.pvr_plan(self.h, C.byref(pt.c), _ptr(x), _ptr(y), _ptr(poses), int(tile), int(mode),
+                               _stream(stream)))
+        return self.pvr_plan_info()
+
+    def pvr_plan_info(self):
+        t, m, n = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+        self._chk(lib.pvr_plan_info(self.h, C.byref(t), C.byref(m), C.byref(n)))
+        return int(t.value), int(m.value), int(n.value)
+
+    def pvr_plan_clear(self):
+        self._chk(lib.pvr_plan_clear(self.h))
+
+    def pvr_graph_capture(self, x, y, pt: PatchTable, poses, state, mask, p=None, w_patch=None,
+                          stream=None):
+        self._graph_keep = (x, y, pt, poses, state, mask, p, w_patch)   # pointers baked into the graph
+        self._chk(lib.pvr_graph_capture(self.h, _ptr(x), _ptr(y), C.byref(pt.c), _ptr(poses), _ptr(state),
+                                        _ptr(mask), _ptr(p), _ptr(w_patch), _stream(stream)))
+
+    def pvr_graph_launch(self, stream=None):
+        self._chk(lib.pvr_graph_launch(self.h, _stream(stream)))
 
     def pvr_register(self, x, y, pt: PatchTable, poses, n_evals, ncc=None, stream=None):
         if ncc is None:

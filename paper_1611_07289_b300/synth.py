@@ -23,6 +23,9 @@ workloads here stand in for its whole-uterus scans:
   jumps (+-15 deg) of the fetus only, 5 % corrupted slices (half zeroed,
   half scaled by 0.3), patches 64 / stride 32 kept when at least half their
   pixels exceed 1 % of the maximum.
+* ``config_uneven``: the uterus volume and stacks with a patch side drawn
+  per slice from {32, 48, 64, 96, 128}, stride half the side (batched
+  patches of uneven sizes).
 * ``config_diff``: the differentiable-forward-model workload, 128^3 voxels
   of 1 mm with nested ellipsoids, 3 orthogonal stacks of 86 slices of
   128x128 pixels at 1x1x1.5 mm, all square patches 48 / stride 24 (4,128
@@ -381,6 +384,18 @@ def config_uterus(seed=7289, device="cpu", slices=96, size=256):
     return dict(name="uterus-256x256x192", geom=geom, stacks=stacks, gt=gt.numpy(),
                 ellipsoids=ells, corrupt=corrupt, a=64, stride=32, fg_frac=0.01, keep_frac=0.5,
                 fwhm_xy=1.2, dz=sp, n_outer=10)
+
+
+def config_uneven(seed=7289, device="cpu", slices=96, size=256, sides=(32, 48, 64, 96, 128)):
+    """Uterus workload with a patch side per slice (module docstring): the
+    config_uterus dictionary plus slice_a, slice_stride (one entry per slice
+    of every stack, in order)."""
+    cfg = config_uterus(seed=seed, device=device, slices=slices, size=size)
+    rng = np.random.default_rng(seed + 1)
+    nk = sum(k for (_, _, k) in cfg["geom"].stack_dims)
+    sa = rng.choice(np.asarray(sides, dtype=np.int32), nk).astype(np.int32)
+    cfg.update(name=cfg["name"] + "-uneven", slice_a=sa, slice_stride=(sa // 2).astype(np.int32))
+    return cfg
 
 
 def config_diff(seed=3, device="cpu"):
