@@ -158,7 +158,7 @@ def _algorithmic_bytes(cls, n_pix, n_vox):
     return {"simulate": 9 * n_pix + 4 * n_vox,        # y in, e out, valid out, x in
             "adjoint": 8 * n_pix + 8 * n_vox,         # e, p in; addon, conf out
             "em": 9 * n_pix,                          # e, valid in; p out
-            "ncc": 18 * n_pix + 4 * n_vox,            # y, s, valid twice; x in
+            "ncc": 4 * n_pix + 4 * n_vox,             # y in, x in (moments and gradient on chip)
             "update": 24 * n_vox}.get(cls)            # x, addon, conf in; x, 0, 0 out
 
 
@@ -270,6 +270,8 @@ def run_ours(args, ws, rank, local, dist):
     dev = f"cuda:{local}"
     cfg, ctx, pt, y, x0, poses0, gen_s, build_s = _setup(dev, args.slices)
     n_pix, n_vox = pt.n_pix, cfg["geom"].n_vox
+    # launch plan for simulate / adjoint tuned on this table (setup, untimed)
+    plan = ctx.pvr_plan(pt, x0, y, poses0)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     gt = torch.as_tensor(cfg["gt"], device=dev)
@@ -393,7 +395,9 @@ def run_ours(args, ws, rank, local, dist):
         "metric": METRIC, "value": ws * n_pix / (t_ms * 1e-3), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": _config_dict(pt.n, n_pix, args.slices), "gpu_launches": int(launches),
+        "config": dict(_config_dict(pt.n, n_pix, args.slices),
+                       launch_plan={"tile": plan[0], "mode": ["one CTA per tile", "work queue"][plan[1]]}),
+        "gpu_launches": int(launches),
         "e2e": {"value": ws * n_pix / (e_t * 1e-3), "unit": UNIT, "ms_per_step": e_t,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
@@ -411,6 +415,126 @@ def run_ours(args, ws, rank, local, dist):
         res["cpu_baseline"] = {"value": info["value"], "unit": UNIT, "cores": info["cores"],
                                "kind": "oracle", "sample": info["sample"]}
     return res
+
+
+def run_uneven(args, ws, rank, local):
+    """Batched patches of uneven sizes (sides 32..128 drawn per slice, stride
+    side / 2) on the uterus volume: simulate + adjoint as one launch per
+    patch size against one planned (tuned) launch over all sizes, and the
+    whole iteration as direct calls against a captured CUDA graph."""
+    import torch
+    from paper_1611_07289_b300 import pvr, synth
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    t0 = time.perf_counter()
+    cfg = synth.config_uneven(device=dev, slices=args.slices)
+    gen_s = time.perf_counter() - t0
+    packed = torch.as_tensor(synth.pack_stacks(cfg["stacks"]), device=dev)
+    prm = pvr.default_params(psf_dz=0.75, max_patches=65536, max_pixels=1 << 27, max_patch_side=128,
+                             reg_evals=2, n_sr=1)
+    ctx = pvr.Context(cfg["geom"], prm)
+    pt, n = ctx.pvr_patches_build_sizes(packed, cfg["slice_a"], cfg["slice_stride"], 0.01, 0.5)
+    y = ctx.pvr_patches_gather(packed, pt)
+    poses0 = torch.zeros((pt.n, 6), dtype=torch.float64, device=dev)
+    x0 = ctx.pvr_volume_init(y, pt, poses0)
+    n_pix, n_vox = pt.n_pix, cfg["geom"].n_vox
+    desc = pt.desc
+    sides = sorted(set(desc[:, 4].tolist()))
+    subs = []
+    for a in sides:
+        rows = torch.nonzero(desc[:, 4] == a).reshape(-1)
+        subs.append((pvr.PatchTable(desc[rows].contiguous(), n_pix, a), poses0[rows].contiguous()))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    sim = torch.empty(n_pix, dtype=torch.float32, device=dev)
+    valid = torch.empty(n_pix, dtype=torch.uint8, device=dev)
+    addon = torch.empty_like(x0)
+    conf = torch.empty_like(x0)
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return float(np.median(ms))
+
+    def per_size():
+        for k, (sub, ps) in enumerate(subs):
+            ctx.pvr_simulate(x0, sub, ps, sim, valid)
+            ctx.pvr_adjoint(sub, ps, y, None, addon, conf, accumulate=k > 0)
+
+    def full():
+        ctx.pvr_simulate(x0, pt, poses0, sim, valid)
+        ctx.pvr_adjoint(pt, poses0, y, None, addon, conf)
+
+    ctx.pvr_plan_clear()
+    ms_size = timed(per_size, args.steps, args.warmup)
+    ms_grid = timed(full, args.steps, args.warmup)
+    plan = ctx.pvr_plan(pt, x0, y, poses0)
+    ms_plan = timed(full, args.steps, args.warmup)
+
+    x, poses = x0.clone(), poses0.clone()
+    state, mask = pvr.new_state(dev), torch.ones(pt.n, dtype=torch.uint8, device=dev)
+
+    def it_direct():
+        ctx.pvr_reconstruct_iter(x, y, pt, poses, state, mask)
+
+    ms_iter = timed(it_direct, args.steps, args.warmup)
+    gs = torch.cuda.Stream(device=dev)
+    x.copy_(x0)
+    poses.copy_(poses0)
+    state.zero_()
+    mask.fill_(1)
+    torch.cuda.synchronize()
+    ctx.pvr_graph_capture(x, y, pt, poses, state, mask, stream=gs)
+    gs.synchronize()
+    sampler = ClockSampler(local)
+    for _ in range(args.warmup):
+        ctx.pvr_graph_launch(stream=gs)
+    gs.synchronize()
+    g_ms = []
+    sampler.start()
+    for _ in range(args.steps):
+        with torch.cuda.stream(gs):
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(gs)
+        ctx.pvr_graph_launch(stream=gs)
+        b.record(gs)
+        gs.synchronize()
+        g_ms.append(a.elapsed_time(b))
+    clocks = sampler.stop()
+    ms_graph = float(np.median(g_ms))
+    peaks, peak_kind = _peaks()
+    abytes = _algorithmic_bytes("simulate", n_pix, n_vox) + _algorithmic_bytes("adjoint", n_pix, n_vox)
+    achieved = abytes / (ms_plan * 1e-3) / 1e9
+    counts = {int(a): int((desc[:, 4] == a).sum()) for a in sides}
+    return {
+        "metric": METRIC, "value": n_pix / (ms_graph * 1e-3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "pvr-uterus-uneven-sides32-128-stride-half", "n_patches": pt.n,
+                   "n_patch_pixels": n_pix, "patches_per_side": counts,
+                   "step": "pvr_reconstruct_iter replayed from a captured CUDA graph",
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "simulate_adjoint_ms": {"one_launch_per_size": ms_size, "one_launch_grid": ms_grid,
+                                "planned": ms_plan, "plan": {"tile": plan[0], "mode": plan[1],
+                                                              "n_items": plan[2]}},
+        "iteration_ms": {"direct_calls": ms_iter, "graph_replay": ms_graph},
+        "roofline": {"bound": "hbm", "kernel": "simulate+adjoint (planned)", "achieved": achieved,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                     "traffic": None, "algorithmic_bytes": abytes, "ms_per_launch": ms_plan,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+        "clocks": clocks, "setup_s": {"generate": gen_s},
+    }
 
 
 def run_reference(args, ws, rank):
@@ -447,12 +571,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--slices", type=int, default=96,
                     help="slices per stack (96 = the benchmark workload; fewer for profiling)")
+    ap.add_argument("--workload", choices=["uterus", "uneven"], default="uterus",
+                    help="uneven: patch sides 32..128 per slice (batched-launch comparison, 1 GPU)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     ws, rank, local = _dist()
     dist = None
     if args.impl == "reference":
         res = run_reference(args, ws, rank)
+    elif args.workload == "uneven":
+        res = run_uneven(args, ws, rank, local) if rank == 0 else None
     else:
         if ws > 1:
             import torch.distributed as dist
