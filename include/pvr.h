@@ -58,6 +58,8 @@ extern "C" {
 #define PVR_MAX_STACKS 16
 #define PVR_MAX_KXY 3
 #define PVR_MAX_KZ 8
+#define PVR_PSF_GAUSSIAN 0
+#define PVR_PSF_TAYLOR_SINC 1
 #define PVR_EM_STATE_LEN 16
 
 typedef enum pvr_status {
@@ -136,6 +138,14 @@ typedef struct pvr_params {
     int32_t max_patches;    /* largest patch count of any call */
     int64_t max_pixels;     /* largest total pixel count of any call */
     int32_t max_patch_side; /* largest patch width or height (1..256) */
+    /* in-plane PSF profile: PVR_PSF_GAUSSIAN (above) or PVR_PSF_TAYLOR_SINC:
+     * weight sinc(1.2067091288 d / psf_fwhm_xy), sinc(u) = sin(pi u)/(pi u)
+     * (full width at half maximum psf_fwhm_xy pixels) summed from its Taylor
+     * series until a term is below psf_sinc_eps times the sum (Sec. II); the
+     * slice profile stays Gaussian.  Weights may be negative; a pixel whose
+     * PSF weight sum is not positive is invalid. */
+    int32_t psf_kind;       /* default PVR_PSF_GAUSSIAN */
+    double psf_sinc_eps;    /* default 1e-12 */
 } pvr_params;
 
 /* Patch table handed to every per-patch call (host struct, device table). */
@@ -307,6 +317,29 @@ PVR_API int pvr_volume_update(pvr_ctx *ctx, float *x, float *addon, float *conf,
 /* Initial volume x = A^T y / A^T 1 (0 where A^T 1 <= conf_eps) at `poses`. */
 PVR_API int pvr_volume_init(pvr_ctx *ctx, float *x, const float *y, const pvr_patches *patches,
                     const double *poses, void *stream);
+
+/* Per-patch evaluation against the acquired patches (Sec. IV-A: metrics
+ * between original 2D patches and patches simulated from the
+ * reconstruction).  Over each patch's valid pixels, with the acquired patch
+ * y as reference: out[5p..5p+4] = {PSNR = 10 log10(I_max^2 / MSE), CC,
+ * SSIM (global, c1 = (0.01 L)^2, c2 = (0.03 L)^2, L = range of y), DSSIM =
+ * (1 - SSIM)/2, mean local SSIM}; map (may be NULL): the DSSIM heat map,
+ * per valid pixel (1 - SSIM)/2 over the valid pixels of its (2w+1)^2
+ * window clipped to the patch, 0 at invalid pixels.  out: float64 [n][5];
+ * map: float32 [n_pix]; w: 0..16. */
+PVR_API int pvr_patch_metrics(pvr_ctx *ctx, const float *y, const float *sim, const uint8_t *valid,
+                              const pvr_patches *patches, int32_t w, double *out, float *map,
+                              void *stream);
+
+/* Rigidity (data-consistency) map (Sec. II, "Identification of Rigid
+ * Regions"): the pixel probabilities p and patch potentials p-bar
+ * integrated into the volume with the reconstruction's PSF,
+ * out = A^T(p * pbar_patch) / A^T 1 where A^T 1 > conf_eps, else 0 -- the
+ * PSF-weighted mean of p * p-bar over the samples that reach each voxel.
+ * p: float32 [n_pix] (e.g. pvr_em_weights' p); pbar: float32 [n] (p-bar or
+ * the patch weight); out: float32 volume. */
+PVR_API int pvr_rigidity_map(pvr_ctx *ctx, const pvr_patches *patches, const double *poses,
+                             const float *p, const float *pbar, float *out, void *stream);
 
 /* NCC of every patch against the volume simulated at its pose, and its
  * gradient with respect to the 6 pose parameters (Sec. II: CC similarity,

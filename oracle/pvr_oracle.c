@@ -21,6 +21,7 @@
  *   or_sim_pose_vjp    d (sum r * sim) / d pose of one patch      (Eq. 1 differentiated through the sample positions)
  *   or_register        per-patch gradient ascent on NCC           (Sec. III "patch-wise gradient descent")
  *   or_metrics         PSNR, CC, SSIM, DSSIM                      (Eqs. cross_corr, PSNR, SSIM, DSSIM)
+ *   or_patch_metrics   the same per patch + local DSSIM heat map  (Sec. IV-A patch evaluation)
  *
  * Where the paper is silent (discretisation of the PSF, the fixed-point
  * sample lattice, EM initialisation, the patch classification rule, the
@@ -61,13 +62,18 @@ typedef struct {
     double thick[OR_MAX_STACKS];
 } or_geom;
 
-/* Gaussian PSF discretisation: in-plane taps at pixel offsets -kxy..kxy,
- * through-plane samples at offsets zeta*dz mm, zeta = -kz..kz. */
+/* PSF discretisation: in-plane taps at pixel offsets -kxy..kxy,
+ * through-plane samples at offsets zeta*dz mm, zeta = -kz..kz.  kind 0:
+ * Gaussian in-plane profile; kind 1: sinc in-plane profile evaluated by its
+ * Taylor series to relative error eps (Sec. II); the through-plane slice
+ * profile is Gaussian in both. */
 typedef struct {
     double fwhm_xy;
     int kxy;
     int kz;
     double dz;
+    int kind;
+    double eps;
 } or_psf;
 
 /* EM / patch-classification parameters. */
@@ -303,13 +309,36 @@ static int or_trilinear(const float *x, int nx, int ny, int nz, const int64_t q[
 }
 
 /* Gaussian PSF weights. gxy[t + kxy], t = -kxy..kxy; gz[z + kz], z = -kz..kz. */
+/* sinc(u) = sin(pi u) / (pi u) by its Maclaurin series 1 - x^2/3! + x^4/5! -
+ * ..., x = pi u (Sec. II, the Taylor-series PSF): terms are added until the
+ * next one is below eps times the partial sum. */
+static double or_sinc_taylor(double u, double eps)
+{
+    double x2 = (M_PI * u) * (M_PI * u), term = 1.0, sum = 1.0;
+    for (int k = 1; k < 200; ++k) {
+        term *= -x2 / ((double)(2 * k) * (double)(2 * k + 1));
+        sum += term;
+        if (fabs(term) <= eps * fabs(sum)) break;
+    }
+    return sum;
+}
+
 static void or_psf_weights(const or_geom *g, const or_psf *psf, int stack, double *gxy, double *gz)
 {
     double fwhm_to_sigma = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
     double sxy = psf->fwhm_xy * fwhm_to_sigma;
     double sz = g->thick[stack] * fwhm_to_sigma;
-    for (int t = -psf->kxy; t <= psf->kxy; ++t)
-        gxy[t + psf->kxy] = (sxy > 0.0) ? exp(-(double)(t * t) / (2.0 * sxy * sxy)) : (t == 0);
+    /* sinc(u) falls to 1/2 at u = 0.6033545644..., so a sinc profile with
+     * full width at half maximum F (pixels) is sinc(1.2067091288 d / F) */
+    const double sinc_fwhm = 1.2067091288;
+    for (int t = -psf->kxy; t <= psf->kxy; ++t) {
+        if (psf->kind == 1)
+            gxy[t + psf->kxy] = (psf->fwhm_xy > 0.0)
+                                    ? or_sinc_taylor(sinc_fwhm * (double)t / psf->fwhm_xy, psf->eps)
+                                    : (t == 0);
+        else
+            gxy[t + psf->kxy] = (sxy > 0.0) ? exp(-(double)(t * t) / (2.0 * sxy * sxy)) : (t == 0);
+    }
     for (int z = -psf->kz; z <= psf->kz; ++z) {
         double off = (double)z * psf->dz;
         gz[z + psf->kz] = (sz > 0.0) ? exp(-(off * off) / (2.0 * sz * sz)) : (z == 0);
@@ -985,6 +1014,78 @@ void or_metrics(const double *ref, const double *img, const uint8_t *mask, size_
 }
 
 /* ---------------------------------------------------------- patch table -- */
+
+/* Per-patch evaluation (Sec. IV-A: metrics between the acquired patches and
+ * the patches simulated from the reconstruction).  For every patch, over its
+ * valid pixels: out[5p..5p+4] = {PSNR, CC, SSIM, DSSIM} of or_metrics with
+ * the acquired patch as reference, and the mean of the local SSIM map.  The
+ * DSSIM heat map (Eq. DSSIM, visualised as maps in Sec. V) takes SSIM over
+ * the valid pixels of the (2w+1) x (2w+1) window around each pixel, clipped
+ * to the patch, with the patch's c1, c2 (L = range of the acquired patch):
+ * map[pix] = (1 - SSIM_local) / 2, 0 at invalid pixels. */
+void or_patch_metrics(const float *y, const float *sim, const uint8_t *valid, const int *desc,
+                      int P, int w, double *out, double *map)
+{
+    for (int p = 0; p < P; ++p) {
+        const int *d = desc + 8 * (size_t)p;
+        int W = d[4], H = d[5];
+        size_t off = (size_t)d[6], n = (size_t)W * H;
+        double *ref = (double *)malloc(n * sizeof(double)), *img = (double *)malloc(n * sizeof(double));
+        for (size_t t = 0; t < n; ++t) {
+            ref[t] = y[off + t];
+            img[t] = sim[off + t];
+        }
+        double mo[5];
+        or_metrics(ref, img, valid + off, n, mo);
+        double rmax = -INFINITY, rmin = INFINITY;
+        for (size_t t = 0; t < n; ++t)
+            if (valid[off + t]) {
+                rmax = ref[t] > rmax ? ref[t] : rmax;
+                rmin = ref[t] < rmin ? ref[t] : rmin;
+            }
+        double L = rmax - rmin, c1 = (0.01 * L) * (0.01 * L), c2 = (0.03 * L) * (0.03 * L);
+        double ssum = 0.0, scnt = 0.0;
+        for (int j = 0; j < H; ++j)
+            for (int i = 0; i < W; ++i) {
+                size_t t = (size_t)j * W + i;
+                map[off + t] = 0.0;
+                if (!valid[off + t]) continue;
+                double k = 0.0, ma = 0.0, mb = 0.0;
+                for (int jj = j - w; jj <= j + w; ++jj)
+                    for (int ii = i - w; ii <= i + w; ++ii) {
+                        if (ii < 0 || jj < 0 || ii >= W || jj >= H) continue;
+                        size_t u = (size_t)jj * W + ii;
+                        if (!valid[off + u]) continue;
+                        k += 1.0;
+                        ma += ref[u];
+                        mb += img[u];
+                    }
+                ma /= k;
+                mb /= k;
+                double va = 0.0, vb = 0.0, cab = 0.0;
+                for (int jj = j - w; jj <= j + w; ++jj)
+                    for (int ii = i - w; ii <= i + w; ++ii) {
+                        if (ii < 0 || jj < 0 || ii >= W || jj >= H) continue;
+                        size_t u = (size_t)jj * W + ii;
+                        if (!valid[off + u]) continue;
+                        va += (ref[u] - ma) * (ref[u] - ma);
+                        vb += (img[u] - mb) * (img[u] - mb);
+                        cab += (ref[u] - ma) * (img[u] - mb);
+                    }
+                va /= k;
+                vb /= k;
+                cab /= k;
+                double ss = ((2.0 * ma * mb + c1) * (2.0 * cab + c2)) / ((ma * ma + mb * mb + c1) * (va + vb + c2));
+                map[off + t] = (1.0 - ss) / 2.0;
+                ssum += ss;
+                scnt += 1.0;
+            }
+        for (int k = 0; k < 4; ++k) out[5 * (size_t)p + k] = mo[k];
+        out[5 * (size_t)p + 4] = scnt > 0.0 ? ssum / scnt : 0.0;
+        free(ref);
+        free(img);
+    }
+}
 
 /* Square patches of side a and stride stride on every slice of every stack
  * (Sec. II "Patch Extraction"): corners x0, y0 = 0, stride, 2 stride, ...

@@ -40,7 +40,8 @@ class _Geom(C.Structure):
 
 
 class _Psf(C.Structure):
-    _fields_ = [("fwhm_xy", C.c_double), ("kxy", C.c_int), ("kz", C.c_int), ("dz", C.c_double)]
+    _fields_ = [("fwhm_xy", C.c_double), ("kxy", C.c_int), ("kz", C.c_int), ("dz", C.c_double),
+                ("kind", C.c_int), ("eps", C.c_double)]
 
 
 class _EmParams(C.Structure):
@@ -103,6 +104,8 @@ def lib():
                                              C.c_double, C.c_double, P(C.c_int), C.c_int,
                                              P(C.c_int64)]
         L.or_patches_build_sizes.restype = C.c_int
+        L.or_patch_metrics.argtypes = [P(C.c_float), P(C.c_float), P(C.c_uint8), P(C.c_int), C.c_int,
+                                       C.c_int, P(C.c_double), P(C.c_double)]
         L.or_psf_table.argtypes = [P(_Geom), P(_Psf), C.c_int, P(C.c_double), P(C.c_double)]
         _lib = L
     return _lib
@@ -135,8 +138,9 @@ def geom(g) -> _Geom:
     return G
 
 
-def psf(fwhm_xy=1.2, kxy=1, kz=3, dz=1.0) -> _Psf:
-    return _Psf(float(fwhm_xy), int(kxy), int(kz), float(dz))
+def psf(fwhm_xy=1.2, kxy=1, kz=3, dz=1.0, kind=0, eps=1e-12) -> _Psf:
+    """kind 0: Gaussian in-plane PSF; kind 1: Taylor-series sinc in-plane."""
+    return _Psf(float(fwhm_xy), int(kxy), int(kz), float(dz), int(kind), float(eps))
 
 
 def em_params(c0=0.9, sigma_floor_rel=1e-3, min_valid_frac=0.1, patch_rule=0,
@@ -353,3 +357,18 @@ def patches_build_sizes(G, stacks, slice_a, slice_stride, fg_frac=0.0, keep_frac
                                  _ptr(ss, C.c_int), float(fg_frac), float(keep_frac),
                                  _ptr(desc, C.c_int), n, C.byref(npix))
     return desc[:n], int(npix.value)
+
+
+def patch_metrics(y, sim, valid, desc, w=3):
+    """Per-patch {PSNR, CC, SSIM, DSSIM, mean local SSIM} (float64 [P, 5]) and
+    the local DSSIM heat map (float64 [n_pix])."""
+    y = _c(y, np.float32)
+    sim = _c(sim, np.float32)
+    valid = _c(valid, np.uint8)
+    desc = _c(desc, np.int32)
+    out = np.zeros((desc.shape[0], 5), dtype=np.float64)
+    m = np.zeros(y.size, dtype=np.float64)
+    lib().or_patch_metrics(_ptr(y, C.c_float), _ptr(sim, C.c_float), _ptr(valid, C.c_uint8),
+                           _ptr(desc, C.c_int), int(desc.shape[0]), int(w), _ptr(out, C.c_double),
+                           _ptr(m, C.c_double))
+    return out, m

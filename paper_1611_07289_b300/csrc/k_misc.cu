@@ -191,6 +191,20 @@ __device__ __forceinline__ double wsum(double v)
     return v;
 }
 
+// Block-wide max of a float (result in every thread); sh: 32 floats.
+__device__ float block_max(float v, float *sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float m = -INFINITY;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sh[w]);
+    __syncthreads();
+    return m;
+}
+
 template <int NV>
 __device__ void block_sums(double *v, double *sh)
 {
@@ -321,6 +335,108 @@ __global__ void k_metrics3(const double *__restrict__ scr1, const double *__rest
     out[4] = mse;
 }
 
+// Per-patch evaluation, one CTA per patch: global PSNR, CC, SSIM, DSSIM of the
+// simulated against the acquired patch over valid pixels (float64 sums), then
+// the local SSIM of every valid pixel over the valid pixels of its
+// (2w+1)^2 window clipped to the patch (same c1, c2), written as the DSSIM
+// heat map, and the mean local SSIM.
+__global__ void __launch_bounds__(256) k_patch_metrics(const float *__restrict__ y,
+                                                       const float *__restrict__ sim,
+                                                       const uint8_t *__restrict__ valid,
+                                                       const int32_t *__restrict__ desc, int w,
+                                                       double *__restrict__ out,
+                                                       float *__restrict__ map)
+{
+    __shared__ double sh[32 * 8];
+    __shared__ double glob[8];
+    const int32_t *d = desc + 8 * (size_t)blockIdx.x;
+    const int W = d[4], H = d[5];
+    const size_t off = (size_t)d[6];
+    const int n = W * H;
+    // pass 1: counts, sums, extremes of the acquired patch
+    double v[5] = {0, 0, 0, 0, 0};
+    float rmax = -INFINITY, rmin = INFINITY;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        if (!valid[off + t]) continue;
+        const double a = y[off + t], b = sim[off + t];
+        v[0] += 1.0;
+        v[1] += a;
+        v[2] += b;
+        rmax = fmaxf(rmax, y[off + t]);
+        rmin = fminf(rmin, y[off + t]);
+    }
+    block_sums<3>(v, sh);
+    rmax = block_max(rmax, (float *)(sh + 32 * 4));
+    rmin = -block_max(-rmin, (float *)(sh + 32 * 4));
+    if (threadIdx.x == 0) {
+        glob[0] = v[0];
+        glob[1] = v[0] > 0.0 ? v[1] / v[0] : 0.0;
+        glob[2] = v[0] > 0.0 ? v[2] / v[0] : 0.0;
+        glob[3] = rmax;
+        glob[4] = rmin;
+    }
+    __syncthreads();
+    const double cnt = glob[0], mr = glob[1], mi = glob[2];
+    // pass 2: centred second moments and squared error
+    double u[4] = {0, 0, 0, 0};
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        if (!valid[off + t]) continue;
+        const double a = (double)y[off + t] - mr, b = (double)sim[off + t] - mi;
+        const double dd = (double)sim[off + t] - (double)y[off + t];
+        u[0] += a * a;
+        u[1] += b * b;
+        u[2] += a * b;
+        u[3] += dd * dd;
+    }
+    block_sums<4>(u, sh);
+    const double L = glob[3] - glob[4];
+    const double c1 = (0.01 * L) * (0.01 * L), c2 = (0.03 * L) * (0.03 * L);
+    double *o = out + 5 * (size_t)blockIdx.x;
+    if (threadIdx.x == 0) {
+        if (cnt > 0.0) {
+            const double vr = u[0] / cnt, vi = u[1] / cnt, cv = u[2] / cnt, mse = u[3] / cnt;
+            o[0] = mse > 0.0 ? 10.0 * log10(glob[3] * glob[3] / mse) : INFINITY;
+            o[1] = (vr > 0.0 && vi > 0.0) ? cv / sqrt(vr * vi) : 0.0;
+            const double ss = ((2.0 * mr * mi + c1) * (2.0 * cv + c2)) / ((mr * mr + mi * mi + c1) * (vr + vi + c2));
+            o[2] = ss;
+            o[3] = (1.0 - ss) / 2.0;
+        } else {
+            o[0] = o[1] = o[2] = o[3] = 0.0;
+        }
+    }
+    // pass 3: local SSIM map
+    double ls[2] = {0.0, 0.0};
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int j = t / W, i = t - j * W;
+        if (!valid[off + t]) {
+            if (map) map[off + t] = 0.f;
+            continue;
+        }
+        double k = 0.0, sa = 0.0, sb = 0.0, saa = 0.0, sbb = 0.0, sab = 0.0;
+        for (int jj = max(j - w, 0); jj <= min(j + w, H - 1); ++jj)
+            for (int ii = max(i - w, 0); ii <= min(i + w, W - 1); ++ii) {
+                const size_t q = off + (size_t)jj * W + ii;
+                if (!valid[q]) continue;
+                const double a = y[q], b = sim[q];
+                k += 1.0;
+                sa += a;
+                sb += b;
+                saa += a * a;
+                sbb += b * b;
+                sab += a * b;
+            }
+        const double ma = sa / k, mb = sb / k;
+        const double va = fmax(saa / k - ma * ma, 0.0), vb = fmax(sbb / k - mb * mb, 0.0);
+        const double cab = sab / k - ma * mb;
+        const double ss = ((2.0 * ma * mb + c1) * (2.0 * cab + c2)) / ((ma * ma + mb * mb + c1) * (va + vb + c2));
+        if (map) map[off + t] = (float)((1.0 - ss) / 2.0);
+        ls[0] += ss;
+        ls[1] += 1.0;
+    }
+    block_sums<2>(ls, sh);
+    if (threadIdx.x == 0) o[4] = ls[1] > 0.0 ? ls[0] / ls[1] : 0.0;
+}
+
 }  // namespace
 
 constexpr int kMetricBlocks = 296;
@@ -378,6 +494,14 @@ cudaError_t launch_patches_gather(const DevGeom *g, const float *stacks, const i
 {
     if (n <= 0) return cudaSuccess;
     k_patch_gather<<<(unsigned)n, 256, 0, st>>>(g, stacks, desc, (long long)n_pix, err, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_patch_metrics(const float *y, const float *sim, const uint8_t *valid, const int32_t *desc,
+                                 int n, int w, double *out, float *map, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_patch_metrics<<<(unsigned)n, 256, 0, st>>>(y, sim, valid, desc, w, out, map);
     return cudaGetLastError();
 }
 

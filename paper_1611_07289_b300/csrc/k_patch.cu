@@ -764,6 +764,7 @@ __device__ __forceinline__ void adjoint_tile(long long gid, const VolDims &vd,
                                              const Tiling &tl, const float *__restrict__ r,
                                              const float *__restrict__ w,
                                              const uint8_t *__restrict__ pmask,
+                                             const float *__restrict__ pweight,
                                              float *__restrict__ addon, float *__restrict__ conf,
                                              float *sm)
 {
@@ -772,6 +773,7 @@ __device__ __forceinline__ void adjoint_tile(long long gid, const VolDims &vd,
     TileInfo ti;
     if (!tile_setup_at(gid, desc, fix, tl, kxy, ti) || !ti.ok) return;
     if (pmask && pmask[ti.p] == 0) return;
+    const float pw = pweight ? pweight[ti.p] : 1.f;   // per-patch factor on r only
     const int np = ti.tw * ti.th;
     float *U = sm, *Uw = sm + ti.L, *CR = sm + 2 * ti.L, *CW = CR + np;
     const float *gz = psf.gz[ti.stack];
@@ -797,6 +799,7 @@ __device__ __forceinline__ void adjoint_tile(long long gid, const VolDims &vd,
             float rr = r ? __ldg(r + o) : 1.f;
             cw = ww / den;
             cr = cw * rr;
+            if (pweight) cr *= pw;
         }
         CR[pp] = cr;
         CW[pp] = cw;
@@ -840,11 +843,12 @@ __global__ void __launch_bounds__(256, 3) k_adjoint(VolDims vd, const int32_t *_
                                                  Tiling tl, const float *__restrict__ r,
                                                  const float *__restrict__ w,
                                                  const uint8_t *__restrict__ pmask,
+                                                 const float *__restrict__ pweight,
                                                  float *__restrict__ addon,
                                                  float *__restrict__ conf)
 {
     extern __shared__ float sm[];
-    adjoint_tile<KXY, KZ, PAIR>(blockIdx.x, vd, desc, fix, psf, tl, r, w, pmask, addon, conf, sm);
+    adjoint_tile<KXY, KZ, PAIR>(blockIdx.x, vd, desc, fix, psf, tl, r, w, pmask, pweight, addon, conf, sm);
 }
 
 // The adjoint as a persistent work queue over listed (patch, tile) slots.
@@ -854,6 +858,7 @@ __global__ void __launch_bounds__(256, 3) k_adjoint_q(VolDims vd, const int32_t 
                                                    Tiling tl, const float *__restrict__ r,
                                                    const float *__restrict__ w,
                                                    const uint8_t *__restrict__ pmask,
+                                                   const float *__restrict__ pweight,
                                                    float *__restrict__ addon,
                                                    float *__restrict__ conf,
                                                    const int32_t *__restrict__ items, int n_items,
@@ -864,7 +869,8 @@ __global__ void __launch_bounds__(256, 3) k_adjoint_q(VolDims vd, const int32_t 
     for (;;) {
         const int it = next_item(counter, &cur);
         if (it >= n_items) break;
-        adjoint_tile<KXY, KZ, PAIR>(items[it], vd, desc, fix, psf, tl, r, w, pmask, addon, conf, sm);
+        adjoint_tile<KXY, KZ, PAIR>(items[it], vd, desc, fix, psf, tl, r, w, pmask, pweight, addon, conf,
+                                    sm);
         __syncthreads();
     }
 }
@@ -1599,7 +1605,7 @@ cudaError_t launch_build_quad(const float *x, float4 *quad, int nx, int ny, int 
 cudaError_t launch_adjoint(const PsfTab &psf, const Tiling &tl, int nx, int ny, int nz,
                            const int32_t *desc, const int32_t *fix, int n, const float *r,
                            const float *w, const uint8_t *pmask, float *addon, float *conf,
-                           int pair, cudaStream_t st, const WorkQueue *wq)
+                           int pair, cudaStream_t st, const WorkQueue *wq, const float *pweight)
 {
     if (n <= 0) return cudaSuccess;
     VolDims vd = vol_dims(nx, ny, nz);
@@ -1618,12 +1624,13 @@ cudaError_t launch_adjoint(const PsfTab &psf, const Tiling &tl, int nx, int ny, 
             if ((e = persistent_grid(k_adjoint_q<KX, KZv, PR>, smem, wq->n_items, &pg)) != cudaSuccess) \
                 return e;                                                                             \
             k_adjoint_q<KX, KZv, PR><<<pg, block, smem, st>>>(vd, desc, fix, psf, tl, r, w, pmask,    \
-                                                              addon, conf, wq->items, wq->n_items,    \
+                                                              pweight, addon, conf, wq->items,        \
+                                                              wq->n_items,                            \
                                                               wq->counter);                           \
         } else {                                                                                      \
             if ((e = prep(k_adjoint<KX, KZv, PR>, smem)) != cudaSuccess) return e;                    \
             k_adjoint<KX, KZv, PR><<<grid, block, smem, st>>>(vd, desc, fix, psf, tl, r, w, pmask,    \
-                                                              addon, conf);                           \
+                                                              pweight, addon, conf);                  \
         }                                                                                             \
     } while (0)
     const bool fast = psf.kxy == 1 && psf.kz == 3;

@@ -242,7 +242,55 @@ int pose_fixed(pvr_ctx *c, const pvr_patches *pp, int max_side, const double *po
 
 }  // namespace
 
+namespace pvr {
+
+// sin(pi u) / (pi u) summed from its Maclaurin series (Sec. II, the
+// Taylor-series PSF) until a term is below eps times the sum.
+double sinc_series(double u, double eps)
+{
+    const double x = 3.14159265358979323846 * u, x2 = x * x;
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 200; ++k) {
+        term = -term * x2 / ((double)(2 * k) * (double)(2 * k + 1));
+        sum += term;
+        if (fabs(term) <= eps * fabs(sum)) break;
+    }
+    return sum;
+}
+
+void make_psf_tab(const pvr_geometry *g, const pvr_params *prm, PsfTab *tab)
+{
+    PsfTab &t = *tab;
+    memset(&t, 0, sizeof t);
+    t.kxy = prm->psf_kxy;
+    t.kz = prm->psf_kz;
+    const double to_sigma = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
+    const double sxy = prm->psf_fwhm_xy * to_sigma;
+    // the sinc reaches half its peak at u = 0.6033545644: a sinc profile of
+    // full width at half maximum F pixels is sinc(1.2067091288 d / F)
+    const double sinc_width = 1.2067091288;
+    for (int d = -t.kxy; d <= t.kxy; ++d) {
+        double v;
+        if (prm->psf_kind == PVR_PSF_TAYLOR_SINC)
+            v = prm->psf_fwhm_xy > 0.0 ? sinc_series(sinc_width * d / prm->psf_fwhm_xy, prm->psf_sinc_eps)
+                                       : (d == 0);
+        else
+            v = sxy > 0.0 ? exp(-(double)(d * d) / (2.0 * sxy * sxy)) : (d == 0);
+        t.gxy[d + t.kxy] = (float)v;
+    }
+    for (int s = 0; s < g->n_stacks; ++s) {
+        const double sz = g->thickness[s] * to_sigma;
+        for (int z = -t.kz; z <= t.kz; ++z) {
+            const double o = z * prm->psf_dz;
+            t.gz[s][z + t.kz] = (float)(sz > 0.0 ? exp(-(o * o) / (2.0 * sz * sz)) : (z == 0));
+        }
+    }
+}
+
+}  // namespace pvr
+
 extern "C" {
+
 
 void pvr_params_default(pvr_params *p)
 {
@@ -271,6 +319,8 @@ void pvr_params_default(pvr_params *p)
     p->max_patches = 65536;
     p->max_pixels = (int64_t)1 << 27;
     p->max_patch_side = 128;
+    p->psf_kind = PVR_PSF_GAUSSIAN;
+    p->psf_sinc_eps = 1e-12;
 }
 
 int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
@@ -302,6 +352,9 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
     if (prm->psf_kxy < 0 || prm->psf_kxy > PVR_MAX_KXY) return bad("psf_kxy outside 0..3");
     if (prm->psf_kz < 0 || prm->psf_kz > PVR_MAX_KZ) return bad("psf_kz outside 0..8");
     if (!(prm->psf_dz > 0.0) || !(prm->psf_fwhm_xy >= 0.0)) return bad("bad PSF size");
+    if (prm->psf_kind != PVR_PSF_GAUSSIAN && prm->psf_kind != PVR_PSF_TAYLOR_SINC) return bad("bad psf_kind");
+    if (prm->psf_kind == PVR_PSF_TAYLOR_SINC && !(prm->psf_sinc_eps > 0.0 && prm->psf_sinc_eps < 1.0))
+        return bad("psf_sinc_eps outside (0, 1)");
     if (prm->n_params != 6) return bad("only rigid (6-parameter) poses are supported");
     if (prm->max_patches < 1 || prm->max_pixels < 1) return bad("capacity must be positive");
     if (prm->max_patch_side < 1 || prm->max_patch_side > kMaxSideLimit)
@@ -332,22 +385,8 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
     c->stack_total = off;
     c->nvox = (int64_t)g->nx * g->ny * g->nz;
 
-    // PSF tables: float64 Gaussian weights rounded to float32
-    PsfTab &t = c->psf;
-    memset(&t, 0, sizeof t);
-    t.kxy = prm->psf_kxy;
-    t.kz = prm->psf_kz;
-    const double to_sigma = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
-    double sxy = prm->psf_fwhm_xy * to_sigma;
-    for (int d = -t.kxy; d <= t.kxy; ++d)
-        t.gxy[d + t.kxy] = (float)(sxy > 0.0 ? exp(-(double)(d * d) / (2.0 * sxy * sxy)) : (d == 0));
-    for (int s = 0; s < g->n_stacks; ++s) {
-        double sz = g->thickness[s] * to_sigma;
-        for (int z = -t.kz; z <= t.kz; ++z) {
-            double o = z * prm->psf_dz;
-            t.gz[s][z + t.kz] = (float)(sz > 0.0 ? exp(-(o * o) / (2.0 * sz * sz)) : (z == 0));
-        }
-    }
+    // PSF tables: float64 weights rounded to float32
+    make_psf_tab(g, prm, &c->psf);
 
     // scratch
     Tiling tl = make_tiling(prm->max_patch_side);
@@ -627,6 +666,44 @@ int pvr_volume_init(pvr_ctx *c, float *x, const float *y, const pvr_patches *pp,
     CUDA_TRY_T(PVR_K_UPDATE, launch_volume_update_pairs(x, c->acc2, c->nvox, 1.0f, (float)c->prm.conf_eps, 1, 1,
                                   st),
              "volume_init");
+    c->launches += (pp->n > 0) + 1;
+    return PVR_OK;
+}
+
+int pvr_patch_metrics(pvr_ctx *c, const float *y, const float *sim, const uint8_t *valid,
+                      const pvr_patches *pp, int32_t w, double *out, float *map, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    int ms;
+    int rc = check_patches(c, pp, &ms);
+    if (rc) return rc;
+    REQUIRE(w >= 0 && w <= 16, "window half-width must be 0..16");
+    REQUIRE(pp->n == 0 || (y && sim && valid && out), "NULL argument");
+    CUDA_TRY(launch_patch_metrics(y, sim, valid, pp->desc, pp->n, w, out, map, (cudaStream_t)stream),
+             "patch_metrics");
+    c->launches += pp->n > 0;
+    return PVR_OK;
+}
+
+int pvr_rigidity_map(pvr_ctx *c, const pvr_patches *pp, const double *poses, const float *p,
+                     const float *pbar, float *out, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    int ms;
+    int rc = check_patches(c, pp, &ms);
+    if (rc) return rc;
+    REQUIRE(out && (pp->n == 0 || (poses && p && pbar)), "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemsetAsync(c->acc2, 0, (size_t)c->nvox * sizeof(float2), st), "clear");
+    if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
+    Tiling tl = make_tiling(ms);
+    CUDA_TRY_T(PVR_K_ADJOINT, launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix,
+                                             pp->n, p, nullptr, nullptr, (float *)c->acc2, nullptr, 1, st,
+                                             nullptr, pbar),
+               "adjoint");
+    CUDA_TRY_T(PVR_K_UPDATE, launch_volume_update_pairs(out, c->acc2, c->nvox, 1.0f, (float)c->prm.conf_eps, 1, 1,
+                                                        st),
+               "rigidity");
     c->launches += (pp->n > 0) + 1;
     return PVR_OK;
 }

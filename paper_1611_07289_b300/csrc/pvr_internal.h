@@ -31,6 +31,10 @@ struct PsfTab {
     float gz[PVR_MAX_STACKS][2 * PVR_MAX_KZ + 1];
 };
 
+// PSF tables of a geometry and parameter set (Gaussian or Taylor-sinc
+// in-plane profile, Gaussian slice profile).
+void make_psf_tab(const pvr_geometry *g, const pvr_params *prm, PsfTab *tab);
+
 // Patch-tile decomposition shared by the per-patch kernels: tile side T
 // pixels, tiles_x * tiles_y tiles per patch (the largest patch's count);
 // block b works on patch b / tpp, tile b % tpp.
@@ -65,10 +69,12 @@ cudaError_t launch_simulate(const DevGeom *g, const PsfTab &psf, const Tiling &t
 cudaError_t launch_build_quad(const float *x, float4 *quad, int nx, int ny, int nz, cudaStream_t st);
 
 // pair = 1: addon points to interleaved (addon, conf) float2 pairs, conf unused.
+// patch_weight (float per patch, may be null) multiplies r, not w.
 cudaError_t launch_adjoint(const PsfTab &psf, const Tiling &tl, int nx, int ny, int nz,
                            const int32_t *desc, const int32_t *fix, int n, const float *r,
                            const float *w, const uint8_t *patch_mask, float *addon, float *conf,
-                           int pair, cudaStream_t st, const WorkQueue *wq = nullptr);
+                           int pair, cudaStream_t st, const WorkQueue *wq = nullptr,
+                           const float *patch_weight = nullptr);
 
 // Weighted SIRT step on interleaved (addon, conf) pairs; optionally clears them.
 cudaError_t launch_volume_update_pairs(float *x, float2 *acc, int64_t nvox, float alpha,
@@ -123,6 +129,9 @@ cudaError_t launch_reg_finish(const double *best, const double *nbest, int n, do
 
 cudaError_t launch_patches_gather(const DevGeom *g, const float *stacks, const int32_t *desc,
                                   int n, int64_t n_pix, int32_t *err, float *y, cudaStream_t st);
+
+cudaError_t launch_patch_metrics(const float *y, const float *sim, const uint8_t *valid, const int32_t *desc,
+                                 int n, int w, double *out, float *map, cudaStream_t st);
 
 cudaError_t launch_metrics(const float *ref, const float *img, const uint8_t *mask, int64_t n,
                            double *scratch, double *out, cudaStream_t st);

@@ -109,21 +109,9 @@ extern "C" PVR_API int pvr_simulate_noalloc(const pvr_geometry *geom, const pvr_
     }
     memcpy(hg.w2v, g->world_to_voxel, 12 * sizeof(double));
     hg.dz = prm->psf_dz;
+    if (prm->psf_kind != PVR_PSF_GAUSSIAN && prm->psf_kind != PVR_PSF_TAYLOR_SINC) return PVR_ERR_INVALID_ARG;
     PsfTab t;
-    memset(&t, 0, sizeof t);
-    t.kxy = prm->psf_kxy;
-    t.kz = prm->psf_kz;
-    const double to_sigma = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
-    double sxy = prm->psf_fwhm_xy * to_sigma;
-    for (int d = -t.kxy; d <= t.kxy; ++d)
-        t.gxy[d + t.kxy] = (float)(sxy > 0.0 ? exp(-(double)(d * d) / (2.0 * sxy * sxy)) : (d == 0));
-    for (int s = 0; s < g->n_stacks; ++s) {
-        double sz = g->thickness[s] * to_sigma;
-        for (int z = -t.kz; z <= t.kz; ++z) {
-            double o = z * prm->psf_dz;
-            t.gz[s][z + t.kz] = (float)(sz > 0.0 ? exp(-(o * o) / (2.0 * sz * sz)) : (z == 0));
-        }
-    }
+    make_psf_tab(g, prm, &t);
 
     cudaStream_t st = (cudaStream_t)stream;
     DevGeom *d_geom = reinterpret_cast<DevGeom *>(base);

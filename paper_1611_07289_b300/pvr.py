@@ -49,7 +49,7 @@ class Params(C.Structure):
                 ("reg_delta_min", C.c_double), ("reg_grow", C.c_double),
                 ("reg_fixed_step", C.c_int32), ("reg_min_valid", C.c_int32), ("n_sr", C.c_int32),
                 ("max_patches", C.c_int32), ("max_pixels", C.c_int64),
-                ("max_patch_side", C.c_int32)]
+                ("max_patch_side", C.c_int32), ("psf_kind", C.c_int32), ("psf_sinc_eps", C.c_double)]
 
 
 class Patches(C.Structure):
@@ -79,6 +79,8 @@ _SIGS = {
     "pvr_volume_init": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, _VP]),
     "pvr_ncc_grad": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, _VP, _VP, _VP]),
     "pvr_pose_grad": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, _VP, _VP]),
+    "pvr_rigidity_map": (C.c_int, [_VP, C.POINTER(Patches), _VP, _VP, _VP, _VP, _VP]),
+    "pvr_patch_metrics": (C.c_int, [_VP, _VP, _VP, _VP, C.POINTER(Patches), C.c_int32, _VP, _VP, _VP]),
     "pvr_plan": (C.c_int, [_VP, C.POINTER(Patches), _VP, _VP, _VP, C.c_int32, C.c_int32, _VP]),
     "pvr_plan_info": (C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pvr_plan_clear": (C.c_int, [_VP]),
@@ -318,6 +320,23 @@ class Context:
         self._chk(lib.pvr_ncc_grad(self.h, _ptr(x), _ptr(y), C.byref(pt.c), _ptr(poses), _ptr(ncc),
                                    _ptr(grad), _stream(stream)))
         return ncc, grad
+
+    def pvr_patch_metrics(self, y, sim, valid, pt: PatchTable, w=3, want_map=True, stream=None):
+        """Per-patch {PSNR, CC, SSIM, DSSIM, mean local SSIM} (float64 [n, 5])
+        and the local DSSIM heat map (float32 [n_pix] or None)."""
+        out = torch.empty((pt.n, 5), dtype=torch.float64, device=y.device)
+        m = torch.empty(pt.n_pix, dtype=torch.float32, device=y.device) if want_map else None
+        self._chk(lib.pvr_patch_metrics(self.h, _ptr(y), _ptr(sim), _ptr(valid), C.byref(pt.c), int(w), _ptr(out),
+                                        _ptr(m), _stream(stream)))
+        return out, m
+
+    def pvr_rigidity_map(self, pt: PatchTable, poses, p, pbar, out=None, stream=None):
+        """A^T(p * p-bar) / A^T 1: the rigidity / data-consistency volume."""
+        if out is None:
+            out = torch.empty(self.vol_shape, dtype=torch.float32, device=poses.device)
+        self._chk(lib.pvr_rigidity_map(self.h, C.byref(pt.c), _ptr(poses), _ptr(p), _ptr(pbar), _ptr(out),
+                                       _stream(stream)))
+        return out
 
     def pvr_pose_grad(self, x, r, pt: PatchTable, poses, grad=None, stream=None):
         """d (sum_pix r * sim) / d pose per patch (float64 [n, 6])."""

@@ -73,6 +73,40 @@ def test_simulate_matches_oracle(pvr, case, kxy, kz):
 
 
 @pytest.mark.parametrize("case", ["uneven", "tiled"])
+def test_taylor_sinc_psf_matches_oracle(pvr, case):
+    """In-plane sinc PSF from its Taylor series (Sec. II).  Its weights have
+    both signs, so the in-volume weight sum decides validity through a sum
+    that can cancel: masks must agree wherever that sum is not within
+    float32 rounding of zero."""
+    geom, desc, npix, poses, rng = CASES[case]()
+    x = rng.uniform(0, 1000, geom.n_vox).astype(np.float32)
+    ctx = pvr.Context(geom, pvr.default_params(psf_kxy=3, psf_kz=3, psf_dz=0.8, psf_fwhm_xy=2.0,
+                                               psf_kind=1, max_patches=4096, max_pixels=1 << 22,
+                                               max_patch_side=256))
+    pt = pvr.PatchTable.from_numpy(desc, npix)
+    sim, valid = ctx.pvr_simulate(_t(x), pt, _t(poses))
+    G, ps = O.geom(geom), O.psf(2.0, 3, 3, 0.8, kind=1)
+    fix = O.pose_fixed(G, ps, desc, poses)
+    rs, rv, den = O.simulate(G, ps, x, desc, fix, npix)
+    sim, valid = sim.cpu().numpy(), valid.cpu().numpy()
+    # no in-volume sample: the sum is exactly zero on both sides
+    sure = (den == 0.0) | (np.abs(den) > 1e-5 * np.abs(den).max())
+    assert np.array_equal(valid[sure], rv[sure]) and (~sure).sum() <= npix // 1000
+    # s = num / den: a weight sum that cancels amplifies the float32 rounding
+    # of the weights and samples by sum|g| / |den|; compare the values where
+    # that factor is below 20 (the interior and most of the border)
+    well = (valid == 1) & (rv == 1) & (np.abs(den) > 0.05 * np.abs(den).max())
+    assert well.sum() > 0.5 * (rv == 1).sum()
+    assert rel_l2(sim[well], rs[well]) < 1e-5
+    # the adjoint divides by the same weight sums: the same well-conditioned pixels
+    r = rng.normal(0, 50, npix).astype(np.float32) * well
+    w = well.astype(np.float32)
+    a, c = ctx.pvr_adjoint(pt, _t(poses), _t(r), _t(w))
+    ra, rc = O.adjoint(G, ps, desc, fix, r=r.astype(np.float64), w=w.astype(np.float64))
+    assert rel_l2(a.cpu().numpy(), ra) < 1e-5 and rel_l2(c.cpu().numpy(), rc) < 1e-5
+
+
+@pytest.mark.parametrize("case", ["uneven", "tiled"])
 def test_adjoint_matches_oracle(pvr, case):
     geom, desc, npix, poses, rng = CASES[case]()
     r = rng.normal(0, 50, npix).astype(np.float32)

@@ -256,3 +256,31 @@ def test_metrics_closed_forms():
     # SSIM drops below 1 for a noisy copy and DSSIM = (1 - SSIM) / 2
     n = O.metrics(ref, ref + rng.normal(0, 100, ref.size))
     assert 0 < n["ssim"] < 1 and abs(n["dssim"] - (1 - n["ssim"]) / 2) < 1e-15
+
+
+def test_patch_metrics_and_local_ssim_map():
+    """Identical patches: SSIM 1 everywhere, DSSIM 0.  Local SSIM of interior
+    pixels equals the box-window formula built from scipy's uniform_filter
+    (an independent construction of the window sums)."""
+    from scipy.ndimage import uniform_filter
+    rng = np.random.default_rng(21)
+    desc = np.array([[0, 0, 0, 0, 20, 16, 0, 0], [0, 1, 0, 0, 9, 7, 320, 0]], dtype=np.int32)
+    npix = 320 + 63
+    y = rng.uniform(100, 900, npix).astype(np.float32)
+    valid = np.ones(npix, np.uint8)
+    out, m = O.patch_metrics(y, y, valid, desc, 3)
+    assert np.allclose(out[:, 2], 1.0) and np.allclose(out[:, 4], 1.0) and np.all(m == 0.0)
+    s = (y + rng.normal(0, 40, npix)).astype(np.float32)
+    out, m = O.patch_metrics(y, s, valid, desc, 3)
+    ref_g = O.metrics(y[:320], s[:320])
+    assert abs(out[0, 0] - ref_g["psnr"]) < 1e-9 and abs(out[0, 2] - ref_g["ssim"]) < 1e-12
+    a = y[:320].reshape(16, 20).astype(np.float64)
+    b = s[:320].reshape(16, 20).astype(np.float64)
+    f = lambda v: uniform_filter(v, size=7, mode="constant")
+    ma, mb = f(a), f(b)
+    va, vb, cab = f(a * a) - ma * ma, f(b * b) - mb * mb, f(a * b) - ma * mb
+    L = a.max() - a.min()
+    c1, c2 = (0.01 * L) ** 2, (0.03 * L) ** 2
+    ss = ((2 * ma * mb + c1) * (2 * cab + c2)) / ((ma * ma + mb * mb + c1) * (va + vb + c2))
+    inner = (slice(3, 13), slice(3, 17))
+    assert np.allclose(m[:320].reshape(16, 20)[inner], (1 - ss[inner]) / 2, rtol=1e-9, atol=1e-12)

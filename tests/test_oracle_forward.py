@@ -309,6 +309,30 @@ def test_multi_size_patch_table_enumeration_and_rejection():
     assert np.array_equal(d3, d4) and n3 == n4
 
 
+def test_taylor_sinc_psf_table():
+    """kind 1: the in-plane weights are sinc(1.2067 d / FWHM) (numpy's sinc),
+    half of the peak at d = FWHM / 2, the through-plane profile unchanged;
+    the forward model still maps a constant volume to constant patches."""
+    rng = np.random.default_rng(11)
+    geom = synth.random_geometry(rng, n=12, n_stacks=2, W=10, H=9, K=3, pix=0.7)
+    G = O.geom(geom)
+    for fwhm in (1.2, 2.5):
+        ps = O.psf(fwhm, 3, 2, 0.8, kind=1)
+        gxy, gz = O.psf_table(G, ps, 0)
+        d = np.arange(-3, 4)
+        assert np.allclose(gxy, np.sinc(1.2067091288 * d / fwhm), rtol=1e-11, atol=1e-14)
+        g0xy, g0z = O.psf_table(G, O.psf(fwhm, 3, 2, 0.8), 0)
+        assert np.array_equal(gz, g0z)
+    ps = O.psf(2.5, 3, 2, 0.8, kind=1)
+    gh, _ = O.psf_table(G, O.psf(2.0, 1, 0, 0.8, kind=1), 0)
+    assert abs(gh[2] - 0.5) < 1e-9          # half maximum one pixel out when FWHM = 2 px
+    desc, npix = synth.all_patches(geom, 4, 3)
+    poses = synth.random_poses(rng, desc.shape[0], rot=10.0, trans=1.0)
+    fix = O.pose_fixed(G, ps, desc, poses)
+    sim, valid, _ = O.simulate(G, ps, np.full(geom.n_vox, 7.0, np.float32), desc, fix, npix)
+    assert valid.sum() > 0 and np.allclose(sim[valid == 1], 7.0, rtol=1e-12)
+
+
 def test_samples_on_the_last_voxel_plane_read_that_plane():
     """A sample exactly on the upper boundary (index N-1) is inside and takes
     the value of that plane."""
