@@ -415,6 +415,41 @@ PVR_API int pvr_graph_capture(pvr_ctx *ctx, float *x, const float *y, const pvr_
 /* Replay the captured iteration on `stream`. */
 PVR_API int pvr_graph_launch(pvr_ctx *ctx, void *stream);
 
+/* ---- learned pose proposal (a small CNN; extends the paper's method) ----
+ * The network reads, per 64x64 patch, the acquired pixels y and the pixels
+ * simulated at the current pose s (each normalised to zero mean and unit
+ * deviation over the valid pixels) and predicts the 6 rigid parameters of
+ * the correction; six 3x3 bf16 convolutions (tensor cores, float32
+ * accumulation), global mean pooling, a float32 linear head.  Training is
+ * mean squared error against given targets with Adam. */
+typedef struct pvr_net pvr_net;
+
+/* Allocates the network, its Adam state and activations for batches of up to
+ * batch_max (1..4096) patches; weights initialised from seed. */
+PVR_API int pvr_net_create(pvr_net **out, int32_t batch_max, uint64_t seed);
+PVR_API int pvr_net_destroy(pvr_net *net);
+/* Number of float32 parameters (conv weights [co][ky][kx][ci] and bias per
+ * layer, then the head [6][64] and bias). */
+PVR_API int64_t pvr_net_param_count(const pvr_net *net);
+/* Copy the float32 parameters to / from HOST memory (set resets Adam). */
+PVR_API int pvr_net_get_params(pvr_net *net, float *host_out);
+PVR_API int pvr_net_set_params(pvr_net *net, const float *host_in);
+/* Gradients of the last pvr_net_train_step, to HOST memory. */
+PVR_API int pvr_net_get_grads(pvr_net *net, float *host_out);
+/* Predictions for patches first .. first+count-1 of the table (count <=
+ * batch_max; the table's max_side must be 64 and rows that are not 64x64
+ * read as empty).  y, s: float32 [n_pix]; valid: uint8 [n_pix] (pixels of s
+ * that are valid); out: device float32 [count][6]. */
+PVR_API int pvr_net_forward(pvr_net *net, const float *y, const float *s, const uint8_t *valid,
+                            const pvr_patches *patches, int32_t first, int32_t count, float *out,
+                            void *stream);
+/* One Adam step (learning rate lr) on the loss mean over the batch of
+ * sum_j (out_j - target_j)^2; target: device float32 [count][6]; loss (device
+ * float32 [1], may be NULL) receives the batch loss before the step. */
+PVR_API int pvr_net_train_step(pvr_net *net, const float *y, const float *s, const uint8_t *valid,
+                               const pvr_patches *patches, int32_t first, int32_t count,
+                               const float *target, float lr, float *loss, void *stream);
+
 /* Evaluation metrics (Sec. IV-A) of img against ref over n values (mask
  * NULL: all): out float64 device [5] = {PSNR = 10 log10(I_max^2/MSE),
  * CC (Eq. cross_corr), SSIM (single global window, Eq. SSIM with the

@@ -80,6 +80,15 @@ _SIGS = {
     "pvr_ncc_grad": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, _VP, _VP, _VP]),
     "pvr_pose_grad": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, _VP, _VP]),
     "pvr_rigidity_map": (C.c_int, [_VP, C.POINTER(Patches), _VP, _VP, _VP, _VP, _VP]),
+    "pvr_net_create": (C.c_int, [C.POINTER(_VP), C.c_int32, C.c_uint64]),
+    "pvr_net_destroy": (C.c_int, [_VP]),
+    "pvr_net_param_count": (C.c_int64, [_VP]),
+    "pvr_net_get_params": (C.c_int, [_VP, _VP]),
+    "pvr_net_set_params": (C.c_int, [_VP, _VP]),
+    "pvr_net_get_grads": (C.c_int, [_VP, _VP]),
+    "pvr_net_forward": (C.c_int, [_VP, _VP, _VP, _VP, C.POINTER(Patches), C.c_int32, C.c_int32, _VP, _VP]),
+    "pvr_net_train_step": (C.c_int, [_VP, _VP, _VP, _VP, C.POINTER(Patches), C.c_int32, C.c_int32, _VP,
+                                     C.c_float, _VP, _VP]),
     "pvr_patch_metrics": (C.c_int, [_VP, _VP, _VP, _VP, C.POINTER(Patches), C.c_int32, _VP, _VP, _VP]),
     "pvr_plan": (C.c_int, [_VP, C.POINTER(Patches), _VP, _VP, _VP, C.c_int32, C.c_int32, _VP]),
     "pvr_plan_info": (C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
@@ -400,6 +409,59 @@ class Context:
         self._chk(lib.pvr_metrics(self.h, _ptr(ref), _ptr(img), _ptr(mask), int(ref.numel()), _ptr(out),
                                   _stream(stream)))
         return out
+
+
+class Net:
+    """pvr_net: the learned pose proposal CNN (float32 master weights,
+    bfloat16 tensor-core convolutions)."""
+
+    def __init__(self, batch_max=256, seed=0):
+        h = C.c_void_p()
+        rc = lib.pvr_net_create(C.byref(h), int(batch_max), int(seed))
+        if rc != 0:
+            raise PvrError(rc, "pvr_net_create failed")
+        self.h, self.batch_max = h, int(batch_max)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib.pvr_net_destroy(self.h)
+            self.h = None
+
+    def _chk(self, rc, what):
+        if rc != 0:
+            raise PvrError(rc, what)
+
+    def param_count(self):
+        return int(lib.pvr_net_param_count(self.h))
+
+    def get_params(self):
+        a = np.zeros(self.param_count(), dtype=np.float32)
+        self._chk(lib.pvr_net_get_params(self.h, a.ctypes.data), "pvr_net_get_params")
+        return a
+
+    def set_params(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        assert a.size == self.param_count()
+        self._chk(lib.pvr_net_set_params(self.h, a.ctypes.data), "pvr_net_set_params")
+
+    def get_grads(self):
+        a = np.zeros(self.param_count(), dtype=np.float32)
+        self._chk(lib.pvr_net_get_grads(self.h, a.ctypes.data), "pvr_net_get_grads")
+        return a
+
+    def forward(self, y, s, valid, pt: PatchTable, first=0, count=None, out=None, stream=None):
+        count = pt.n - first if count is None else count
+        if out is None:
+            out = torch.empty((count, 6), dtype=torch.float32, device=y.device)
+        self._chk(lib.pvr_net_forward(self.h, _ptr(y), _ptr(s), _ptr(valid), C.byref(pt.c), int(first), int(count),
+                                      _ptr(out), _stream(stream)), "pvr_net_forward")
+        return out
+
+    def train_step(self, y, s, valid, pt: PatchTable, first, count, target, lr, loss=None, stream=None):
+        self._chk(lib.pvr_net_train_step(self.h, _ptr(y), _ptr(s), _ptr(valid), C.byref(pt.c), int(first),
+                                         int(count), _ptr(target), float(lr), _ptr(loss), _stream(stream)),
+                  "pvr_net_train_step")
+        return loss
 
 
 def pvr_simulate_noalloc(geom, params: Params, x, pt: PatchTable, poses, sim, valid, stream=None):
