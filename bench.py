@@ -537,6 +537,66 @@ def run_uneven(args, ws, rank, local):
     }
 
 
+def run_proposal(args, ws, rank, local):
+    """Learned pose proposal on the uterus workload: train the CNN on pairs
+    the forward model makes from random uterus phantoms, then reconstruct
+    from the acquired positions with and without the proposal (+ NCC
+    fallback) before registration, and compare PSNR against wall time."""
+    import torch
+    from paper_1611_07289_b300 import proposal, pvr
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    cfg, ctx, pt, y, x0, poses0, gen_s, build_s = _setup(dev, args.slices)
+    gt = torch.as_tensor(cfg["gt"], device=dev)
+    net = pvr.Net(batch_max=256, seed=7)
+    net.reserve(pt.n, pt.n_pix)
+    vols = proposal.phantom_volumes(cfg["geom"], range(100, 108), dev)
+    losses, train_s = proposal.train(net, ctx, vols, pt, args.pairs, batch=256, lr=2e-3,
+                                     log=lambda m: print(m, file=sys.stderr))
+    held = proposal.phantom_volumes(cfg["geom"], [200], dev)[0]
+    before, after, taken = proposal.evaluate_proposal(net, ctx, held, pt, 2048)
+    prm = ctx.params
+    prm.reg_evals, prm.n_sr = 10, 2
+    rctx = pvr.Context(cfg["geom"], prm)
+    rctx.pvr_plan(pt, x0, y, poses0)
+
+    def run(use_net):
+        x, poses = x0.clone(), poses0.clone()
+        state, mask = pvr.new_state(dev), torch.ones(pt.n, dtype=torch.uint8, device=dev)
+        curve = [(0.0, float(rctx.pvr_metrics(gt, x)[0]))]
+        t = 0.0
+        for it in range(args.outer):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if use_net and it < args.propose_iters:
+                net.propose(rctx, x, y, pt, poses, proposal.SCALE)
+            rctx.pvr_reconstruct_iter(x, y, pt, poses, state, mask)
+            torch.cuda.synchronize()
+            t += time.perf_counter() - t0
+            curve.append((t, float(rctx.pvr_metrics(gt, x)[0])))
+        return curve
+
+    run(False)                      # warm-up of every kernel
+    plain = run(False)
+    learned = run(True)
+    best_plain = max(p for _, p in plain)
+    target = best_plain - 0.1
+    reach = lambda c: next((tt for tt, p in c if p >= target), None)
+    return {
+        "metric": "time to the plain method's best PSNR (within 0.1 dB), learned proposal vs plain",
+        "value": reach(learned), "unit": "s", "higher_is_better": False, "n_gpus": 1,
+        "plain_s_to_psnr": reach(plain), "plain_best_psnr_db": best_plain,
+        "learned_best_psnr_db": max(p for _, p in learned),
+        "curves": {"plain": plain, "learned": learned},
+        "training": {"pairs": args.pairs, "batch": 256, "seconds": train_s, "loss_first_last": [losses[0], losses[-1]],
+                     "phantoms": 8, "held_out_mean_abs_pose_error_before": before.tolist(),
+                     "held_out_mean_abs_pose_error_after": after.tolist(), "held_out_taken_fraction": taken},
+        "config": {"workload": WORKLOAD, "n_patches": pt.n, "outer_iterations": args.outer,
+                   "reg_evals": 10, "n_sr": 2, "proposal_iterations": args.propose_iters},
+        "data": "synthetic", "dtype": "bf16 network / f32 reconstruction",
+    }
+
+
 def run_reference(args, ws, rank):
     """The FP64 oracle as the reference arm: rank 0 only, on the host cores."""
     if rank != 0:
@@ -571,8 +631,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--slices", type=int, default=96,
                     help="slices per stack (96 = the benchmark workload; fewer for profiling)")
-    ap.add_argument("--workload", choices=["uterus", "uneven"], default="uterus",
-                    help="uneven: patch sides 32..128 per slice (batched-launch comparison, 1 GPU)")
+    ap.add_argument("--workload", choices=["uterus", "uneven", "proposal"], default="uterus",
+                    help="uneven: patch sides 32..128 per slice (batched-launch comparison, 1 GPU); "
+                         "proposal: learned pose proposal, time to PSNR against plain registration")
+    ap.add_argument("--pairs", type=int, default=200000, help="training pairs (proposal workload)")
+    ap.add_argument("--outer", type=int, default=8, help="outer iterations (proposal workload)")
+    ap.add_argument("--propose-iters", type=int, default=2, help="iterations that start with the proposal")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     ws, rank, local = _dist()
@@ -581,6 +645,8 @@ def main():
         res = run_reference(args, ws, rank)
     elif args.workload == "uneven":
         res = run_uneven(args, ws, rank, local) if rank == 0 else None
+    elif args.workload == "proposal":
+        res = run_proposal(args, ws, rank, local) if rank == 0 else None
     else:
         if ws > 1:
             import torch.distributed as dist

@@ -450,6 +450,21 @@ PVR_API int pvr_net_train_step(pvr_net *net, const float *y, const float *s, con
                                const pvr_patches *patches, int32_t first, int32_t count,
                                const float *target, float lr, float *loss, void *stream);
 
+/* Scratch of pvr_pose_propose for tables of up to max_patches patches and
+ * max_pixels pixels (allocates; call once before proposing). */
+PVR_API int pvr_net_reserve(pvr_net *net, int32_t max_patches, int64_t max_pixels);
+
+/* Learned pose proposal with fallback: simulate every 64x64 patch at its
+ * pose, let the network predict a correction (output k times scale[k], a
+ * HOST double[6], in pose units: mm, degrees), evaluate NCC at the plain and
+ * at the corrected pose, and keep the corrected pose only where NCC rises.
+ * poses: float64 [n][6] in/out; accepted (device int32 [n], may be NULL):
+ * 1 where the proposal was taken.  Run NCC registration (pvr_register /
+ * pvr_reconstruct_iter) afterwards to refine. */
+PVR_API int pvr_pose_propose(pvr_ctx *ctx, pvr_net *net, const float *x, const float *y,
+                             const pvr_patches *patches, const double *scale, double *poses,
+                             int32_t *accepted, void *stream);
+
 /* Evaluation metrics (Sec. IV-A) of img against ref over n values (mask
  * NULL: all): out float64 device [5] = {PSNR = 10 log10(I_max^2/MSE),
  * CC (Eq. cross_corr), SSIM (single global window, Eq. SSIM with the

@@ -406,6 +406,32 @@ __global__ void k_to_bf16(const float *__restrict__ a, __nv_bfloat16 *__restrict
         b[i] = __float2bfloat16(a[i]);
 }
 
+// trial[p][k] = poses[p][k] + scale[k] * out[p][k] (network correction in
+// pose units)
+__global__ void k_propose_trial(const double *__restrict__ poses, const float *__restrict__ out, int n,
+                                double s0, double s1, double s2, double s3, double s4, double s5,
+                                double *__restrict__ trial)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 6 * n) return;
+    const int k = i % 6;
+    const double sc = k == 0 ? s0 : k == 1 ? s1 : k == 2 ? s2 : k == 3 ? s3 : k == 4 ? s4 : s5;
+    trial[i] = poses[i] + sc * (double)out[i];
+}
+
+// Keep the proposal where it raises NCC, else the plain pose.
+__global__ void k_propose_select(const double *__restrict__ ncc0, const double *__restrict__ ncc1,
+                                 const double *__restrict__ trial, int n, double *__restrict__ poses,
+                                 int32_t *__restrict__ accepted)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const bool take = ncc1[p] > ncc0[p];
+    if (take)
+        for (int k = 0; k < 6; ++k) poses[6 * (size_t)p + k] = trial[6 * (size_t)p + k];
+    if (accepted) accepted[p] = take ? 1 : 0;
+}
+
 template <class LA, class LB, class EP>
 cudaError_t gemm(LA la, LB lb, EP ep, long long M, long long N, int K, int split, cudaStream_t st)
 {
@@ -479,6 +505,23 @@ cudaError_t cnn_adam(float *w, const float *gw, float *m1, float *m2, long long 
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
     k_adam<<<256, 256, 0, st>>>(w, gw, m1, m2, n, lr, b1, b2, 1e-8f, c1, c2, wb);
+    return cudaGetLastError();
+}
+
+cudaError_t cnn_propose_trial(const double *poses, const float *out, int n, const double scale[6], double *trial,
+                              cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_propose_trial<<<(6 * n + 255) / 256, 256, 0, st>>>(poses, out, n, scale[0], scale[1], scale[2], scale[3],
+                                                          scale[4], scale[5], trial);
+    return cudaGetLastError();
+}
+
+cudaError_t cnn_propose_select(const double *ncc0, const double *ncc1, const double *trial, int n, double *poses,
+                               int32_t *accepted, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_propose_select<<<(n + 255) / 256, 256, 0, st>>>(ncc0, ncc1, trial, n, poses, accepted);
     return cudaGetLastError();
 }
 

@@ -32,6 +32,10 @@ cudaError_t cnn_head_backward(const float *out, const float *target, int B, int 
 cudaError_t cnn_adam(float *w, const float *gw, float *m1, float *m2, long long n, float lr, int step,
                      __nv_bfloat16 *wb, cudaStream_t st);
 cudaError_t cnn_to_bf16(const float *a, __nv_bfloat16 *b, long long n, cudaStream_t st);
+cudaError_t cnn_propose_trial(const double *poses, const float *out, int n, const double scale[6], double *trial,
+                              cudaStream_t st);
+cudaError_t cnn_propose_select(const double *ncc0, const double *ncc1, const double *trial, int n, double *poses,
+                               int32_t *accepted, cudaStream_t st);
 }  // namespace pvr
 
 using namespace pvr;
@@ -59,13 +63,19 @@ struct pvr_net {
     __nv_bfloat16 *img = nullptr, *act[kNL] = {}, *gact[kNL] = {};
     float *pooled = nullptr, *out = nullptr, *loss = nullptr;
     int step = 0;
+    // scratch of pvr_pose_propose (pvr_net_reserve)
+    int64_t res_patches = 0, res_pixels = 0;
+    float *sim = nullptr, *props = nullptr;
+    uint8_t *valid = nullptr;
+    double *trial = nullptr, *ncc = nullptr;
 };
 
 namespace {
 
 void net_free(pvr_net *n)
 {
-    void *p[] = {n->w, n->gw, n->m1, n->m2, n->wb, n->img, n->pooled, n->out, n->loss};
+    void *p[] = {n->w, n->gw, n->m1, n->m2, n->wb, n->img, n->pooled, n->out, n->loss,
+                 n->sim, n->props, n->valid, n->trial, n->ncc};
     for (void *q : p)
         if (q) cudaFree(q);
     for (int l = 0; l < kNL; ++l) {
@@ -238,6 +248,52 @@ PVR_API int pvr_net_train_step(pvr_net *n, const float *y, const float *s, const
     ++n->step;
     if (cnn_adam(n->w, n->gw, n->m1, n->m2, n->n_params, lr, n->step, n->wb, st) != cudaSuccess) return PVR_ERR_CUDA;
     if (loss && cudaMemcpyAsync(loss, n->loss, sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return PVR_ERR_CUDA;
+    return PVR_OK;
+}
+
+PVR_API int pvr_net_reserve(pvr_net *n, int32_t max_patches, int64_t max_pixels)
+{
+    if (!n || max_patches < 1 || max_pixels < 1) return PVR_ERR_INVALID_ARG;
+    void *p[] = {n->sim, n->props, n->valid, n->trial, n->ncc};
+    for (void *q : p)
+        if (q) cudaFree(q);
+    n->sim = n->props = nullptr;
+    n->valid = nullptr;
+    n->trial = n->ncc = nullptr;
+    n->res_patches = n->res_pixels = 0;
+    cudaError_t e = cudaMalloc((void **)&n->sim, (size_t)max_pixels * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&n->valid, (size_t)max_pixels);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&n->props, (size_t)max_patches * kOut * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&n->trial, (size_t)max_patches * 6 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&n->ncc, (size_t)max_patches * 2 * sizeof(double));
+    if (e != cudaSuccess) return PVR_ERR_CUDA;
+    n->res_patches = max_patches;
+    n->res_pixels = max_pixels;
+    return PVR_OK;
+}
+
+PVR_API int pvr_pose_propose(pvr_ctx *ctx, pvr_net *n, const float *x, const float *y, const pvr_patches *pp,
+                             const double *scale, double *poses, int32_t *accepted, void *stream)
+{
+    if (!ctx || !n || !pp || !scale) return PVR_ERR_INVALID_ARG;
+    if (pp->n == 0) return PVR_OK;
+    if (!x || !y || !poses || pp->max_side != kSide) return PVR_ERR_INVALID_ARG;
+    if (pp->n > n->res_patches || pp->n_pix > n->res_pixels) return PVR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    // the patches simulated at the current poses, the network's corrections
+    if ((rc = pvr_simulate(ctx, x, pp, poses, n->sim, n->valid, stream))) return rc;
+    for (int first = 0; first < pp->n; first += n->batch_max) {
+        const int cnt = pp->n - first < n->batch_max ? pp->n - first : n->batch_max;
+        if ((rc = pvr_net_forward(n, y, n->sim, n->valid, pp, first, cnt, n->props + (size_t)first * kOut, stream)))
+            return rc;
+    }
+    if (cnn_propose_trial(poses, n->props, pp->n, scale, n->trial, st) != cudaSuccess) return PVR_ERR_CUDA;
+    // NCC at the plain and at the proposed pose; keep the better
+    if ((rc = pvr_ncc_grad(ctx, x, y, pp, poses, n->ncc, nullptr, stream))) return rc;
+    if ((rc = pvr_ncc_grad(ctx, x, y, pp, n->trial, n->ncc + pp->n, nullptr, stream))) return rc;
+    if (cnn_propose_select(n->ncc, n->ncc + pp->n, n->trial, pp->n, poses, accepted, st) != cudaSuccess)
         return PVR_ERR_CUDA;
     return PVR_OK;
 }

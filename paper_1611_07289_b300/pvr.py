@@ -89,6 +89,8 @@ _SIGS = {
     "pvr_net_forward": (C.c_int, [_VP, _VP, _VP, _VP, C.POINTER(Patches), C.c_int32, C.c_int32, _VP, _VP]),
     "pvr_net_train_step": (C.c_int, [_VP, _VP, _VP, _VP, C.POINTER(Patches), C.c_int32, C.c_int32, _VP,
                                      C.c_float, _VP, _VP]),
+    "pvr_net_reserve": (C.c_int, [_VP, C.c_int32, C.c_int64]),
+    "pvr_pose_propose": (C.c_int, [_VP, _VP, _VP, _VP, C.POINTER(Patches), _VP, _VP, _VP, _VP]),
     "pvr_patch_metrics": (C.c_int, [_VP, _VP, _VP, _VP, C.POINTER(Patches), C.c_int32, _VP, _VP, _VP]),
     "pvr_plan": (C.c_int, [_VP, C.POINTER(Patches), _VP, _VP, _VP, C.c_int32, C.c_int32, _VP]),
     "pvr_plan_info": (C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
@@ -456,6 +458,16 @@ class Net:
         self._chk(lib.pvr_net_forward(self.h, _ptr(y), _ptr(s), _ptr(valid), C.byref(pt.c), int(first), int(count),
                                       _ptr(out), _stream(stream)), "pvr_net_forward")
         return out
+
+    def reserve(self, max_patches, max_pixels):
+        self._chk(lib.pvr_net_reserve(self.h, int(max_patches), int(max_pixels)), "pvr_net_reserve")
+
+    def propose(self, ctx: "Context", x, y, pt: PatchTable, poses, scale, accepted=None, stream=None):
+        """In place on poses: the network's correction where it raises NCC."""
+        sc = (C.c_double * 6)(*[float(v) for v in scale])
+        self._chk(lib.pvr_pose_propose(ctx.h, self.h, _ptr(x), _ptr(y), C.byref(pt.c), sc, _ptr(poses),
+                                       _ptr(accepted), _stream(stream)), "pvr_pose_propose")
+        return poses
 
     def train_step(self, y, s, valid, pt: PatchTable, first, count, target, lr, loss=None, stream=None):
         self._chk(lib.pvr_net_train_step(self.h, _ptr(y), _ptr(s), _ptr(valid), C.byref(pt.c), int(first),

@@ -79,3 +79,29 @@ def test_cnn_training_lowers_the_loss(pvr):
         net.train_step(Y, S, V, pt, 0, B, T, 3e-3, loss)
         losses.append(float(loss))
     assert losses[-1] < 0.3 * losses[0], losses[::10]
+
+
+def test_proposal_keeps_the_better_pose(pvr):
+    """pvr_pose_propose: every output pose is the plain pose or the proposed
+    one, and NCC at the output is never below NCC at the plain pose."""
+    from paper_1611_07289_b300 import proposal, synth
+    cfg = synth.config_tiny(noise=False)
+    geom = cfg["geom"]
+    desc, npix = synth.all_patches(geom, 64, 64)
+    ctx = pvr.Context(geom, pvr.default_params(max_patches=256, max_pixels=1 << 20, max_patch_side=64))
+    pt = pvr.PatchTable.from_numpy(desc, npix)
+    x = torch.as_tensor(cfg["gt"], device="cuda")
+    zeros = torch.zeros((pt.n, 6), dtype=torch.float64, device="cuda")
+    y, _ = ctx.pvr_simulate(x, pt, zeros)
+    rng = np.random.default_rng(5)
+    poses = torch.as_tensor(synth.random_poses(rng, pt.n, rot=6.0, trans=3.0), device="cuda")
+    net = pvr.Net(batch_max=16, seed=9)
+    net.reserve(pt.n, npix)
+    out = poses.clone()
+    acc = torch.zeros(pt.n, dtype=torch.int32, device="cuda")
+    net.propose(ctx, x, y, pt, out, proposal.SCALE, acc)
+    n0, _ = ctx.pvr_ncc_grad(x, y, pt, poses, want_grad=False)
+    n1, _ = ctx.pvr_ncc_grad(x, y, pt, out, want_grad=False)
+    same = torch.all(out == poses, dim=1)
+    assert torch.equal(same, acc == 0)
+    assert torch.all(n1[~same] > n0[~same]) and torch.all(n1[same] == n0[same])
