@@ -26,6 +26,9 @@ workloads here stand in for its whole-uterus scans:
 * ``config_uneven``: the uterus volume and stacks with a patch side drawn
   per slice from {32, 48, 64, 96, 128}, stride half the side (batched
   patches of uneven sizes).
+* ``config_skew``: interleaved motion-free and skewed slices (the skew
+  motion model of the paper's adult-brain experiment) of a nested-ellipsoid
+  phantom, three orthogonal stacks.
 * ``config_diff``: the differentiable-forward-model workload, 128^3 voxels
   of 1 mm with nested ellipsoids, 3 orthogonal stacks of 86 slices of
   128x128 pixels at 1x1x1.5 mm, all square patches 48 / stride 24 (4,128
@@ -396,6 +399,44 @@ def config_uneven(seed=7289, device="cpu", slices=96, size=256, sides=(32, 48, 6
     sa = rng.choice(np.asarray(sides, dtype=np.int32), nk).astype(np.int32)
     cfg.update(name=cfg["name"] + "-uneven", slice_a=sa, slice_stride=(sa // 2).astype(np.int32))
     return cfg
+
+
+def skew_matrix(theta_deg):
+    """The skew (shear) motion of the paper's adult-brain experiment (Sec. IV):
+    ones on the diagonal and S = tan(theta) off the diagonal."""
+    S = math.tan(math.radians(theta_deg))
+    return np.array([[1.0, S, S], [S, 1.0, S], [S, S, 1.0]])
+
+
+def config_skew(theta_deg=5.0, seed=1283, device="cpu", n=96, spacing=1.25, noise=0.0):
+    """Skew-motion workload after the paper's adult-brain study (data not
+    available, a nested-ellipsoid phantom instead): n^3 voxels of `spacing`
+    mm, axial / coronal / sagittal stacks of n x n pixels at spacing x
+    spacing x 2 spacing mm whose slices alternate between the motion-free
+    phantom (even slices) and the phantom skewed by skew_matrix(theta)
+    about its centre (odd slices), as interleaved acquisition would give."""
+    rng = np.random.default_rng(seed)
+    dims = (n, n, n)
+    w2v, v2w = volume_geometry(dims, spacing)
+    K = n // 2
+    axes = [((1, 0, 0), (0, 1, 0), (0, 0, 1)),
+            ((1, 0, 0), (0, 0, 1), (0, 1, 0)),
+            ((0, 1, 0), (0, 0, 1), (1, 0, 0))]
+    p2w = [stack_matrix(u, v, w, n, n, K, spacing, 2 * spacing) for (u, v, w) in axes]
+    geom = Geometry(dims, w2v, v2w, [(n, n, K)] * 3, p2w, [2 * spacing] * 3)
+    ells = phantom_nested(rng, n * spacing)
+    T = skew_matrix(theta_deg)
+    Ti = np.linalg.inv(T)
+
+    def motion(s, k):
+        # the phantom occupies T p in skewed slices; acquisition maps the
+        # scanner point p to the anatomy point T^-1 p
+        return (Ti, np.zeros(3)) if k % 2 else (np.eye(3), np.zeros(3))
+
+    stacks = acquire(ells, geom, motion, rng, noise, device=device)
+    gt = ground_truth(ells, geom, device=device)
+    return dict(name=f"skew-{theta_deg}deg", geom=geom, stacks=stacks, gt=gt.numpy(), ellipsoids=ells,
+                skew=T, a=32, stride=16, fg_frac=0.01, keep_frac=0.5, fwhm_xy=1.2, dz=spacing)
 
 
 def config_diff(seed=3, device="cpu"):

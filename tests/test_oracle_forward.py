@@ -350,3 +350,16 @@ def test_samples_on_the_last_voxel_plane_read_that_plane():
     sim, valid, _ = O.simulate(G, ps, x, desc, fix, 24)
     assert np.all(valid == 1)
     assert np.array_equal(sim, vol[n - 1, 12:16, 10:16].reshape(-1).astype(np.float64))
+
+
+def test_skew_motion_workload():
+    """Skew matrix of the adult-brain experiment; with theta = 0 the skewed
+    slices equal the motion-free ones, with theta > 0 only odd slices move."""
+    T = synth.skew_matrix(10.0)
+    S = np.tan(np.radians(10.0))
+    assert np.allclose(T, [[1, S, S], [S, 1, S], [S, S, 1]])
+    c0 = synth.config_skew(theta_deg=0.0, n=24)
+    c1 = synth.config_skew(theta_deg=8.0, n=24)
+    for a, b in zip(c0["stacks"], c1["stacks"]):
+        assert np.array_equal(a[0::2], b[0::2])
+        assert np.abs(a[1::2] - b[1::2]).max() > 1.0
