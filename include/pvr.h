@@ -154,6 +154,9 @@ typedef struct pvr_patches {
     int32_t n;              /* number of patches, 0..max_patches */
     int32_t max_side;       /* largest w or h in the table (0: max_patch_side) */
     int64_t n_pix;          /* pixels: every pix_off + w*h <= n_pix <= max_pixels */
+    const uint8_t *member;  /* device uint8 [n_pix] or NULL: pixels with member 0 lie in
+                               their patch's rectangle but not in the patch (superpixel
+                               patches); they are invalid everywhere */
 } pvr_patches;
 
 typedef struct pvr_ctx pvr_ctx;
@@ -234,6 +237,23 @@ PVR_API int pvr_patches_build_sizes(pvr_ctx *ctx, const float *stacks, const int
                                     const int32_t *slice_stride, double fg_frac, double keep_frac,
                                     int32_t *desc_out, int32_t max_out, int32_t *n_out,
                                     int64_t *n_pix_out, void *stream);
+
+/* Superpixel patch table (Sec. II "Patch Extraction": SLIC superpixels of
+ * initial size a and compactness t, D^2 = d_c^2 + (d_s / a)^2 t^2, dilated by
+ * gamma pixels with a square element).  Every superpixel of every slice
+ * whose dilated bounding box fits min(max_patch_side, 128) becomes a row
+ * {stack, slice, x0, y0, w, h, pix_off, 0} (box of the dilated superpixel)
+ * when at least keep_frac of its member pixels exceed fg_frac * I_max;
+ * member_out (device uint8, capacity max_pixels) receives, per box pixel,
+ * 1 if it belongs to the dilated superpixel: pass it as pvr_patches.member.
+ * Centres start on a grid of max(1, round(W/a)) x max(1, round(H/a)) cells;
+ * n_iter assignment/update rounds (intensity sums exact, see the design
+ * notes).  a >= 2; gamma 0..32; n_iter 1..100.  Allocates and frees its own
+ * scratch; synchronises `stream`; n_out, n_pix_out: HOST pointers. */
+PVR_API int pvr_patches_build_slic(pvr_ctx *ctx, const float *stacks, int32_t a, double compactness,
+                                   int32_t gamma, int32_t n_iter, double fg_frac, double keep_frac,
+                                   int32_t *desc_out, uint8_t *member_out, int32_t max_out,
+                                   int32_t *n_out, int64_t *n_pix_out, void *stream);
 
 /* Copy every patch's pixels out of the packed stacks into y (float32
  * [n_pix], patch after patch, row-major). */

@@ -771,11 +771,12 @@ static int or_reg_sample(const or_geom *g, const float *x, const int64_t *f, con
  * positions: d s / d theta = sum_samples g * grad_trilinear . d q / d theta
  * / den, the normalisation den treated as constant (it changes only where a
  * sample leaves the volume).  exact selects the fixed-point lattice or plain
- * FP64 positions (or_reg_sample).  Returns 0 when the exact lattice is out of
- * range (every pixel invalid). */
+ * FP64 positions (or_reg_sample).  member (indexed like the patch pixels,
+ * may be NULL): pixels with member 0 are not part of the patch.  Returns 0
+ * when the exact lattice is out of range (every pixel invalid). */
 static int or_patch_sim_jac(const or_geom *g, const or_psf *psf, const float *x, const int *d,
-                            const double *th, int n_params, int exact, double *s, uint8_t *ok,
-                            double *J)
+                            const double *th, int n_params, int exact, const uint8_t *member,
+                            double *s, uint8_t *ok, double *J)
 {
     int K = psf->kxy, Kz = psf->kz, w = d[4], h = d[5];
     int64_t f[16];
@@ -815,7 +816,7 @@ static int or_patch_sim_jac(const or_geom *g, const or_psf *psf, const float *x,
                         }
                     }
             size_t o = (size_t)j * w + i;
-            if (dn > 0.0) {
+            if (dn > 0.0 && (!member || member[(size_t)d[6] + o])) {
                 ok[o] = 1;
                 s[o] = num / dn;
                 for (int k = 0; k < n_params; ++k) J[o * n_params + k] = jac[k] / dn;
@@ -830,7 +831,8 @@ static int or_patch_sim_jac(const or_geom *g, const or_psf *psf, const float *x,
  * the patch pixels (offset d[6]).  Returns sum_pix r_pix s_pix over the
  * valid pixels; grad receives n_params values. */
 double or_sim_pose_vjp(const or_geom *g, const or_psf *psf, const float *x, const double *r,
-                       const int *d, const double *th, int n_params, int exact, double *grad)
+                       const int *d, const double *th, int n_params, int exact, const uint8_t *member,
+                       double *grad)
 {
     size_t npx = (size_t)d[4] * d[5], off = (size_t)d[6];
     for (int k = 0; k < n_params; ++k) grad[k] = 0.0;
@@ -838,7 +840,7 @@ double or_sim_pose_vjp(const or_geom *g, const or_psf *psf, const float *x, cons
     double *J = (double *)calloc(npx * (size_t)n_params, sizeof(double));
     uint8_t *ok = (uint8_t *)calloc(npx, 1);
     double val = 0.0;
-    if (or_patch_sim_jac(g, psf, x, d, th, n_params, exact, s, ok, J))
+    if (or_patch_sim_jac(g, psf, x, d, th, n_params, exact, member, s, ok, J))
         for (size_t o = 0; o < npx; ++o)
             if (ok[o]) {
                 val += r[off + o] * s[o];
@@ -859,14 +861,14 @@ double or_sim_pose_vjp(const or_geom *g, const or_psf *psf, const float *x, cons
  * Returns the NCC; grad receives n_params values. */
 double or_ncc_grad(const or_geom *g, const or_psf *psf, const float *x, const float *y,
                    const int *d, const double *th, int n_params, int min_valid, int exact,
-                   double *grad)
+                   const uint8_t *member, double *grad)
 {
     size_t npx = (size_t)d[4] * d[5], off = (size_t)d[6];
     for (int k = 0; k < n_params; ++k) grad[k] = 0.0;
     double *s = (double *)calloc(npx, sizeof(double));
     double *J = (double *)calloc(npx * (size_t)n_params, sizeof(double));
     uint8_t *ok = (uint8_t *)calloc(npx, 1);
-    if (!or_patch_sim_jac(g, psf, x, d, th, n_params, exact, s, ok, J)) {
+    if (!or_patch_sim_jac(g, psf, x, d, th, n_params, exact, member, s, ok, J)) {
         free(s);
         free(J);
         free(ok);
@@ -937,7 +939,7 @@ void or_register(const or_geom *g, const or_psf *psf, const or_reg_params *rp, c
         for (int k = 0; k < np; ++k)
             scale[k] = k < 3 ? 1.0 : (np == 12 ? half_diag : half_diag * (M_PI / 180.0));
         memcpy(best, th, sizeof(double) * np);
-        double nbest = or_ncc_grad(g, psf, x, y, d, best, np, rp->min_valid, 1, gbest);
+        double nbest = or_ncc_grad(g, psf, x, y, d, best, np, rp->min_valid, 1, NULL, gbest);
         double delta = rp->delta0;
         int done = (nbest == 0.0);
         for (int ev = 1; ev < rp->n_eval && !done; ++ev) {
@@ -948,7 +950,7 @@ void or_register(const or_geom *g, const or_psf *psf, const or_reg_params *rp, c
             gn = sqrt(gn);
             if (!(gn > 0.0)) break;
             for (int k = 0; k < np; ++k) trial[k] = best[k] + delta * (gbest[k] / scale[k]) / gn / scale[k];
-            double nt = or_ncc_grad(g, psf, x, y, d, trial, np, rp->min_valid, 1, gt);
+            double nt = or_ncc_grad(g, psf, x, y, d, trial, np, rp->min_valid, 1, NULL, gt);
             if (rp->fixed_step || nt > nbest) {
                 memcpy(best, trial, sizeof(double) * np);
                 memcpy(gbest, gt, sizeof(double) * np);

@@ -88,10 +88,10 @@ def lib():
         L.or_volume_update.argtypes = [P(C.c_double), P(C.c_double), P(C.c_double), C.c_size_t,
                                        C.c_double, C.c_double]
         L.or_ncc_grad.argtypes = [P(_Geom), P(_Psf), P(C.c_float), P(C.c_float), P(C.c_int),
-                                  P(C.c_double), C.c_int, C.c_int, C.c_int, P(C.c_double)]
+                                  P(C.c_double), C.c_int, C.c_int, C.c_int, P(C.c_uint8), P(C.c_double)]
         L.or_ncc_grad.restype = C.c_double
         L.or_sim_pose_vjp.argtypes = [P(_Geom), P(_Psf), P(C.c_float), P(C.c_double), P(C.c_int),
-                                      P(C.c_double), C.c_int, C.c_int, P(C.c_double)]
+                                      P(C.c_double), C.c_int, C.c_int, P(C.c_uint8), P(C.c_double)]
         L.or_sim_pose_vjp.restype = C.c_double
         L.or_register.argtypes = [P(_Geom), P(_Psf), P(_RegParams), P(C.c_float), P(C.c_float),
                                   P(C.c_int), C.c_int, P(C.c_double), P(C.c_double)]
@@ -238,16 +238,18 @@ def volume_update(x, addon, conf, alpha=1.0, conf_eps=1e-6):
     return xo
 
 
-def ncc_grad(G, ps, x, y, drow, theta, n_params=6, min_valid=16, exact=True):
-    """NCC of one patch and its pose gradient; returns (ncc, grad)."""
+def ncc_grad(G, ps, x, y, drow, theta, n_params=6, min_valid=16, exact=True, member=None):
+    """NCC of one patch and its pose gradient; returns (ncc, grad).  member:
+    uint8 per patch pixel (indexed like y) or None."""
     x = _c(x, np.float32)
     y = _c(y, np.float32)
     drow = _c(drow, np.int32)
     th = _c(theta, np.float64)
+    m = None if member is None else _c(member, np.uint8)
     g = np.zeros(n_params, dtype=np.float64)
     v = lib().or_ncc_grad(C.byref(G), C.byref(ps), _ptr(x, C.c_float), _ptr(y, C.c_float),
                           _ptr(drow, C.c_int), _ptr(th, C.c_double), int(n_params), int(min_valid),
-                          int(bool(exact)), _ptr(g, C.c_double))
+                          int(bool(exact)), _ptr(m, C.c_uint8), _ptr(g, C.c_double))
     return float(v), g
 
 
@@ -261,7 +263,7 @@ def sim_pose_vjp(G, ps, x, r, drow, theta, n_params=6, exact=True):
     g = np.zeros(n_params, dtype=np.float64)
     v = lib().or_sim_pose_vjp(C.byref(G), C.byref(ps), _ptr(x, C.c_float), _ptr(r, C.c_double),
                               _ptr(drow, C.c_int), _ptr(th, C.c_double), int(n_params),
-                              int(bool(exact)), _ptr(g, C.c_double))
+                              int(bool(exact)), None, _ptr(g, C.c_double))
     return float(v), g
 
 

@@ -489,6 +489,14 @@ size_t patches_slice_scratch_bytes(int n_slices)
     return (size_t)(n_slices + 1) * sizeof(SliceCand);
 }
 
+cudaError_t launch_stack_max(const float *stacks, int64_t total, unsigned *imax_key, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(imax_key, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    if (total > 0) k_stack_max<<<296, 256, 0, st>>>(stacks, (long long)total, imax_key);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_patches_gather(const DevGeom *g, const float *stacks, const int32_t *desc,
                                   int n, int64_t n_pix, int32_t *err, float *y, cudaStream_t st)
 {

@@ -44,6 +44,12 @@ __device__ __forceinline__ int qdiv(int a, float r)
     return (int)(((float)a + 0.5f) * r);
 }
 
+// Pixel o (index into the patch-pixel arrays) belongs to its patch.
+__device__ __forceinline__ bool member_ok(const Tiling &tl, size_t o)
+{
+    return !tl.member || tl.member[o];
+}
+
 // Decode block -> (patch, tile); returns false for an empty tile or a
 // patch whose descriptor row failed validation in the pose kernel.
 __device__ __forceinline__ bool tile_setup_at(long long gid, const int32_t *__restrict__ desc,
@@ -587,9 +593,9 @@ __device__ __forceinline__ void simulate_tile(long long gid, const SRC &x, const
         const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
         float num = inplane(A, ti.Lw, kxy, psf.gxy, ci, cj);
         float den = inplane(B, ti.Lw, kxy, psf.gxy, ci, cj);
-        bool v = den > 0.f;
-        float s = v ? num / den : 0.f;
         size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
+        bool v = den > 0.f && member_ok(tl, o);
+        float s = v ? num / den : 0.f;
         if (y) {
             float e = v ? __ldg(y + o) - s : 0.f;
             out[o] = e;
@@ -794,7 +800,7 @@ __device__ __forceinline__ void adjoint_tile(long long gid, const VolDims &vd,
         float den = inplane(U, ti.Lw, kxy, psf.gxy, ci, cj);
         size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
         float cr = 0.f, cw = 0.f;
-        if (den > 0.f) {
+        if (den > 0.f && member_ok(tl, o)) {
             float ww = w ? __ldg(w + o) : 1.f;
             float rr = r ? __ldg(r + o) : 1.f;
             cw = ww / den;
@@ -1043,9 +1049,9 @@ __global__ void __launch_bounds__(256, 4) k_ncc_moments(const SRC x, VolDims vd,
         const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
         float num = inplane(A, ti.Lw, kxy, psf.gxy, ci, cj);
         float den = inplane(B, ti.Lw, kxy, psf.gxy, ci, cj);
-        bool v = den > 0.f;
-        float sv = v ? num / den : 0.f;
         size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
+        bool v = den > 0.f && member_ok(tl, o);
+        float sv = v ? num / den : 0.f;
         if (s_buf) {   // kept for the separate gradient pass only
             s_buf[o] = sv;
             v_buf[o] = v ? 1 : 0;
@@ -1337,9 +1343,9 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
         for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
             const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
             const float den = inplane(B, ti.Lw, kxy, psf.gxy, ci, cj);
-            if (den > 0.f) {
+            const size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
+            if (den > 0.f && member_ok(tl, o)) {
                 const float sv = inplane(A, ti.Lw, kxy, psf.gxy, ci, cj) / den;
-                const size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
                 const float a = __ldg(y + o);
                 ++cnt;
                 f1.add(a);
@@ -1375,10 +1381,10 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
         for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
             const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
             const float den = inplane(B, ti.Lw, kxy, psf.gxy, ci, cj);
+            const size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
             float c = 0.f;
-            if (den > 0.f) {
+            if (den > 0.f && member_ok(tl, o)) {
                 const float sv = inplane(A, ti.Lw, kxy, psf.gxy, ci, cj) / den;
-                const size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
                 c = (a_sc * (__ldg(y + o) - my) - b_sc * (sv - ms)) / den;
             }
             C[pp] = c;
@@ -1436,11 +1442,9 @@ __global__ void __launch_bounds__(256, 4) k_pose_vjp(const SRC x, VolDims vd,
         for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
             const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
             const float den = inplane(B, ti.Lw, kxy, psf.gxy, ci, cj);
+            const size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
             float c = 0.f;
-            if (den > 0.f) {
-                const size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
-                c = __ldg(r + o) / den;
-            }
+            if (den > 0.f && member_ok(tl, o)) c = __ldg(r + o) / den;
             C[pp] = c;
         }
         __syncthreads();

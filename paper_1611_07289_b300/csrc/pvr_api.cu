@@ -29,6 +29,12 @@ cudaError_t launch_patches_build(const DevGeom *g, const pvr_geometry &hg, const
                                  int32_t *keep, int64_t *n_cand_out, unsigned *imax_key,
                                  int32_t *counts, void *slice_scratch, cudaStream_t st);
 size_t patches_slice_scratch_bytes(int n_slices);
+cudaError_t launch_stack_max(const float *stacks, int64_t total, unsigned *imax_key, cudaStream_t st);
+cudaError_t launch_patches_build_slic(const DevGeom *g, const pvr_geometry &hg, const float *stacks, int64_t total,
+                                      int a, double t, int gamma, int n_iter, double fg_frac, double keep_frac,
+                                      int max_side, int32_t *desc_out, int max_out, uint8_t *member_out,
+                                      int64_t max_pix, unsigned *imax_key, int32_t *counts, int64_t *n_centres_out,
+                                      cudaStream_t st);
 }  // namespace pvr
 
 using namespace pvr;
@@ -112,7 +118,7 @@ int cuda_check(pvr_ctx *c, cudaError_t e, const char *what)
     return fail(c, PVR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-Tiling make_tiling(int max_side)
+Tiling make_tiling(int max_side, const pvr_patches *pp = nullptr)
 {
     Tiling t;
     t.T = max_side <= kMaxTile ? max_side : kMaxTile;
@@ -120,6 +126,7 @@ Tiling make_tiling(int max_side)
     t.tiles_x = (max_side + t.T - 1) / t.T;
     t.tiles_y = t.tiles_x;
     t.tpp = t.tiles_x * t.tiles_y;
+    t.member = pp ? pp->member : nullptr;
     return t;
 }
 
@@ -143,6 +150,7 @@ const WorkQueue *plan_for(pvr_ctx *c, const pvr_patches *pp, int max_side, Tilin
         max_side > c->plan_tl.T * c->plan_tl.tiles_x)
         return nullptr;
     *tl = c->plan_tl;
+    tl->member = pp->member;
     if (c->plan_mode != 1) return nullptr;
     wq->items = c->plan_items;
     wq->n_items = c->plan_n_items;
@@ -528,6 +536,36 @@ int pvr_patches_build_sizes(pvr_ctx *c, const float *stacks, const int32_t *slic
     return PVR_OK;
 }
 
+int pvr_patches_build_slic(pvr_ctx *c, const float *stacks, int32_t a, double compactness, int32_t gamma,
+                           int32_t n_iter, double fg_frac, double keep_frac, int32_t *desc_out, uint8_t *member_out,
+                           int32_t max_out, int32_t *n_out, int64_t *n_pix_out, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    REQUIRE(stacks && desc_out && member_out && n_out && n_pix_out, "NULL argument");
+    REQUIRE(a >= 2 && gamma >= 0 && gamma <= 32 && n_iter >= 1 && n_iter <= 100, "a >= 2, gamma 0..32, n_iter 1..100");
+    REQUIRE(compactness > 0.0 && isfinite(compactness), "compactness must be positive");
+    REQUIRE(max_out >= 0, "max_out < 0");
+    REQUIRE(isfinite(fg_frac) && isfinite(keep_frac), "non-finite level");
+    const int max_side = c->prm.max_patch_side < 128 ? c->prm.max_patch_side : 128;
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemsetAsync(c->counts, 0, 4 * sizeof(int32_t), st), "clear counts");
+    CUDA_TRY(launch_stack_max(stacks, c->stack_total, c->imax_key, st), "stack max");
+    int64_t nc = 0;
+    CUDA_TRY(launch_patches_build_slic(c->d_geom, c->geom, stacks, c->stack_total, a, compactness, gamma, n_iter,
+                                       fg_frac, keep_frac, max_side, desc_out, max_out, member_out,
+                                       c->prm.max_pixels, c->imax_key, c->counts, &nc, st),
+             "patches_build_slic");
+    c->launches += 2 + 2 * (int64_t)n_iter + 4;
+    int32_t h[4];
+    CUDA_TRY(cudaMemcpyAsync(h, c->counts, sizeof h, cudaMemcpyDeviceToHost, st), "read counts");
+    CUDA_TRY(cudaStreamSynchronize(st), "synchronise");
+    *n_out = h[0];
+    *n_pix_out = ((int64_t)(uint32_t)h[1]) | ((int64_t)h[2] << 32);
+    REQUIRE(*n_pix_out <= c->prm.max_pixels, "superpixel patches need %lld pixels, above max_pixels",
+            (long long)*n_pix_out);
+    return PVR_OK;
+}
+
 int pvr_patches_build(pvr_ctx *c, const float *stacks, int32_t a, int32_t stride, double fg_frac,
                       double keep_frac, int32_t *desc_out, int32_t max_out, int32_t *n_out,
                       int64_t *n_pix_out, void *stream)
@@ -579,7 +617,7 @@ int pvr_simulate(pvr_ctx *c, const float *x, const pvr_patches *pp, const double
     if (pp->n == 0) return PVR_OK;
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     if ((rc = build_quad(c, x, st))) return rc;
-    Tiling tl = make_tiling(ms);
+    Tiling tl = make_tiling(ms, pp);
     WorkQueue wqs;
     const WorkQueue *wq = plan_for(c, pp, ms, &tl, &wqs);
     CUDA_TRY_T(PVR_K_SIMULATE, launch_simulate(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x,
@@ -604,7 +642,7 @@ int pvr_adjoint(pvr_ctx *c, const pvr_patches *pp, const double *poses, const fl
     // reduction per voxel corner), then copy / add into the caller's arrays
     CUDA_TRY(cudaMemsetAsync(c->acc2, 0, (size_t)c->nvox * sizeof(float2), st), "clear");
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
-    Tiling tl = make_tiling(ms);
+    Tiling tl = make_tiling(ms, pp);
     WorkQueue wqs;
     const WorkQueue *wq = plan_for(c, pp, ms, &tl, &wqs);
     CUDA_TRY_T(PVR_K_ADJOINT, launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix, pp->n,
@@ -626,7 +664,7 @@ int pvr_em_weights(pvr_ctx *c, const float *y, const float *sim, const uint8_t *
     REQUIRE(y && valid && state && mask_out && p, "NULL argument");
     REQUIRE(mask_in != mask_out, "mask_in and mask_out must not alias");
     cudaStream_t st = (cudaStream_t)stream;
-    Tiling tl = make_tiling(ms);
+    Tiling tl = make_tiling(ms, pp);
     CUDA_TRY_T(PVR_K_EM, launch_em_stats(y, sim, valid, pp->desc, pp->n, pp->n_pix, tl, c->err, c->part, st),
              "em_stats");
     CUDA_TRY_T(PVR_K_EM, launch_em(y, sim, valid, pp->desc, pp->n, pp->n_pix, tl, c->err, state, mask_in,
@@ -659,7 +697,7 @@ int pvr_volume_init(pvr_ctx *c, float *x, const float *y, const pvr_patches *pp,
     cudaStream_t st = (cudaStream_t)stream;
     CUDA_TRY(cudaMemsetAsync(c->acc2, 0, (size_t)c->nvox * sizeof(float2), st), "clear");
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
-    Tiling tl = make_tiling(ms);
+    Tiling tl = make_tiling(ms, pp);
     CUDA_TRY_T(PVR_K_ADJOINT, launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix, pp->n,
                             y, nullptr, nullptr, (float *)c->acc2, nullptr, 1, st),
              "adjoint");
@@ -696,7 +734,7 @@ int pvr_rigidity_map(pvr_ctx *c, const pvr_patches *pp, const double *poses, con
     cudaStream_t st = (cudaStream_t)stream;
     CUDA_TRY(cudaMemsetAsync(c->acc2, 0, (size_t)c->nvox * sizeof(float2), st), "clear");
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
-    Tiling tl = make_tiling(ms);
+    Tiling tl = make_tiling(ms, pp);
     CUDA_TRY_T(PVR_K_ADJOINT, launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix,
                                              pp->n, p, nullptr, nullptr, (float *)c->acc2, nullptr, 1, st,
                                              nullptr, pbar),
@@ -720,7 +758,7 @@ int pvr_ncc_grad(pvr_ctx *c, const float *x, const float *y, const pvr_patches *
     if (pp->n == 0) return PVR_OK;
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     if ((rc = build_quad(c, x, st))) return rc;
-    Tiling tl = make_tiling(ms);
+    Tiling tl = make_tiling(ms, pp);
     CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, c->quad, y,
                              pp->desc, c->fix, poses, pp->n, c->s_buf, c->v_buf, c->part,
                              grad ? c->gpart : nullptr, nullptr, c->prm.reg_min_valid, c->gbuf,
@@ -745,7 +783,7 @@ int pvr_pose_grad(pvr_ctx *c, const float *x, const float *r, const pvr_patches 
     if (pp->n == 0) return PVR_OK;
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     if ((rc = build_quad(c, x, st))) return rc;
-    Tiling tl = make_tiling(ms);
+    Tiling tl = make_tiling(ms, pp);
     CUDA_TRY_T(PVR_K_NCC, launch_pose_vjp(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, c->quad, r,
                                           pp->desc, c->fix, pp->n, c->gpart, c->gbuf, c->gbuf_tiles, st),
                "pose_vjp");
@@ -763,7 +801,7 @@ static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_p
     (void)x;
     int n = pp->n;
     if (n == 0 || n_evals <= 0) return PVR_OK;
-    Tiling tl = make_tiling(ms);
+    Tiling tl = make_tiling(ms, pp);
     CUDA_TRY(launch_reg_init(poses, n, c->best, c->trial, c->delta, c->active, c->prm.reg_delta0, st),
              "reg_init");
     c->launches += 1;
@@ -819,7 +857,7 @@ int pvr_reconstruct_iter(pvr_ctx *c, float *x, const float *y, const pvr_patches
     if ((rc = build_quad(c, x, st))) return rc;
     if ((rc = register_impl(c, x, y, pp, ms, poses, c->prm.reg_evals, nullptr, st))) return rc;
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
-    Tiling tl = make_tiling(ms);
+    Tiling tl = make_tiling(ms, pp);
     WorkQueue wqs;
     const WorkQueue *wq = plan_for(c, pp, ms, &tl, &wqs);
     CUDA_TRY(cudaMemsetAsync(c->acc2, 0, (size_t)c->nvox * sizeof(float2), st), "clear");
@@ -917,6 +955,7 @@ int pvr_plan(pvr_ctx *c, const pvr_patches *pp, const float *x, const float *y, 
     std::vector<Cand> cands;
     for (int T : sides) {
         Tiling tl = make_tiling_t(ms, T);
+        tl.member = pp->member;
         if (mode != 0) cands.push_back({tl, 1, tile_items(desc, pp->n, tl)});
         if (mode != 1) cands.push_back({tl, 0, {}});
     }

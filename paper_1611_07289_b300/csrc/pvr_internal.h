@@ -41,6 +41,7 @@ void make_psf_tab(const pvr_geometry *g, const pvr_params *prm, PsfTab *tab);
 struct Tiling {
     int T;
     int tiles_x, tiles_y, tpp;
+    const uint8_t *member = nullptr;   // per patch pixel: 1 = part of the patch (null: all)
 };
 
 // Persistent work queue over the non-empty (patch, tile) slots of a patch

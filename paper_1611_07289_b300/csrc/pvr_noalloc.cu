@@ -129,6 +129,7 @@ extern "C" PVR_API int pvr_simulate_noalloc(const pvr_geometry *geom, const pvr_
     tl.T = max_side <= 64 ? max_side : 64;
     tl.tiles_x = tl.tiles_y = (max_side + tl.T - 1) / tl.T;
     tl.tpp = tl.tiles_x * tl.tiles_y;
+    tl.member = pp->member;
     if (launch_simulate(d_geom, t, tl, g->nx, g->ny, g->nz, x, nullptr, pp->desc, d_fix, pp->n, nullptr, sim,
                         valid, nullptr, st) != cudaSuccess)
         return PVR_ERR_CUDA;

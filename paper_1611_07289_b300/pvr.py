@@ -54,7 +54,7 @@ class Params(C.Structure):
 
 class Patches(C.Structure):
     _fields_ = [("desc", C.c_void_p), ("n", C.c_int32), ("max_side", C.c_int32),
-                ("n_pix", C.c_int64)]
+                ("n_pix", C.c_int64), ("member", C.c_void_p)]
 
 
 _VP = C.c_void_p
@@ -69,6 +69,9 @@ _SIGS = {
                                     C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64), _VP]),
     "pvr_patches_build_sizes": (C.c_int, [_VP, _VP, _VP, _VP, C.c_double, C.c_double, _VP, C.c_int32,
                                           C.POINTER(C.c_int32), C.POINTER(C.c_int64), _VP]),
+    "pvr_patches_build_slic": (C.c_int, [_VP, _VP, C.c_int32, C.c_double, C.c_int32, C.c_int32, C.c_double,
+                                         C.c_double, _VP, _VP, C.c_int32, C.POINTER(C.c_int32),
+                                         C.POINTER(C.c_int64), _VP]),
     "pvr_patches_gather": (C.c_int, [_VP, _VP, C.POINTER(Patches), _VP, _VP]),
     "pvr_pose_to_fixed": (C.c_int, [_VP, C.POINTER(Patches), _VP, _VP, _VP]),
     "pvr_simulate": (C.c_int, [_VP, _VP, C.POINTER(Patches), _VP, _VP, _VP, _VP]),
@@ -176,7 +179,7 @@ class PatchTable:
     """Device patch table int32 [n, 8] plus the host-side counts the C ABI
     needs (pvr_patches)."""
 
-    def __init__(self, desc: torch.Tensor, n_pix: int, max_side: int = 0):
+    def __init__(self, desc: torch.Tensor, n_pix: int, max_side: int = 0, member=None):
         assert desc.dtype == torch.int32 and desc.is_cuda and desc.dim() == 2 and desc.shape[1] == 8
         self.desc = desc.contiguous()
         self.n = int(desc.shape[0])
@@ -184,8 +187,13 @@ class PatchTable:
         if max_side <= 0 and self.n > 0:
             max_side = int(desc[:, 4:6].max().item())
         self.max_side = int(max_side)
+        self.member = None
+        if member is not None:
+            assert member.dtype == torch.uint8 and member.is_cuda and member.numel() >= self.n_pix
+            self.member = member.contiguous()
         self.c = Patches(C.c_void_p(self.desc.data_ptr()) if self.n else None, self.n,
-                         self.max_side, self.n_pix)
+                         self.max_side, self.n_pix,
+                         C.c_void_p(self.member.data_ptr()) if self.member is not None else None)
 
     @classmethod
     def from_numpy(cls, desc_np, n_pix, device="cuda"):
@@ -259,6 +267,24 @@ class Context:
         nn = min(int(n.value), int(max_out))
         ms = int(sa.max()) if sa.size else 0
         return PatchTable(desc[:nn].clone(), int(npix.value), ms), int(n.value)
+
+    def pvr_patches_build_slic(self, stacks, a, compactness, gamma, n_iter=10, fg_frac=0.0, keep_frac=0.0,
+                               max_out=None, stream=None):
+        """Superpixel patch table with membership masks (PatchTable.member)."""
+        if max_out is None:
+            max_out = self.params.max_patches
+        desc = torch.zeros((max(max_out, 1), 8), dtype=torch.int32, device=stacks.device)
+        member = torch.zeros(int(self.params.max_pixels), dtype=torch.uint8, device=stacks.device)
+        n = C.c_int32(0)
+        npix = C.c_int64(0)
+        self._chk(lib.pvr_patches_build_slic(self.h, _ptr(stacks), int(a), float(compactness), int(gamma),
+                                             int(n_iter), float(fg_frac), float(keep_frac), _ptr(desc),
+                                             _ptr(member), int(max_out), C.byref(n), C.byref(npix),
+                                             _stream(stream)))
+        nn = min(int(n.value), int(max_out))
+        d = desc[:nn].clone()
+        ms = int(d[:, 4:6].max().item()) if nn else 1
+        return PatchTable(d, int(npix.value), ms, member[:max(int(npix.value), 1)].clone()), int(n.value)
 
     def pvr_patches_gather(self, stacks, pt: PatchTable, y=None, stream=None):
         if y is None:

@@ -120,9 +120,13 @@ def test_iteration_plan_and_graph_match_direct_call(pvr, planned):
     s.synchronize()
     assert torch.equal(p2, p0) and torch.equal(m2, m0)
     assert rel_l2(x2.cpu().numpy(), x0.cpu().numpy()) < 1e-5
-    # a second replay continues from the updated state, like a second call
-    ctx.pvr_reconstruct_iter(x1, y, pt, p1, st1, m1)
+    # a second replay continues from the updated state, like a direct call
+    # from copies of that state (same inputs: the registration decisions
+    # agree, only the adjoint's reduction order differs)
+    x3, p3, st3, m3 = x2.clone(), p2.clone(), st2.clone(), m2.clone()
+    ctx.pvr_reconstruct_iter(x3, y, pt, p3, st3, m3)
     ctx.pvr_graph_launch(stream=s)
     s.synchronize()
-    assert rel_l2(x2.cpu().numpy(), x1.cpu().numpy()) < 1e-5
+    assert torch.equal(p2, p3) and torch.equal(m2, m3)
+    assert rel_l2(x2.cpu().numpy(), x3.cpu().numpy()) < 1e-5
     ctx.pvr_plan_clear()
