@@ -179,6 +179,21 @@ def _profile_traffic(cls):
     return float(m.group(1))
 
 
+L1_BYTES_PER_CLK_SM = 128   # nominal L1 load bandwidth of an SM
+
+
+def _gathered_bytes(cls, desc, kxy=1, kz=3):
+    """Trilinear corner bytes a gather kernel class reads per launch group:
+    every lattice point of every patch (its w x h pixels plus a kxy halo)
+    takes 2 kz + 1 through-plane samples of 8 float32 corners.  None for the
+    scatter and streaming classes."""
+    if cls not in ("simulate", "ncc"):
+        return None
+    w = desc[:, 4].astype(np.int64) + 2 * kxy
+    h = desc[:, 5].astype(np.int64) + 2 * kxy
+    return int((w * h).sum()) * (2 * kz + 1) * 8 * 4
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
@@ -405,6 +420,7 @@ def run_ours(args, ws, rank, local, dist):
                      "algorithmic_bytes": abytes, "ms_per_launch": dom_ms,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                      else "fallback 6.4 TB/s"},
+        "onchip": _onchip(dom, prof, pt, clocks),
         "kernels": breakdown,
         "clocks": clocks,
         "s_per_iteration": t_ms * 1e-3, "psnr_db": {"before": psnr0, "after_timed_steps": psnr1},
@@ -415,6 +431,23 @@ def run_ours(args, ws, rank, local, dist):
         res["cpu_baseline"] = {"value": info["value"], "unit": UNIT, "cores": info["cores"],
                                "kind": "oracle", "sample": info["sample"]}
     return res
+
+
+def _onchip(dom, prof, pt, clocks):
+    """The gather kernels' own bound: trilinear corner values read through L1
+    per second against the nominal L1 load bandwidth at the SM clock seen."""
+    import torch
+    gb = _gathered_bytes(dom, pt.desc.cpu().numpy())
+    if gb is None:
+        return None
+    ms = prof[dom][0] / max(prof[dom][1], 1)
+    mhz = clocks.get("sm_mhz") or 2032.0
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = n_sm * L1_BYTES_PER_CLK_SM * mhz * 1e6 / 1e9
+    ach = gb / (ms * 1e-3) / 1e9
+    return {"bound": "l1", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "gathered_bytes": gb, "what": "trilinear corner values gathered, 8 x 4 B per sample",
+            "peak_source": f"nominal {L1_BYTES_PER_CLK_SM} B/clock/SM x {n_sm} SMs x {mhz:.0f} MHz"}
 
 
 def run_uneven(args, ws, rank, local):

@@ -1032,7 +1032,10 @@ __global__ void __launch_bounds__(256, 4) k_ncc_moments(const SRC x, VolDims vd,
     const int order = ti.ok ? pick_order(ti, kz) : kAlongCol;
     if (!G) {
         if (ti.ok) {
-            lattice_forward<KZ, false, SRC>(x, vd, ti, kxy, kz, gz, order, A, B);
+            if (tile_interior(ti, vd, kxy, kz))
+                lattice_forward<KZ, true, SRC>(x, vd, ti, kxy, kz, gz, order, A, B);
+            else
+                lattice_forward<KZ, false, SRC>(x, vd, ti, kxy, kz, gz, order, A, B);
         } else {
             for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) A[lp] = B[lp] = 0.f;
         }
