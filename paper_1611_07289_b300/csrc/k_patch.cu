@@ -256,6 +256,23 @@ __device__ __forceinline__ bool tile_interior(const TileInfo &ti, const VolDims 
     return true;
 }
 
+// True when every through-plane sample of the lattice point at q0 lies
+// strictly inside the volume (the FAST condition of tile_interior for one
+// walk): positions are affine in zeta, so its two end samples decide.  Used
+// in border tiles to run the lanes whose walks are inside on the FAST code
+// (same results: the in-volume tests pass and no clamp applies).
+__device__ __forceinline__ bool walk_inside(const VolDims &vd, const TileInfo &ti, const unsigned q0[3], int kz)
+{
+    const unsigned lim[3] = {vd.ux, vd.uy, vd.uz};
+    bool ok = true;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const unsigned a = q0[r] - (unsigned)kz * ti.ez[r], b = q0[r] + (unsigned)kz * ti.ez[r];
+        ok = ok && a < lim[r] && b < lim[r];
+    }
+    return ok;
+}
+
 // Through-plane walks with cell-face reuse.  The through-plane samples of a
 // lattice point are one PSF step apart along e_zeta.  Walking them in the
 // direction in which e_zeta's largest voxel component FA is positive, a
@@ -299,54 +316,80 @@ __device__ __forceinline__ size_t axis_stride(const VolDims &vd, int a)
     return a == 0 ? (size_t)1 : (a == 1 ? (size_t)vd.nx : (size_t)vd.nx * vd.ny);
 }
 
+// One cell face from every lane of a warp (valid lanes only), merged across
+// neighbouring lanes first.  Lanes hold neighbouring lattice points along the
+// traversal axis, so lane l + 1's face usually starts one voxel further along
+// A1 than lane l's: then its two low-A1 corners are lane l's two high-A1
+// corners, lane l adds them to its own before reducing, and lane l + 1 skips
+// them.  The test compares exact voxel indices (a volume of fewer than 2^31
+// voxels, interior cells only, so index + s1 never wraps), so it only removes
+// duplicate reductions: about a quarter of them per face.  Every lane of the
+// warp must call this together.
 template <bool PAIR>
-__device__ __forceinline__ void face_red(float *addon, float *conf, size_t idx, size_t s1, size_t s2,
-                                         const float r[4], const float w[4])
+__device__ __forceinline__ void face_red_warp(float *addon, float *conf, bool valid, unsigned idx,
+                                              unsigned s1, unsigned s2, float r[4], float w[4])
 {
-    const size_t o[4] = {0, s1, s2, s1 + s2};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (PAIR) {
-            atomicAdd(reinterpret_cast<float2 *>(addon) + idx + o[k], make_float2(r[k], w[k]));
-        } else {
-            if (addon) atomicAdd(addon + idx + o[k], r[k]);
-            if (conf) atomicAdd(conf + idx + o[k], w[k]);
-        }
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned key = valid ? idx : 0xffffffffu;
+    const unsigned nkey = __shfl_down_sync(full, key, 1);
+    const float nr0 = __shfl_down_sync(full, r[0], 1), nr2 = __shfl_down_sync(full, r[2], 1);
+    const float nw0 = __shfl_down_sync(full, w[0], 1), nw2 = __shfl_down_sync(full, w[2], 1);
+    const bool take = valid && lane != 31 && nkey == key + s1;
+    if (take) {
+        r[1] += nr0;
+        r[3] += nr2;
+        w[1] += nw0;
+        w[3] += nw2;
     }
+    const bool given = __shfl_up_sync(full, take, 1) && lane != 0;
+    if (!valid) return;
+    auto red = [&](unsigned i, float a, float b) {
+        if (PAIR) {
+            atomicAdd(reinterpret_cast<float2 *>(addon) + i, make_float2(a, b));
+        } else {
+            if (addon) atomicAdd(addon + i, a);
+            if (conf) atomicAdd(conf + i, b);
+        }
+    };
+    if (!given) {
+        red(idx, r[0], w[0]);
+        red(idx + s2, r[2], w[2]);
+    }
+    red(idx + s1, r[1], w[1]);
+    red(idx + s1 + s2, r[3], w[3]);
 }
 
-// Adjoint walk of one lattice point with weights ur, uw (times g_z per sample).
+// walk_scatter with the faces merged across lanes (face_red_warp): every
+// lane of the warp runs the same walk; lanes without a lattice point (act
+// false) and samples outside the volume take part with no reductions of
+// their own.  FAST: interior tile (no in-volume tests, no last-plane clamp).
 template <int FA, int KZ, bool PAIR, bool FAST>
-__device__ __forceinline__ void walk_scatter(const VolDims &vd, const TileInfo &ti, const unsigned q0[3],
-                                             int kz_rt, const float *__restrict__ gz, const Walk &wk,
-                                             float ur, float uw, float *addon, float *conf)
+__device__ __forceinline__ void walk_scatter_warp(const VolDims &vd, const TileInfo &ti, const unsigned q0[3],
+                                                  int kz_rt, const float *__restrict__ gz, const Walk &wk,
+                                                  float ur, float uw, bool act, float *addon, float *conf)
 {
     constexpr int A1 = FaceAxes<FA>::A1, A2 = FaceAxes<FA>::A2;
+    const unsigned full = 0xffffffffu;
     const int kz = KZ >= 0 ? KZ : kz_rt;
-    const size_t s1 = axis_stride(vd, A1), s2 = axis_stride(vd, A2), sf = axis_stride(vd, FA);
-    const size_t nxy = (size_t)vd.nx * vd.ny;
+    const unsigned s1 = (unsigned)axis_stride(vd, A1), s2 = (unsigned)axis_stride(vd, A2);
+    const unsigned sf = (unsigned)axis_stride(vd, FA);
     float pr[4] = {0.f, 0.f, 0.f, 0.f}, pw[4] = {0.f, 0.f, 0.f, 0.f};
-    size_t pidx = 0;
+    unsigned pidx = 0;
     bool have = false;
     int pb[3] = {-2, -2, -2};
-#pragma unroll
+#pragma unroll 1
     for (int t = 0; t <= 2 * kz; ++t) {
         const int z = wk.z0 + t * wk.dz;
-        unsigned q[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) q[r] = q0[r] + (unsigned)z * ti.ez[r];
-        if (!FAST && !inside(vd, q[0], q[1], q[2])) {
-            if (have) face_red<PAIR>(addon, conf, pidx, s1, s2, pr, pw);
-            have = false;
-            pb[FA] = -2;
-            continue;
-        }
+        const unsigned qx = q0[0] + (unsigned)z * ti.ez[0], qy = q0[1] + (unsigned)z * ti.ez[1];
+        const unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
+        const bool ins = FAST || inside(vd, qx, qy, qz);
         int b[3];
         float f[3];
-        split<FAST>(q[0], vd.nx, b[0], f[0]);
-        split<FAST>(q[1], vd.ny, b[1], f[1]);
-        split<FAST>(q[2], vd.nz, b[2], f[2]);
-        const size_t idx = (size_t)b[2] * nxy + (size_t)b[1] * vd.nx + b[0];
+        split<FAST>(qx, vd.nx, b[0], f[0]);
+        split<FAST>(qy, vd.ny, b[1], f[1]);
+        split<FAST>(qz, vd.nz, b[2], f[2]);
+        const unsigned idx = ((unsigned)b[2] * (unsigned)vd.ny + (unsigned)b[1]) * (unsigned)vd.nx + (unsigned)b[0];
         const float g = gz[z + kz];
         const float f1 = f[A1], f2 = f[A2];
         const float wf[4] = {(1.f - f1) * (1.f - f2), f1 * (1.f - f2), (1.f - f1) * f2, f1 * f2};
@@ -358,29 +401,54 @@ __device__ __forceinline__ void walk_scatter(const VolDims &vd, const TileInfo &
             lr[k] = ar * lo * wf[k];
             lw[k] = aw * lo * wf[k];
         }
-        if (have && b[FA] == pb[FA] + 1 && b[A1] == pb[A1] && b[A2] == pb[A2]) {
+        // the previous sample's upper face: merged into this lower face when
+        // it is the same face, else reduced on its own
+        const bool merge = have && ins && b[FA] == pb[FA] + 1 && b[A1] == pb[A1] && b[A2] == pb[A2];
+        const bool pv = act && have && !merge;
+        if (__any_sync(full, pv)) face_red_warp<PAIR>(addon, conf, pv, pidx, s1, s2, pr, pw);
+        if (merge) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                pr[k] += lr[k];
-                pw[k] += lw[k];
+                lr[k] += pr[k];
+                lw[k] += pw[k];
             }
-            face_red<PAIR>(addon, conf, pidx, s1, s2, pr, pw);
-        } else {
-            if (have) face_red<PAIR>(addon, conf, pidx, s1, s2, pr, pw);
-            face_red<PAIR>(addon, conf, idx, s1, s2, lr, lw);
         }
+        const bool cv = act && ins;
+        if (FAST || __any_sync(full, cv)) face_red_warp<PAIR>(addon, conf, cv, idx, s1, s2, lr, lw);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             pr[k] = ar * hi * wf[k];
             pw[k] = aw * hi * wf[k];
         }
         pidx = idx + sf;
-        have = true;
+        have = ins;
         pb[0] = b[0];
         pb[1] = b[1];
         pb[2] = b[2];
     }
-    if (have) face_red<PAIR>(addon, conf, pidx, s1, s2, pr, pw);
+    const bool pv = act && have;
+    if (__any_sync(full, pv)) face_red_warp<PAIR>(addon, conf, pv, pidx, s1, s2, pr, pw);
+}
+
+// Through-plane PSF sums of one lattice point: acc = sum g_z trilinear
+// (when want_a), den = sum g_z over the in-volume samples.
+template <int KZ, bool FAST, class SRC>
+__device__ __forceinline__ void walk_forward(const SRC &src, const VolDims &vd, const TileInfo &ti,
+                                             const unsigned q0[3], int kz_rt, const float *__restrict__ gz,
+                                             bool want_a, float &acc, float &den)
+{
+    const int kz = KZ >= 0 ? KZ : kz_rt;
+#pragma unroll
+    for (int z = -kz; z <= kz; ++z) {
+        unsigned qx = q0[0] + (unsigned)z * ti.ez[0];
+        unsigned qy = q0[1] + (unsigned)z * ti.ez[1];
+        unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
+        if (FAST || inside(vd, qx, qy, qz)) {
+            float g = gz[z + kz];
+            if (want_a) acc = fmaf(g, trilinear<FAST>(src, vd, qx, qy, qz), acc);
+            den += g;
+        }
+    }
 }
 
 // Phase 1 of the forward model: through-plane PSF sums at every lattice
@@ -400,17 +468,11 @@ __device__ __forceinline__ void lattice_forward(const SRC src, const VolDims &vd
             unsigned q0[3];
             lattice_pos(ti, kxy, li, lj, q0);
             float acc = 0.f, den = 0.f;
-#pragma unroll
-            for (int z = -kz; z <= kz; ++z) {
-                unsigned qx = q0[0] + (unsigned)z * ti.ez[0];
-                unsigned qy = q0[1] + (unsigned)z * ti.ez[1];
-                unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
-                if (FAST || inside(vd, qx, qy, qz)) {
-                    float g = gz[z + kz];
-                    if (A) acc = fmaf(g, trilinear<FAST>(src, vd, qx, qy, qz), acc);
-                    den += g;
-                }
-            }
+            // border tile: warps whose walks are all inside take the FAST code
+            if (FAST || __all_sync(__activemask(), walk_inside(vd, ti, q0, kz)))
+                walk_forward<KZ, true>(src, vd, ti, q0, kz, gz, A != nullptr, acc, den);
+            else
+                walk_forward<KZ, false>(src, vd, ti, q0, kz, gz, A != nullptr, acc, den);
             int sidx = lj * ti.Lw + li;
             if (A) A[sidx] = acc;
             B[sidx] = den;
@@ -730,18 +792,33 @@ __device__ __forceinline__ void adjoint_scatter(const VolDims &vd, const TileInf
 {
     const int order = pick_order(ti, kz);
     if (order != kAlongZeta) {
+        // warps walk together and merge faces across lanes
         const Walk wk = zeta_walk(ti, kz);
-        for (int it = threadIdx.x; it < ti.L; it += blockDim.x) {
-            int li, lj;
-            lattice_coords(ti, order, it, li, lj);
-            const int sidx = lj * ti.Lw + li;
-            float ur = U[sidx], uw = Uw[sidx];
-            if (ur == 0.f && uw == 0.f) continue;
-            unsigned q0[3];
-            lattice_pos(ti, kxy, li, lj, q0);
-            if (wk.fa == 2) walk_scatter<2, KZ, PAIR, FAST>(vd, ti, q0, kz, gz, wk, ur, uw, addon, conf);
-            else if (wk.fa == 1) walk_scatter<1, KZ, PAIR, FAST>(vd, ti, q0, kz, gz, wk, ur, uw, addon, conf);
-            else walk_scatter<0, KZ, PAIR, FAST>(vd, ti, q0, kz, gz, wk, ur, uw, addon, conf);
+        for (int base = threadIdx.x & ~31; base < ti.L; base += blockDim.x) {
+            const int it = base + (threadIdx.x & 31);
+            bool act = false;
+            float ur = 0.f, uw = 0.f;
+            unsigned q0[3] = {0u, 0u, 0u};
+            if (it < ti.L) {
+                int li, lj;
+                lattice_coords(ti, order, it, li, lj);
+                const int sidx = lj * ti.Lw + li;
+                ur = U[sidx];
+                uw = Uw[sidx];
+                act = ur != 0.f || uw != 0.f;
+                lattice_pos(ti, kxy, li, lj, q0);
+            }
+            if (!__any_sync(0xffffffffu, act)) continue;
+            // border tile: warps whose walks are all inside take the FAST code
+            if (FAST || __all_sync(0xffffffffu, !act || walk_inside(vd, ti, q0, kz))) {
+                if (wk.fa == 2) walk_scatter_warp<2, KZ, PAIR, true>(vd, ti, q0, kz, gz, wk, ur, uw, act, addon, conf);
+                else if (wk.fa == 1) walk_scatter_warp<1, KZ, PAIR, true>(vd, ti, q0, kz, gz, wk, ur, uw, act, addon, conf);
+                else walk_scatter_warp<0, KZ, PAIR, true>(vd, ti, q0, kz, gz, wk, ur, uw, act, addon, conf);
+            } else {
+                if (wk.fa == 2) walk_scatter_warp<2, KZ, PAIR, false>(vd, ti, q0, kz, gz, wk, ur, uw, act, addon, conf);
+                else if (wk.fa == 1) walk_scatter_warp<1, KZ, PAIR, false>(vd, ti, q0, kz, gz, wk, ur, uw, act, addon, conf);
+                else walk_scatter_warp<0, KZ, PAIR, false>(vd, ti, q0, kz, gz, wk, ur, uw, act, addon, conf);
+            }
         }
     } else {
         const int zl = threadIdx.x & 7, zeta = zl - kz;
@@ -907,6 +984,33 @@ __device__ __forceinline__ float tri_grad(const SRC &src, const VolDims &vd, uns
     return fmaf(fz, c1 - c0, c0);
 }
 
+// Through-plane sums of one lattice point with the trilinear gradient:
+// a = sum g_z trilinear, b = sum g_z, ga = sum g_z grad, gb = sum g_z zeta grad
+// over the in-volume samples.
+template <int KZ, bool FAST, class SRC>
+__device__ __forceinline__ void walk_grad(const SRC &src, const VolDims &vd, const TileInfo &ti,
+                                          const unsigned q0[3], int kz_rt, const float *__restrict__ gz,
+                                          float &a, float &b, float ga[3], float gb[3])
+{
+    const int kz = KZ >= 0 ? KZ : kz_rt;
+#pragma unroll
+    for (int z = -kz; z <= kz; ++z) {
+        unsigned qx = q0[0] + (unsigned)z * ti.ez[0];
+        unsigned qy = q0[1] + (unsigned)z * ti.ez[1];
+        unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
+        if (!FAST && !inside(vd, qx, qy, qz)) continue;
+        float gr[3];
+        const float w = gz[z + kz];
+        a = fmaf(w, tri_grad<FAST>(src, vd, qx, qy, qz, gr), a);
+        b += w;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            ga[r] = fmaf(w, gr[r], ga[r]);
+            gb[r] = fmaf(w * (float)z, gr[r], gb[r]);
+        }
+    }
+}
+
 // Gather pass of the NCC moments kernel: A, B into shared memory and the
 // gradient sums GA, GB into G (FAST: interior tile).
 template <int KZ, bool FAST, class SRC>
@@ -923,22 +1027,11 @@ __device__ __forceinline__ void moments_gather(const SRC src, const VolDims &vd,
             if (ti.ok) {
                 unsigned q0[3];
                 lattice_pos(ti, kxy, li, lj, q0);
-#pragma unroll
-                for (int z = -kz; z <= kz; ++z) {
-                    unsigned qx = q0[0] + (unsigned)z * ti.ez[0];
-                    unsigned qy = q0[1] + (unsigned)z * ti.ez[1];
-                    unsigned qz = q0[2] + (unsigned)z * ti.ez[2];
-                    if (!FAST && !inside(vd, qx, qy, qz)) continue;
-                    float gr[3];
-                    const float w = gz[z + kz];
-                    a = fmaf(w, tri_grad<FAST>(src, vd, qx, qy, qz, gr), a);
-                    b += w;
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        ga[r] = fmaf(w, gr[r], ga[r]);
-                        gb[r] = fmaf(w * (float)z, gr[r], gb[r]);
-                    }
-                }
+                // border tile: warps whose walks are all inside take the FAST code
+                if (FAST || __all_sync(__activemask(), walk_inside(vd, ti, q0, kz)))
+                    walk_grad<KZ, true>(src, vd, ti, q0, kz, gz, a, b, ga, gb);
+                else
+                    walk_grad<KZ, false>(src, vd, ti, q0, kz, gz, a, b, ga, gb);
             }
             const int si = lj * ti.Lw + li;
             A[si] = a;
@@ -1213,6 +1306,24 @@ __device__ __forceinline__ void grad_lattice_moments(const TileInfo &ti, int kxy
     }
 }
 
+// Plane stride of a persistent CTA's gradient slot: Lmax rounded up to 32
+// floats, so that every slot starts on a 128-byte L2 line.
+__host__ __device__ __forceinline__ int slot_stride(int Lmax)
+{
+    return (Lmax + 31) & ~31;
+}
+
+// Drop a CTA's gradient slot (6 planes of stride Gs, 128-byte aligned) from L2
+// without writing it back: its values are dead once the tile's gradient
+// moments are summed, and a write-back would only cost HBM bandwidth.
+// discard.global.L2 acts as a write of undefined values, so the callers put a
+// barrier after the last read and another before the slot is written again.
+__device__ __forceinline__ void discard_slot(float *G, int Gs)
+{
+    for (int l = threadIdx.x * 32; l < 6 * Gs; l += blockDim.x * 32)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(G + l) : "memory");
+}
+
 // ----------------------------------------------------------------- K6b --
 // Pose gradient of NCC from the gradient sums K6a streamed to gbuf.
 // dNCC/ds_i = ((y_i - my)/sd - ncc (s_i - ms)/vs)/N; pixel coefficient
@@ -1320,7 +1431,8 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
     __shared__ int sh_ok;
     const int kxy = KXY >= 0 ? KXY : psf.kxy;
     const int kz = KZ >= 0 ? KZ : psf.kz;
-    float *G = scratch + (size_t)blockIdx.x * 6 * Lmax;
+    const int Gs = slot_stride(Lmax);
+    float *G = scratch + (size_t)blockIdx.x * 6 * Gs;
     float *A = sm, *B = sm + Lmax, *C = sm + 2 * Lmax;
     for (long long gid = blockIdx.x; gid < n_tiles; gid += gridDim.x) {
         TileInfo ti;
@@ -1336,9 +1448,9 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
         const float *gz = psf.gz[ti.stack];
         const int order = pick_order(ti, kz);
         if (tile_interior(ti, vd, kxy, kz))
-            moments_gather<KZ, true, SRC>(x, vd, ti, kxy, kz, order, gz, A, B, G, Lmax);
+            moments_gather<KZ, true, SRC>(x, vd, ti, kxy, kz, order, gz, A, B, G, Gs);
         else
-            moments_gather<KZ, false, SRC>(x, vd, ti, kxy, kz, order, gz, A, B, G, Lmax);
+            moments_gather<KZ, false, SRC>(x, vd, ti, kxy, kz, order, gz, A, B, G, Gs);
         __syncthreads();
         FFSum f1, f2, f3, f4, f5;
         int cnt = 0;
@@ -1377,6 +1489,8 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
         __syncthreads();
         if (!sh_ok) {
             if (threadIdx.x < kGradStride) gp[threadIdx.x] = 0.0;
+            discard_slot(G, Gs);
+            __syncthreads();
             continue;
         }
         // dNCC/ds per pixel over its PSF weight (as K6b), from the same A, B
@@ -1394,7 +1508,7 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
         }
         __syncthreads();
         float mo[12];
-        grad_lattice_moments(ti, kxy, psf.gxy, C, G, Lmax, mo);
+        grad_lattice_moments(ti, kxy, psf.gxy, C, G, Gs, mo);
         double mom[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) mom[k] = (double)mo[k];
@@ -1403,6 +1517,8 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
             for (int k = 0; k < 12; ++k) gp[k] = mom[k];
             for (int k = 12; k < kGradStride; ++k) gp[k] = 0.0;
         }
+        discard_slot(G, Gs);
+        __syncthreads();
     }
 }
 
@@ -1424,7 +1540,8 @@ __global__ void __launch_bounds__(256, 4) k_pose_vjp(const SRC x, VolDims vd,
     __shared__ double red[32 * 12];
     const int kxy = KXY >= 0 ? KXY : psf.kxy;
     const int kz = KZ >= 0 ? KZ : psf.kz;
-    float *G = scratch + (size_t)blockIdx.x * 6 * Lmax;
+    const int Gs = slot_stride(Lmax);
+    float *G = scratch + (size_t)blockIdx.x * 6 * Gs;
     float *A = sm, *B = sm + Lmax, *C = sm + 2 * Lmax;
     for (long long gid = blockIdx.x; gid < n_tiles; gid += gridDim.x) {
         TileInfo ti;
@@ -1437,9 +1554,9 @@ __global__ void __launch_bounds__(256, 4) k_pose_vjp(const SRC x, VolDims vd,
         const float *gz = psf.gz[ti.stack];
         const int order = pick_order(ti, kz);
         if (tile_interior(ti, vd, kxy, kz))
-            moments_gather<KZ, true, SRC>(x, vd, ti, kxy, kz, order, gz, A, B, G, Lmax);
+            moments_gather<KZ, true, SRC>(x, vd, ti, kxy, kz, order, gz, A, B, G, Gs);
         else
-            moments_gather<KZ, false, SRC>(x, vd, ti, kxy, kz, order, gz, A, B, G, Lmax);
+            moments_gather<KZ, false, SRC>(x, vd, ti, kxy, kz, order, gz, A, B, G, Gs);
         __syncthreads();
         const int np = ti.tw * ti.th;
         for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
@@ -1452,7 +1569,7 @@ __global__ void __launch_bounds__(256, 4) k_pose_vjp(const SRC x, VolDims vd,
         }
         __syncthreads();
         float mo[12];
-        grad_lattice_moments(ti, kxy, psf.gxy, C, G, Lmax, mo);
+        grad_lattice_moments(ti, kxy, psf.gxy, C, G, Gs, mo);
         double mom[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) mom[k] = (double)mo[k];
@@ -1461,6 +1578,8 @@ __global__ void __launch_bounds__(256, 4) k_pose_vjp(const SRC x, VolDims vd,
             for (int k = 0; k < 12; ++k) gp[k] = mom[k];
             for (int k = 12; k < kGradStride; ++k) gp[k] = 0.0;
         }
+        discard_slot(G, Gs);
+        __syncthreads();
     }
 }
 
@@ -1650,8 +1769,9 @@ cudaError_t launch_adjoint(const PsfTab &psf, const Tiling &tl, int nx, int ny, 
 }
 
 cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &tl, int nx, int ny,
-                            int nz, const float4 *quad, const float *y, const int32_t *desc,
-                            const int32_t *fix, const double *poses, int n, float *s_buf,
+                            int nz, const float *xplain, const float4 *quad, const float *y,
+                            const int32_t *desc, const int32_t *fix, const double *poses, int n,
+                            float *s_buf,
                             uint8_t *v_buf, double *part, double *gpart, const int32_t *active,
                             int min_valid, float *gbuf, long long gbuf_tiles, cudaStream_t st)
 {
@@ -1665,28 +1785,33 @@ cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &t
     const bool fast = psf.kxy == 1 && psf.kz == 3;
     cudaError_t e;
     if (gpart && tl.tpp == 1) {
-        // one-tile patches: the fused persistent kernel, one scratch slot per CTA
+        // one-tile patches: the fused persistent kernel, one scratch slot per
+        // CTA.  It gathers from the plain volume: the scratch slots in flight
+        // (about 60 MB) then share L2 with 50 MB of volume instead of the
+        // 200 MB quad copy, and stay on chip.
+        const PlainVol xp{xplain};
         size_t smem3 = (size_t)(2 * Lmax + tl.T * tl.T) * sizeof(float);
         int dev = 0, nsm = 0, per_sm = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         if (fast) {
-            if ((e = prep(k_ncc_fused<1, 3, QuadVol>, smem3)) != cudaSuccess) return e;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ncc_fused<1, 3, QuadVol>, 256, smem3);
+            if ((e = prep(k_ncc_fused<1, 3, PlainVol>, smem3)) != cudaSuccess) return e;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ncc_fused<1, 3, PlainVol>, 256, smem3);
         } else {
-            if ((e = prep(k_ncc_fused<-1, -1, QuadVol>, smem3)) != cudaSuccess) return e;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ncc_fused<-1, -1, QuadVol>, 256, smem3);
+            if ((e = prep(k_ncc_fused<-1, -1, PlainVol>, smem3)) != cudaSuccess) return e;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ncc_fused<-1, -1, PlainVol>, 256, smem3);
         }
         if (e != cudaSuccess) return e;
         long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
         if (grid > total) grid = total;
-        if (grid > gbuf_tiles) grid = gbuf_tiles;
+        const long long slots = gbuf_tiles * Lmax / slot_stride(Lmax);   // padded slots in the scratch
+        if (grid > slots) grid = slots;
         if (grid <= 0) return cudaErrorInvalidValue;
         if (fast)
-            k_ncc_fused<1, 3, QuadVol><<<(unsigned)grid, 256, smem3, st>>>(x, vd, desc, fix, psf, tl, total, y, active,
+            k_ncc_fused<1, 3, PlainVol><<<(unsigned)grid, 256, smem3, st>>>(xp, vd, desc, fix, psf, tl, total, y, active,
                                                                   part, gpart, gbuf, Lmax, min_valid);
         else
-            k_ncc_fused<-1, -1, QuadVol><<<(unsigned)grid, 256, smem3, st>>>(x, vd, desc, fix, psf, tl, total, y,
+            k_ncc_fused<-1, -1, PlainVol><<<(unsigned)grid, 256, smem3, st>>>(xp, vd, desc, fix, psf, tl, total, y,
                                                                     active, part, gpart, gbuf, Lmax,
                                                                     min_valid);
         return cudaGetLastError();
@@ -1723,13 +1848,13 @@ cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &t
 }
 
 cudaError_t launch_pose_vjp(const PsfTab &psf, const Tiling &tl, int nx, int ny, int nz,
-                            const float4 *quad, const float *r, const int32_t *desc,
+                            const float *xplain, const float *r, const int32_t *desc,
                             const int32_t *fix, int n, double *gpart, float *gbuf,
                             long long gbuf_tiles, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     VolDims vd = vol_dims(nx, ny, nz);
-    const QuadVol x{quad};
+    const PlainVol x{xplain};
     const int Lmax = (tl.T + 2 * psf.kxy) * (tl.T + 2 * psf.kxy);
     const long long total = (long long)n * tl.tpp;
     const size_t smem = (size_t)(2 * Lmax + tl.T * tl.T) * sizeof(float);
@@ -1739,22 +1864,23 @@ cudaError_t launch_pose_vjp(const PsfTab &psf, const Tiling &tl, int nx, int ny,
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if (fast) {
-        if ((e = prep(k_pose_vjp<1, 3, QuadVol>, smem)) != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pose_vjp<1, 3, QuadVol>, 256, smem);
+        if ((e = prep(k_pose_vjp<1, 3, PlainVol>, smem)) != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pose_vjp<1, 3, PlainVol>, 256, smem);
     } else {
-        if ((e = prep(k_pose_vjp<-1, -1, QuadVol>, smem)) != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pose_vjp<-1, -1, QuadVol>, 256, smem);
+        if ((e = prep(k_pose_vjp<-1, -1, PlainVol>, smem)) != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pose_vjp<-1, -1, PlainVol>, 256, smem);
     }
     if (e != cudaSuccess) return e;
     long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
     if (grid > total) grid = total;
-    if (grid > gbuf_tiles) grid = gbuf_tiles;
+    const long long slots = gbuf_tiles * Lmax / slot_stride(Lmax);   // padded slots in the scratch
+    if (grid > slots) grid = slots;
     if (grid <= 0) return cudaErrorInvalidValue;
     if (fast)
-        k_pose_vjp<1, 3, QuadVol><<<(unsigned)grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, total, r,
+        k_pose_vjp<1, 3, PlainVol><<<(unsigned)grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, total, r,
                                                                      gpart, gbuf, Lmax);
     else
-        k_pose_vjp<-1, -1, QuadVol><<<(unsigned)grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, total, r,
+        k_pose_vjp<-1, -1, PlainVol><<<(unsigned)grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, total, r,
                                                                        gpart, gbuf, Lmax);
     return cudaGetLastError();
 }

@@ -759,7 +759,7 @@ int pvr_ncc_grad(pvr_ctx *c, const float *x, const float *y, const pvr_patches *
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     if ((rc = build_quad(c, x, st))) return rc;
     Tiling tl = make_tiling(ms, pp);
-    CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, c->quad, y,
+    CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, c->quad, y,
                              pp->desc, c->fix, poses, pp->n, c->s_buf, c->v_buf, c->part,
                              grad ? c->gpart : nullptr, nullptr, c->prm.reg_min_valid, c->gbuf,
                              c->gbuf_tiles, st),
@@ -782,9 +782,8 @@ int pvr_pose_grad(pvr_ctx *c, const float *x, const float *r, const pvr_patches 
     cudaStream_t st = (cudaStream_t)stream;
     if (pp->n == 0) return PVR_OK;
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
-    if ((rc = build_quad(c, x, st))) return rc;
     Tiling tl = make_tiling(ms, pp);
-    CUDA_TRY_T(PVR_K_NCC, launch_pose_vjp(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, c->quad, r,
+    CUDA_TRY_T(PVR_K_NCC, launch_pose_vjp(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, r,
                                           pp->desc, c->fix, pp->n, c->gpart, c->gbuf, c->gbuf_tiles, st),
                "pose_vjp");
     CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(c->d_geom, pp->desc, poses, pp->n, tl, nullptr, c->gpart,
@@ -798,7 +797,6 @@ int pvr_pose_grad(pvr_ctx *c, const float *x, const float *r, const pvr_patches 
 static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_patches *pp, int ms,
                          double *poses, int n_evals, double *ncc_out, cudaStream_t st)
 {
-    (void)x;
     int n = pp->n;
     if (n == 0 || n_evals <= 0) return PVR_OK;
     Tiling tl = make_tiling(ms, pp);
@@ -812,7 +810,7 @@ static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_p
         // never be used, so it computes the NCC alone
         const bool need_grad = ev < n_evals - 1;
         double *gpart = need_grad ? c->gpart : nullptr, *grad = need_grad ? c->grad_tmp : nullptr;
-        CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, c->quad, y,
+        CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, c->quad, y,
                                  pp->desc, c->fix, c->trial, n, c->s_buf, c->v_buf, c->part,
                                  gpart, c->active, c->prm.reg_min_valid, c->gbuf, c->gbuf_tiles,
                                  st),

@@ -95,8 +95,9 @@ cudaError_t launch_volume_update(float *x, float *addon, float *conf, int64_t nv
 // streams per-lattice-point gradient sums through gbuf, in chunks of whole
 // patches of at most gbuf_tiles tiles.
 cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &tl, int nx, int ny,
-                            int nz, const float4 *quad, const float *y, const int32_t *desc,
-                            const int32_t *fix, const double *poses, int n, float *s_buf,
+                            int nz, const float *xplain, const float4 *quad, const float *y,
+                            const int32_t *desc, const int32_t *fix, const double *poses, int n,
+                            float *s_buf,
                             uint8_t *v_buf, double *part, double *gpart, const int32_t *active,
                             int min_valid, float *gbuf, long long gbuf_tiles, cudaStream_t st);
 size_t ncc_gbuf_floats_per_tile(const Tiling &tl, int kxy);
@@ -107,7 +108,7 @@ int ncc_launch_count(const Tiling &tl, int n, bool grad, long long gbuf_tiles);
 // moments of sum_pix r_pix sim_pix into gpart (contracted per patch by
 // launch_ncc_finish with part = null).
 cudaError_t launch_pose_vjp(const PsfTab &psf, const Tiling &tl, int nx, int ny, int nz,
-                            const float4 *quad, const float *r, const int32_t *desc,
+                            const float *x, const float *r, const int32_t *desc,
                             const int32_t *fix, int n, double *gpart, float *gbuf,
                             long long gbuf_tiles, cudaStream_t st);
 

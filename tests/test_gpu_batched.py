@@ -116,6 +116,9 @@ def test_iteration_plan_and_graph_match_direct_call(pvr, planned):
     ctx.pvr_graph_capture(x2, y, pt, p2, st2, m2, stream=s)
     s.synchronize()
     assert torch.equal(x2.reshape(-1), _t(planned["x"]))     # capture runs nothing
+    # calls on one context must not overlap on the GPU: order s after the
+    # default stream's work (torch streams do not wait for it by themselves)
+    s.wait_stream(torch.cuda.current_stream())
     ctx.pvr_graph_launch(stream=s)
     s.synchronize()
     assert torch.equal(p2, p0) and torch.equal(m2, m0)
@@ -125,6 +128,7 @@ def test_iteration_plan_and_graph_match_direct_call(pvr, planned):
     # agree, only the adjoint's reduction order differs)
     x3, p3, st3, m3 = x2.clone(), p2.clone(), st2.clone(), m2.clone()
     ctx.pvr_reconstruct_iter(x3, y, pt, p3, st3, m3)
+    s.wait_stream(torch.cuda.current_stream())
     ctx.pvr_graph_launch(stream=s)
     s.synchronize()
     assert torch.equal(p2, p3) and torch.equal(m2, m3)
