@@ -613,6 +613,72 @@ struct FFSum {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// Warp sum of float-float values (two-sum at every level, about 48
+// significant bits) on the float32 pipe: float64 arithmetic runs at a small
+// fraction of the float32 rate on this GPU, so per-thread double shuffles and
+// adds would dominate a tile's reductions.
+__device__ __forceinline__ void warp_sum_ff(float &hi, float &lo)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+        const float s = hi + oh, bb = s - hi;
+        const float err = (hi - (s - bb)) + (oh - bb);
+        hi = s;
+        lo = (lo + ol) + err;
+    }
+}
+
+// Block sums of NV float-float accumulators as doubles in out (valid in
+// thread 0): float-float within each warp, float64 across the warps.
+// red: shared scratch of 32 * NV doubles.  Ends with a barrier.  Not
+// inlined (see block_sum_fd).
+template <int NV>
+__device__ __noinline__ void block_sum_ff(FFSum (&f)[NV], double (&out)[NV], double *red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) warp_sum_ff(f[k].hi, f[k].lo);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[wid * NV + k] = f[k].value();
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += red[w * NV + k];
+            out[k] = t;
+        }
+    __syncthreads();
+}
+
+// Block sums of NV float32 values as doubles in out (valid in thread 0):
+// float32 within each warp (32 terms), float64 across the warps.  Ends with
+// a barrier.  Not inlined: inlined into the persistent kernels it made the
+// register allocator spill hundreds of bytes of their tile loops.
+template <int NV>
+__device__ __noinline__ void block_sum_fd(float (&v)[NV], double (&out)[NV], double *red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[wid * NV + k] = (double)v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += red[w * NV + k];
+            out[k] = t;
+        }
+    __syncthreads();
+}
+
 // ------------------------------------------------------------------ K2 --
 // Forward model.  y == null: write sim, valid.  y != null: write the
 // residual e = y - sim (0 where invalid) and valid, plus per-tile partials
@@ -1162,8 +1228,9 @@ __global__ void __launch_bounds__(256, 4) k_ncc_moments(const SRC x, VolDims vd,
             f5.add_prod(a, sv);
         }
     }
-    double m[6] = {(double)cnt, f1.value(), f2.value(), f3.value(), f4.value(), f5.value()};
-    block_sum<6>(m, red);
+    FFSum fs[6] = {FFSum{(float)cnt, 0.f}, f1, f2, f3, f4, f5};   // counts <= 2^24: exact
+    double m[6];
+    block_sum_ff<6>(fs, m, red);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) pt[k] = m[k];
@@ -1266,31 +1333,62 @@ __device__ void pose_jacobian(const DevGeom *__restrict__ g, const int32_t *d, c
     }
 }
 
+// Pixel coefficients of the NCC gradient live in a zero-padded array:
+// pixel (ci, cj) of the tile at Cp[(cj + 2 kxy) cw + ci + 2 kxy] with
+// cw = tw + 4 kxy, so that the transposed in-plane taps of every lattice
+// point (halo included) read in bounds without tests.  At most
+// (T + 4 kxy)^2 floats.
+__device__ __forceinline__ int cpad_w(const TileInfo &ti, int kxy) { return ti.tw + 4 * kxy; }
+__device__ __forceinline__ int cpad_at(const TileInfo &ti, int kxy, int ci, int cj)
+{
+    return (cj + 2 * kxy) * cpad_w(ti, kxy) + ci + 2 * kxy;
+}
+
+// Zero the border of the padded coefficient array (the pixels' entries are
+// written by the pixel loops).
+__device__ __forceinline__ void cpad_border(const TileInfo &ti, int kxy, float *Cp)
+{
+    const int cw = cpad_w(ti, kxy), b = 2 * kxy, top = 2 * b * cw, side = 2 * b * ti.th;
+    for (int k = threadIdx.x; k < top + side; k += blockDim.x) {
+        int at;
+        if (k < top) {
+            const int r = k / cw, c = k - r * cw;                // rows 0..b-1, then the b below the tile
+            at = (r < b ? r : ti.th + r) * cw + c;
+        } else {
+            const int t = k - top, r = t / (2 * b), c = t - r * 2 * b;   // b columns each side
+            at = (r + b) * cw + (c < b ? c : ti.tw + c);
+        }
+        Cp[at] = 0.f;
+    }
+}
+
 // Lattice phase of the NCC gradient: the transposed in-plane taps of the
-// pixel coefficients C give the lattice weight U; with the gradient sums
-// GA, GB of the lattice point (planes of G, Lmax apart, read through L2) it
-// accumulates M1 = sum U GA (i - cu), M2 = sum U GA (j - cv), M4 = sum U GB,
-// M3 = sum U GA into mo[0..2], mo[3..5], mo[6..8], mo[9..11] (float32 per
-// thread over its few lattice points).
-__device__ __forceinline__ void grad_lattice_moments(const TileInfo &ti, int kxy, const float *gxy,
-                                                     const float *C, const float *G, int Lmax,
+// pixel coefficients (padded array Cp) give the lattice weight U; with the
+// gradient sums GA, GB of the lattice point (planes of G, Lmax apart, read
+// through L2) it accumulates M1 = sum U GA (i - cu), M2 = sum U GA (j - cv),
+// M4 = sum U GB, M3 = sum U GA into mo[0..2], mo[3..5], mo[6..8], mo[9..11]
+// (float32 per thread over its few lattice points).  The zero padding adds
+// exact zeros where a tap falls outside the tile, so the sums equal those of
+// a loop that skips them.
+template <int KXY>
+__device__ __forceinline__ void grad_lattice_moments(const TileInfo &ti, int kxy_rt, const float *gxy,
+                                                     const float *Cp, const float *G, int Lmax,
                                                      float mo[12])
 {
+    const int kxy = KXY >= 0 ? KXY : kxy_rt;
     const float cu = 0.5f * (float)(ti.w - 1), cv = 0.5f * (float)(ti.h - 1);
+    const int cw = cpad_w(ti, kxy);
 #pragma unroll
     for (int k = 0; k < 12; ++k) mo[k] = 0.f;
     for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) {
         const int lj = qdiv(lp, ti.rLw), li = lp - lj * ti.Lw;
+        const float *c0 = Cp + (lj + kxy) * cw + (li + kxy);
         float u = 0.f;
+#pragma unroll
         for (int dj = -kxy; dj <= kxy; ++dj) {
-            int cj = lj - kxy - dj;
-            if (cj < 0 || cj >= ti.th) continue;
             float rr = 0.f;
-            for (int di = -kxy; di <= kxy; ++di) {
-                int ci = li - kxy - di;
-                if (ci < 0 || ci >= ti.tw) continue;
-                rr = fmaf(gxy[di + kxy], C[cj * ti.tw + ci], rr);
-            }
+#pragma unroll
+            for (int di = -kxy; di <= kxy; ++di) rr = fmaf(gxy[di + kxy], c0[-dj * cw - di], rr);
             u = fmaf(gxy[dj + kxy], rr, u);
         }
         if (u == 0.f) continue;
@@ -1382,6 +1480,7 @@ __global__ void __launch_bounds__(256) k_ncc_grad(VolDims vd, const DevGeom *__r
     lattice_forward<KZ>(PlainVol{nullptr}, vd, ti, kxy, kz, psf.gz[ti.stack], kAlongCol, nullptr, U);
     __syncthreads();
     const float a_sc = sh_coef[0], b_sc = sh_coef[1], my = sh_coef[2], ms = sh_coef[3];
+    cpad_border(ti, kxy, C);
     for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
         const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
         size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
@@ -1390,15 +1489,13 @@ __global__ void __launch_bounds__(256) k_ncc_grad(VolDims vd, const DevGeom *__r
             float den = inplane(U, ti.Lw, kxy, psf.gxy, ci, cj);
             c = (a_sc * (__ldg(y + o) - my) - b_sc * (s_buf[o] - ms)) / den;
         }
-        C[pp] = c;
+        C[cpad_at(ti, kxy, ci, cj)] = c;
     }
     __syncthreads();
     float mo[12];
-    grad_lattice_moments(ti, kxy, psf.gxy, C, gbuf + (size_t)blockIdx.x * 6 * Lmax, Lmax, mo);
+    grad_lattice_moments<KXY>(ti, kxy, psf.gxy, C, gbuf + (size_t)blockIdx.x * 6 * Lmax, Lmax, mo);
     double mom[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) mom[k] = (double)mo[k];
-    block_sum<12>(mom, red);
+    block_sum_fd<12>(mo, mom, red);
     if (threadIdx.x == 0) {
         for (int k = 0; k < 12; ++k) gp[k] = mom[k];
         for (int k = 12; k < kGradStride; ++k) gp[k] = 0.0;
@@ -1455,12 +1552,14 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
         FFSum f1, f2, f3, f4, f5;
         int cnt = 0;
         const int np = ti.tw * ti.th;
+        cpad_border(ti, kxy, C);
         for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
             const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
             const float den = inplane(B, ti.Lw, kxy, psf.gxy, ci, cj);
             const size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
             if (den > 0.f && member_ok(tl, o)) {
                 const float sv = inplane(A, ti.Lw, kxy, psf.gxy, ci, cj) / den;
+                C[cpad_at(ti, kxy, ci, cj)] = sv;   // kept for the gradient pass
                 const float a = __ldg(y + o);
                 ++cnt;
                 f1.add(a);
@@ -1470,8 +1569,9 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
                 f5.add_prod(a, sv);
             }
         }
-        double m[6] = {(double)cnt, f1.value(), f2.value(), f3.value(), f4.value(), f5.value()};
-        block_sum<6>(m, red);
+        FFSum fs[6] = {FFSum{(float)cnt, 0.f}, f1, f2, f3, f4, f5};   // counts <= 2^24: exact
+        double m[6];
+        block_sum_ff<6>(fs, m, red);
         if (threadIdx.x == 0) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) pt[k] = m[k];
@@ -1499,20 +1599,16 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
             const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
             const float den = inplane(B, ti.Lw, kxy, psf.gxy, ci, cj);
             const size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
+            const int at = cpad_at(ti, kxy, ci, cj);
             float c = 0.f;
-            if (den > 0.f && member_ok(tl, o)) {
-                const float sv = inplane(A, ti.Lw, kxy, psf.gxy, ci, cj) / den;
-                c = (a_sc * (__ldg(y + o) - my) - b_sc * (sv - ms)) / den;
-            }
-            C[pp] = c;
+            if (den > 0.f && member_ok(tl, o)) c = (a_sc * (__ldg(y + o) - my) - b_sc * (C[at] - ms)) / den;
+            C[at] = c;
         }
         __syncthreads();
         float mo[12];
-        grad_lattice_moments(ti, kxy, psf.gxy, C, G, Gs, mo);
+        grad_lattice_moments<KXY>(ti, kxy, psf.gxy, C, G, Gs, mo);
         double mom[12];
-#pragma unroll
-        for (int k = 0; k < 12; ++k) mom[k] = (double)mo[k];
-        block_sum<12>(mom, red);   // ends with a barrier: A, B, C, G free for the next tile
+        block_sum_fd<12>(mo, mom, red);   // ends with a barrier: A, B, C, G free for the next tile
         if (threadIdx.x == 0) {
             for (int k = 0; k < 12; ++k) gp[k] = mom[k];
             for (int k = 12; k < kGradStride; ++k) gp[k] = 0.0;
@@ -1559,21 +1655,20 @@ __global__ void __launch_bounds__(256, 4) k_pose_vjp(const SRC x, VolDims vd,
             moments_gather<KZ, false, SRC>(x, vd, ti, kxy, kz, order, gz, A, B, G, Gs);
         __syncthreads();
         const int np = ti.tw * ti.th;
+        cpad_border(ti, kxy, C);
         for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
             const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
             const float den = inplane(B, ti.Lw, kxy, psf.gxy, ci, cj);
             const size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
             float c = 0.f;
             if (den > 0.f && member_ok(tl, o)) c = __ldg(r + o) / den;
-            C[pp] = c;
+            C[cpad_at(ti, kxy, ci, cj)] = c;
         }
         __syncthreads();
         float mo[12];
-        grad_lattice_moments(ti, kxy, psf.gxy, C, G, Gs, mo);
+        grad_lattice_moments<KXY>(ti, kxy, psf.gxy, C, G, Gs, mo);
         double mom[12];
-#pragma unroll
-        for (int k = 0; k < 12; ++k) mom[k] = (double)mo[k];
-        block_sum<12>(mom, red);   // ends with a barrier: A, B, C, G free for the next tile
+        block_sum_fd<12>(mo, mom, red);   // ends with a barrier: A, B, C, G free for the next tile
         if (threadIdx.x == 0) {
             for (int k = 0; k < 12; ++k) gp[k] = mom[k];
             for (int k = 12; k < kGradStride; ++k) gp[k] = 0.0;
@@ -1780,7 +1875,8 @@ cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &t
     const QuadVol x{quad};
     size_t smem = smem_forward(tl, psf.kxy);
     const int Lmax = (tl.T + 2 * psf.kxy) * (tl.T + 2 * psf.kxy);
-    size_t smem2 = (size_t)(Lmax + tl.T * tl.T) * sizeof(float);
+    const int Cmax = (tl.T + 4 * psf.kxy) * (tl.T + 4 * psf.kxy);   // padded coefficient array
+    size_t smem2 = (size_t)(Lmax + Cmax) * sizeof(float);
     const long long total = (long long)n * tl.tpp;
     const bool fast = psf.kxy == 1 && psf.kz == 3;
     cudaError_t e;
@@ -1790,7 +1886,7 @@ cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &t
         // (about 60 MB) then share L2 with 50 MB of volume instead of the
         // 200 MB quad copy, and stay on chip.
         const PlainVol xp{xplain};
-        size_t smem3 = (size_t)(2 * Lmax + tl.T * tl.T) * sizeof(float);
+        size_t smem3 = (size_t)(2 * Lmax + Cmax) * sizeof(float);
         int dev = 0, nsm = 0, per_sm = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
@@ -1857,7 +1953,8 @@ cudaError_t launch_pose_vjp(const PsfTab &psf, const Tiling &tl, int nx, int ny,
     const PlainVol x{xplain};
     const int Lmax = (tl.T + 2 * psf.kxy) * (tl.T + 2 * psf.kxy);
     const long long total = (long long)n * tl.tpp;
-    const size_t smem = (size_t)(2 * Lmax + tl.T * tl.T) * sizeof(float);
+    const int Cmax = (tl.T + 4 * psf.kxy) * (tl.T + 4 * psf.kxy);   // padded coefficient array
+    const size_t smem = (size_t)(2 * Lmax + Cmax) * sizeof(float);
     const bool fast = psf.kxy == 1 && psf.kz == 3;
     int dev = 0, nsm = 0, per_sm = 0;
     cudaError_t e;
