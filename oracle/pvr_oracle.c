@@ -109,8 +109,10 @@ enum {
 /* sin and cos of an angle in degrees.  Reduction to r in [-45, 45] degrees by
  * the nearest multiple of 90, then the Maclaurin series of sin and cos in
  * nested (Horner) form, truncated after the x^23 / x^22 terms (remainder
- * below 1e-26 for |x| <= pi/4).  Only IEEE +,-,*,/ are used, in a fixed
- * order, so the result is reproducible bit for bit on any IEEE machine. */
+ * below 1e-26 for |x| <= pi/4); each nesting step multiplies by the correctly
+ * rounded reciprocal of its integer denominator.  Only IEEE +,-,*,/ are used,
+ * in a fixed order, so the result is reproducible bit for bit on any IEEE
+ * machine. */
 static void or_sincos_deg(double deg, double *s_out, double *c_out)
 {
     double k = nearbyint(deg / 90.0);
@@ -119,8 +121,8 @@ static void or_sincos_deg(double deg, double *s_out, double *c_out)
     double x2 = x * x;
     double ts = 1.0, tc = 1.0;
     for (int n = 11; n >= 1; --n) {
-        ts = 1.0 - (x2 * ts) / (double)((2 * n) * (2 * n + 1));
-        tc = 1.0 - (x2 * tc) / (double)((2 * n - 1) * (2 * n));
+        ts = 1.0 - (x2 * ts) * (1.0 / (double)((2 * n) * (2 * n + 1)));
+        tc = 1.0 - (x2 * tc) * (1.0 / (double)((2 * n - 1) * (2 * n)));
     }
     double sr = x * ts, cr = tc;
     long q = ((long)fmod(k, 4.0) + 4) % 4;

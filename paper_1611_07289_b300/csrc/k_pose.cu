@@ -16,10 +16,26 @@ __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a,
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
 
+// One nesting step N of the sine and cosine series and the steps below it:
+// ts <- 1 - x^2 ts / ((2N)(2N+1)), tc <- 1 - x^2 tc / ((2N-1)(2N)), each
+// division a multiplication by the correctly rounded reciprocal of the
+// integer denominator (a compile-time IEEE double constant).
+template <int N>
+__device__ __forceinline__ void series_steps(double x2, double &ts, double &tc)
+{
+    constexpr double is = 1.0 / (double)((2 * N) * (2 * N + 1));
+    constexpr double ic = 1.0 / (double)((2 * N - 1) * (2 * N));
+    ts = dsub(1.0, dmul(dmul(x2, ts), is));
+    tc = dsub(1.0, dmul(dmul(x2, tc), ic));
+    if constexpr (N > 1) series_steps<N - 1>(x2, ts, tc);
+}
+
 // sin, cos of an angle in degrees: nearest multiple k of 90 degrees, rest
 // r in [-45, 45] degrees, x = r * pi/180, then sin x = x (1 - x^2/(2*3) (1 -
 // x^2/(4*5) (...))) and cos x = 1 - x^2/(1*2) (1 - x^2/(3*4) (...)) with 11
-// nested factors each (truncation error < 1e-26 for |x| <= pi/4); the
+// nested factors each (truncation error < 1e-26 for |x| <= pi/4), every
+// factor a multiplication by the correctly rounded reciprocal of its
+// denominator (float64 division is a long instruction sequence); the
 // quadrant k mod 4 permutes and negates the pair.
 __device__ void sincos_deg_series(double deg, double *s_out, double *c_out)
 {
@@ -28,11 +44,7 @@ __device__ void sincos_deg_series(double deg, double *s_out, double *c_out)
     double x = dmul(r, 0.017453292519943295769);
     double x2 = dmul(x, x);
     double ts = 1.0, tc = 1.0;
-#pragma unroll
-    for (int n = 11; n >= 1; --n) {
-        ts = dsub(1.0, ddiv(dmul(x2, ts), (double)((2 * n) * (2 * n + 1))));
-        tc = dsub(1.0, ddiv(dmul(x2, tc), (double)((2 * n - 1) * (2 * n))));
-    }
+    series_steps<11>(x2, ts, tc);
     double sr = dmul(x, ts), cr = tc;
     long long q = ((long long)fmod(k, 4.0) + 4) % 4;
     if (q == 0) { *s_out = sr; *c_out = cr; }
