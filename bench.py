@@ -10,7 +10,10 @@ dz = 0.75 mm.
 One step = one pvr_reconstruct_iter: 2 NCC evaluations of every patch with
 a registration accept/propose, the fixed-point lattice of the new poses,
 simulate + residual, EM weights with patch classification, weighted adjoint,
-SIRT update (every row of the hot-path table).  The patch table is built
+SIRT update (every row of the hot-path table).  The patches are one tile
+each, so the NCC kernels also leave the forward model and residual at each
+patch's best pose, and the super-resolution pass takes them from there
+instead of simulating a second time.  The patch table is built
 once before timing.  value = patch-pixels processed per second (all ranks).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]

@@ -815,39 +815,9 @@ __global__ void __launch_bounds__(256) k_simulate_q(const SRC x, VolDims vd,
 // ------------------------------------------------------------------ K4 --
 // Adjoint.  Pixel coefficients cr = w r / den, cw = w / den (valid pixels),
 // transposed in-plane taps into lattice weights U, U', then every in-volume
-// sample adds U g_z tri and U' g_z tri to its 8 voxels (float atomics).
-// Add one in-volume sample's contributions ar, aw (already times g_z) to the
-// 8 voxels of its cell: PAIR = interleaved (addon, conf) float2 pairs with one
-// vector reduction per voxel, otherwise two separate arrays.
-template <bool PAIR, bool FAST = false>
-__device__ __forceinline__ void scatter_sample(const VolDims &vd, unsigned qx, unsigned qy,
-                                               unsigned qz, float ar, float aw, float *addon,
-                                               float *conf)
-{
-    int bx, by, bz;
-    float fx, fy, fz;
-    split<FAST>(qx, vd.nx, bx, fx);
-    split<FAST>(qy, vd.ny, by, fy);
-    split<FAST>(qz, vd.nz, bz, fz);
-    const size_t nxy = (size_t)vd.nx * vd.ny;
-    size_t base = (size_t)bz * nxy + (size_t)by * vd.nx + bx;
-    float wx[2] = {1.f - fx, fx}, wy[2] = {1.f - fy, fy}, wz[2] = {1.f - fz, fz};
-#pragma unroll
-    for (int cz = 0; cz < 2; ++cz)
-#pragma unroll
-        for (int cy = 0; cy < 2; ++cy)
-#pragma unroll
-            for (int cx = 0; cx < 2; ++cx) {
-                float t = wx[cx] * wy[cy] * wz[cz];
-                size_t idx = base + cz * nxy + cy * vd.nx + cx;
-                if (PAIR) {
-                    atomicAdd(reinterpret_cast<float2 *>(addon) + idx, make_float2(ar * t, aw * t));
-                } else {
-                    if (addon) atomicAdd(addon + idx, ar * t);
-                    if (conf) atomicAdd(conf + idx, aw * t);
-                }
-            }
-}
+// sample adds U g_z tri and U' g_z tri to its 8 voxels (float atomics;
+// PAIR = interleaved (addon, conf) float2 pairs with one vector reduction
+// per voxel, otherwise two separate arrays).
 
 // Phase 3 of the adjoint: scatter of every in-volume sample of the tile in
 // its traversal order (FAST: interior tile, no in-volume tests).
@@ -887,20 +857,90 @@ __device__ __forceinline__ void adjoint_scatter(const VolDims &vd, const TileInf
             }
         }
     } else {
+        // eight lanes per lattice point, one per through-plane sample; the
+        // samples step mostly along x here, so lane zl + 1's cell usually
+        // starts one voxel after lane zl's: its four low-x corners are lane
+        // zl's four high-x corners, added there before the reductions
+        // (exact index comparison, as in face_red_warp)
+        const unsigned full = 0xffffffffu;
         const int zl = threadIdx.x & 7, zeta = zl - kz;
-        if (zl <= 2 * kz) {
-            const float g = gz[zl];
-            for (int lp = threadIdx.x >> 3; lp < ti.L; lp += blockDim.x >> 3) {
-                float ur = U[lp], uw = Uw[lp];
-                if (ur == 0.f && uw == 0.f) continue;
+        const bool zon = zl <= 2 * kz;
+        const float g = zon ? gz[zl] : 0.f;
+        const int ngrp = blockDim.x >> 3;
+        const unsigned nx = (unsigned)vd.nx, nxy = vd.nxy;
+        for (int base = 0; base < ti.L; base += ngrp) {
+            const int lp = base + (threadIdx.x >> 3);
+            bool valid = false;
+            unsigned idx = 0xffffffffu;
+            float cr[2][2][2], cw[2][2][2];   // [z][y][x] corner contributions
+            if (zon && lp < ti.L) {
+                const float ur = U[lp], uw = Uw[lp];
                 unsigned q[3];
                 const int lj = qdiv(lp, ti.rLw);
                 lattice_pos(ti, kxy, lp - lj * ti.Lw, lj, q);
-                unsigned qx = q[0] + (unsigned)zeta * ti.ez[0];
-                unsigned qy = q[1] + (unsigned)zeta * ti.ez[1];
-                unsigned qz = q[2] + (unsigned)zeta * ti.ez[2];
-                if (FAST || inside(vd, qx, qy, qz)) scatter_sample<PAIR, FAST>(vd, qx, qy, qz, g * ur, g * uw, addon, conf);
+                const unsigned qx = q[0] + (unsigned)zeta * ti.ez[0];
+                const unsigned qy = q[1] + (unsigned)zeta * ti.ez[1];
+                const unsigned qz = q[2] + (unsigned)zeta * ti.ez[2];
+                valid = (ur != 0.f || uw != 0.f) && (FAST || inside(vd, qx, qy, qz));
+                if (valid) {
+                    int bx, by, bz;
+                    float fx, fy, fz;
+                    split<FAST>(qx, vd.nx, bx, fx);
+                    split<FAST>(qy, vd.ny, by, fy);
+                    split<FAST>(qz, vd.nz, bz, fz);
+                    idx = ((unsigned)bz * (unsigned)vd.ny + (unsigned)by) * nx + (unsigned)bx;
+                    const float wx[2] = {1.f - fx, fx}, wy[2] = {1.f - fy, fy}, wz[2] = {1.f - fz, fz};
+                    const float ar = g * ur, aw = g * uw;
+#pragma unroll
+                    for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+                        for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+                            for (int cx = 0; cx < 2; ++cx) {
+                                const float t = wx[cx] * wy[cy] * wz[cz];
+                                cr[cz][cy][cx] = ar * t;
+                                cw[cz][cy][cx] = aw * t;
+                            }
+                }
             }
+            if (!__any_sync(full, valid)) continue;
+            if (!valid) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) cr[c >> 1][c & 1][0] = cw[c >> 1][c & 1][0] = 0.f;
+            }
+            const unsigned nkey = __shfl_down_sync(full, idx, 1, 8);
+            float nr[4], nw[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                nr[c] = __shfl_down_sync(full, cr[c >> 1][c & 1][0], 1, 8);
+                nw[c] = __shfl_down_sync(full, cw[c >> 1][c & 1][0], 1, 8);
+            }
+            const bool take = valid && zl < 7 && nkey == idx + 1u;
+            if (take) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    cr[c >> 1][c & 1][1] += nr[c];
+                    cw[c >> 1][c & 1][1] += nw[c];
+                }
+            }
+            const bool given = __shfl_up_sync(full, take, 1, 8) && zl > 0;
+            if (!valid) continue;
+#pragma unroll
+            for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+                for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+                    for (int cx = 0; cx < 2; ++cx) {
+                        if (cx == 0 && given) continue;
+                        const unsigned at = idx + (unsigned)cz * nxy + (unsigned)cy * nx + (unsigned)cx;
+                        if (PAIR) {
+                            atomicAdd(reinterpret_cast<float2 *>(addon) + at,
+                                      make_float2(cr[cz][cy][cx], cw[cz][cy][cx]));
+                        } else {
+                            if (addon) atomicAdd(addon + at, cr[cz][cy][cx]);
+                            if (conf) atomicAdd(conf + at, cw[cz][cy][cx]);
+                        }
+                    }
         }
     }
 }
@@ -1021,6 +1061,88 @@ __global__ void __launch_bounds__(256, 3) k_adjoint_q(VolDims vd, const int32_t 
         adjoint_tile<KXY, KZ, PAIR>(items[it], vd, desc, fix, psf, tl, r, w, pmask, pweight, addon, conf,
                                     sm);
         __syncthreads();
+    }
+}
+
+__device__ __noinline__ bool ncc_of_sums(const double m[6], int min_valid, double &ncc, double &my, double &ms,
+                                         double &sd, double &vs, double &n);
+
+// Forward model of a tile at the evaluated pose, written as the forward-model
+// kernel writes it (BestSim): per pixel e = y - s and the valid flag, per tile
+// {N, sum e^2, min e, max e} from the same per-thread order and reductions.
+// sv(ci, cj) gives the simulated value of a valid pixel; B holds the PSF
+// weights of the tile lattice.  sred: shared scratch of 128 floats.  Every
+// thread of the block calls it; ends with a barrier.
+template <class SV>
+__device__ __forceinline__ void best_write(const TileInfo &ti, const Tiling &tl, int kxy, const float *gxy,
+                                           const float *B, SV sv, const float *__restrict__ y, const BestSim &bs,
+                                           long long gid, float *sred)
+{
+    float se2 = 0.f, emin = INFINITY, emax = -INFINITY;
+    int nval = 0;
+    const int np = ti.tw * ti.th;
+    for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
+        const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
+        const float den = inplane(B, ti.Lw, kxy, gxy, ci, cj);
+        const size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
+        const bool v = den > 0.f && member_ok(tl, o);
+        const float s = v ? sv(ci, cj, den) : 0.f;
+        const float e = v ? __ldg(y + o) - s : 0.f;
+        bs.e[o] = e;
+        bs.valid[o] = v ? 1 : 0;
+        if (v) {
+            se2 = fmaf(e, e, se2);
+            emin = fminf(emin, e);
+            emax = fmaxf(emax, e);
+            ++nval;
+        }
+    }
+    float acc[2] = {(float)nval, se2};
+    const float mn = warp_min(emin), mx = warp_max(emax);
+    float *rmn = sred + 64, *rmx = sred + 96;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        rmn[wid] = mn;
+        rmx[wid] = mx;
+    }
+    block_sum_f<2>(acc, sred);
+    if (threadIdx.x == 0) {
+        float a = INFINITY, b = -INFINITY;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a = fminf(a, rmn[w]);
+            b = fmaxf(b, rmx[w]);
+        }
+        double *pt = bs.part + (size_t)gid * kPartStride;
+        pt[0] = (double)acc[0];
+        pt[1] = (double)acc[1];
+        pt[2] = (double)a;
+        pt[3] = (double)b;
+    }
+    __syncthreads();
+}
+
+// best_write for a tile without samples: a table slot without a tile (the
+// forward-model kernel zeroes its partials) or a pose outside the
+// fixed-point range (every pixel invalid).
+__device__ __forceinline__ void best_write_empty(bool has, const TileInfo &ti, const BestSim &bs, long long gid)
+{
+    double *pt = bs.part + (size_t)gid * kPartStride;
+    if (!has) {
+        if (threadIdx.x < kPartStride) pt[threadIdx.x] = 0.0;
+        return;
+    }
+    const int np = ti.tw * ti.th;
+    for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
+        const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
+        const size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
+        bs.e[o] = 0.f;
+        bs.valid[o] = 0;
+    }
+    if (threadIdx.x == 0) {
+        pt[0] = 0.0;
+        pt[1] = 0.0;
+        pt[2] = (double)INFINITY;
+        pt[3] = (double)-INFINITY;
     }
 }
 
@@ -1171,10 +1293,12 @@ __global__ void __launch_bounds__(256, 4) k_ncc_moments(const SRC x, VolDims vd,
                                                      float *__restrict__ s_buf,
                                                      uint8_t *__restrict__ v_buf,
                                                      double *__restrict__ part,
-                                                     float *__restrict__ gbuf, int Lmax)
+                                                     float *__restrict__ gbuf, int Lmax, int min_valid,
+                                                     BestSim bs)
 {
     extern __shared__ float sm[];
     __shared__ double red[32 * 6];
+    __shared__ int sh_best;
     const int kxy = KXY >= 0 ? KXY : psf.kxy;
     const int kz = KZ >= 0 ? KZ : psf.kz;
     const long long gid = tile_base + blockIdx.x;
@@ -1183,6 +1307,7 @@ __global__ void __launch_bounds__(256, 4) k_ncc_moments(const SRC x, VolDims vd,
     double *pt = part + (size_t)gid * kPartStride;
     if (!has || (active && !active[ti.p])) {
         if (threadIdx.x < kPartStride) pt[threadIdx.x] = 0.0;
+        if (bs.mode == 1 && !has) best_write_empty(has, ti, bs, gid);
         return;
     }
     float *A = sm, *B = sm + ti.L;
@@ -1235,12 +1360,30 @@ __global__ void __launch_bounds__(256, 4) k_ncc_moments(const SRC x, VolDims vd,
 #pragma unroll
         for (int k = 0; k < 6; ++k) pt[k] = m[k];
         pt[6] = pt[7] = 0.0;
+        if (bs.mode) {   // one-tile patches only: the tile's sums are the patch's
+            double ncc, my, ms, sd, vs, n;
+            const bool ok = ncc_of_sums(m, min_valid, ncc, my, ms, sd, vs, n);
+            sh_best = bs.mode == 1 || (bs.mode == 2 && (bs.fixed || (ok ? ncc : 0.0) > bs.nbest[ti.p]));
+        }
+    }
+    if (bs.mode) {
+        __syncthreads();
+        if (sh_best) {
+            if (ti.ok)
+                best_write(ti, tl, kxy, psf.gxy, B,
+                           [&](int ci, int cj, float den) { return inplane(A, ti.Lw, kxy, psf.gxy, ci, cj) / den; },
+                           y, bs, gid, reinterpret_cast<float *>(red));
+            else
+                best_write_empty(true, ti, bs, gid);
+        }
     }
 }
 
 // NCC of a patch from its tile moments (float64).  Returns false when
-// degenerate (fewer than min_valid pixels or a constant patch).
-__device__ bool ncc_of_sums(const double m[6], int min_valid, double &ncc, double &my, double &ms,
+// degenerate (fewer than min_valid pixels or a constant patch).  Not inlined:
+// the NCC kernels' acceptance test and k_ncc_finish must run the same
+// instructions on the same sums.
+__device__ __noinline__ bool ncc_of_sums(const double m[6], int min_valid, double &ncc, double &my, double &ms,
                             double &sd, double &vs, double &n)
 {
     n = m[0];
@@ -1520,12 +1663,12 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
                                                       double *__restrict__ part,
                                                       double *__restrict__ gpart,
                                                       float *__restrict__ scratch, int Lmax,
-                                                      int min_valid)
+                                                      int min_valid, BestSim bs)
 {
     extern __shared__ float sm[];
     __shared__ double red[32 * 12];
     __shared__ float sh_coef[4];
-    __shared__ int sh_ok;
+    __shared__ int sh_ok, sh_best;
     const int kxy = KXY >= 0 ? KXY : psf.kxy;
     const int kz = KZ >= 0 ? KZ : psf.kz;
     const int Gs = slot_stride(Lmax);
@@ -1540,6 +1683,7 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
         if (!has || !ti.ok || (active && !active[ti.p])) {
             if (threadIdx.x < kPartStride) pt[threadIdx.x] = 0.0;
             if (threadIdx.x < kGradStride) gp[threadIdx.x] = 0.0;
+            if (bs.mode == 1 && (!has || !ti.ok)) best_write_empty(has, ti, bs, gid);
             continue;
         }
         const float *gz = psf.gz[ti.stack];
@@ -1585,8 +1729,13 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
                 sh_coef[2] = (float)my;
                 sh_coef[3] = (float)ms;
             }
+            // the registration's acceptance test on the NCC k_ncc_finish reports
+            sh_best = bs.mode == 1 || (bs.mode == 2 && (bs.fixed || (ok ? ncc : 0.0) > bs.nbest[ti.p]));
         }
         __syncthreads();
+        if (sh_best)
+            best_write(ti, tl, kxy, psf.gxy, B, [&](int ci, int cj, float) { return C[cpad_at(ti, kxy, ci, cj)]; },
+                       y, bs, gid, reinterpret_cast<float *>(red));
         if (!sh_ok) {
             if (threadIdx.x < kGradStride) gp[threadIdx.x] = 0.0;
             discard_slot(G, Gs);
@@ -1868,8 +2017,13 @@ cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &t
                             const int32_t *desc, const int32_t *fix, const double *poses, int n,
                             float *s_buf,
                             uint8_t *v_buf, double *part, double *gpart, const int32_t *active,
-                            int min_valid, float *gbuf, long long gbuf_tiles, cudaStream_t st)
+                            int min_valid, float *gbuf, long long gbuf_tiles, cudaStream_t st,
+                            const BestSim &bs_in)
 {
+    // the best-pose forward model is kept for one-tile patches only (the
+    // acceptance test needs the whole patch's NCC inside the tile's block)
+    BestSim bs = bs_in;
+    if (tl.tpp != 1) bs.mode = 0;
     if (n <= 0) return cudaSuccess;
     VolDims vd = vol_dims(nx, ny, nz);
     const QuadVol x{quad};
@@ -1905,11 +2059,11 @@ cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &t
         if (grid <= 0) return cudaErrorInvalidValue;
         if (fast)
             k_ncc_fused<1, 3, PlainVol><<<(unsigned)grid, 256, smem3, st>>>(xp, vd, desc, fix, psf, tl, total, y, active,
-                                                                  part, gpart, gbuf, Lmax, min_valid);
+                                                                  part, gpart, gbuf, Lmax, min_valid, bs);
         else
             k_ncc_fused<-1, -1, PlainVol><<<(unsigned)grid, 256, smem3, st>>>(xp, vd, desc, fix, psf, tl, total, y,
                                                                     active, part, gpart, gbuf, Lmax,
-                                                                    min_valid);
+                                                                    min_valid, bs);
         return cudaGetLastError();
     }
     // chunks of whole patches that fit the gradient scratch
@@ -1928,10 +2082,10 @@ cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &t
         float *gb = gpart ? gbuf : nullptr;
         if (fast)
             k_ncc_moments<1, 3, QuadVol><<<grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, base, y, active, s_buf,
-                                                         v_buf, part, gb, Lmax);
+                                                         v_buf, part, gb, Lmax, min_valid, bs);
         else
             k_ncc_moments<-1, -1, QuadVol><<<grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, base, y, active,
-                                                           s_buf, v_buf, part, gb, Lmax);
+                                                           s_buf, v_buf, part, gb, Lmax, min_valid, bs);
         if (!gpart) continue;
         if (fast)
             k_ncc_grad<1, 3><<<grid, 256, smem2, st>>>(vd, g, desc, fix, psf, tl, base, y, poses, active,

@@ -58,6 +58,7 @@ struct pvr_ctx {
     DevGeom *d_geom = nullptr;
     int32_t *fix = nullptr;
     double *part = nullptr, *gpart = nullptr, *pstat = nullptr;
+    double *epart = nullptr;   // EM tile partials of the forward model kept by the registration
     double *pbar = nullptr, *wsc = nullptr, *emblk = nullptr;
     uint8_t *elig = nullptr;
     int32_t *err = nullptr;
@@ -219,7 +220,7 @@ cudaError_t dalloc(T **p, size_t n)
 
 void free_all(pvr_ctx *c)
 {
-    void *ptrs[] = {c->d_geom, c->fix, c->part, c->gpart, c->pstat, c->pbar, c->wsc, c->emblk, c->elig,
+    void *ptrs[] = {c->d_geom, c->fix, c->part, c->epart, c->gpart, c->pstat, c->pbar, c->wsc, c->emblk, c->elig,
                     c->err, c->best, c->gbest, c->nbest, c->trial, c->delta, c->ncc_tmp,
                     c->grad_tmp, c->active, c->s_buf, c->e_buf, c->p_buf, c->v_buf,
                     c->valid_buf, c->mask_tmp, c->acc2, c->quad, c->gbuf, c->keep, c->imax_key,
@@ -414,6 +415,7 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
     ALLOC(c->d_geom, 1);
     ALLOC(c->fix, P * kFixStride);
     ALLOC(c->part, slots);
+    ALLOC(c->epart, P * kPartStride);
     ALLOC(c->gpart, P * (size_t)c->tpp_alloc * kGradStride);
     ALLOC(c->plan_items, P * (size_t)c->tpp_alloc);
     ALLOC(c->plan_counter, 4);
@@ -794,12 +796,27 @@ int pvr_pose_grad(pvr_ctx *c, const float *x, const float *r, const pvr_patches 
 }
 
 // Registration rounds; gathers from c->quad, which the caller has built from x.
+// keep_best: for one-tile patches, the NCC kernels also leave the forward
+// model at each patch's best pose in e_buf, valid_buf and epart (BestSim);
+// *kept tells whether they did.
 static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_patches *pp, int ms,
-                         double *poses, int n_evals, double *ncc_out, cudaStream_t st)
+                         double *poses, int n_evals, double *ncc_out, cudaStream_t st,
+                         bool keep_best = false, bool *kept = nullptr)
 {
     int n = pp->n;
+    if (kept) *kept = false;
     if (n == 0 || n_evals <= 0) return PVR_OK;
     Tiling tl = make_tiling(ms, pp);
+    keep_best = keep_best && tl.tpp == 1;
+    BestSim bs;
+    if (keep_best) {
+        bs.mode = 1;
+        bs.e = c->e_buf;
+        bs.valid = c->valid_buf;
+        bs.part = c->epart;
+        bs.nbest = c->nbest;
+        bs.fixed = c->prm.reg_fixed_step != 0;
+    }
     CUDA_TRY(launch_reg_init(poses, n, c->best, c->trial, c->delta, c->active, c->prm.reg_delta0, st),
              "reg_init");
     c->launches += 1;
@@ -813,8 +830,9 @@ static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_p
         CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, c->quad, y,
                                  pp->desc, c->fix, c->trial, n, c->s_buf, c->v_buf, c->part,
                                  gpart, c->active, c->prm.reg_min_valid, c->gbuf, c->gbuf_tiles,
-                                 st),
+                                 st, bs),
                  "ncc_grad");
+        if (keep_best) bs.mode = 2;   // after the first evaluation: accepted trials only
         CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(c->d_geom, pp->desc, c->trial, n, tl, c->part, gpart, c->prm.reg_min_valid,
                                    c->ncc_tmp, grad, st),
                  "ncc_finish");
@@ -826,6 +844,7 @@ static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_p
     }
     CUDA_TRY(launch_reg_finish(c->best, c->nbest, n, poses, ncc_out, st), "reg_finish");
     c->launches += 1;
+    if (kept) *kept = keep_best;
     return PVR_OK;
 }
 
@@ -853,26 +872,35 @@ int pvr_reconstruct_iter(pvr_ctx *c, float *x, const float *y, const pvr_patches
     REQUIRE(x && y && state && mask && (pp->n == 0 || poses), "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = build_quad(c, x, st))) return rc;
-    if ((rc = register_impl(c, x, y, pp, ms, poses, c->prm.reg_evals, nullptr, st))) return rc;
-    if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
+    // one-tile patches under the super-resolution tiling too: the
+    // registration's NCC kernels keep the forward model at the final poses,
+    // and the first pass below reuses it instead of simulating again
     Tiling tl = make_tiling(ms, pp);
     WorkQueue wqs;
     const WorkQueue *wq = plan_for(c, pp, ms, &tl, &wqs);
+    bool kept = false;
+    if ((rc = register_impl(c, x, y, pp, ms, poses, c->prm.reg_evals, nullptr, st, tl.tpp == 1, &kept)))
+        return rc;
+    if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     CUDA_TRY(cudaMemsetAsync(c->acc2, 0, (size_t)c->nvox * sizeof(float2), st), "clear");
     for (int it = 0; it < c->prm.n_sr; ++it) {
         // x changes with every SR pass: refresh its quad copy after the first
         if (it > 0 && (rc = build_quad(c, x, st))) return rc;
         // the work queue visits non-empty tiles only: empty slots of the EM
         // partials must read as zero
-        if (wq)
-            CUDA_TRY(cudaMemsetAsync(c->part, 0, (size_t)pp->n * tl.tpp * kPartStride * sizeof(double), st),
-                     "clear partials");
-        CUDA_TRY_T(PVR_K_SIMULATE, launch_simulate(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x,
-                                                   c->quad, pp->desc, c->fix, pp->n, y, c->e_buf,
-                                                   c->valid_buf, c->part, st, wq),
-                 "simulate");
+        const bool reuse = it == 0 && kept;
+        double *part = reuse ? c->epart : c->part;
+        if (!reuse) {
+            if (wq)
+                CUDA_TRY(cudaMemsetAsync(c->part, 0, (size_t)pp->n * tl.tpp * kPartStride * sizeof(double), st),
+                         "clear partials");
+            CUDA_TRY_T(PVR_K_SIMULATE, launch_simulate(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x,
+                                                       c->quad, pp->desc, c->fix, pp->n, y, c->e_buf,
+                                                       c->valid_buf, c->part, st, wq),
+                     "simulate");
+        }
         CUDA_TRY_T(PVR_K_EM, launch_em(c->e_buf, nullptr, c->valid_buf, pp->desc, pp->n, pp->n_pix, tl, c->err,
-                           state, mask, c->mask_tmp, c->p_buf, w_patch, nullptr, c->part, c->pstat,
+                           state, mask, c->mask_tmp, c->p_buf, w_patch, nullptr, part, c->pstat,
                            c->pbar, c->wsc, c->elig, c->emblk, c->prm, st),
                  "em");
         CUDA_TRY(cudaMemcpyAsync(mask, c->mask_tmp, (size_t)pp->n, cudaMemcpyDeviceToDevice, st),
@@ -883,7 +911,7 @@ int pvr_reconstruct_iter(pvr_ctx *c, float *x, const float *y, const pvr_patches
         CUDA_TRY_T(PVR_K_UPDATE, launch_volume_update_pairs(x, c->acc2, c->nvox, (float)c->prm.alpha,
                                       (float)c->prm.conf_eps, 1, 0, st),
                  "volume_update");
-        c->launches += (pp->n > 0 ? 3 : 1) + em_launch_count(pp->n, c->prm);
+        c->launches += (pp->n > 0 ? (reuse ? 2 : 3) : 1) + em_launch_count(pp->n, c->prm);
     }
     if (p && pp->n_pix > 0)
         CUDA_TRY(cudaMemcpyAsync(p, c->p_buf, (size_t)pp->n_pix * sizeof(float),

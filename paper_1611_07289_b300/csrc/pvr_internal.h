@@ -53,6 +53,22 @@ struct WorkQueue {
     int *counter = nullptr;
 };
 
+// Forward model at the best pose, kept by the registration for one-tile
+// patches so that the first super-resolution pass of the same iteration
+// need not simulate again: residual e = y - s, valid flag and the EM tile
+// partials {N, sum e^2, min e, max e}, as the forward-model kernel writes
+// them.  mode 0: off; 1: every evaluated tile (the first evaluation, at the
+// starting pose); 2: tiles whose NCC improves on nbest (the registration's
+// acceptance rule; every tile with fixed steps).
+struct BestSim {
+    float *e = nullptr;
+    uint8_t *valid = nullptr;
+    double *part = nullptr;
+    const double *nbest = nullptr;
+    int mode = 0;
+    int fixed = 0;
+};
+
 // Launchers (each returns cudaGetLastError() of its launches).
 cudaError_t launch_pose_to_fixed(const DevGeom *g, const int32_t *desc, const double *poses,
                                  int n, int64_t n_pix, int max_side, int kxy, int kz,
@@ -99,7 +115,8 @@ cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &t
                             const int32_t *desc, const int32_t *fix, const double *poses, int n,
                             float *s_buf,
                             uint8_t *v_buf, double *part, double *gpart, const int32_t *active,
-                            int min_valid, float *gbuf, long long gbuf_tiles, cudaStream_t st);
+                            int min_valid, float *gbuf, long long gbuf_tiles, cudaStream_t st,
+                            const BestSim &bs = BestSim());
 size_t ncc_gbuf_floats_per_tile(const Tiling &tl, int kxy);
 // Kernel launches launch_ncc_grad makes for these arguments.
 int ncc_launch_count(const Tiling &tl, int n, bool grad, long long gbuf_tiles);
