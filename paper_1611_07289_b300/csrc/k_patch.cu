@@ -1067,6 +1067,36 @@ __global__ void __launch_bounds__(256, 3) k_adjoint_q(VolDims vd, const int32_t 
 __device__ __noinline__ bool ncc_of_sums(const double m[6], int min_valid, double &ncc, double &my, double &ms,
                                          double &sd, double &vs, double &n);
 
+// EM tile partials {N, sum e^2, min e, max e} of a best_write tile from the
+// threads' own counts, sums and extremes (the forward-model kernel's
+// reductions).  sred: shared scratch of 128 floats.  Ends with a barrier.
+__device__ __forceinline__ void best_part(int nval, float se2, float emin, float emax, const BestSim &bs,
+                                          long long gid, float *sred)
+{
+    float acc[2] = {(float)nval, se2};
+    const float mn = warp_min(emin), mx = warp_max(emax);
+    float *rmn = sred + 64, *rmx = sred + 96;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        rmn[wid] = mn;
+        rmx[wid] = mx;
+    }
+    block_sum_f<2>(acc, sred);
+    if (threadIdx.x == 0) {
+        float a = INFINITY, b = -INFINITY;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a = fminf(a, rmn[w]);
+            b = fmaxf(b, rmx[w]);
+        }
+        double *pt = bs.part + (size_t)gid * kPartStride;
+        pt[0] = (double)acc[0];
+        pt[1] = (double)acc[1];
+        pt[2] = (double)a;
+        pt[3] = (double)b;
+    }
+    __syncthreads();
+}
+
 // Forward model of a tile at the evaluated pose, written as the forward-model
 // kernel writes it (BestSim): per pixel e = y - s and the valid flag, per tile
 // {N, sum e^2, min e, max e} from the same per-thread order and reductions.
@@ -1097,28 +1127,7 @@ __device__ __forceinline__ void best_write(const TileInfo &ti, const Tiling &tl,
             ++nval;
         }
     }
-    float acc[2] = {(float)nval, se2};
-    const float mn = warp_min(emin), mx = warp_max(emax);
-    float *rmn = sred + 64, *rmx = sred + 96;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-        rmn[wid] = mn;
-        rmx[wid] = mx;
-    }
-    block_sum_f<2>(acc, sred);
-    if (threadIdx.x == 0) {
-        float a = INFINITY, b = -INFINITY;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            a = fminf(a, rmn[w]);
-            b = fmaxf(b, rmx[w]);
-        }
-        double *pt = bs.part + (size_t)gid * kPartStride;
-        pt[0] = (double)acc[0];
-        pt[1] = (double)acc[1];
-        pt[2] = (double)a;
-        pt[3] = (double)b;
-    }
-    __syncthreads();
+    best_part(nval, se2, emin, emax, bs, gid, sred);
 }
 
 // best_write for a tile without samples: a table slot without a tile (the
@@ -1283,7 +1292,7 @@ __device__ __forceinline__ void moments_gather(const SRC src, const VolDims &vd,
 // trilinear gradient of every sample and streams, per lattice point,
 // GA = sum g_z grad and GB = sum g_z zeta grad (3 planes each, Lmax apart)
 // to gbuf for K6b, which therefore gathers nothing.
-template <int KXY, int KZ, class SRC>
+template <int KXY, int KZ, class SRC, bool KEEP>
 __global__ void __launch_bounds__(256, 4) k_ncc_moments(const SRC x, VolDims vd,
                                                      const int32_t *__restrict__ desc,
                                                      const int32_t *__restrict__ fix, PsfTab psf,
@@ -1307,7 +1316,7 @@ __global__ void __launch_bounds__(256, 4) k_ncc_moments(const SRC x, VolDims vd,
     double *pt = part + (size_t)gid * kPartStride;
     if (!has || (active && !active[ti.p])) {
         if (threadIdx.x < kPartStride) pt[threadIdx.x] = 0.0;
-        if (bs.mode == 1 && !has) best_write_empty(has, ti, bs, gid);
+        if (KEEP && bs.mode == 1 && !has) best_write_empty(has, ti, bs, gid);
         return;
     }
     float *A = sm, *B = sm + ti.L;
@@ -1332,6 +1341,8 @@ __global__ void __launch_bounds__(256, 4) k_ncc_moments(const SRC x, VolDims vd,
     FFSum f1, f2, f3, f4, f5;
     int cnt = 0;
     const int np = ti.tw * ti.th;
+    const bool keep_all = KEEP && bs.mode == 1;   // residuals written in this pass
+    float se2 = 0.f, emin = INFINITY, emax = -INFINITY;
     for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
         const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
         float num = inplane(A, ti.Lw, kxy, psf.gxy, ci, cj);
@@ -1343,6 +1354,7 @@ __global__ void __launch_bounds__(256, 4) k_ncc_moments(const SRC x, VolDims vd,
             s_buf[o] = sv;
             v_buf[o] = v ? 1 : 0;
         }
+        float e = 0.f;
         if (v) {
             float a = __ldg(y + o);
             ++cnt;
@@ -1351,8 +1363,19 @@ __global__ void __launch_bounds__(256, 4) k_ncc_moments(const SRC x, VolDims vd,
             f3.add_prod(a, a);
             f4.add_prod(sv, sv);
             f5.add_prod(a, sv);
+            if (KEEP) {
+                e = a - sv;
+                se2 = fmaf(e, e, se2);
+                emin = fminf(emin, e);
+                emax = fmaxf(emax, e);
+            }
+        }
+        if (keep_all) {
+            bs.e[o] = e;
+            bs.valid[o] = v ? 1 : 0;
         }
     }
+    if (keep_all) best_part(cnt, se2, emin, emax, bs, gid, reinterpret_cast<float *>(red));
     FFSum fs[6] = {FFSum{(float)cnt, 0.f}, f1, f2, f3, f4, f5};   // counts <= 2^24: exact
     double m[6];
     block_sum_ff<6>(fs, m, red);
@@ -1360,22 +1383,18 @@ __global__ void __launch_bounds__(256, 4) k_ncc_moments(const SRC x, VolDims vd,
 #pragma unroll
         for (int k = 0; k < 6; ++k) pt[k] = m[k];
         pt[6] = pt[7] = 0.0;
-        if (bs.mode) {   // one-tile patches only: the tile's sums are the patch's
+        if (KEEP && bs.mode) {   // one-tile patches only: the tile's sums are the patch's
             double ncc, my, ms, sd, vs, n;
             const bool ok = ncc_of_sums(m, min_valid, ncc, my, ms, sd, vs, n);
-            sh_best = bs.mode == 1 || (bs.mode == 2 && (bs.fixed || (ok ? ncc : 0.0) > bs.nbest[ti.p]));
+            sh_best = bs.mode == 2 && (bs.fixed || (ok ? ncc : 0.0) > bs.nbest[ti.p]);
         }
     }
-    if (bs.mode) {
+    if (KEEP && bs.mode == 2) {
         __syncthreads();
-        if (sh_best) {
-            if (ti.ok)
-                best_write(ti, tl, kxy, psf.gxy, B,
-                           [&](int ci, int cj, float den) { return inplane(A, ti.Lw, kxy, psf.gxy, ci, cj) / den; },
-                           y, bs, gid, reinterpret_cast<float *>(red));
-            else
-                best_write_empty(true, ti, bs, gid);
-        }
+        if (sh_best)
+            best_write(ti, tl, kxy, psf.gxy, B,
+                       [&](int ci, int cj, float den) { return inplane(A, ti.Lw, kxy, psf.gxy, ci, cj) / den; },
+                       y, bs, gid, reinterpret_cast<float *>(red));
     }
 }
 
@@ -1683,7 +1702,10 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
         if (!has || !ti.ok || (active && !active[ti.p])) {
             if (threadIdx.x < kPartStride) pt[threadIdx.x] = 0.0;
             if (threadIdx.x < kGradStride) gp[threadIdx.x] = 0.0;
+            // no samples: every pixel invalid, NCC 0 (accepted by the same rule)
             if (bs.mode == 1 && (!has || !ti.ok)) best_write_empty(has, ti, bs, gid);
+            if (bs.mode == 2 && has && !ti.ok && !(active && !active[ti.p]) && (bs.fixed || 0.0 > bs.nbest[ti.p]))
+                best_write_empty(true, ti, bs, gid);
             continue;
         }
         const float *gz = psf.gz[ti.stack];
@@ -1696,12 +1718,17 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
         FFSum f1, f2, f3, f4, f5;
         int cnt = 0;
         const int np = ti.tw * ti.th;
+        // first evaluation keeping the forward model: residuals written in this pass
+        const bool keep_all = bs.mode == 1;
+        float se2 = 0.f, emin = INFINITY, emax = -INFINITY;
         cpad_border(ti, kxy, C);
         for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
             const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
             const float den = inplane(B, ti.Lw, kxy, psf.gxy, ci, cj);
             const size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
-            if (den > 0.f && member_ok(tl, o)) {
+            const bool v = den > 0.f && member_ok(tl, o);
+            float e = 0.f;
+            if (v) {
                 const float sv = inplane(A, ti.Lw, kxy, psf.gxy, ci, cj) / den;
                 C[cpad_at(ti, kxy, ci, cj)] = sv;   // kept for the gradient pass
                 const float a = __ldg(y + o);
@@ -1711,8 +1738,17 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
                 f3.add_prod(a, a);
                 f4.add_prod(sv, sv);
                 f5.add_prod(a, sv);
+                e = a - sv;
+                se2 = fmaf(e, e, se2);
+                emin = fminf(emin, e);
+                emax = fmaxf(emax, e);
+            }
+            if (keep_all) {
+                bs.e[o] = e;
+                bs.valid[o] = v ? 1 : 0;
             }
         }
+        if (keep_all) best_part(cnt, se2, emin, emax, bs, gid, reinterpret_cast<float *>(red));
         FFSum fs[6] = {FFSum{(float)cnt, 0.f}, f1, f2, f3, f4, f5};   // counts <= 2^24: exact
         double m[6];
         block_sum_ff<6>(fs, m, red);
@@ -1730,7 +1766,7 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
                 sh_coef[3] = (float)ms;
             }
             // the registration's acceptance test on the NCC k_ncc_finish reports
-            sh_best = bs.mode == 1 || (bs.mode == 2 && (bs.fixed || (ok ? ncc : 0.0) > bs.nbest[ti.p]));
+            sh_best = bs.mode == 2 && (bs.fixed || (ok ? ncc : 0.0) > bs.nbest[ti.p]);
         }
         __syncthreads();
         if (sh_best)
@@ -2069,23 +2105,34 @@ cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &t
     // chunks of whole patches that fit the gradient scratch
     long long chunk = gpart ? (gbuf_tiles / tl.tpp) * tl.tpp : total;
     if (chunk <= 0) return cudaErrorInvalidValue;
+    const bool keep = bs.mode != 0;
     if (fast) {
-        if ((e = prep(k_ncc_moments<1, 3, QuadVol>, smem)) != cudaSuccess) return e;
+        if ((e = prep(k_ncc_moments<1, 3, QuadVol, false>, smem)) != cudaSuccess) return e;
+        if ((e = prep(k_ncc_moments<1, 3, QuadVol, true>, smem)) != cudaSuccess) return e;
         if ((e = prep(k_ncc_grad<1, 3>, smem2)) != cudaSuccess) return e;
     } else {
-        if ((e = prep(k_ncc_moments<-1, -1, QuadVol>, smem)) != cudaSuccess) return e;
+        if ((e = prep(k_ncc_moments<-1, -1, QuadVol, false>, smem)) != cudaSuccess) return e;
+        if ((e = prep(k_ncc_moments<-1, -1, QuadVol, true>, smem)) != cudaSuccess) return e;
         if ((e = prep(k_ncc_grad<-1, -1>, smem2)) != cudaSuccess) return e;
     }
     if (!gpart) s_buf = nullptr, v_buf = nullptr;
     for (long long base = 0; base < total; base += chunk) {
         unsigned grid = (unsigned)((total - base) < chunk ? (total - base) : chunk);
         float *gb = gpart ? gbuf : nullptr;
-        if (fast)
-            k_ncc_moments<1, 3, QuadVol><<<grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, base, y, active, s_buf,
-                                                         v_buf, part, gb, Lmax, min_valid, bs);
+        if (fast && keep)
+            k_ncc_moments<1, 3, QuadVol, true><<<grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, base, y, active,
+                                                                     s_buf, v_buf, part, gb, Lmax, min_valid, bs);
+        else if (fast)
+            k_ncc_moments<1, 3, QuadVol, false><<<grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, base, y, active,
+                                                                      s_buf, v_buf, part, gb, Lmax, min_valid, bs);
+        else if (keep)
+            k_ncc_moments<-1, -1, QuadVol, true><<<grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, base, y,
+                                                                       active, s_buf, v_buf, part, gb, Lmax,
+                                                                       min_valid, bs);
         else
-            k_ncc_moments<-1, -1, QuadVol><<<grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, base, y, active,
-                                                           s_buf, v_buf, part, gb, Lmax, min_valid, bs);
+            k_ncc_moments<-1, -1, QuadVol, false><<<grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, base, y,
+                                                                        active, s_buf, v_buf, part, gb, Lmax,
+                                                                        min_valid, bs);
         if (!gpart) continue;
         if (fast)
             k_ncc_grad<1, 3><<<grid, 256, smem2, st>>>(vd, g, desc, fix, psf, tl, base, y, poses, active,
