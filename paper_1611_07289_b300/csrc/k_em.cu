@@ -237,10 +237,66 @@ __global__ void __launch_bounds__(256) k_em_estep(const float *__restrict__ y,
 // [7] number of eligible patches.  bpart: kEmBlockMax x 8 float64.
 constexpr int kEmBlockMax = 512;
 
+// Grid-wide fold without a second launch: every block publishes its
+// partials, fences, and counts itself in; the block that arrives last (every
+// partial visible after its own fence) does the fold and resets the counter
+// for the next launch.  No block waits for another.
+__device__ __forceinline__ bool last_block(unsigned *counter)
+{
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(counter, 1u);
+        s_last = prev == gridDim.x - 1;
+        if (s_last) *counter = 0u;
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last;
+}
+
 __device__ __forceinline__ void store_block(double *bpart, const double *v, int nv)
 {
     if (threadIdx.x == 0)
         for (int k = 0; k < nv; ++k) bpart[(size_t)blockIdx.x * 8 + k] = v[k];
+}
+
+// Fold of k_em_patch_pot: pixel-level M-step, patch outlier density, first-
+// call initialisation of the patch-level model.
+__device__ void em_patch_head(int nb, const double *__restrict__ bpart, double *__restrict__ state,
+                              double *__restrict__ pstat, double c0, int rule)
+{
+    double sp = 0, spe2 = 0, ps = 0, ps2 = 0, ne = 0, mn = INFINITY, mx = -INFINITY;
+    for (int b = 0; b < nb; ++b) {
+        const double *v = bpart + 8 * (size_t)b;
+        sp += v[0];
+        spe2 += v[1];
+        ps += v[2];
+        ps2 += v[3];
+        ne += v[4];
+        mn = fmin(mn, v[5]);
+        mx = fmax(mx, v[6]);
+    }
+    double sfloor = pstat[0], npart = state[PVR_ST_N_PART];
+    if (sp > 0.0) {
+        double s2 = spe2 / sp;
+        state[PVR_ST_SIGMA2] = s2 < sfloor ? sfloor : s2;
+    }
+    if (npart > 0.0) state[PVR_ST_C] = clampd(sp / npart, 1e-3, 1.0 - 1e-3);
+    state[PVR_ST_SUM_P] = sp;
+    state[PVR_ST_SUM_PE2] = spe2;
+    double mp = (ne > 0.0 && mx - mn >= 1e-12) ? 1.0 / (mx - mn) : 0.0;
+    pstat[5] = mp;
+    pstat[6] = rule == 1 ? 1.0 : 0.0;
+    pstat[7] = ne;
+    if (rule == 0 && pstat[1] != 0.0) {
+        double mu = ne > 0.0 ? ps / ne : 0.0;
+        double var = ne > 0.0 ? ps2 / ne - mu * mu : 0.0;
+        state[PVR_ST_MU_P] = mu;
+        state[PVR_ST_SIGMA2_P] = var < 1e-4 ? 1e-4 : var;
+        state[PVR_ST_C_P] = clampd(c0, 1e-3, 1.0 - 1e-3);
+    }
 }
 
 // 5 + 6: M-step sums of the participating patches, potentials, eligibility.
@@ -250,7 +306,9 @@ __global__ void __launch_bounds__(256) k_em_patch_pot(const int32_t *__restrict_
                                                       const double *__restrict__ part,
                                                       double min_valid_frac, double *__restrict__ pbar,
                                                       uint8_t *__restrict__ elig,
-                                                      double *__restrict__ bpart)
+                                                      double *__restrict__ bpart, double *__restrict__ state,
+                                                      double *__restrict__ pstat, double c0, int rule,
+                                                      unsigned *__restrict__ counter)
 {
     __shared__ double sh[32 * 5];
     double a[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, mn[1] = {INFINITY}, mx[1] = {-INFINITY};
@@ -286,58 +344,42 @@ __global__ void __launch_bounds__(256) k_em_patch_pot(const int32_t *__restrict_
     block_reduce<1>(mx, sh, 2);
     double v[7] = {a[0], a[1], a[2], a[3], a[4], mn[0], mx[0]};
     store_block(bpart, v, 7);
+    if (last_block(counter) && threadIdx.x == 0) em_patch_head(gridDim.x, bpart, state, pstat, c0, rule);
 }
 
-// Fold of k_em_patch_pot: pixel-level M-step, patch outlier density, first-
-// call initialisation of the patch-level model.
-__global__ void k_em_patch_head(int nb, const double *__restrict__ bpart, double *__restrict__ state,
-                                double *__restrict__ pstat, double c0, int rule)
+// M-step of the patch-level model; stops the loop when m_p = 0 or no weight.
+__device__ void em_patch_mstep(int nb, const double *__restrict__ bpart, double *__restrict__ state,
+                               double *__restrict__ pstat)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double sp = 0, spe2 = 0, ps = 0, ps2 = 0, ne = 0, mn = INFINITY, mx = -INFINITY;
+    if (pstat[6] != 0.0) return;
+    if (pstat[5] == 0.0) {
+        pstat[6] = 1.0;
+        return;
+    }
+    double sw = 0, swp = 0, swp2 = 0;
     for (int b = 0; b < nb; ++b) {
-        const double *v = bpart + 8 * (size_t)b;
-        sp += v[0];
-        spe2 += v[1];
-        ps += v[2];
-        ps2 += v[3];
-        ne += v[4];
-        mn = fmin(mn, v[5]);
-        mx = fmax(mx, v[6]);
+        sw += bpart[8 * (size_t)b];
+        swp += bpart[8 * (size_t)b + 1];
+        swp2 += bpart[8 * (size_t)b + 2];
     }
-    double sfloor = pstat[0], npart = state[PVR_ST_N_PART];
-    if (sp > 0.0) {
-        double s2 = spe2 / sp;
-        state[PVR_ST_SIGMA2] = s2 < sfloor ? sfloor : s2;
+    if (!(sw > 0.0)) {
+        pstat[6] = 1.0;
+        return;
     }
-    if (npart > 0.0) state[PVR_ST_C] = clampd(sp / npart, 1e-3, 1.0 - 1e-3);
-    state[PVR_ST_SUM_P] = sp;
-    state[PVR_ST_SUM_PE2] = spe2;
-    double mp = (ne > 0.0 && mx - mn >= 1e-12) ? 1.0 / (mx - mn) : 0.0;
-    pstat[5] = mp;
-    pstat[6] = rule == 1 ? 1.0 : 0.0;
-    pstat[7] = ne;
-    if (rule == 0 && pstat[1] != 0.0) {
-        double mu = ne > 0.0 ? ps / ne : 0.0;
-        double var = ne > 0.0 ? ps2 / ne - mu * mu : 0.0;
-        state[PVR_ST_MU_P] = mu;
-        state[PVR_ST_SIGMA2_P] = var < 1e-4 ? 1e-4 : var;
-        state[PVR_ST_C_P] = clampd(c0, 1e-3, 1.0 - 1e-3);
-    }
+    double mu = swp / sw;
+    double v2 = swp2 / sw - mu * mu;
+    state[PVR_ST_MU_P] = mu;
+    state[PVR_ST_SIGMA2_P] = v2 < 1e-4 ? 1e-4 : v2;
+    state[PVR_ST_C_P] = clampd(sw / pstat[7], 1e-3, 1.0 - 1e-3);
 }
 
 // E-step of the patch-level model: w = G c_p / (G c_p + m_p (1 - c_p)),
 // G the one-sided Gaussian density of pbar; w = 1 if m_p = 0; 0 if not
 // eligible.  bpart = {sum w, sum w pbar, sum w pbar^2} over eligible patches.
-__global__ void __launch_bounds__(256) k_em_patch_estep(int n, const uint8_t *__restrict__ elig,
-                                                        const double *__restrict__ pbar,
-                                                        const double *__restrict__ state,
-                                                        const double *__restrict__ pstat,
-                                                        double *__restrict__ wsc,
-                                                        double *__restrict__ bpart)
+__device__ void em_patch_estep_block(int n, const uint8_t *__restrict__ elig, const double *__restrict__ pbar,
+                                     const double *__restrict__ state, const double *__restrict__ pstat,
+                                     double *__restrict__ wsc, double *__restrict__ bpart, double *sh)
 {
-    __shared__ double sh[32 * 3];
-    if (pstat[6] != 0.0) return;   // the loop has stopped: keep the last weights
     const double mu = state[PVR_ST_MU_P], v2 = state[PVR_ST_SIGMA2_P], cp = state[PVR_ST_C_P];
     const double mp = pstat[5];
     const double gnorm = 1.0 / (sqrt(2.0 * 3.14159265358979323846) * sqrt(v2));
@@ -364,30 +406,31 @@ __global__ void __launch_bounds__(256) k_em_patch_estep(int n, const uint8_t *__
     store_block(bpart, a, 3);
 }
 
-// M-step of the patch-level model; stops the loop when m_p = 0 or no weight.
-__global__ void k_em_patch_mstep(int nb, const double *__restrict__ bpart, double *__restrict__ state,
-                                 double *__restrict__ pstat)
+// With mstep, the last block to finish runs the M-step on the partials.
+__global__ void __launch_bounds__(256) k_em_patch_estep(int n, const uint8_t *__restrict__ elig,
+                                                        const double *__restrict__ pbar,
+                                                        double *__restrict__ state,
+                                                        double *__restrict__ pstat,
+                                                        double *__restrict__ wsc,
+                                                        double *__restrict__ bpart, int mstep,
+                                                        unsigned *__restrict__ counter)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0 || pstat[6] != 0.0) return;
-    if (pstat[5] == 0.0) {
-        pstat[6] = 1.0;
-        return;
-    }
-    double sw = 0, swp = 0, swp2 = 0;
-    for (int b = 0; b < nb; ++b) {
-        sw += bpart[8 * (size_t)b];
-        swp += bpart[8 * (size_t)b + 1];
-        swp2 += bpart[8 * (size_t)b + 2];
-    }
-    if (!(sw > 0.0)) {
-        pstat[6] = 1.0;
-        return;
-    }
-    double mu = swp / sw;
-    double v2 = swp2 / sw - mu * mu;
-    state[PVR_ST_MU_P] = mu;
-    state[PVR_ST_SIGMA2_P] = v2 < 1e-4 ? 1e-4 : v2;
-    state[PVR_ST_C_P] = clampd(sw / pstat[7], 1e-3, 1.0 - 1e-3);
+    __shared__ double sh[32 * 3];
+    // the loop has stopped: keep the last weights (every block still counts in)
+    if (pstat[6] == 0.0) em_patch_estep_block(n, elig, pbar, state, pstat, wsc, bpart, sh);
+    if (last_block(counter) && mstep && threadIdx.x == 0) em_patch_mstep(gridDim.x, bpart, state, pstat);
+}
+
+// Fold of k_em_patch_final: patch counts into the EM state.
+__device__ void em_patch_tail(int nb, const double *__restrict__ bpart, double *__restrict__ state,
+                              const double *__restrict__ pstat, int rule)
+{
+    double nin = 0.0;
+    for (int b = 0; b < nb; ++b) nin += bpart[8 * (size_t)b];
+    state[PVR_ST_N_ELIG] = pstat[7];
+    state[PVR_ST_N_IN] = nin;
+    if (rule == 0) state[PVR_ST_M_P] = pstat[5];
+    state[PVR_ST_INIT] = 1.0;
 }
 
 // Masks and outputs; bpart[0] = number of inlier patches of the block.
@@ -398,7 +441,9 @@ __global__ void __launch_bounds__(256) k_em_patch_final(int n, const uint8_t *__
                                                         uint8_t *__restrict__ mask_out,
                                                         float *__restrict__ w_patch,
                                                         float *__restrict__ pbar_out,
-                                                        double *__restrict__ bpart)
+                                                        double *__restrict__ bpart, double *__restrict__ state,
+                                                        const double *__restrict__ pstat,
+                                                        unsigned *__restrict__ counter)
 {
     __shared__ double sh[32];
     double cnt[1] = {0.0};
@@ -412,19 +457,9 @@ __global__ void __launch_bounds__(256) k_em_patch_final(int n, const uint8_t *__
     }
     block_reduce<1>(cnt, sh, 0);
     store_block(bpart, cnt, 1);
+    if (last_block(counter) && threadIdx.x == 0) em_patch_tail(gridDim.x, bpart, state, pstat, rule);
 }
 
-__global__ void k_em_patch_tail(int nb, const double *__restrict__ bpart, double *__restrict__ state,
-                                const double *__restrict__ pstat, int rule)
-{
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double nin = 0.0;
-    for (int b = 0; b < nb; ++b) nin += bpart[8 * (size_t)b];
-    state[PVR_ST_N_ELIG] = pstat[7];
-    state[PVR_ST_N_IN] = nin;
-    if (rule == 0) state[PVR_ST_M_P] = pstat[5];
-    state[PVR_ST_INIT] = 1.0;
-}
 
 // Weighted SIRT step (rows of A sum to one): x <- max(x + alpha addon / conf, 0)
 // where conf > eps; init_mode: x <- conf > eps ? addon / conf : 0.  Optionally
@@ -609,7 +644,7 @@ cudaError_t launch_em(const float *y, const float *sim, const uint8_t *valid, co
                       int n, int64_t n_pix, const Tiling &tl, int32_t *err, double *state,
                       const uint8_t *mask_in, uint8_t *mask_out, float *p, float *w_patch,
                       float *pbar_out, double *part, double *pstat, double *pbar, double *wsc,
-                      uint8_t *elig, double *bpart, const pvr_params &prm, cudaStream_t st)
+                      uint8_t *elig, double *bpart, unsigned *counter, const pvr_params &prm, cudaStream_t st)
 {
     k_em_prepare<<<1, kRedThreads, 0, st>>>(n, tl.tpp, mask_in, part, state, pstat, prm.em_c0,
                                             prm.em_sigma_floor_rel);
@@ -620,26 +655,24 @@ cudaError_t launch_em(const float *y, const float *sim, const uint8_t *valid, co
     if (nb > kEmBlockMax) nb = kEmBlockMax;
     if (nb < 1) nb = 1;
     const int rule = prm.patch_rule == 1 ? 1 : 0;
+    // each patch-level kernel's last block runs the fold that follows it
+    // (head, M-step, tail) on the block partials
     k_em_patch_pot<<<nb, 256, 0, st>>>(desc, n, tl.tpp, mask_in, part, prm.em_min_valid_frac, pbar,
-                                       elig, bpart);
-    k_em_patch_head<<<1, 32, 0, st>>>(nb, bpart, state, pstat, prm.em_c0, rule);
+                                       elig, bpart, state, pstat, prm.em_c0, rule, counter);
     if (rule == 0) {
-        for (int it = 0; it < prm.patch_em_iters; ++it) {
-            k_em_patch_estep<<<nb, 256, 0, st>>>(n, elig, pbar, state, pstat, wsc, bpart);
-            k_em_patch_mstep<<<1, 32, 0, st>>>(nb, bpart, state, pstat);
-        }
-        k_em_patch_estep<<<nb, 256, 0, st>>>(n, elig, pbar, state, pstat, wsc, bpart);
+        for (int it = 0; it <= prm.patch_em_iters; ++it)
+            k_em_patch_estep<<<nb, 256, 0, st>>>(n, elig, pbar, state, pstat, wsc, bpart,
+                                                 it < prm.patch_em_iters, counter);
     }
     k_em_patch_final<<<nb, 256, 0, st>>>(n, elig, pbar, wsc, rule, prm.patch_threshold, mask_out,
-                                         w_patch, pbar_out, bpart);
-    k_em_patch_tail<<<1, 32, 0, st>>>(nb, bpart, state, pstat, rule);
+                                         w_patch, pbar_out, bpart, state, pstat, counter);
     return cudaGetLastError();
 }
 
 // Number of kernel launches launch_em makes.
 int em_launch_count(int n, const pvr_params &prm)
 {
-    return (n > 0 ? 2 : 1) + 2 + (prm.patch_rule == 1 ? 0 : 2 * prm.patch_em_iters + 1) + 2;
+    return (n > 0 ? 2 : 1) + 1 + (prm.patch_rule == 1 ? 0 : prm.patch_em_iters + 1) + 1;
 }
 
 cudaError_t launch_volume_update(float *x, float *addon, float *conf, int64_t nvox, float alpha,

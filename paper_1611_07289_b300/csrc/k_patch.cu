@@ -1097,6 +1097,9 @@ __device__ __forceinline__ void best_part(int nval, float se2, float emin, float
     __syncthreads();
 }
 
+// The kept residuals and flags are stored with the streaming (evict-first)
+// policy: they are read again only after the registration, and must not push
+// the persistent NCC kernel's gradient scratch out of L2.
 // Forward model of a tile at the evaluated pose, written as the forward-model
 // kernel writes it (BestSim): per pixel e = y - s and the valid flag, per tile
 // {N, sum e^2, min e, max e} from the same per-thread order and reductions.
@@ -1118,8 +1121,8 @@ __device__ __forceinline__ void best_write(const TileInfo &ti, const Tiling &tl,
         const bool v = den > 0.f && member_ok(tl, o);
         const float s = v ? sv(ci, cj, den) : 0.f;
         const float e = v ? __ldg(y + o) - s : 0.f;
-        bs.e[o] = e;
-        bs.valid[o] = v ? 1 : 0;
+        __stcs(bs.e + o, e);
+        __stcs(reinterpret_cast<signed char *>(bs.valid) + o, (signed char)(v ? 1 : 0));
         if (v) {
             se2 = fmaf(e, e, se2);
             emin = fminf(emin, e);
@@ -1144,8 +1147,8 @@ __device__ __forceinline__ void best_write_empty(bool has, const TileInfo &ti, c
     for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
         const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
         const size_t o = (size_t)ti.off + (size_t)(ti.j0 + cj) * ti.w + (ti.i0 + ci);
-        bs.e[o] = 0.f;
-        bs.valid[o] = 0;
+        __stcs(bs.e + o, 0.f);
+        __stcs(reinterpret_cast<signed char *>(bs.valid) + o, (signed char)0);
     }
     if (threadIdx.x == 0) {
         pt[0] = 0.0;
@@ -1371,8 +1374,8 @@ __global__ void __launch_bounds__(256, 4) k_ncc_moments(const SRC x, VolDims vd,
             }
         }
         if (keep_all) {
-            bs.e[o] = e;
-            bs.valid[o] = v ? 1 : 0;
+            __stcs(bs.e + o, e);
+            __stcs(reinterpret_cast<signed char *>(bs.valid) + o, (signed char)(v ? 1 : 0));
         }
     }
     if (keep_all) best_part(cnt, se2, emin, emax, bs, gid, reinterpret_cast<float *>(red));
@@ -1744,8 +1747,8 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
                 emax = fmaxf(emax, e);
             }
             if (keep_all) {
-                bs.e[o] = e;
-                bs.valid[o] = v ? 1 : 0;
+                __stcs(bs.e + o, e);
+                __stcs(reinterpret_cast<signed char *>(bs.valid) + o, (signed char)(v ? 1 : 0));
             }
         }
         if (keep_all) best_part(cnt, se2, emin, emax, bs, gid, reinterpret_cast<float *>(red));

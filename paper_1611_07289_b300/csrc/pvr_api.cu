@@ -21,7 +21,7 @@ cudaError_t launch_em(const float *y, const float *sim, const uint8_t *valid, co
                       int n, int64_t n_pix, const Tiling &tl, int32_t *err, double *state,
                       const uint8_t *mask_in, uint8_t *mask_out, float *p, float *w_patch,
                       float *pbar_out, double *part, double *pstat, double *pbar, double *wsc,
-                      uint8_t *elig, double *bpart, const pvr_params &prm, cudaStream_t st);
+                      uint8_t *elig, double *bpart, unsigned *counter, const pvr_params &prm, cudaStream_t st);
 int em_launch_count(int n, const pvr_params &prm);
 cudaError_t launch_patches_build(const DevGeom *g, const pvr_geometry &hg, const float *stacks,
                                  int64_t total, const int32_t *slice_a, const int32_t *slice_stride,
@@ -60,6 +60,7 @@ struct pvr_ctx {
     double *part = nullptr, *gpart = nullptr, *pstat = nullptr;
     double *epart = nullptr;   // EM tile partials of the forward model kept by the registration
     double *pbar = nullptr, *wsc = nullptr, *emblk = nullptr;
+    unsigned *emcount = nullptr;   // arrival counter of the EM kernels' last-block folds (kept at 0)
     uint8_t *elig = nullptr;
     int32_t *err = nullptr;
     double *best = nullptr, *gbest = nullptr, *nbest = nullptr, *trial = nullptr, *delta = nullptr;
@@ -220,7 +221,7 @@ cudaError_t dalloc(T **p, size_t n)
 
 void free_all(pvr_ctx *c)
 {
-    void *ptrs[] = {c->d_geom, c->fix, c->part, c->epart, c->gpart, c->pstat, c->pbar, c->wsc, c->emblk, c->elig,
+    void *ptrs[] = {c->d_geom, c->fix, c->part, c->epart, c->gpart, c->pstat, c->pbar, c->wsc, c->emblk, c->emcount, c->elig,
                     c->err, c->best, c->gbest, c->nbest, c->trial, c->delta, c->ncc_tmp,
                     c->grad_tmp, c->active, c->s_buf, c->e_buf, c->p_buf, c->v_buf,
                     c->valid_buf, c->mask_tmp, c->acc2, c->quad, c->gbuf, c->keep, c->imax_key,
@@ -423,6 +424,7 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
     ALLOC(c->pbar, P);
     ALLOC(c->wsc, P);
     ALLOC(c->emblk, 512 * 8);
+    ALLOC(c->emcount, 1);
     ALLOC(c->elig, P);
     ALLOC(c->err, 1);
     ALLOC(c->best, P * kRegStride);
@@ -459,6 +461,7 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
 #undef ALLOC
     if (e == cudaSuccess) e = cudaMemcpy(c->d_geom, &hg, sizeof hg, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(c->emcount, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(c->acc2, 0, (size_t)c->nvox * sizeof(float2));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -671,7 +674,7 @@ int pvr_em_weights(pvr_ctx *c, const float *y, const float *sim, const uint8_t *
              "em_stats");
     CUDA_TRY_T(PVR_K_EM, launch_em(y, sim, valid, pp->desc, pp->n, pp->n_pix, tl, c->err, state, mask_in,
                        mask_out, p, w_patch, pbar, c->part, c->pstat, c->pbar, c->wsc, c->elig,
-                       c->emblk, c->prm, st),
+                       c->emblk, c->emcount, c->prm, st),
              "em");
     c->launches += (pp->n > 0) + em_launch_count(pp->n, c->prm);
     return PVR_OK;
@@ -901,7 +904,7 @@ int pvr_reconstruct_iter(pvr_ctx *c, float *x, const float *y, const pvr_patches
         }
         CUDA_TRY_T(PVR_K_EM, launch_em(c->e_buf, nullptr, c->valid_buf, pp->desc, pp->n, pp->n_pix, tl, c->err,
                            state, mask, c->mask_tmp, c->p_buf, w_patch, nullptr, part, c->pstat,
-                           c->pbar, c->wsc, c->elig, c->emblk, c->prm, st),
+                           c->pbar, c->wsc, c->elig, c->emblk, c->emcount, c->prm, st),
                  "em");
         CUDA_TRY(cudaMemcpyAsync(mask, c->mask_tmp, (size_t)pp->n, cudaMemcpyDeviceToDevice, st),
                  "mask copy");
