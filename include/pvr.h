@@ -399,7 +399,11 @@ PVR_API int pvr_register(pvr_ctx *ctx, const float *x, const float *y, const pvr
  * of e with pixel weight mask_patch * p, SIRT update of x.  x: in/out;
  * poses: in/out; state: EM state in/out; mask: uint8 [n] in/out (set to 1
  * before the first call); p (float32 [n_pix]) and w_patch (float32 [n])
- * receive the last pass's weights (either may be NULL). */
+ * receive the last pass's weights (either may be NULL).  When every patch
+ * is one tile (sides <= 64 pixels and no 32-pixel launch plan), the
+ * registration's NCC evaluations already compute the forward model at each
+ * patch's best pose; the first pass uses it instead of simulating again
+ * (the same values up to float32 summation order). */
 PVR_API int pvr_reconstruct_iter(pvr_ctx *ctx, float *x, const float *y, const pvr_patches *patches,
                          double *poses, double *state, uint8_t *mask, float *p, float *w_patch,
                          void *stream);
