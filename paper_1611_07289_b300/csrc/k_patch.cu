@@ -1685,7 +1685,7 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
                                                       double *__restrict__ part,
                                                       double *__restrict__ gpart,
                                                       float *__restrict__ scratch, int Lmax,
-                                                      int min_valid, BestSim bs)
+                                                      int min_valid, BestSim bs, int *__restrict__ counter)
 {
     extern __shared__ float sm[];
     __shared__ double red[32 * 12];
@@ -1696,7 +1696,15 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
     const int Gs = slot_stride(Lmax);
     float *G = scratch + (size_t)blockIdx.x * 6 * Gs;
     float *A = sm, *B = sm + Lmax, *C = sm + 2 * Lmax;
-    for (long long gid = blockIdx.x; gid < n_tiles; gid += gridDim.x) {
+    __shared__ int cur;
+    for (;;) {
+        // tiles from a shared counter (CTAs that finish early take more);
+        // the barrier first: every thread has read the previous index
+        __syncthreads();
+        if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
+        __syncthreads();
+        const long long gid = cur;
+        if (gid >= n_tiles) break;
         TileInfo ti;
         const bool has = tile_setup_at(gid, desc, fix, tl, kxy, ti);
         double *pt = part + (size_t)gid * kPartStride;
@@ -2056,7 +2064,7 @@ cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &t
                             const int32_t *desc, const int32_t *fix, const double *poses, int n,
                             float *s_buf,
                             uint8_t *v_buf, double *part, double *gpart, const int32_t *active,
-                            int min_valid, float *gbuf, long long gbuf_tiles, cudaStream_t st,
+                            int min_valid, float *gbuf, long long gbuf_tiles, int *counter, cudaStream_t st,
                             const BestSim &bs_in)
 {
     // the best-pose forward model is kept for one-tile patches only (the
@@ -2096,13 +2104,14 @@ cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &t
         const long long slots = gbuf_tiles * Lmax / slot_stride(Lmax);   // padded slots in the scratch
         if (grid > slots) grid = slots;
         if (grid <= 0) return cudaErrorInvalidValue;
+        if ((e = cudaMemsetAsync(counter, 0, sizeof(int), st)) != cudaSuccess) return e;
         if (fast)
             k_ncc_fused<1, 3, PlainVol><<<(unsigned)grid, 256, smem3, st>>>(xp, vd, desc, fix, psf, tl, total, y, active,
-                                                                  part, gpart, gbuf, Lmax, min_valid, bs);
+                                                                  part, gpart, gbuf, Lmax, min_valid, bs, counter);
         else
             k_ncc_fused<-1, -1, PlainVol><<<(unsigned)grid, 256, smem3, st>>>(xp, vd, desc, fix, psf, tl, total, y,
                                                                     active, part, gpart, gbuf, Lmax,
-                                                                    min_valid, bs);
+                                                                    min_valid, bs, counter);
         return cudaGetLastError();
     }
     // chunks of whole patches that fit the gradient scratch

@@ -61,6 +61,7 @@ struct pvr_ctx {
     double *epart = nullptr;   // EM tile partials of the forward model kept by the registration
     double *pbar = nullptr, *wsc = nullptr, *emblk = nullptr;
     unsigned *emcount = nullptr;   // arrival counter of the EM kernels' last-block folds (kept at 0)
+    int *ncc_counter = nullptr;    // tile counter of the persistent NCC kernel
     uint8_t *elig = nullptr;
     int32_t *err = nullptr;
     double *best = nullptr, *gbest = nullptr, *nbest = nullptr, *trial = nullptr, *delta = nullptr;
@@ -221,7 +222,7 @@ cudaError_t dalloc(T **p, size_t n)
 
 void free_all(pvr_ctx *c)
 {
-    void *ptrs[] = {c->d_geom, c->fix, c->part, c->epart, c->gpart, c->pstat, c->pbar, c->wsc, c->emblk, c->emcount, c->elig,
+    void *ptrs[] = {c->d_geom, c->fix, c->part, c->epart, c->gpart, c->pstat, c->pbar, c->wsc, c->emblk, c->emcount, c->ncc_counter, c->elig,
                     c->err, c->best, c->gbest, c->nbest, c->trial, c->delta, c->ncc_tmp,
                     c->grad_tmp, c->active, c->s_buf, c->e_buf, c->p_buf, c->v_buf,
                     c->valid_buf, c->mask_tmp, c->acc2, c->quad, c->gbuf, c->keep, c->imax_key,
@@ -425,6 +426,7 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
     ALLOC(c->wsc, P);
     ALLOC(c->emblk, 512 * 8);
     ALLOC(c->emcount, 1);
+    ALLOC(c->ncc_counter, 1);
     ALLOC(c->elig, P);
     ALLOC(c->err, 1);
     ALLOC(c->best, P * kRegStride);
@@ -767,7 +769,7 @@ int pvr_ncc_grad(pvr_ctx *c, const float *x, const float *y, const pvr_patches *
     CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, c->quad, y,
                              pp->desc, c->fix, poses, pp->n, c->s_buf, c->v_buf, c->part,
                              grad ? c->gpart : nullptr, nullptr, c->prm.reg_min_valid, c->gbuf,
-                             c->gbuf_tiles, st),
+                             c->gbuf_tiles, c->ncc_counter, st),
              "ncc_grad");
     CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(c->d_geom, pp->desc, poses, pp->n, tl, c->part, c->gpart, c->prm.reg_min_valid, ncc,
                                grad, st),
@@ -833,7 +835,7 @@ static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_p
         CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, c->quad, y,
                                  pp->desc, c->fix, c->trial, n, c->s_buf, c->v_buf, c->part,
                                  gpart, c->active, c->prm.reg_min_valid, c->gbuf, c->gbuf_tiles,
-                                 st, bs),
+                                 c->ncc_counter, st, bs),
                  "ncc_grad");
         if (keep_best) bs.mode = 2;   // after the first evaluation: accepted trials only
         CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(c->d_geom, pp->desc, c->trial, n, tl, c->part, gpart, c->prm.reg_min_valid,

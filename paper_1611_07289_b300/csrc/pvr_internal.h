@@ -115,7 +115,7 @@ cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &t
                             const int32_t *desc, const int32_t *fix, const double *poses, int n,
                             float *s_buf,
                             uint8_t *v_buf, double *part, double *gpart, const int32_t *active,
-                            int min_valid, float *gbuf, long long gbuf_tiles, cudaStream_t st,
+                            int min_valid, float *gbuf, long long gbuf_tiles, int *counter, cudaStream_t st,
                             const BestSim &bs = BestSim());
 size_t ncc_gbuf_floats_per_tile(const Tiling &tl, int kxy);
 // Kernel launches launch_ncc_grad makes for these arguments.

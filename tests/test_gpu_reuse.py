@@ -54,5 +54,11 @@ def test_reused_forward_model_matches_simulating_pass(pvr, fixed, evals, n_sr):
                     st.cpu().numpy()))
     (x0, p0, m0, pp0, w0, s0), (x1, p1, m1, pp1, w1, s1) = out
     assert np.array_equal(p0, p1) and np.array_equal(m0, m1)
-    assert rel_l2(x0, x1) < 1e-5 and rel_l2(pp0, pp1) < 1e-5 and rel_l2(w0, w1) < 1e-5
-    assert np.allclose(s0, s1, rtol=1e-5, atol=1e-9)
+    assert rel_l2(x0, x1) < 1e-5 and rel_l2(pp0, pp1) < 1e-5
+    # the patch posteriors sit in the tail of the p-bar mixture, where a
+    # relative change d of p-bar changes ln w by about d p-bar |p-bar - mu| /
+    # sigma^2 (hundreds of times d with sigma^2 at its 1e-4 floor); a second
+    # pass starts from volumes that differ in the float reduction order of the
+    # adjoint (~1e-7), so they get a looser bound
+    assert rel_l2(w0, w1) < 1e-4
+    assert np.allclose(s0, s1, rtol=1e-4, atol=1e-9)
