@@ -1826,7 +1826,8 @@ __global__ void __launch_bounds__(256, 4) k_pose_vjp(const SRC x, VolDims vd,
                                                      Tiling tl, long long n_tiles,
                                                      const float *__restrict__ r,
                                                      double *__restrict__ gpart,
-                                                     float *__restrict__ scratch, int Lmax)
+                                                     float *__restrict__ scratch, int Lmax,
+                                                     int *__restrict__ counter)
 {
     extern __shared__ float sm[];
     __shared__ double red[32 * 12];
@@ -1835,7 +1836,14 @@ __global__ void __launch_bounds__(256, 4) k_pose_vjp(const SRC x, VolDims vd,
     const int Gs = slot_stride(Lmax);
     float *G = scratch + (size_t)blockIdx.x * 6 * Gs;
     float *A = sm, *B = sm + Lmax, *C = sm + 2 * Lmax;
-    for (long long gid = blockIdx.x; gid < n_tiles; gid += gridDim.x) {
+    __shared__ int cur;
+    for (;;) {
+        // tiles from a shared counter, as in k_ncc_fused
+        __syncthreads();
+        if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
+        __syncthreads();
+        const long long gid = cur;
+        if (gid >= n_tiles) break;
         TileInfo ti;
         const bool has = tile_setup_at(gid, desc, fix, tl, kxy, ti);
         double *gp = gpart + (size_t)gid * kGradStride;
@@ -2159,7 +2167,7 @@ cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &t
 cudaError_t launch_pose_vjp(const PsfTab &psf, const Tiling &tl, int nx, int ny, int nz,
                             const float *xplain, const float *r, const int32_t *desc,
                             const int32_t *fix, int n, double *gpart, float *gbuf,
-                            long long gbuf_tiles, cudaStream_t st)
+                            long long gbuf_tiles, int *counter, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     VolDims vd = vol_dims(nx, ny, nz);
@@ -2186,12 +2194,13 @@ cudaError_t launch_pose_vjp(const PsfTab &psf, const Tiling &tl, int nx, int ny,
     const long long slots = gbuf_tiles * Lmax / slot_stride(Lmax);   // padded slots in the scratch
     if (grid > slots) grid = slots;
     if (grid <= 0) return cudaErrorInvalidValue;
+    if ((e = cudaMemsetAsync(counter, 0, sizeof(int), st)) != cudaSuccess) return e;
     if (fast)
         k_pose_vjp<1, 3, PlainVol><<<(unsigned)grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, total, r,
-                                                                     gpart, gbuf, Lmax);
+                                                                     gpart, gbuf, Lmax, counter);
     else
         k_pose_vjp<-1, -1, PlainVol><<<(unsigned)grid, 256, smem, st>>>(x, vd, desc, fix, psf, tl, total, r,
-                                                                       gpart, gbuf, Lmax);
+                                                                       gpart, gbuf, Lmax, counter);
     return cudaGetLastError();
 }
 

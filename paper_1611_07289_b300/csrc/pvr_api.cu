@@ -791,7 +791,8 @@ int pvr_pose_grad(pvr_ctx *c, const float *x, const float *r, const pvr_patches 
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     Tiling tl = make_tiling(ms, pp);
     CUDA_TRY_T(PVR_K_NCC, launch_pose_vjp(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, r,
-                                          pp->desc, c->fix, pp->n, c->gpart, c->gbuf, c->gbuf_tiles, st),
+                                          pp->desc, c->fix, pp->n, c->gpart, c->gbuf, c->gbuf_tiles,
+                                          c->ncc_counter, st),
                "pose_vjp");
     CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(c->d_geom, pp->desc, poses, pp->n, tl, nullptr, c->gpart,
                                                    c->prm.reg_min_valid, nullptr, grad, st),

@@ -127,7 +127,7 @@ int ncc_launch_count(const Tiling &tl, int n, bool grad, long long gbuf_tiles);
 cudaError_t launch_pose_vjp(const PsfTab &psf, const Tiling &tl, int nx, int ny, int nz,
                             const float *x, const float *r, const int32_t *desc,
                             const int32_t *fix, int n, double *gpart, float *gbuf,
-                            long long gbuf_tiles, cudaStream_t st);
+                            long long gbuf_tiles, int *counter, cudaStream_t st);
 
 // part == null: only the gradient (from gpart), no NCC.
 cudaError_t launch_ncc_finish(const DevGeom *g, const int32_t *desc, const double *poses, int n,
