@@ -161,7 +161,9 @@ def _algorithmic_bytes(cls, n_pix, n_vox):
     return {"simulate": 9 * n_pix + 4 * n_vox,        # y in, e out, valid out, x in
             "adjoint": 8 * n_pix + 8 * n_vox,         # e, p in; addon, conf out
             "em": 9 * n_pix,                          # e, valid in; p out
-            "ncc": 4 * n_pix + 4 * n_vox,             # y in, x in (moments and gradient on chip)
+            "ncc": 4 * n_pix + 4 * n_vox,             # y in, x in (moments and gradient on chip; the
+                                                      # kept forward model's writes, up to 5 B per
+                                                      # pixel per evaluation, are not counted)
             "update": 24 * n_vox}.get(cls)            # x, addon, conf in; x, 0, 0 out
 
 

@@ -812,6 +812,36 @@ __global__ void __launch_bounds__(256) k_simulate_q(const SRC x, VolDims vd,
     }
 }
 
+// Pixel coefficients (of the adjoint and of the NCC gradient) live in a
+// zero-padded array:
+// pixel (ci, cj) of the tile at Cp[(cj + 2 kxy) cw + ci + 2 kxy] with
+// cw = tw + 4 kxy, so that the transposed in-plane taps of every lattice
+// point (halo included) read in bounds without tests.  At most
+// (T + 4 kxy)^2 floats.
+__device__ __forceinline__ int cpad_w(const TileInfo &ti, int kxy) { return ti.tw + 4 * kxy; }
+__device__ __forceinline__ int cpad_at(const TileInfo &ti, int kxy, int ci, int cj)
+{
+    return (cj + 2 * kxy) * cpad_w(ti, kxy) + ci + 2 * kxy;
+}
+
+// Zero the border of the padded coefficient array (the pixels' entries are
+// written by the pixel loops).
+__device__ __forceinline__ void cpad_border(const TileInfo &ti, int kxy, float *Cp)
+{
+    const int cw = cpad_w(ti, kxy), b = 2 * kxy, top = 2 * b * cw, side = 2 * b * ti.th;
+    for (int k = threadIdx.x; k < top + side; k += blockDim.x) {
+        int at;
+        if (k < top) {
+            const int r = k / cw, c = k - r * cw;                // rows 0..b-1, then the b below the tile
+            at = (r < b ? r : ti.th + r) * cw + c;
+        } else {
+            const int t = k - top, r = t / (2 * b), c = t - r * 2 * b;   // b columns each side
+            at = (r + b) * cw + (c < b ? c : ti.tw + c);
+        }
+        Cp[at] = 0.f;
+    }
+}
+
 // ------------------------------------------------------------------ K4 --
 // Adjoint.  Pixel coefficients cr = w r / den, cw = w / den (valid pixels),
 // transposed in-plane taps into lattice weights U, U', then every in-volume
@@ -964,7 +994,10 @@ __device__ __forceinline__ void adjoint_tile(long long gid, const VolDims &vd,
     if (pmask && pmask[ti.p] == 0) return;
     const float pw = pweight ? pweight[ti.p] : 1.f;   // per-patch factor on r only
     const int np = ti.tw * ti.th;
-    float *U = sm, *Uw = sm + ti.L, *CR = sm + 2 * ti.L, *CW = CR + np;
+    // pixel coefficients in zero-padded arrays (cpad_at): the transposed taps
+    // of phase 2 then read in bounds without tests
+    const int cw_ = cpad_w(ti, kxy);
+    float *U = sm, *Uw = sm + ti.L, *CR = sm + 2 * ti.L, *CW = CR + cw_ * (ti.th + 4 * kxy);
     const float *gz = psf.gz[ti.stack];
     const bool interior = tile_interior(ti, vd, kxy, kz);
     // phase 0: in-volume PSF weight per lattice point (no gathers); inside
@@ -978,6 +1011,8 @@ __device__ __forceinline__ void adjoint_tile(long long gid, const VolDims &vd,
     }
     __syncthreads();
     // phase 1: pixel coefficients
+    cpad_border(ti, kxy, CR);
+    cpad_border(ti, kxy, CW);
     for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
         const int cj = qdiv(pp, ti.rtw), ci = pp - cj * ti.tw;
         float den = inplane(U, ti.Lw, kxy, psf.gxy, ci, cj);
@@ -990,26 +1025,25 @@ __device__ __forceinline__ void adjoint_tile(long long gid, const VolDims &vd,
             cr = cw * rr;
             if (pweight) cr *= pw;
         }
-        CR[pp] = cr;
-        CW[pp] = cw;
+        CR[cpad_at(ti, kxy, ci, cj)] = cr;
+        CW[cpad_at(ti, kxy, ci, cj)] = cw;
     }
     __syncthreads();
     // phase 2: transposed in-plane taps into lattice weights
     for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) {
         const int lj = qdiv(lp, ti.rLw), li = lp - lj * ti.Lw;   // lattice point = pixel (li - kxy, lj - kxy) of the tile
+        const int at = (lj + kxy) * cw_ + (li + kxy);          // that pixel in the padded arrays
         float ur = 0.f, uw = 0.f;
+#pragma unroll
         for (int dj = -kxy; dj <= kxy; ++dj) {
-            int cj = lj - kxy - dj;
-            if (cj < 0 || cj >= ti.th) continue;
             float rr = 0.f, rw = 0.f;
+#pragma unroll
             for (int di = -kxy; di <= kxy; ++di) {
-                int ci = li - kxy - di;
-                if (ci < 0 || ci >= ti.tw) continue;
-                float g = psf.gxy[di + kxy];
-                rr = fmaf(g, CR[cj * ti.tw + ci], rr);
-                rw = fmaf(g, CW[cj * ti.tw + ci], rw);
+                const float g = psf.gxy[di + kxy];
+                rr = fmaf(g, CR[at - dj * cw_ - di], rr);
+                rw = fmaf(g, CW[at - dj * cw_ - di], rw);
             }
-            float g = psf.gxy[dj + kxy];
+            const float g = psf.gxy[dj + kxy];
             ur = fmaf(g, rr, ur);
             uw = fmaf(g, rw, uw);
         }
@@ -1498,35 +1532,6 @@ __device__ void pose_jacobian(const DevGeom *__restrict__ g, const int32_t *d, c
     }
 }
 
-// Pixel coefficients of the NCC gradient live in a zero-padded array:
-// pixel (ci, cj) of the tile at Cp[(cj + 2 kxy) cw + ci + 2 kxy] with
-// cw = tw + 4 kxy, so that the transposed in-plane taps of every lattice
-// point (halo included) read in bounds without tests.  At most
-// (T + 4 kxy)^2 floats.
-__device__ __forceinline__ int cpad_w(const TileInfo &ti, int kxy) { return ti.tw + 4 * kxy; }
-__device__ __forceinline__ int cpad_at(const TileInfo &ti, int kxy, int ci, int cj)
-{
-    return (cj + 2 * kxy) * cpad_w(ti, kxy) + ci + 2 * kxy;
-}
-
-// Zero the border of the padded coefficient array (the pixels' entries are
-// written by the pixel loops).
-__device__ __forceinline__ void cpad_border(const TileInfo &ti, int kxy, float *Cp)
-{
-    const int cw = cpad_w(ti, kxy), b = 2 * kxy, top = 2 * b * cw, side = 2 * b * ti.th;
-    for (int k = threadIdx.x; k < top + side; k += blockDim.x) {
-        int at;
-        if (k < top) {
-            const int r = k / cw, c = k - r * cw;                // rows 0..b-1, then the b below the tile
-            at = (r < b ? r : ti.th + r) * cw + c;
-        } else {
-            const int t = k - top, r = t / (2 * b), c = t - r * 2 * b;   // b columns each side
-            at = (r + b) * cw + (c < b ? c : ti.tw + c);
-        }
-        Cp[at] = 0.f;
-    }
-}
-
 // Lattice phase of the NCC gradient: the transposed in-plane taps of the
 // pixel coefficients (padded array Cp) give the lattice weight U; with the
 // gradient sums GA, GB of the lattice point (planes of G, Lmax apart, read
@@ -1929,7 +1934,8 @@ size_t smem_forward(const Tiling &tl, int kxy)
 size_t smem_adjoint(const Tiling &tl, int kxy)
 {
     size_t L = (size_t)(tl.T + 2 * kxy) * (tl.T + 2 * kxy);
-    return (2 * L + 2 * (size_t)tl.T * tl.T) * sizeof(float);
+    size_t Cp = (size_t)(tl.T + 4 * kxy) * (tl.T + 4 * kxy);   // padded pixel coefficients
+    return (2 * L + 2 * Cp) * sizeof(float);
 }
 
 // Quad copy of the volume for QuadVol gathers: q[i] = (x[i], x[i + 1],
