@@ -586,7 +586,7 @@ int pvr_patches_build(pvr_ctx *c, const float *stacks, int32_t a, int32_t stride
 int pvr_patches_gather(pvr_ctx *c, const float *stacks, const pvr_patches *pp, float *y, void *stream)
 {
     if (!c) return PVR_ERR_INVALID_ARG;
-    int ms;
+    int ms = 0;
     int rc = check_patches(c, pp, &ms);
     if (rc) return rc;
     REQUIRE(stacks && y, "NULL argument");
@@ -601,7 +601,7 @@ int pvr_pose_to_fixed(pvr_ctx *c, const pvr_patches *pp, const double *poses, in
                       void *stream)
 {
     if (!c) return PVR_ERR_INVALID_ARG;
-    int ms;
+    int ms = 0;
     int rc = check_patches(c, pp, &ms);
     if (rc) return rc;
     REQUIRE(pp->n == 0 || (poses && fix), "NULL argument");
@@ -616,7 +616,7 @@ int pvr_simulate(pvr_ctx *c, const float *x, const pvr_patches *pp, const double
                  uint8_t *valid, void *stream)
 {
     if (!c) return PVR_ERR_INVALID_ARG;
-    int ms;
+    int ms = 0;
     int rc = check_patches(c, pp, &ms);
     if (rc) return rc;
     REQUIRE(pp->n == 0 || (x && poses && sim && valid), "NULL argument");
@@ -639,7 +639,7 @@ int pvr_adjoint(pvr_ctx *c, const pvr_patches *pp, const double *poses, const fl
                 const float *w, float *addon, float *conf, int32_t accumulate, void *stream)
 {
     if (!c) return PVR_ERR_INVALID_ARG;
-    int ms;
+    int ms = 0;
     int rc = check_patches(c, pp, &ms);
     if (rc) return rc;
     REQUIRE(addon || conf, "addon and conf are both NULL");
@@ -665,7 +665,7 @@ int pvr_em_weights(pvr_ctx *c, const float *y, const float *sim, const uint8_t *
                    float *p, float *w_patch, float *pbar, void *stream)
 {
     if (!c) return PVR_ERR_INVALID_ARG;
-    int ms;
+    int ms = 0;
     int rc = check_patches(c, pp, &ms);
     if (rc) return rc;
     REQUIRE(y && valid && state && mask_out && p, "NULL argument");
@@ -697,7 +697,7 @@ int pvr_volume_init(pvr_ctx *c, float *x, const float *y, const pvr_patches *pp,
                     const double *poses, void *stream)
 {
     if (!c) return PVR_ERR_INVALID_ARG;
-    int ms;
+    int ms = 0;
     int rc = check_patches(c, pp, &ms);
     if (rc) return rc;
     REQUIRE(x && y && (pp->n == 0 || poses), "NULL argument");
@@ -719,7 +719,7 @@ int pvr_patch_metrics(pvr_ctx *c, const float *y, const float *sim, const uint8_
                       const pvr_patches *pp, int32_t w, double *out, float *map, void *stream)
 {
     if (!c) return PVR_ERR_INVALID_ARG;
-    int ms;
+    int ms = 0;
     int rc = check_patches(c, pp, &ms);
     if (rc) return rc;
     REQUIRE(w >= 0 && w <= 16, "window half-width must be 0..16");
@@ -734,7 +734,7 @@ int pvr_rigidity_map(pvr_ctx *c, const pvr_patches *pp, const double *poses, con
                      const float *pbar, float *out, void *stream)
 {
     if (!c) return PVR_ERR_INVALID_ARG;
-    int ms;
+    int ms = 0;
     int rc = check_patches(c, pp, &ms);
     if (rc) return rc;
     REQUIRE(out && (pp->n == 0 || (poses && p && pbar)), "NULL argument");
@@ -757,7 +757,7 @@ int pvr_ncc_grad(pvr_ctx *c, const float *x, const float *y, const pvr_patches *
                  const double *poses, double *ncc, double *grad, void *stream)
 {
     if (!c) return PVR_ERR_INVALID_ARG;
-    int ms;
+    int ms = 0;
     int rc = check_patches(c, pp, &ms);
     if (rc) return rc;
     REQUIRE(pp->n == 0 || (x && y && poses && ncc), "NULL argument");
@@ -782,7 +782,7 @@ int pvr_pose_grad(pvr_ctx *c, const float *x, const float *r, const pvr_patches 
                   const double *poses, double *grad, void *stream)
 {
     if (!c) return PVR_ERR_INVALID_ARG;
-    int ms;
+    int ms = 0;
     int rc = check_patches(c, pp, &ms);
     if (rc) return rc;
     REQUIRE(pp->n == 0 || (x && r && poses && grad), "NULL argument");
@@ -858,7 +858,7 @@ int pvr_register(pvr_ctx *c, const float *x, const float *y, const pvr_patches *
                  int32_t n_evals, double *ncc, void *stream)
 {
     if (!c) return PVR_ERR_INVALID_ARG;
-    int ms;
+    int ms = 0;
     int rc = check_patches(c, pp, &ms);
     if (rc) return rc;
     REQUIRE(n_evals >= 0, "n_evals < 0");
@@ -872,7 +872,7 @@ int pvr_reconstruct_iter(pvr_ctx *c, float *x, const float *y, const pvr_patches
                          double *state, uint8_t *mask, float *p, float *w_patch, void *stream)
 {
     if (!c) return PVR_ERR_INVALID_ARG;
-    int ms;
+    int ms = 0;
     int rc = check_patches(c, pp, &ms);
     if (rc) return rc;
     REQUIRE(x && y && state && mask && (pp->n == 0 || poses), "NULL argument");
@@ -958,7 +958,7 @@ int pvr_plan(pvr_ctx *c, const pvr_patches *pp, const float *x, const float *y, 
              int32_t tile, int32_t mode, void *stream)
 {
     if (!c) return PVR_ERR_INVALID_ARG;
-    int ms;
+    int ms = 0;
     int rc = check_patches(c, pp, &ms);
     if (rc) return rc;
     REQUIRE(tile == 0 || tile == 32 || tile == 64, "tile must be 0 (tune), 32 or 64");
