@@ -4,9 +4,10 @@
 //
 // Pixel work (residual statistics, E-step) runs on the same (patch, tile)
 // grid as the forward model and leaves float64 partial sums per tile, so
-// every reduction is deterministic: single-CTA kernels fold the partials in
-// a fixed order in float64 (the M-step and the patch-level model, whose
-// stability needs it).
+// every reduction is deterministic: the partials are folded in a fixed order
+// in float64 (the M-step and the patch-level model, whose stability needs
+// it), by a single-CTA kernel or by the last block of the kernel that wrote
+// them.
 #include <math.h>
 
 #include "pvr_internal.h"
@@ -230,9 +231,9 @@ __global__ void __launch_bounds__(256) k_em_estep(const float *__restrict__ y,
 }
 
 // Steps 5-7: M-step, patch potentials and patch classification, spread over
-// the grid (one thread per patch) with single-block folds of the per-block
-// partial sums in between -- the patch-level model evaluates a float64
-// exponential per patch and EM iteration.
+// the grid (one thread per patch); the per-block partial sums are folded by
+// the last block of each kernel (last_block) -- the patch-level model
+// evaluates a float64 exponential per patch and EM iteration.
 // pstat: [5] patch outlier density m_p, [6] stop flag of the patch EM loop,
 // [7] number of eligible patches.  bpart: kEmBlockMax x 8 float64.
 constexpr int kEmBlockMax = 512;
