@@ -657,7 +657,11 @@ cudaError_t launch_em(const float *y, const float *sim, const uint8_t *valid, co
     if (nb < 1) nb = 1;
     const int rule = prm.patch_rule == 1 ? 1 : 0;
     // each patch-level kernel's last block runs the fold that follows it
-    // (head, M-step, tail) on the block partials
+    // (head, M-step, tail) on the block partials; the arrival counter returns
+    // to 0 after every such kernel, and is zeroed here as well so that a call
+    // after an aborted one starts clean
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
     k_em_patch_pot<<<nb, 256, 0, st>>>(desc, n, tl.tpp, mask_in, part, prm.em_min_valid_frac, pbar,
                                        elig, bpart, state, pstat, prm.em_c0, rule, counter);
     if (rule == 0) {
