@@ -892,11 +892,13 @@ int pvr_reconstruct_iter(pvr_ctx *c, float *x, const float *y, const pvr_patches
     for (int it = 0; it < c->prm.n_sr; ++it) {
         // x changes with every SR pass: refresh its quad copy after the first
         if (it > 0 && (rc = build_quad(c, x, st))) return rc;
-        // the work queue visits non-empty tiles only: empty slots of the EM
-        // partials must read as zero
+        // first pass after a registration that kept the forward model: the
+        // residuals, valid flags and EM partials are already in place
         const bool reuse = it == 0 && kept;
         double *part = reuse ? c->epart : c->part;
         if (!reuse) {
+            // the work queue visits non-empty tiles only: empty slots of the
+            // EM partials must read as zero
             if (wq)
                 CUDA_TRY(cudaMemsetAsync(c->part, 0, (size_t)pp->n * tl.tpp * kPartStride * sizeof(double), st),
                          "clear partials");
