@@ -22,6 +22,14 @@ struct TileRange {
     int p, t, off, w, i0, j0, tw, th;
 };
 
+// Row of pixel pp of a tile tw pixels wide, from r = 1 / tw: (pp + 0.5) / tw
+// lies at least 0.5 / tw from an integer and the two float roundings move it
+// by less than that for pp < 2^22, so truncation gives floor(pp / tw).
+__device__ __forceinline__ int tile_row(int pp, float r)
+{
+    return (int)(((float)pp + 0.5f) * r);
+}
+
 // Returns false for an empty tile or a descriptor whose pixel range is not
 // inside [0, n_pix) (then err gets bit 1 and nothing is touched).
 __device__ __forceinline__ bool tile_range(const int32_t *__restrict__ desc, const Tiling &tl,
@@ -98,8 +106,10 @@ __global__ void __launch_bounds__(256) k_em_stats(const float *__restrict__ y,
     }
     double a[2] = {0.0, 0.0};
     double mn[1] = {INFINITY}, mx[1] = {-INFINITY};
+    const float rtw = 1.0f / (float)r.tw;
     for (int pp = threadIdx.x; pp < r.tw * r.th; pp += blockDim.x) {
-        size_t o = (size_t)r.off + (size_t)(r.j0 + pp / r.tw) * r.w + r.i0 + pp % r.tw;
+        const int row = tile_row(pp, rtw);
+        size_t o = (size_t)r.off + (size_t)(r.j0 + row) * r.w + r.i0 + (pp - row * r.tw);
         if (!valid[o]) continue;
         float e = sim ? y[o] - sim[o] : y[o];
         a[0] += 1.0;
@@ -196,8 +206,10 @@ __global__ void __launch_bounds__(256) k_em_estep(const float *__restrict__ y,
     const float inv2s2 = (float)pstat[3], K = (float)pstat[4];
     const bool part_in = !mask_in || mask_in[r.p];
     float sp = 0.f, spe2 = 0.f, sp2 = 0.f, nv = 0.f;
+    const float rtw = 1.0f / (float)r.tw;
     for (int pp = threadIdx.x; pp < r.tw * r.th; pp += blockDim.x) {
-        size_t o = (size_t)r.off + (size_t)(r.j0 + pp / r.tw) * r.w + r.i0 + pp % r.tw;
+        const int row = tile_row(pp, rtw);
+        size_t o = (size_t)r.off + (size_t)(r.j0 + row) * r.w + r.i0 + (pp - row * r.tw);
         float pv = 0.f;
         if (valid[o]) {
             float e = sim ? y[o] - sim[o] : y[o];
