@@ -161,9 +161,11 @@ def _algorithmic_bytes(cls, n_pix, n_vox):
     return {"simulate": 9 * n_pix + 4 * n_vox,        # y in, e out, valid out, x in
             "adjoint": 8 * n_pix + 8 * n_vox,         # e, p in; addon, conf out
             "em": 9 * n_pix,                          # e, valid in; p out
-            "ncc": 4 * n_pix + 4 * n_vox,             # y in, x in (moments and gradient on chip; the
-                                                      # kept forward model's writes, up to 5 B per
-                                                      # pixel per evaluation, are not counted)
+            # y in, x in (moments and gradient on chip), plus the kept forward
+            # model: e and valid (5 B per pixel) written by the first of the
+            # step's two evaluations -- 2.5 B per pixel per evaluation; the
+            # second evaluation's rewrites for accepted trials are not counted
+            "ncc": 4 * n_pix + 4 * n_vox + (5 * n_pix) // 2,
             "update": 24 * n_vox}.get(cls)            # x, addon, conf in; x, 0, 0 out
 
 
