@@ -4,7 +4,7 @@
  * PVR (patch-to-volume reconstruction, Alansary et al., arXiv:1611.07289)
  * reconstructs a high-resolution volume x from many small 2-D patches y_s of
  * motion-corrupted slice stacks (Sec. II, Eq. patch), each patch with its own
- * rigid pose, by alternating patch-to-volume registration with NCC (Sec. II),
+ * rigid or affine pose, by alternating patch-to-volume registration with NCC (Sec. II),
  * super-resolution through the PSF forward model x_i = W_i y + n_i,
  * W_i = D B T_i (Eq. 1) and its adjoint, and EM outlier rejection at pixel
  * and patch level (Sec. II, Eqs. m, p, p-bar).
@@ -28,10 +28,15 @@
  *    int32 [n][8] rows {stack, slice, x0, y0, w, h, pix_off, 0}: the patch
  *    covers columns x0..x0+w-1, rows y0..y0+h-1 of the slice; its pixels are
  *    stored row-major at pix_off .. pix_off + w*h - 1 of every per-pixel
- *    array.  Poses: float64 [n][6] = (tx, ty, tz in mm, rx, ry, rz in
- *    degrees), transform T(w) = R (w - c) + c + t, R = Rz Ry Rx, c = world
- *    centre of the patch rectangle; T maps an acquired sample position
- *    (scanner world) to the reconstruction's world frame.
+ *    array.  Poses: float64 [n][n_params] (pvr_params.n_params).
+ *    Rigid (6): (tx, ty, tz in mm, rx, ry, rz in degrees), transform
+ *    T(w) = R (w - c) + c + t, R = Rz Ry Rx.  Affine (12): (tx, ty, tz in
+ *    mm, d00, d01, d02, d10, ..., d22), T(w) = (I + D)(w - c) + c + t with D
+ *    the 3x3 matrix given row-major (Eq. 1: T_i is the patch's motion; Sec.
+ *    II registers patches under rigid or affine motion).  c = world centre
+ *    of the patch rectangle; T maps an acquired sample position (scanner
+ *    world) to the reconstruction's world frame.  Pose gradients have the
+ *    same [n][n_params] layout.
  *  - Geometry: 3x4 row-major affine matrices (implied last row 0 0 0 1):
  *    world_to_voxel maps mm to voxel index (voxel centres at integers);
  *    pixel_to_world[s] maps (column, row, slice) of stack s to mm.
@@ -125,7 +130,7 @@ typedef struct pvr_params {
     double patch_threshold; /* rule 1 threshold on p-bar (0.5) */
     int32_t patch_em_iters; /* patch-level EM iterations per call (5) */
     /* registration */
-    int32_t n_params;       /* 6 = rigid (only value this build supports) */
+    int32_t n_params;       /* 6 = rigid, 12 = affine (pose layout above) */
     int32_t reg_evals;      /* NCC evaluations per registration round (40) */
     double reg_delta0;      /* initial step in scaled units (2) */
     double reg_delta_min;   /* stop below this step (0.01) */
@@ -294,11 +299,22 @@ PVR_API int pvr_simulate(pvr_ctx *ctx, const float *x, const pvr_patches *patche
  * The first call on a device looks the array up with that device current;
  * make that first call before any stream capture begins.  All calls share
  * the one array: calls that overlap on the GPU race, so serialise them.
- * Malformed patch rows are skipped (their pixels are not written); there is
- * no context, so no error message and no pvr_device_status for this call. */
+ * The geometry and the PSF / pose settings pass the checks of
+ * pvr_ctx_create (PVR_ERR_INVALID_ARG, nothing enqueued); n_params 6 or 12.
+ * Malformed patch rows and non-finite poses are skipped (their pixels are
+ * not written) and set the array's error word, which pvr_noalloc_status
+ * reports; there is no context, so no error message. */
 PVR_API int pvr_simulate_noalloc(const pvr_geometry *geom, const pvr_params *params, const float *x,
                                  const pvr_patches *patches, const double *poses, float *sim,
                                  uint8_t *valid, void *stream);
+
+/* Error word of pvr_simulate_noalloc on the current device: synchronises
+ * `stream`, reads the word and clears it.  It collects every call since the
+ * last read: PVR_OK, PVR_ERR_BOUNDS (a patch row outside its stack or
+ * pixel range) or PVR_ERR_NUMERIC (a pose with a non-finite sample map).
+ * Allocates nothing; the same sharing rule as pvr_simulate_noalloc applies.
+ * (The paper has no counterpart: part of the deployment variant.) */
+PVR_API int pvr_noalloc_status(void *stream);
 
 /* Adjoint of pvr_simulate (the super-resolution update's back-projection):
  * addon = A^T (w .* r), conf = A^T w, A the matrix of pvr_simulate at these
@@ -362,11 +378,11 @@ PVR_API int pvr_rigidity_map(pvr_ctx *ctx, const pvr_patches *patches, const dou
                              const float *p, const float *pbar, float *out, void *stream);
 
 /* NCC of every patch against the volume simulated at its pose, and its
- * gradient with respect to the 6 pose parameters (Sec. II: CC similarity,
+ * gradient with respect to the n_params pose parameters (Sec. II: CC similarity,
  * Eq. cross_corr with population deviations, over valid pixels; the PSF
  * normalisation is held constant in the derivative).  Fewer than
  * reg_min_valid valid pixels or a constant patch: NCC = 0, gradient 0.
- * ncc: float64 [n]; grad: float64 [n][6] (may be NULL). */
+ * ncc: float64 [n]; grad: float64 [n][n_params] (may be NULL). */
 PVR_API int pvr_ncc_grad(pvr_ctx *ctx, const float *x, const float *y, const pvr_patches *patches,
                  const double *poses, double *ncc, double *grad, void *stream);
 
@@ -378,7 +394,7 @@ PVR_API int pvr_ncc_grad(pvr_ctx *ctx, const float *x, const float *y, const pvr
  * x) it gives both gradients of any loss of the simulated patches.  The PSF
  * weights are recomputed, nothing is stored by the forward call.
  * x: float32 volume; r: float32 [n_pix] (dL/dsim; invalid pixels ignored);
- * poses: float64 [n][6]; grad: float64 [n][6] out.  This entry point extends
+ * poses, grad (out): float64 [n][n_params].  This entry point extends
  * the paper's method (the paper differentiates only NCC). */
 PVR_API int pvr_pose_grad(pvr_ctx *ctx, const float *x, const float *r, const pvr_patches *patches,
                           const double *poses, double *grad, void *stream);
@@ -386,10 +402,12 @@ PVR_API int pvr_pose_grad(pvr_ctx *ctx, const float *x, const float *r, const pv
 /* Patch-wise gradient ascent on NCC (Sec. II; Sec. III "patch-wise gradient
  * descent"): n_evals NCC evaluations per patch, the first at the current
  * pose, then trials best + delta * g/|g| in scaled units (translations in
- * mm, angles x patch half-diagonal in radians); a trial that strictly
- * improves NCC is kept (delta *= reg_grow), otherwise delta halves; a patch
- * stops when delta < reg_delta_min.  reg_fixed_step: always accept.
- * poses: float64 [n][6] in/out; ncc: float64 [n] best NCC (may be NULL). */
+ * mm, rigid angles x patch half-diagonal in radians, affine entries x patch
+ * half-diagonal: one unit moves the patch edge by about 1 mm); a trial that
+ * strictly improves NCC is kept (delta *= reg_grow), otherwise delta halves;
+ * a patch stops when delta < reg_delta_min.  reg_fixed_step: always accept.
+ * poses: float64 [n][n_params] in/out; ncc: float64 [n] best NCC (may be
+ * NULL). */
 PVR_API int pvr_register(pvr_ctx *ctx, const float *x, const float *y, const pvr_patches *patches,
                  double *poses, int32_t n_evals, double *ncc, void *stream);
 
@@ -482,7 +500,9 @@ PVR_API int pvr_net_reserve(pvr_net *net, int32_t max_patches, int64_t max_pixel
  * pose, let the network predict a correction (output k times scale[k], a
  * HOST double[6], in pose units: mm, degrees), evaluate NCC at the plain and
  * at the corrected pose, and keep the corrected pose only where NCC rises.
- * poses: float64 [n][6] in/out; accepted (device int32 [n], may be NULL):
+ * The network predicts rigid corrections: the context must use rigid poses
+ * (n_params 6; otherwise PVR_ERR_UNSUPPORTED).  poses: float64 [n][6]
+ * in/out; accepted (device int32 [n], may be NULL):
  * 1 where the proposal was taken.  Run NCC registration (pvr_register /
  * pvr_reconstruct_iter) afterwards to refine. */
 PVR_API int pvr_pose_propose(pvr_ctx *ctx, pvr_net *net, const float *x, const float *y,

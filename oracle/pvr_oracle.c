@@ -921,9 +921,14 @@ double or_ncc_grad(const or_geom *g, const or_psf *psf, const float *x, const fl
  * translations in mm, rigid angles times the patch half-diagonal r (mm) in
  * radians, affine entries times r.  After an accepted trial delta is
  * multiplied by grow (1 = plain halving scheme).
- * poses are updated in place; ncc_out receives the best NCC. */
+ * poses are updated in place; ncc_out receives the best NCC.  margin_out
+ * (may be NULL) receives per patch the smallest |NCC(trial) - NCC(best)|
+ * over the acceptance decisions taken (infinity if none): a test that
+ * compares another implementation's accept / reject path with this one can
+ * tell which decisions lie within rounding of a tie. */
 void or_register(const or_geom *g, const or_psf *psf, const or_reg_params *rp, const float *x,
-                 const float *y, const int *desc, int P, double *poses, double *ncc_out)
+                 const float *y, const int *desc, int P, double *poses, double *ncc_out,
+                 double *margin_out)
 {
     int np = rp->n_params;
 #pragma omp parallel for schedule(dynamic, 1)
@@ -943,6 +948,7 @@ void or_register(const or_geom *g, const or_psf *psf, const or_reg_params *rp, c
         memcpy(best, th, sizeof(double) * np);
         double nbest = or_ncc_grad(g, psf, x, y, d, best, np, rp->min_valid, 1, NULL, gbest);
         double delta = rp->delta0;
+        double margin = INFINITY;
         int done = (nbest == 0.0);
         for (int ev = 1; ev < rp->n_eval && !done; ++ev) {
             /* step in scaled coordinates u = theta * scale: du = delta * gu / |gu|,
@@ -953,6 +959,7 @@ void or_register(const or_geom *g, const or_psf *psf, const or_reg_params *rp, c
             if (!(gn > 0.0)) break;
             for (int k = 0; k < np; ++k) trial[k] = best[k] + delta * (gbest[k] / scale[k]) / gn / scale[k];
             double nt = or_ncc_grad(g, psf, x, y, d, trial, np, rp->min_valid, 1, NULL, gt);
+            if (fabs(nt - nbest) < margin) margin = fabs(nt - nbest);
             if (rp->fixed_step || nt > nbest) {
                 memcpy(best, trial, sizeof(double) * np);
                 memcpy(gbest, gt, sizeof(double) * np);
@@ -965,6 +972,7 @@ void or_register(const or_geom *g, const or_psf *psf, const or_reg_params *rp, c
         }
         memcpy(th, best, sizeof(double) * np);
         if (ncc_out) ncc_out[p] = nbest;
+        if (margin_out) margin_out[p] = margin;
     }
 }
 

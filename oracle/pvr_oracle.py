@@ -94,7 +94,7 @@ def lib():
                                       P(C.c_double), C.c_int, C.c_int, P(C.c_uint8), P(C.c_double)]
         L.or_sim_pose_vjp.restype = C.c_double
         L.or_register.argtypes = [P(_Geom), P(_Psf), P(_RegParams), P(C.c_float), P(C.c_float),
-                                  P(C.c_int), C.c_int, P(C.c_double), P(C.c_double)]
+                                  P(C.c_int), C.c_int, P(C.c_double), P(C.c_double), P(C.c_double)]
         L.or_metrics.argtypes = [P(C.c_double), P(C.c_double), P(C.c_uint8), C.c_size_t,
                                  P(C.c_double)]
         L.or_patches_build.argtypes = [P(_Geom), P(C.c_float), C.c_int, C.c_int, C.c_double,
@@ -267,17 +267,20 @@ def sim_pose_vjp(G, ps, x, r, drow, theta, n_params=6, exact=True):
     return float(v), g
 
 
-def register(G, ps, rp, x, y, desc, poses):
-    """Patch-wise gradient ascent on NCC; returns (new poses, best NCC per patch)."""
+def register(G, ps, rp, x, y, desc, poses, margin=False):
+    """Patch-wise gradient ascent on NCC; returns (new poses, best NCC per
+    patch) and, with margin=True, also the smallest |NCC(trial) - NCC(best)|
+    of each patch's acceptance decisions."""
     x = _c(x, np.float32)
     y = _c(y, np.float32)
     desc = _c(desc, np.int32)
     po = np.array(poses, dtype=np.float64, copy=True, order="C")
     ncc = np.zeros(desc.shape[0], dtype=np.float64)
+    mg = np.zeros(desc.shape[0], dtype=np.float64)
     lib().or_register(C.byref(G), C.byref(ps), C.byref(rp), _ptr(x, C.c_float), _ptr(y, C.c_float),
                       _ptr(desc, C.c_int), int(desc.shape[0]), _ptr(po, C.c_double),
-                      _ptr(ncc, C.c_double))
-    return po, ncc
+                      _ptr(ncc, C.c_double), _ptr(mg, C.c_double))
+    return (po, ncc, mg) if margin else (po, ncc)
 
 
 def metrics(ref, img, mask=None):

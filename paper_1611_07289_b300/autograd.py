@@ -25,7 +25,8 @@ from . import pvr as _pvr
 class SimulatePatches(torch.autograd.Function):
     """sim, valid = SimulatePatches.apply(x, poses, ctx, patch_table)
 
-    x: float32 volume [nz, ny, nx] on the GPU; poses: float64 [n, 6];
+    x: float32 volume [nz, ny, nx] on the GPU; poses: float64 [n, n_params]
+    (6 rigid or 12 affine, as the context);
     ctx: pvr.Context; patch_table: pvr.PatchTable.  sim: float32 [n_pix];
     valid: uint8 [n_pix] (not differentiable)."""
 

@@ -559,25 +559,28 @@ __global__ void __launch_bounds__(256) k_split_pairs(const float2 *__restrict__ 
 
 // ---------------------------------------------------------- registration --
 
-__global__ void k_reg_init(const double *__restrict__ poses, int n, double *__restrict__ best,
+__global__ void k_reg_init(const double *__restrict__ poses, int n_params, int n, double *__restrict__ best,
                            double *__restrict__ trial, double *__restrict__ delta,
                            int32_t *__restrict__ active, double delta0)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    for (int k = 0; k < 6; ++k) {
-        double v = poses[6 * (size_t)p + k];
+    for (int k = 0; k < n_params; ++k) {
+        double v = poses[(size_t)n_params * p + k];
         best[kRegStride * (size_t)p + k] = v;
-        trial[6 * (size_t)p + k] = v;
+        trial[(size_t)n_params * p + k] = v;
     }
     delta[p] = delta0;
     active[p] = 1;
 }
 
 // Judge evaluation `eval` (NCC and gradient at the trial pose) and propose
-// the next trial: best + delta (g/s) / |g/s| / s, s = per-parameter scale.
-__global__ void k_reg_step(const DevGeom *__restrict__ g, const int32_t *__restrict__ desc, int n,
-                           int eval, int last, const double *__restrict__ ncc,
+// the next trial: best + delta (g/s) / |g/s| / s, s = per-parameter scale
+// (translations 1 mm; rigid angles the patch half-diagonal times pi/180,
+// affine entries the half-diagonal, so that one scaled unit moves the patch
+// edge by about 1 mm).
+__global__ void k_reg_step(const DevGeom *__restrict__ g, const int32_t *__restrict__ desc, int n_params,
+                           int n, int eval, int last, const double *__restrict__ ncc,
                            const double *__restrict__ grad, double *__restrict__ best,
                            double *__restrict__ gbest, double *__restrict__ nbest,
                            double *__restrict__ trial, double *__restrict__ delta,
@@ -587,20 +590,20 @@ __global__ void k_reg_step(const DevGeom *__restrict__ g, const int32_t *__restr
     if (p >= n || !active[p]) return;
     double *b = best + kRegStride * (size_t)p;
     double *gb = gbest + kRegStride * (size_t)p;
-    double *tr = trial + 6 * (size_t)p;
+    double *tr = trial + (size_t)n_params * p;
     // grad is null on the last evaluation (no further step uses it)
-    const double *gr = grad ? grad + 6 * (size_t)p : nullptr;
+    const double *gr = grad ? grad + (size_t)n_params * p : nullptr;
     double v = ncc[p];
     if (eval == 0) {
         nbest[p] = v;
         if (gr)
-            for (int k = 0; k < 6; ++k) gb[k] = gr[k];
+            for (int k = 0; k < n_params; ++k) gb[k] = gr[k];
         if (v == 0.0) {
             active[p] = 0;
             return;
         }
     } else if (fixed || v > nbest[p]) {
-        for (int k = 0; k < 6; ++k) {
+        for (int k = 0; k < n_params; ++k) {
             b[k] = tr[k];
             if (gr) gb[k] = gr[k];
         }
@@ -619,25 +622,29 @@ __global__ void k_reg_step(const DevGeom *__restrict__ g, const int32_t *__restr
     double cw = sqrt(S[0] * S[0] + S[4] * S[4] + S[8] * S[8]) * (double)d[4];
     double ch = sqrt(S[1] * S[1] + S[5] * S[5] + S[9] * S[9]) * (double)d[5];
     double hd = 0.5 * sqrt(cw * cw + ch * ch);
-    double sc[6] = {1.0, 1.0, 1.0, hd * (3.14159265358979323846 / 180.0),
-                    hd * (3.14159265358979323846 / 180.0), hd * (3.14159265358979323846 / 180.0)};
+    const double sl = n_params == 12 ? hd : hd * (3.14159265358979323846 / 180.0);
     double gn = 0.0;
-    for (int k = 0; k < 6; ++k) gn = __dadd_rn(gn, __dmul_rn(__ddiv_rn(gb[k], sc[k]), __ddiv_rn(gb[k], sc[k])));
+    for (int k = 0; k < n_params; ++k) {
+        const double sk = k < 3 ? 1.0 : sl;
+        gn = __dadd_rn(gn, __dmul_rn(__ddiv_rn(gb[k], sk), __ddiv_rn(gb[k], sk)));
+    }
     gn = __dsqrt_rn(gn);
     if (!(gn > 0.0)) {
         active[p] = 0;
         return;
     }
-    for (int k = 0; k < 6; ++k)
-        tr[k] = __dadd_rn(b[k], __ddiv_rn(__ddiv_rn(__dmul_rn(delta[p], __ddiv_rn(gb[k], sc[k])), gn), sc[k]));
+    for (int k = 0; k < n_params; ++k) {
+        const double sk = k < 3 ? 1.0 : sl;
+        tr[k] = __dadd_rn(b[k], __ddiv_rn(__ddiv_rn(__dmul_rn(delta[p], __ddiv_rn(gb[k], sk)), gn), sk));
+    }
 }
 
 __global__ void k_reg_finish(const double *__restrict__ best, const double *__restrict__ nbest,
-                             int n, double *__restrict__ poses, double *__restrict__ ncc_out)
+                             int n_params, int n, double *__restrict__ poses, double *__restrict__ ncc_out)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    for (int k = 0; k < 6; ++k) poses[6 * (size_t)p + k] = best[kRegStride * (size_t)p + k];
+    for (int k = 0; k < n_params; ++k) poses[(size_t)n_params * p + k] = best[kRegStride * (size_t)p + k];
     if (ncc_out) ncc_out[p] = nbest[p];
 }
 
@@ -737,11 +744,11 @@ cudaError_t launch_split_pairs(const float2 *acc, int64_t nvox, float *addon, fl
     return cudaGetLastError();
 }
 
-cudaError_t launch_reg_init(const double *poses, int n, double *best, double *trial, double *delta,
+cudaError_t launch_reg_init(const double *poses, int n_params, int n, double *best, double *trial, double *delta,
                             int32_t *active, double delta0, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    k_reg_init<<<(n + 127) / 128, 128, 0, st>>>(poses, n, best, trial, delta, active, delta0);
+    k_reg_init<<<(n + 127) / 128, 128, 0, st>>>(poses, n_params, n, best, trial, delta, active, delta0);
     return cudaGetLastError();
 }
 
@@ -751,17 +758,17 @@ cudaError_t launch_reg_step(const DevGeom *g, const int32_t *desc, int n, int ev
                             const pvr_params &prm, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    k_reg_step<<<(n + 127) / 128, 128, 0, st>>>(g, desc, n, eval, last, ncc, grad, best, gbest,
+    k_reg_step<<<(n + 127) / 128, 128, 0, st>>>(g, desc, prm.n_params, n, eval, last, ncc, grad, best, gbest,
                                                 nbest, trial, delta, active, prm.reg_delta_min,
                                                 prm.reg_grow, prm.reg_fixed_step);
     return cudaGetLastError();
 }
 
-cudaError_t launch_reg_finish(const double *best, const double *nbest, int n, double *poses,
+cudaError_t launch_reg_finish(const double *best, const double *nbest, int n_params, int n, double *poses,
                               double *ncc_out, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    k_reg_finish<<<(n + 127) / 128, 128, 0, st>>>(best, nbest, n, poses, ncc_out);
+    k_reg_finish<<<(n + 127) / 128, 128, 0, st>>>(best, nbest, n_params, n, poses, ncc_out);
     return cudaGetLastError();
 }
 

@@ -1465,70 +1465,74 @@ __device__ bool ncc_from_moments(const double *part, int p, int tpp, int min_val
     return ncc_of_sums(m, min_valid, ncc, my, ms, sd, vs, n);
 }
 
-// Pose Jacobian of the sample positions (voxel units per parameter unit):
-// dq/dtheta_k = J1 (i - cu) + J2 (j - cv) + J4 zeta + J3 with (i, j) the patch
-// pixel, (cu, cv) its centre; jc[k] = {J1(3), J2(3), J4(3), J3(3)}.
-// Translations: J3 = columns of world_to_voxel.  Rotation k: J = W R_k' S per
-// degree, R_k' = d(Rz Ry Rx)/d angle_k (float64, math-library trigonometry:
-// the gradient is not part of the integer-exact path).
-__device__ void pose_jacobian(const DevGeom *__restrict__ g, const int32_t *d, const double *th,
-                              double jc[6][12])
+// Derivatives of the linear part of the patch transform, one 3x3 matrix per
+// non-translation parameter: rigid (Rz Ry Rx, angles in degrees) the
+// derivative of the product with respect to each angle, per degree;
+// affine (I + D) the unit matrix of the entry D_rc.  float64 with
+// math-library trigonometry: the gradient is not part of the
+// integer-exact path.
+__device__ void linear_derivs(const double *th, int n_params, double dL[9][9])
+{
+    if (n_params == 12) {
+        for (int k = 0; k < 9; ++k)
+            for (int e = 0; e < 9; ++e) dL[k][e] = e == k ? 1.0 : 0.0;
+        return;
+    }
+    const double dg = 3.14159265358979323846 / 180.0;
+    double sx, cx, sy, cy, sz, cz;
+    sincos(th[3] * dg, &sx, &cx);
+    sincos(th[4] * dg, &sy, &cy);
+    sincos(th[5] * dg, &sz, &cz);
+    const double Rx[9] = {1, 0, 0, 0, cx, -sx, 0, sx, cx};
+    const double Ry[9] = {cy, 0, sy, 0, 1, 0, -sy, 0, cy};
+    const double Rz[9] = {cz, -sz, 0, sz, cz, 0, 0, 0, 1};
+    const double dRx[9] = {0, 0, 0, 0, -sx, -cx, 0, cx, -sx};
+    const double dRy[9] = {-sy, 0, cy, 0, 0, 0, -cy, 0, -sy};
+    const double dRz[9] = {-sz, -cz, 0, cz, -sz, 0, 0, 0, 0};
+    for (int a = 0; a < 3; ++a) {
+        // angle a: x (rx), y (ry), z (rz); the derivative replaces that factor
+        const double *Am = a == 2 ? dRz : Rz, *Bm = a == 1 ? dRy : Ry, *Cm = a == 0 ? dRx : Rx;
+        double AB[9];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c)
+                AB[3 * r + c] = Am[3 * r] * Bm[c] + Am[3 * r + 1] * Bm[3 + c] + Am[3 * r + 2] * Bm[6 + c];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c)
+                dL[a][3 * r + c] =
+                    (AB[3 * r] * Cm[c] + AB[3 * r + 1] * Cm[3 + c] + AB[3 * r + 2] * Cm[6 + c]) * dg;
+    }
+}
+
+// Pose Jacobian of the sample positions (voxel units per parameter unit),
+// column k: dq/dtheta_k = J1 (i - cu) + J2 (j - cv) + J4 zeta + J3 with
+// (i, j) the patch pixel, (cu, cv) its centre; jc = {J1(3), J2(3), J4(3),
+// J3(3)}.  Translations: J3 = columns of world_to_voxel.  Linear-part
+// parameters: J = W dL S (the patch centre cancels), J4 scaled to one PSF
+// step along the normal.
+__device__ void pose_jacobian_col(const DevGeom *__restrict__ g, const int32_t *d, const double dL[9][9], int k,
+                                  double jc[12])
 {
     const double *S = g->p2w[d[0]];
     const double *W = g->w2v;
-    const double dg = 3.14159265358979323846 / 180.0;
-    double ax = th[3] * dg, ay = th[4] * dg, az = th[5] * dg;
-    double sx = sin(ax), cx = cos(ax), sy = sin(ay), cy = cos(ay), sz = sin(az), cz = cos(az);
-    double Rx[9] = {1, 0, 0, 0, cx, -sx, 0, sx, cx};
-    double Ry[9] = {cy, 0, sy, 0, 1, 0, -sy, 0, cy};
-    double Rz[9] = {cz, -sz, 0, sz, cz, 0, 0, 0, 1};
-    double dRx[9] = {0, 0, 0, 0, -sx, -cx, 0, cx, -sx};
-    double dRy[9] = {-sy, 0, cy, 0, 0, 0, -cy, 0, -sy};
-    double dRz[9] = {-sz, -cz, 0, cz, -sz, 0, 0, 0, 0};
-    double n2 = S[2] * S[2] + S[6] * S[6] + S[10] * S[10];
-    double zs = g->dz / sqrt(n2);
-    for (int k = 0; k < 6; ++k) {
-        double Q[9];
-        if (k < 3) {
-            for (int r = 0; r < 3; ++r) {
-                jc[k][r] = 0.0;
-                jc[k][3 + r] = 0.0;
-                jc[k][6 + r] = 0.0;
-                jc[k][9 + r] = W[4 * r + k];
-            }
-            continue;
-        }
-        const double *Am = (k == 5) ? dRz : Rz;
-        const double *Bm = (k == 4) ? dRy : Ry;
-        const double *Cm = (k == 3) ? dRx : Rx;
-        double AB[9], ABC[9], WA[9];
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) {
-                AB[3 * r + c] = 0.0;
-                for (int t = 0; t < 3; ++t) AB[3 * r + c] += Am[3 * r + t] * Bm[3 * t + c];
-            }
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) {
-                ABC[3 * r + c] = 0.0;
-                for (int t = 0; t < 3; ++t) ABC[3 * r + c] += AB[3 * r + t] * Cm[3 * t + c];
-            }
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) {
-                WA[3 * r + c] = 0.0;
-                for (int t = 0; t < 3; ++t) WA[3 * r + c] += W[4 * r + t] * ABC[3 * t + c];
-            }
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) {
-                Q[3 * r + c] = 0.0;
-                for (int t = 0; t < 3; ++t) Q[3 * r + c] += WA[3 * r + t] * S[4 * t + c];
-                Q[3 * r + c] *= dg;
-            }
+    if (k < 3) {
         for (int r = 0; r < 3; ++r) {
-            jc[k][r] = Q[3 * r + 0];
-            jc[k][3 + r] = Q[3 * r + 1];
-            jc[k][6 + r] = Q[3 * r + 2] * zs;
-            jc[k][9 + r] = 0.0;
+            jc[r] = jc[3 + r] = jc[6 + r] = 0.0;
+            jc[9 + r] = W[4 * r + k];
         }
+        return;
+    }
+    const double *D = dL[k - 3];
+    const double n2 = S[2] * S[2] + S[6] * S[6] + S[10] * S[10];
+    const double zs = g->dz / sqrt(n2);
+    double WD[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) WD[3 * r + c] = W[4 * r] * D[c] + W[4 * r + 1] * D[3 + c] + W[4 * r + 2] * D[6 + c];
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) {
+            const double q = WD[3 * r] * S[c] + WD[3 * r + 1] * S[4 + c] + WD[3 * r + 2] * S[8 + c];
+            jc[3 * c + r] = c == 2 ? q * zs : q;
+        }
+        jc[9 + r] = 0.0;
     }
 }
 
@@ -1889,7 +1893,7 @@ __global__ void __launch_bounds__(256, 4) k_pose_vjp(const SRC x, VolDims vd,
 
 // Per patch: NCC from the tile moments, and the pose gradient as the
 // contraction of the summed gradient moments with the pose Jacobian.
-__global__ void k_ncc_finish(const DevGeom *__restrict__ g, int n, int tpp,
+__global__ void k_ncc_finish(const DevGeom *__restrict__ g, int n_params, int n, int tpp,
                              const int32_t *__restrict__ desc, const double *__restrict__ poses,
                              const double *__restrict__ part, const double *__restrict__ gpart,
                              int min_valid, double *__restrict__ ncc, double *__restrict__ grad)
@@ -1903,9 +1907,9 @@ __global__ void k_ncc_finish(const DevGeom *__restrict__ g, int n, int tpp,
         ncc[p] = ok ? v : 0.0;
     }
     if (!grad) return;
-    double *gr = grad + 6 * (size_t)p;
+    double *gr = grad + (size_t)n_params * p;
     if (!ok) {
-        for (int k = 0; k < 6; ++k) gr[k] = 0.0;
+        for (int k = 0; k < n_params; ++k) gr[k] = 0.0;
         return;
     }
     double mom[12];
@@ -1914,13 +1918,15 @@ __global__ void k_ncc_finish(const DevGeom *__restrict__ g, int n, int tpp,
         for (int t = 0; t < tpp; ++t) s += gpart[((size_t)p * tpp + t) * kGradStride + k];
         mom[k] = s;
     }
-    double jc[6][12];
-    pose_jacobian(g, desc + 8 * (size_t)p, poses + 6 * (size_t)p, jc);
-    for (int k = 0; k < 6; ++k) {
+    const int32_t *d = desc + 8 * (size_t)p;
+    double dL[9][9];
+    linear_derivs(poses + (size_t)n_params * p, n_params, dL);
+    for (int k = 0; k < n_params; ++k) {
+        double jc[12];
+        pose_jacobian_col(g, d, dL, k, jc);
         double gsum = 0.0;
         for (int r = 0; r < 3; ++r)
-            gsum += jc[k][r] * mom[r] + jc[k][3 + r] * mom[3 + r] + jc[k][6 + r] * mom[6 + r] +
-                    jc[k][9 + r] * mom[9 + r];
+            gsum += jc[r] * mom[r] + jc[3 + r] * mom[3 + r] + jc[6 + r] * mom[6 + r] + jc[9 + r] * mom[9 + r];
         gr[k] = gsum;
     }
 }
@@ -2225,13 +2231,13 @@ int ncc_launch_count(const Tiling &tl, int n, bool grad, long long gbuf_tiles)
     return chunk > 0 ? (int)(2 * ((total + chunk - 1) / chunk)) : 0;
 }
 
-cudaError_t launch_ncc_finish(const DevGeom *g, const int32_t *desc, const double *poses, int n,
-                              const Tiling &tl, const double *part, const double *gpart,
+cudaError_t launch_ncc_finish(const DevGeom *g, const int32_t *desc, const double *poses, int n_params,
+                              int n, const Tiling &tl, const double *part, const double *gpart,
                               int min_valid, double *ncc, double *grad, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    k_ncc_finish<<<(n + 127) / 128, 128, 0, st>>>(g, n, tl.tpp, desc, poses, part, gpart, min_valid,
-                                                  ncc, grad);
+    k_ncc_finish<<<(n + 127) / 128, 128, 0, st>>>(g, n_params, n, tl.tpp, desc, poses, part, gpart,
+                                                  min_valid, ncc, grad);
     return cudaGetLastError();
 }
 

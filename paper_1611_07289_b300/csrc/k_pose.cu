@@ -1,5 +1,7 @@
 // K1: patch pose -> fixed-point sample lattice (Eq. 1: the motion part T_i
-// of W_i = D B T_i), one thread per patch, float64.
+// of W_i = D B T_i), one thread per patch, float64.  Rigid poses (6
+// parameters: translation in mm, Rz Ry Rx angles in degrees) or affine poses
+// (12: translation and the 3x3 matrix D of the linear part I + D, row-major).
 //
 // The integer lattice must be reproducible bit for bit by any IEEE machine,
 // so every float64 operation is an explicit round-to-nearest intrinsic
@@ -71,6 +73,14 @@ __device__ void rotation_zyx(const double *th, double L[9])
     L[8] = dmul(cy, cx);
 }
 
+// Affine linear part I + D (D row-major in th[3..11]), each entry one
+// rounded addition (an exact copy off the diagonal).
+__device__ void affine_linear(const double *th, double L[9])
+{
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) L[3 * r + c] = dadd(r == c ? 1.0 : 0.0, th[3 + 3 * r + c]);
+}
+
 __device__ __forceinline__ double dot3_rows(const double *a, double x, double y, double z)
 {
     return dadd(dadd(dmul(a[0], x), dmul(a[1], y)), dmul(a[2], z));
@@ -86,7 +96,7 @@ __device__ __forceinline__ bool quantise(double v, long long *out)
 }
 
 __global__ void k_pose_to_fixed(const DevGeom *__restrict__ g, const int32_t *__restrict__ desc,
-                                const double *__restrict__ poses, int n, long long n_pix,
+                                const double *__restrict__ poses, int n_params, int n, long long n_pix,
                                 int max_side, int kxy, int kz, int32_t *__restrict__ fix,
                                 int32_t *__restrict__ err)
 {
@@ -107,11 +117,14 @@ __global__ void k_pose_to_fixed(const DevGeom *__restrict__ g, const int32_t *__
         for (int i = 0; i < kFixStride; ++i) f[i] = 0;
         return;
     }
-    const double *th = poses + 6 * (size_t)p;
+    const double *th = poses + (size_t)n_params * p;
     const double *S = g->p2w[st];
     const double *W = g->w2v;
     double L[9], c[3], tau[3], A[12], M[12];
-    rotation_zyx(th, L);
+    if (n_params == 12)
+        affine_linear(th, L);
+    else
+        rotation_zyx(th, L);
     // patch centre in world
     double u = dadd((double)x0, dmul((double)(w - 1), 0.5));
     double v = dadd((double)y0, dmul((double)(h - 1), 0.5));
@@ -174,14 +187,14 @@ __global__ void k_pose_to_fixed(const DevGeom *__restrict__ g, const int32_t *__
 
 }  // namespace
 
-cudaError_t launch_pose_to_fixed(const DevGeom *g, const int32_t *desc, const double *poses, int n,
-                                 int64_t n_pix, int max_side, int kxy, int kz, int32_t *fix,
+cudaError_t launch_pose_to_fixed(const DevGeom *g, const int32_t *desc, const double *poses, int n_params,
+                                 int n, int64_t n_pix, int max_side, int kxy, int kz, int32_t *fix,
                                  int32_t *err, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     int bs = 128;
-    k_pose_to_fixed<<<(n + bs - 1) / bs, bs, 0, st>>>(g, desc, poses, n, (long long)n_pix, max_side,
-                                                      kxy, kz, fix, err);
+    k_pose_to_fixed<<<(n + bs - 1) / bs, bs, 0, st>>>(g, desc, poses, n_params, n, (long long)n_pix,
+                                                      max_side, kxy, kz, fix, err);
     return cudaGetLastError();
 }
 

@@ -244,8 +244,8 @@ int build_quad(pvr_ctx *c, const float *x, cudaStream_t st)
 // K1 for a patch table at `poses` into the context's fixed table.
 int pose_fixed(pvr_ctx *c, const pvr_patches *pp, int max_side, const double *poses, cudaStream_t st)
 {
-    CUDA_TRY_T(PVR_K_POSE, launch_pose_to_fixed(c->d_geom, pp->desc, poses, pp->n, pp->n_pix, max_side,
-                                  c->psf.kxy, c->psf.kz, c->fix, c->err, st),
+    CUDA_TRY_T(PVR_K_POSE, launch_pose_to_fixed(c->d_geom, pp->desc, poses, c->prm.n_params, pp->n, pp->n_pix,
+                                                max_side, c->psf.kxy, c->psf.kz, c->fix, c->err, st),
              "pose_to_fixed");
     c->launches += pp->n > 0;
     return PVR_OK;
@@ -298,6 +298,38 @@ void make_psf_tab(const pvr_geometry *g, const pvr_params *prm, PsfTab *tab)
     }
 }
 
+// Checks of a geometry and the PSF / pose settings shared by every entry
+// point that takes them (context creation and the context-free forward
+// model); returns null when valid, else a one-line reason.
+const char *validate_setup(const pvr_geometry *g, const pvr_params *prm)
+{
+    if (g->nx < 2 || g->ny < 2 || g->nz < 2 || g->nx > 2048 || g->ny > 2048 || g->nz > 2048)
+        return "volume sizes must be 2..2048";
+    if ((int64_t)g->nx * g->ny * g->nz >= ((int64_t)1 << 31)) return "the volume must have fewer than 2^31 voxels";
+    if (g->n_stacks < 1 || g->n_stacks > PVR_MAX_STACKS) return "n_stacks outside 1..16";
+    for (int s = 0; s < g->n_stacks; ++s) {
+        if (g->stack_w[s] < 1 || g->stack_h[s] < 1 || g->stack_k[s] < 1) return "empty stack";
+        if (!(g->thickness[s] >= 0.0) || !isfinite(g->thickness[s])) return "bad slice thickness";
+        for (int i = 0; i < 12; ++i)
+            if (!isfinite(g->pixel_to_world[s][i])) return "non-finite pixel_to_world";
+        const double *S = g->pixel_to_world[s];
+        if (!(S[2] * S[2] + S[6] * S[6] + S[10] * S[10] > 0.0)) return "zero slice axis";
+    }
+    for (int i = 0; i < 12; ++i)
+        if (!isfinite(g->world_to_voxel[i])) return "non-finite world_to_voxel";
+    if (prm->psf_kxy < 0 || prm->psf_kxy > PVR_MAX_KXY) return "psf_kxy outside 0..3";
+    if (prm->psf_kz < 0 || prm->psf_kz > PVR_MAX_KZ) return "psf_kz outside 0..8";
+    if (!(prm->psf_dz > 0.0) || !isfinite(prm->psf_dz) || !(prm->psf_fwhm_xy >= 0.0) || !isfinite(prm->psf_fwhm_xy))
+        return "bad PSF size";
+    if (prm->psf_kind != PVR_PSF_GAUSSIAN && prm->psf_kind != PVR_PSF_TAYLOR_SINC) return "bad psf_kind";
+    if (prm->psf_kind == PVR_PSF_TAYLOR_SINC && !(prm->psf_sinc_eps > 0.0 && prm->psf_sinc_eps < 1.0))
+        return "psf_sinc_eps outside (0, 1)";
+    if (prm->n_params != 6 && prm->n_params != 12) return "n_params must be 6 (rigid) or 12 (affine)";
+    return nullptr;
+}
+
+int ctx_n_params(const pvr_ctx *c) { return c->prm.n_params; }
+
 }  // namespace pvr
 
 extern "C" {
@@ -345,28 +377,7 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
         delete c;
         return PVR_ERR_INVALID_ARG;
     };
-    if (g->nx < 2 || g->ny < 2 || g->nz < 2 || g->nx > 2048 || g->ny > 2048 || g->nz > 2048)
-        return bad("volume sizes must be 2..2048");
-    if ((int64_t)g->nx * g->ny * g->nz >= ((int64_t)1 << 31))
-        return bad("the volume must have fewer than 2^31 voxels");
-    if (g->n_stacks < 1 || g->n_stacks > PVR_MAX_STACKS) return bad("n_stacks outside 1..16");
-    for (int s = 0; s < g->n_stacks; ++s) {
-        if (g->stack_w[s] < 1 || g->stack_h[s] < 1 || g->stack_k[s] < 1) return bad("empty stack");
-        if (!(g->thickness[s] >= 0.0) || !isfinite(g->thickness[s])) return bad("bad slice thickness");
-        for (int i = 0; i < 12; ++i)
-            if (!isfinite(g->pixel_to_world[s][i])) return bad("non-finite pixel_to_world");
-        const double *S = g->pixel_to_world[s];
-        if (!(S[2] * S[2] + S[6] * S[6] + S[10] * S[10] > 0.0)) return bad("zero slice axis");
-    }
-    for (int i = 0; i < 12; ++i)
-        if (!isfinite(g->world_to_voxel[i])) return bad("non-finite world_to_voxel");
-    if (prm->psf_kxy < 0 || prm->psf_kxy > PVR_MAX_KXY) return bad("psf_kxy outside 0..3");
-    if (prm->psf_kz < 0 || prm->psf_kz > PVR_MAX_KZ) return bad("psf_kz outside 0..8");
-    if (!(prm->psf_dz > 0.0) || !(prm->psf_fwhm_xy >= 0.0)) return bad("bad PSF size");
-    if (prm->psf_kind != PVR_PSF_GAUSSIAN && prm->psf_kind != PVR_PSF_TAYLOR_SINC) return bad("bad psf_kind");
-    if (prm->psf_kind == PVR_PSF_TAYLOR_SINC && !(prm->psf_sinc_eps > 0.0 && prm->psf_sinc_eps < 1.0))
-        return bad("psf_sinc_eps outside (0, 1)");
-    if (prm->n_params != 6) return bad("only rigid (6-parameter) poses are supported");
+    if (const char *why = validate_setup(g, prm)) return bad(why);
     if (prm->max_patches < 1 || prm->max_pixels < 1) return bad("capacity must be positive");
     if (prm->max_patch_side < 1 || prm->max_patch_side > kMaxSideLimit)
         return bad("max_patch_side outside 1..256");
@@ -432,10 +443,10 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
     ALLOC(c->best, P * kRegStride);
     ALLOC(c->gbest, P * kRegStride);
     ALLOC(c->nbest, P);
-    ALLOC(c->trial, P * 6);
+    ALLOC(c->trial, P * 12);
     ALLOC(c->delta, P);
     ALLOC(c->ncc_tmp, P);
-    ALLOC(c->grad_tmp, P * 6);
+    ALLOC(c->grad_tmp, P * 12);
     ALLOC(c->active, P);
     ALLOC(c->s_buf, NP);
     ALLOC(c->e_buf, NP);
@@ -605,8 +616,8 @@ int pvr_pose_to_fixed(pvr_ctx *c, const pvr_patches *pp, const double *poses, in
     int rc = check_patches(c, pp, &ms);
     if (rc) return rc;
     REQUIRE(pp->n == 0 || (poses && fix), "NULL argument");
-    CUDA_TRY(launch_pose_to_fixed(c->d_geom, pp->desc, poses, pp->n, pp->n_pix, ms, c->psf.kxy,
-                                  c->psf.kz, fix, c->err, (cudaStream_t)stream),
+    CUDA_TRY(launch_pose_to_fixed(c->d_geom, pp->desc, poses, c->prm.n_params, pp->n, pp->n_pix, ms,
+                                  c->psf.kxy, c->psf.kz, fix, c->err, (cudaStream_t)stream),
              "pose_to_fixed");
     c->launches += pp->n > 0;
     return PVR_OK;
@@ -771,8 +782,8 @@ int pvr_ncc_grad(pvr_ctx *c, const float *x, const float *y, const pvr_patches *
                              grad ? c->gpart : nullptr, nullptr, c->prm.reg_min_valid, c->gbuf,
                              c->gbuf_tiles, c->ncc_counter, st),
              "ncc_grad");
-    CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(c->d_geom, pp->desc, poses, pp->n, tl, c->part, c->gpart, c->prm.reg_min_valid, ncc,
-                               grad, st),
+    CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(c->d_geom, pp->desc, poses, c->prm.n_params, pp->n, tl, c->part,
+                                                   c->gpart, c->prm.reg_min_valid, ncc, grad, st),
              "ncc_finish");
     c->launches += ncc_launch_count(tl, pp->n, grad != nullptr, c->gbuf_tiles) + (pp->n > 0);
     return PVR_OK;
@@ -794,8 +805,8 @@ int pvr_pose_grad(pvr_ctx *c, const float *x, const float *r, const pvr_patches 
                                           pp->desc, c->fix, pp->n, c->gpart, c->gbuf, c->gbuf_tiles,
                                           c->ncc_counter, st),
                "pose_vjp");
-    CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(c->d_geom, pp->desc, poses, pp->n, tl, nullptr, c->gpart,
-                                                   c->prm.reg_min_valid, nullptr, grad, st),
+    CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(c->d_geom, pp->desc, poses, c->prm.n_params, pp->n, tl, nullptr,
+                                                   c->gpart, c->prm.reg_min_valid, nullptr, grad, st),
                "pose_vjp_finish");
     c->launches += 2;
     return PVR_OK;
@@ -823,7 +834,8 @@ static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_p
         bs.nbest = c->nbest;
         bs.fixed = c->prm.reg_fixed_step != 0;
     }
-    CUDA_TRY(launch_reg_init(poses, n, c->best, c->trial, c->delta, c->active, c->prm.reg_delta0, st),
+    CUDA_TRY(launch_reg_init(poses, c->prm.n_params, n, c->best, c->trial, c->delta, c->active,
+                             c->prm.reg_delta0, st),
              "reg_init");
     c->launches += 1;
     for (int ev = 0; ev < n_evals; ++ev) {
@@ -839,8 +851,8 @@ static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_p
                                  c->ncc_counter, st, bs),
                  "ncc_grad");
         if (keep_best) bs.mode = 2;   // after the first evaluation: accepted trials only
-        CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(c->d_geom, pp->desc, c->trial, n, tl, c->part, gpart, c->prm.reg_min_valid,
-                                   c->ncc_tmp, grad, st),
+        CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(c->d_geom, pp->desc, c->trial, c->prm.n_params, n, tl, c->part,
+                                                       gpart, c->prm.reg_min_valid, c->ncc_tmp, grad, st),
                  "ncc_finish");
         CUDA_TRY_T(PVR_K_REG_STEP, launch_reg_step(c->d_geom, pp->desc, n, ev, ev == n_evals - 1, c->ncc_tmp,
                                  grad, c->best, c->gbest, c->nbest, c->trial, c->delta,
@@ -848,7 +860,7 @@ static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_p
                  "reg_step");
         c->launches += ncc_launch_count(tl, n, need_grad, c->gbuf_tiles) + 2;
     }
-    CUDA_TRY(launch_reg_finish(c->best, c->nbest, n, poses, ncc_out, st), "reg_finish");
+    CUDA_TRY(launch_reg_finish(c->best, c->nbest, c->prm.n_params, n, poses, ncc_out, st), "reg_finish");
     c->launches += 1;
     if (kept) *kept = keep_best;
     return PVR_OK;

@@ -35,6 +35,13 @@ struct PsfTab {
 // in-plane profile, Gaussian slice profile).
 void make_psf_tab(const pvr_geometry *g, const pvr_params *prm, PsfTab *tab);
 
+// Geometry and PSF / pose-parameter checks shared by pvr_ctx_create and the
+// context-free forward model: null when valid, else a one-line reason.
+const char *validate_setup(const pvr_geometry *g, const pvr_params *prm);
+
+// Pose parameter count (6 or 12) of a context.
+int ctx_n_params(const pvr_ctx *c);
+
 // Patch-tile decomposition shared by the per-patch kernels: tile side T
 // pixels, tiles_x * tiles_y tiles per patch (the largest patch's count);
 // block b works on patch b / tpp, tile b % tpp.
@@ -70,8 +77,9 @@ struct BestSim {
 };
 
 // Launchers (each returns cudaGetLastError() of its launches).
+// poses: float64 [n][n_params], n_params 6 (rigid) or 12 (affine).
 cudaError_t launch_pose_to_fixed(const DevGeom *g, const int32_t *desc, const double *poses,
-                                 int n, int64_t n_pix, int max_side, int kxy, int kz,
+                                 int n_params, int n, int64_t n_pix, int max_side, int kxy, int kz,
                                  int32_t *fix, int32_t *err, cudaStream_t st);
 
 // Forward model from x (quad == null) or from the quad copy of x.
@@ -129,12 +137,14 @@ cudaError_t launch_pose_vjp(const PsfTab &psf, const Tiling &tl, int nx, int ny,
                             const int32_t *fix, int n, double *gpart, float *gbuf,
                             long long gbuf_tiles, int *counter, cudaStream_t st);
 
-// part == null: only the gradient (from gpart), no NCC.
-cudaError_t launch_ncc_finish(const DevGeom *g, const int32_t *desc, const double *poses, int n,
-                              const Tiling &tl, const double *part, const double *gpart,
+// part == null: only the gradient (from gpart), no NCC.  poses and grad:
+// float64 [n][n_params].
+cudaError_t launch_ncc_finish(const DevGeom *g, const int32_t *desc, const double *poses, int n_params,
+                              int n, const Tiling &tl, const double *part, const double *gpart,
                               int min_valid, double *ncc, double *grad, cudaStream_t st);
 
-cudaError_t launch_reg_init(const double *poses, int n, double *best, double *trial,
+// Registration state: best / gbest [n][kRegStride], trial and grad [n][n_params].
+cudaError_t launch_reg_init(const double *poses, int n_params, int n, double *best, double *trial,
                             double *delta, int32_t *active, double delta0, cudaStream_t st);
 
 cudaError_t launch_reg_step(const DevGeom *g, const int32_t *desc, int n, int eval, int last,
@@ -142,7 +152,7 @@ cudaError_t launch_reg_step(const DevGeom *g, const int32_t *desc, int n, int ev
                             double *nbest, double *trial, double *delta, int32_t *active,
                             const pvr_params &prm, cudaStream_t st);
 
-cudaError_t launch_reg_finish(const double *best, const double *nbest, int n, double *poses,
+cudaError_t launch_reg_finish(const double *best, const double *nbest, int n_params, int n, double *poses,
                               double *ncc_out, cudaStream_t st);
 
 

@@ -277,6 +277,7 @@ PVR_API int pvr_pose_propose(pvr_ctx *ctx, pvr_net *n, const float *x, const flo
                              const double *scale, double *poses, int32_t *accepted, void *stream)
 {
     if (!ctx || !n || !pp || !scale) return PVR_ERR_INVALID_ARG;
+    if (ctx_n_params(ctx) != 6) return PVR_ERR_UNSUPPORTED;   // the network predicts rigid corrections
     if (pp->n == 0) return PVR_OK;
     if (!x || !y || !poses || pp->max_side != kSide) return PVR_ERR_INVALID_ARG;
     if (pp->n > n->res_patches || pp->n_pix > n->res_pixels) return PVR_ERR_INVALID_ARG;

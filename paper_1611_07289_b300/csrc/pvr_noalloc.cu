@@ -11,13 +11,16 @@
 // whose scratch is a file-scope device array: every GPU that loads the
 // library carries it until the process exits, and no call allocates.
 //
-// Limits: at most kNoAllocMaxPatches patches per call; every other argument
-// rule is that of pvr_simulate.  All calls share the one array, so calls
-// that overlap on the GPU (different streams, or different host threads on
-// the same device) race; serialise them.  The first call on a device looks
-// up the array's device address (cudaGetSymbolAddress) once, with that
-// device current -- make that first call before starting any stream
-// capture.
+// Limits: at most kNoAllocMaxPatches patches per call; the geometry and
+// PSF / pose settings pass the same checks as in pvr_ctx_create.  All calls
+// share the one array, so calls that overlap on the GPU (different streams,
+// or different host threads on the same device) race; serialise them.  The
+// first call on a device looks up the array's device address
+// (cudaGetSymbolAddress) once, with that device current -- make that first
+// call before starting any stream capture.  Problems only the device sees
+// (a malformed patch row, a non-finite pose) set the array's error word,
+// which stays set over later calls until pvr_noalloc_status reads and
+// clears it.
 #include <math.h>
 #include <string.h>
 
@@ -42,6 +45,20 @@ constexpr int kMaxDevices = 64;
 std::mutex g_lock;
 unsigned char *g_addr[kMaxDevices] = {};
 
+// Device address of the scratch on the current device (null on failure).
+unsigned char *scratch_base()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_lock);
+    if (!g_addr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return nullptr;
+        g_addr[dev] = (unsigned char *)ptr;
+    }
+    return g_addr[dev];
+}
+
 // Store the geometry (a kernel parameter) into the scratch, stream-ordered.
 __global__ void k_store_geometry(DevGeom g, unsigned char *dst)
 {
@@ -63,31 +80,12 @@ extern "C" PVR_API int pvr_simulate_noalloc(const pvr_geometry *geom, const pvr_
     if (pp->n == 0) return PVR_OK;
     if (!pp->desc || !x || !poses || !sim || !valid) return PVR_ERR_INVALID_ARG;
     const pvr_geometry *g = geom;
-    if (g->nx < 2 || g->ny < 2 || g->nz < 2 || g->nx > 2048 || g->ny > 2048 || g->nz > 2048)
-        return PVR_ERR_INVALID_ARG;
-    if (g->n_stacks < 1 || g->n_stacks > PVR_MAX_STACKS) return PVR_ERR_INVALID_ARG;
-    if (prm->psf_kxy < 0 || prm->psf_kxy > PVR_MAX_KXY || prm->psf_kz < 0 || prm->psf_kz > PVR_MAX_KZ)
-        return PVR_ERR_INVALID_ARG;
-    if (!(prm->psf_dz > 0.0) || !(prm->psf_fwhm_xy >= 0.0) || prm->n_params != 6)
-        return PVR_ERR_INVALID_ARG;
+    if (validate_setup(g, prm)) return PVR_ERR_INVALID_ARG;
     int max_side = pp->max_side > 0 ? pp->max_side : prm->max_patch_side;
     if (max_side < 1 || max_side > 256 || pp->n_pix < 1 || pp->n_pix >= ((int64_t)1 << 31))
         return PVR_ERR_INVALID_ARG;
-
-    // device address of the scratch on the current device (set up once)
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PVR_ERR_CUDA;
-    unsigned char *base;
-    {
-        std::lock_guard<std::mutex> lk(g_lock);
-        if (!g_addr[dev]) {
-            void *ptr = nullptr;
-            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr)
-                return PVR_ERR_CUDA;
-            g_addr[dev] = (unsigned char *)ptr;
-        }
-        base = g_addr[dev];
-    }
+    unsigned char *base = scratch_base();
+    if (!base) return PVR_ERR_CUDA;
 
     // geometry and PSF tables, as pvr_ctx_create derives them
     DevGeom hg;
@@ -98,8 +96,6 @@ extern "C" PVR_API int pvr_simulate_noalloc(const pvr_geometry *geom, const pvr_
     hg.n_stacks = g->n_stacks;
     long long off = 0;
     for (int s = 0; s < g->n_stacks; ++s) {
-        if (g->stack_w[s] < 1 || g->stack_h[s] < 1 || g->stack_k[s] < 1 || !(g->thickness[s] >= 0.0))
-            return PVR_ERR_INVALID_ARG;
         hg.sw[s] = g->stack_w[s];
         hg.sh[s] = g->stack_h[s];
         hg.sk[s] = g->stack_k[s];
@@ -109,7 +105,6 @@ extern "C" PVR_API int pvr_simulate_noalloc(const pvr_geometry *geom, const pvr_
     }
     memcpy(hg.w2v, g->world_to_voxel, 12 * sizeof(double));
     hg.dz = prm->psf_dz;
-    if (prm->psf_kind != PVR_PSF_GAUSSIAN && prm->psf_kind != PVR_PSF_TAYLOR_SINC) return PVR_ERR_INVALID_ARG;
     PsfTab t;
     make_psf_tab(g, prm, &t);
 
@@ -118,12 +113,12 @@ extern "C" PVR_API int pvr_simulate_noalloc(const pvr_geometry *geom, const pvr_
     int32_t *d_fix = reinterpret_cast<int32_t *>(base + kGeomBytes);
     int32_t *d_err = reinterpret_cast<int32_t *>(base + kErrOffset);
     // every call rewrites the geometry and the table rows it uses; the error
-    // word must start at zero
+    // word is sticky (zero when the library loads, cleared by
+    // pvr_noalloc_status)
     k_store_geometry<<<1, 1, 0, st>>>(hg, base);
     if (cudaGetLastError() != cudaSuccess) return PVR_ERR_CUDA;
-    if (cudaMemsetAsync(d_err, 0, sizeof(int32_t), st) != cudaSuccess) return PVR_ERR_CUDA;
-    if (launch_pose_to_fixed(d_geom, pp->desc, poses, pp->n, pp->n_pix, max_side, t.kxy, t.kz, d_fix,
-                             d_err, st) != cudaSuccess)
+    if (launch_pose_to_fixed(d_geom, pp->desc, poses, prm->n_params, pp->n, pp->n_pix, max_side, t.kxy, t.kz,
+                             d_fix, d_err, st) != cudaSuccess)
         return PVR_ERR_CUDA;
     Tiling tl;
     tl.T = max_side <= 64 ? max_side : 64;
@@ -133,5 +128,20 @@ extern "C" PVR_API int pvr_simulate_noalloc(const pvr_geometry *geom, const pvr_
     if (launch_simulate(d_geom, t, tl, g->nx, g->ny, g->nz, x, nullptr, pp->desc, d_fix, pp->n, nullptr, sim,
                         valid, nullptr, st) != cudaSuccess)
         return PVR_ERR_CUDA;
+    return PVR_OK;
+}
+
+extern "C" PVR_API int pvr_noalloc_status(void *stream)
+{
+    unsigned char *base = scratch_base();
+    if (!base) return PVR_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *d_err = reinterpret_cast<int32_t *>(base + kErrOffset);
+    int32_t h = 0;
+    if (cudaMemcpyAsync(&h, d_err, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PVR_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return PVR_ERR_CUDA;
+    if (h != 0 && cudaMemsetAsync(d_err, 0, sizeof h, st) != cudaSuccess) return PVR_ERR_CUDA;
+    if (h & 1) return PVR_ERR_BOUNDS;
+    if (h & 2) return PVR_ERR_NUMERIC;
     return PVR_OK;
 }

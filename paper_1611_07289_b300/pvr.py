@@ -106,6 +106,7 @@ _SIGS = {
     "pvr_metrics": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int64, _VP, _VP]),
     "pvr_simulate_noalloc": (C.c_int, [C.POINTER(Geometry), C.POINTER(Params), _VP,
                                        C.POINTER(Patches), _VP, _VP, _VP, _VP]),
+    "pvr_noalloc_status": (C.c_int, [_VP]),
     "pvr_profile_enable": (C.c_int, [_VP, C.c_int32]),
     "pvr_profile_read": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_int64), _VP]),
 }
@@ -214,6 +215,7 @@ class Context:
         if rc != 0:
             raise PvrError(rc, "pvr_ctx_create failed (see stderr)")
         self.h = h
+        self.n_params = int(self.params.n_params)
 
     def close(self):
         if getattr(self, "h", None):
@@ -353,7 +355,7 @@ class Context:
         if ncc is None:
             ncc = torch.empty(pt.n, dtype=torch.float64, device=dev)
         if grad is None and want_grad:
-            grad = torch.empty((pt.n, 6), dtype=torch.float64, device=dev)
+            grad = torch.empty((pt.n, self.n_params), dtype=torch.float64, device=dev)
         self._chk(lib.pvr_ncc_grad(self.h, _ptr(x), _ptr(y), C.byref(pt.c), _ptr(poses), _ptr(ncc),
                                    _ptr(grad), _stream(stream)))
         return ncc, grad
@@ -376,9 +378,9 @@ class Context:
         return out
 
     def pvr_pose_grad(self, x, r, pt: PatchTable, poses, grad=None, stream=None):
-        """d (sum_pix r * sim) / d pose per patch (float64 [n, 6])."""
+        """d (sum_pix r * sim) / d pose per patch (float64 [n, n_params])."""
         if grad is None:
-            grad = torch.empty((pt.n, 6), dtype=torch.float64, device=x.device)
+            grad = torch.empty((pt.n, self.n_params), dtype=torch.float64, device=x.device)
         self._chk(lib.pvr_pose_grad(self.h, _ptr(x), _ptr(r), C.byref(pt.c), _ptr(poses), _ptr(grad),
                                     _stream(stream)))
         return grad
@@ -509,6 +511,12 @@ def pvr_simulate_noalloc(geom, params: Params, x, pt: PatchTable, poses, sim, va
     g = geometry(geom) if not isinstance(geom, Geometry) else geom
     return int(lib.pvr_simulate_noalloc(C.byref(g), C.byref(params), _ptr(x), C.byref(pt.c),
                                         _ptr(poses), _ptr(sim), _ptr(valid), _stream(stream)))
+
+
+def pvr_noalloc_status(stream=None):
+    """Read and clear the error word of pvr_simulate_noalloc on the current
+    device (synchronises); returns the pvr_status code."""
+    return int(lib.pvr_noalloc_status(_stream(stream)))
 
 
 def new_state(device="cuda"):

@@ -80,9 +80,47 @@ def test_defaults_and_host_argument_checks(pvr):
     g.pixel_to_world[0][2] = 1.0
     bad = pvr.default_params(psf_kz=99)
     assert pvr.lib.pvr_ctx_create(C.byref(h), C.byref(g), C.byref(bad)) == -1
-    bad = pvr.default_params(n_params=12)
+    bad = pvr.default_params(n_params=7)   # 6 (rigid) and 12 (affine) only
     assert pvr.lib.pvr_ctx_create(C.byref(h), C.byref(g), C.byref(bad)) == -1
     assert pvr.lib.pvr_ctx_create(None, C.byref(g), C.byref(p)) == -1
     # calls on a NULL context fail cleanly
     assert pvr.lib.pvr_simulate(None, None, None, None, None, None, None) == -1
     assert pvr.lib.pvr_last_error(None) == b"null context"
+
+
+def test_noalloc_host_checks_match_context_creation(pvr):
+    """pvr_simulate_noalloc runs the geometry / PSF checks of pvr_ctx_create on
+    the host, before any device call: a non-finite matrix, a zero slice axis,
+    a bad Taylor-sinc tolerance or an unknown pose size is rejected."""
+    def geom():
+        g = pvr.Geometry()
+        g.nx = g.ny = g.nz = 8
+        g.n_stacks = 1
+        g.stack_w[0] = g.stack_h[0] = g.stack_k[0] = 4
+        for i, v in enumerate((1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0)):
+            g.world_to_voxel[i] = v
+            g.pixel_to_world[0][i] = v
+        g.thickness[0] = 1.0
+        return g
+    dummy = C.c_void_p(16)   # never dereferenced: the checks fail first
+    pt = pvr.Patches(dummy, 1, 4, 16, None)
+    p = pvr.default_params()
+
+    def call(g, prm):
+        return pvr.lib.pvr_simulate_noalloc(C.byref(g), C.byref(prm), dummy, C.byref(pt), dummy, dummy,
+                                            dummy, None)
+    g = geom()
+    g.pixel_to_world[0][3] = float("nan")
+    assert call(g, p) == -1
+    g = geom()
+    g.world_to_voxel[5] = float("inf")
+    assert call(g, p) == -1
+    g = geom()
+    g.pixel_to_world[0][10] = 0.0   # slice axis (column 2) becomes zero
+    assert call(g, p) == -1
+    g = geom()
+    g.nx = g.ny = g.nz = 2048       # 2^33 voxels
+    assert call(g, p) == -1
+    assert call(geom(), pvr.default_params(psf_kind=1, psf_sinc_eps=0.0)) == -1
+    assert call(geom(), pvr.default_params(n_params=7)) == -1
+    assert call(geom(), pvr.default_params(psf_dz=float("nan"))) == -1

@@ -5,9 +5,12 @@ max_patch_side 64: one 64x64 tile per CTA).
 
 The oracle cannot process 74M patch-pixels in seconds, so it is compared on
 sampled patches of the full-size GPU outputs (forward model, NCC and its
-gradient), on the full patch table and lattice (cheap and bit-exact), and
-through properties that hold at any size (the adjoint's dot-product test,
-the EM statistics on the full pixel set)."""
+gradient), on the full patch table and lattice (cheap and bit-exact), on
+sampled rows of the adjoint scattered over the full grid (element by
+element, every stack: the axial, coronal and sagittal ones and the oblique
+30-degree one), and through properties that hold at any size (the
+adjoint's dot-product test, the EM statistics on the full pixel set).  The
+affine lattice and NCC gradient are checked the same way."""
 import numpy as np
 import pytest
 import torch
@@ -88,6 +91,75 @@ def test_full_adjoint_dot_product(full):
     # conf = A^T 1 restricted to valid pixels: its total is the number of valid pixels
     _, valid = ctx.pvr_simulate(torch.as_tensor(x, device="cuda"), pt, P)
     assert abs(float(conf.double().sum()) - float(valid.double().sum())) < 1e-4 * float(valid.double().sum())
+
+
+def test_full_adjoint_sampled_rows_elementwise(full):
+    """pvr_adjoint of 24 sampled rows (6 per stack) at the full volume size,
+    element by element against the oracle over all 12.6 M voxels: the
+    sagittal stack runs the through-plane (zeta) lane order of the scatter,
+    the others the lattice orders, and the oblique stack crosses cell faces
+    along all three axes."""
+    ctx, pt = full["ctx"], full["pt"]
+    desc = pt.desc.cpu().numpy()
+    rng = np.random.default_rng(31)
+    stacks = np.unique(desc[:, 0])
+    assert len(stacks) == 4
+    idx = np.sort(np.concatenate([rng.choice(np.flatnonzero(desc[:, 0] == s), 6, replace=False)
+                                  for s in stacks]))
+    d, _, npix = _sample(desc, np.zeros(pt.n_pix, np.float32), idx)
+    poses = full["poses"][idx]
+    r = rng.normal(size=npix).astype(np.float32)
+    w = rng.uniform(0.2, 1.0, npix).astype(np.float32)
+    sub = full["pvr"].PatchTable.from_numpy(d, npix)
+    addon, conf = ctx.pvr_adjoint(sub, torch.as_tensor(poses, device="cuda"),
+                                  torch.as_tensor(r, device="cuda"), torch.as_tensor(w, device="cuda"))
+    fix = O.pose_fixed(full["G"], full["ps"], d, poses)
+    ra, rc = O.adjoint(full["G"], full["ps"], d, fix, r=r.astype(np.float64), w=w.astype(np.float64))
+    ga, gc = addon.cpu().numpy().reshape(-1), conf.cpu().numpy().reshape(-1)
+    assert np.count_nonzero(rc) > 24 * 4096
+    # the same voxels are reached, and the values agree
+    assert np.array_equal(gc > 0, rc > 0)
+    assert rel_l2(ga, ra) < 1e-5 and rel_l2(gc, rc) < 1e-5
+    # per stack as well (each stack's rows alone)
+    for s in stacks:
+        rows = np.flatnonzero(d[:, 0] == s)
+        ds, _, nps = _sample(d, np.zeros(npix, np.float32), rows)
+        pix = np.concatenate([np.arange(int(d[k, 6]), int(d[k, 6]) + int(d[k, 4] * d[k, 5])) for k in rows])
+        a1, c1 = ctx.pvr_adjoint(full["pvr"].PatchTable.from_numpy(ds, nps), torch.as_tensor(poses[rows], device="cuda"),
+                                 torch.as_tensor(r[pix], device="cuda"), torch.as_tensor(w[pix], device="cuda"))
+        f1 = O.pose_fixed(full["G"], full["ps"], ds, poses[rows])
+        ra1, rc1 = O.adjoint(full["G"], full["ps"], ds, f1, r=r[pix].astype(np.float64), w=w[pix].astype(np.float64))
+        assert rel_l2(a1.cpu().numpy(), ra1) < 1e-5 and rel_l2(c1.cpu().numpy(), rc1) < 1e-5, s
+
+
+def test_full_affine_lattice_and_ncc_gradient(full):
+    """Affine poses (12 parameters, breathing-like stretch and shear) at full
+    size: the lattice of all patches bit-exact, NCC and gradient on sampled
+    patches."""
+    pvr = full["pvr"]
+    prm = pvr.default_params(psf_dz=0.75, max_patches=32768, max_pixels=1 << 27, max_patch_side=64,
+                             n_params=12)
+    ctx = pvr.Context(full["geom"], prm)
+    pt = full["pt"]
+    rng = np.random.default_rng(41)
+    poses = np.concatenate([rng.uniform(-3, 3, (pt.n, 3)), rng.uniform(-0.05, 0.05, (pt.n, 9))], 1)
+    P = torch.as_tensor(poses, device="cuda")
+    desc = pt.desc.cpu().numpy()
+    fix = ctx.pvr_pose_to_fixed(pt, P)
+    rfix = O.pose_fixed(full["G"], full["ps"], desc, poses, n_params=12)
+    assert np.array_equal(fix.cpu().numpy()[:, :13].astype(np.int64), rfix[:, :13])
+    x = full["cfg"]["gt"].reshape(-1).astype(np.float32)
+    ncc, grad = ctx.pvr_ncc_grad(torch.as_tensor(x, device="cuda"), full["y"], pt, P)
+    ncc, grad = ncc.cpu().numpy(), grad.cpu().numpy()
+    y_np = full["y"].cpu().numpy()
+    idx = np.sort(rng.choice(desc.shape[0], 12, replace=False))
+    d, ys, _ = _sample(desc, y_np, idx)
+    for k, s in enumerate(idx):
+        rn, rg = O.ncc_grad(full["G"], full["ps"], x, ys, d[k], poses[s], n_params=12)
+        assert abs(ncc[s] - rn) < 2e-5, (s, ncc[s], rn)
+        if rn != 0.0:
+            assert np.linalg.norm(grad[s] - rg) <= 2e-3 * np.linalg.norm(rg) + 1e-9, (s, grad[s], rg)
+    ctx.close()
 
 
 def test_full_ncc_gradient_sampled_patches(full):

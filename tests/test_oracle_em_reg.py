@@ -11,7 +11,9 @@ against facts fixed by statistics and algebra (not by re-typing formulas):
   monotonically and keeps x >= 0;
 * NCC: self-similarity 1, invariance to positive affine intensity changes,
   sign flip for negative scaling; gradient = central finite differences;
-* noiseless registration recovers a known rigid transform;
+* noiseless registration recovers a known rigid transform, and a known
+  affine one (12 parameters; the affine gradient equals central finite
+  differences too);
 * PSNR of a known MSE, CC/SSIM of identical images.
 """
 import math
@@ -239,6 +241,63 @@ def test_noiseless_registration_recovers_known_transform():
     err_r = np.abs(got[:, 3:] - th_true[:, 3:]).max()
     assert np.all(ncc > 0.999)
     assert err_t < 0.1 and err_r < 0.1, (err_t, err_r)
+
+
+def test_affine_ncc_gradient_matches_finite_differences():
+    geom, x, d, npix = _reg_case(1)
+    G = O.geom(geom)
+    ps = O.psf(1.2, 1, 3, 1.0)
+    fix = O.pose_fixed(G, ps, d, np.zeros((d.shape[0], 6)))
+    y, _, _ = O.simulate(G, ps, x, d, fix, npix)
+    y = y.astype(np.float32)
+    rng = np.random.default_rng(13)
+    h = 1e-5
+    for s in range(3):
+        th = np.concatenate([rng.uniform(-2, 2, 3), rng.uniform(-0.05, 0.05, 9)])
+        _, g = O.ncc_grad(G, ps, x, y, d[s], th, n_params=12, exact=False)
+        fd = np.zeros(12)
+        for k in range(12):
+            tp, tm = th.copy(), th.copy()
+            tp[k] += h
+            tm[k] -= h
+            fd[k] = (O.ncc_grad(G, ps, x, y, d[s], tp, n_params=12, exact=False)[0]
+                     - O.ncc_grad(G, ps, x, y, d[s], tm, n_params=12, exact=False)[0]) / (2 * h)
+        assert np.linalg.norm(g - fd) <= 2e-3 * np.linalg.norm(fd) + 1e-9, (g, fd)
+        # the D entries move samples by (w - c), so their gradient is far from zero
+        assert np.linalg.norm(g[3:]) > 10 * np.linalg.norm(g[:3]) * 1e-3
+
+
+def test_noiseless_affine_registration_recovers_known_transform():
+    from scipy.ndimage import gaussian_filter
+    geom, _, d, npix = _reg_case(2)
+    tex = gaussian_filter(np.random.default_rng(8).normal(size=(64, 64, 64)), 2.5)
+    x = (500 + 400 * tex / tex.std()).astype(np.float32).reshape(-1)
+    G = O.geom(geom)
+    ps = O.psf(1.2, 1, 3, 1.0)
+    rng = np.random.default_rng(14)
+    P = d.shape[0]
+    # a stretch / shear of a few per cent (breathing-like), the in-plane part
+    # observable from a 2-D patch; the out-of-plane column of D moves
+    # samples only by zeta steps (weakly observable) and stays at its truth
+    th_true = np.concatenate([rng.uniform(-1, 1, (P, 3)), rng.uniform(-0.04, 0.04, (P, 9))], 1)
+    fix = O.pose_fixed(G, ps, d, th_true, n_params=12)
+    y, _, _ = O.simulate(G, ps, x, d, fix, npix)
+    start = th_true.copy()
+    start[:, :3] += rng.uniform(-2, 2, (P, 3))
+    start[:, 3:] += rng.uniform(-0.04, 0.04, (P, 9))
+    rp = O.reg_params(n_params=12, n_eval=400, delta0=2.0, delta_min=1e-5)
+    got, ncc = O.register(G, ps, rp, x, y.astype(np.float32), d, start)
+    assert np.all(ncc > 0.9999)
+    # residual displacement over the patch: |dt + dD (w - c)| at the patch corners (mm)
+    for s in range(P):
+        S = np.asarray(geom.p2w[int(d[s, 0])])
+        half = np.array([(d[s, 4] - 1) / 2.0, (d[s, 5] - 1) / 2.0])
+        dD = (got[s, 3:] - th_true[s, 3:]).reshape(3, 3)
+        for sx in (-1, 1):
+            for sy in (-1, 1):
+                u = S[:, 0] * sx * half[0] + S[:, 1] * sy * half[1]
+                disp = (got[s, :3] - th_true[s, :3]) + dD @ u
+                assert np.linalg.norm(disp) < 0.05, (s, disp)
 
 
 def test_metrics_closed_forms():

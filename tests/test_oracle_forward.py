@@ -11,7 +11,11 @@ mathematics, independent of the oracle's own code:
 * the adjoint equals A^T of that dense matrix, and the dot-product test holds
   to 1e-12;
 * integer-voxel translations and 90-degree rotations give exact permutations
-  of voxel values.
+  of voxel values;
+* affine poses (T(w) = (I + D)(w - c) + c + t, 12 parameters): the dense
+  operator equals the same independent construction with the linear part
+  I + D, D = 0 reproduces the rigid identity lattice bit for bit, and the
+  lattice vectors agree with a numpy composition to one Q11.20 quantum.
 """
 import math
 
@@ -47,7 +51,10 @@ def _independent_dense_A(geom, desc, poses, fwhm_xy, kxy, kz, dz):
         P = np.asarray(geom.p2w[s])
         nrm = P[:, 2] / np.linalg.norm(P[:, 2])
         sz = geom.thickness[s] * to_sigma
-        R = Rotation.from_euler("ZYX", [th[5], th[4], th[3]], degrees=True).as_matrix()
+        if len(th) == 12:   # affine: linear part I + D, D row-major
+            R = np.eye(3) + np.asarray(th[3:12]).reshape(3, 3)
+        else:
+            R = Rotation.from_euler("ZYX", [th[5], th[4], th[3]], degrees=True).as_matrix()
         c = P @ np.array([x0 + (w - 1) / 2.0, y0 + (h - 1) / 2.0, k, 1.0])
         for j in range(h):
             for i in range(w):
@@ -144,6 +151,60 @@ def test_dense_operator_matches_independent_construction():
     addon, conf = O.adjoint(G, ps, desc, fix, r=r, w=w)
     np.testing.assert_allclose(addon, A.T @ (w * r), atol=1e-12)
     np.testing.assert_allclose(conf, A.T @ w, atol=1e-12)
+
+
+def _affine_poses(rng, n, dmax=0.12, trans=1.0):
+    return np.concatenate([rng.uniform(-trans, trans, (n, 3)), rng.uniform(-dmax, dmax, (n, 9))], 1)
+
+
+def test_affine_dense_operator_matches_independent_construction():
+    rng, geom, desc, npix, _, G, ps = _small_case(seed=5)
+    poses = _affine_poses(rng, desc.shape[0])
+    fix = O.pose_fixed(G, ps, desc, poses, n_params=12)
+    nv = geom.n_vox
+    A = np.zeros((npix, nv))
+    for v in range(nv):
+        e = np.zeros(nv, dtype=np.float32)
+        e[v] = 1.0
+        A[:, v], _, _ = O.simulate(G, ps, e, desc, fix, npix)
+    A_ind = _independent_dense_A(geom, desc, poses, 1.2, 1, 2, 1.0)
+    assert np.abs(A).sum() > 10.0
+    np.testing.assert_allclose(A, A_ind, atol=2e-5)
+    # a rigid pose read as affine is a different transform: the poses matter
+    fix6 = O.pose_fixed(G, ps, desc, poses[:, :6])
+    assert not np.array_equal(fix6[:, :12], fix[:, :12])
+
+
+def test_affine_identity_equals_rigid_identity_lattice():
+    """D = 0 and zero angles both give the linear part I exactly, so the
+    lattices agree bit for bit for any translation."""
+    rng, geom, desc, npix, _, G, ps = _small_case(seed=6)
+    t = rng.uniform(-2, 2, (desc.shape[0], 3))
+    rigid = np.concatenate([t, np.zeros((desc.shape[0], 3))], 1)
+    affine = np.concatenate([t, np.zeros((desc.shape[0], 9))], 1)
+    assert np.array_equal(O.pose_fixed(G, ps, desc, rigid), O.pose_fixed(G, ps, desc, affine, n_params=12))
+
+
+def test_affine_lattice_matches_numpy_within_one_quantum():
+    rng = np.random.default_rng(19)
+    geom = synth.random_geometry(rng, n=20, n_stacks=2, W=8, H=8, K=4, thick=2.0)
+    desc, _ = synth.all_patches(geom, 4, 4)
+    poses = _affine_poses(rng, desc.shape[0], dmax=0.3, trans=3.0)
+    G = O.geom(geom)
+    ps = O.psf(1.2, 1, 2, 0.7)
+    fix = O.pose_fixed(G, ps, desc, poses, n_params=12)
+    W2V = np.asarray(geom.w2v)
+    for d, th, f in zip(desc, poses, fix):
+        P = np.asarray(geom.p2w[int(d[0])])
+        L = np.eye(3) + th[3:].reshape(3, 3)
+        c = P @ np.array([d[2] + (d[4] - 1) / 2.0, d[3] + (d[5] - 1) / 2.0, d[1], 1.0])
+        o = W2V[:, :3] @ (L @ (P @ np.array([d[2], d[3], d[1], 1.0]) - c) + c + th[:3]) + W2V[:, 3]
+        ei = W2V[:, :3] @ L @ P[:, 0]
+        ej = W2V[:, :3] @ L @ P[:, 1]
+        ez = W2V[:, :3] @ L @ (P[:, 2] / np.linalg.norm(P[:, 2]) * 0.7)
+        assert f[12] == 1
+        for vec, sl in ((o, slice(0, 3)), (ei, slice(3, 6)), (ej, slice(6, 9)), (ez, slice(9, 12))):
+            assert np.max(np.abs(np.round(vec * 2**20) - f[sl])) <= 1
 
 
 @pytest.mark.parametrize("seed", [1, 2])

@@ -3,7 +3,7 @@
 differentiable simulate:
 
 * it equals central finite differences of its own value with FP64 sample
-  positions (smooth in the pose);
+  positions (smooth in the pose), for rigid and affine poses;
 * its value in fixed-point mode is sum r * sim of the pinned forward model;
 * on a volume that is linear in the voxel coordinates trilinear
   interpolation is exact, every pixel of an in-volume patch moves by the
@@ -50,6 +50,24 @@ def test_pose_vjp_matches_finite_differences():
         assert np.linalg.norm(g - fd) <= 2e-3 * np.linalg.norm(fd) + 1e-9, (g, fd)
         _, ge = O.sim_pose_vjp(G, ps, x, r, d[s], th, exact=True)
         assert np.linalg.norm(ge - g) <= 1e-3 * np.linalg.norm(g)
+
+
+def test_affine_pose_vjp_matches_finite_differences():
+    geom, x, d, npix, rng = _case(6)
+    G, ps = O.geom(geom), O.psf(1.2, 1, 3, 1.0)
+    r = rng.normal(size=npix)
+    h = 1e-5
+    for s in range(2):
+        th = np.concatenate([rng.uniform(-2, 2, 3), rng.uniform(-0.05, 0.05, 9)])
+        _, g = O.sim_pose_vjp(G, ps, x, r, d[s], th, n_params=12, exact=False)
+        fd = np.zeros(12)
+        for k in range(12):
+            tp, tm = th.copy(), th.copy()
+            tp[k] += h
+            tm[k] -= h
+            fd[k] = (O.sim_pose_vjp(G, ps, x, r, d[s], tp, n_params=12, exact=False)[0]
+                     - O.sim_pose_vjp(G, ps, x, r, d[s], tm, n_params=12, exact=False)[0]) / (2 * h)
+        assert np.linalg.norm(g - fd) <= 2e-3 * np.linalg.norm(fd) + 1e-9, (g, fd)
 
 
 def test_pose_vjp_value_is_the_forward_model():
