@@ -8,13 +8,22 @@ their pixels exceed 1 % of the maximum.  Gaussian PSF kxy = 1, kz = 3,
 dz = 0.75 mm.
 
 One step = one pvr_reconstruct_iter: 2 NCC evaluations of every patch with
-a registration accept/propose, the fixed-point lattice of the new poses,
+a registration accept/propose (affine poses, 12 parameters: the workload's
+breathing motion is affine), the fixed-point lattice of the new poses,
 simulate + residual, EM weights with patch classification, weighted adjoint,
 SIRT update (every row of the hot-path table).  The patches are one tile
 each, so the NCC kernels also leave the forward model and residual at each
 patch's best pose, and the super-resolution pass takes them from there
 instead of simulating a second time.  The patch table is built
 once before timing.  value = patch-pixels processed per second (all ranks).
+
+The line's "iteration" field times the method's whole outer iteration on the
+same workload (registration until the step falls below 0.01 or 40 NCC
+evaluations, then 5 super-resolution passes) for 10 outer iterations from
+the initial volume, with the volume PSNR against the phantom after each:
+seconds per iteration, the best PSNR, the iteration and time at which it is
+reached (without a regulariser the SIRT iterations semi-converge, so the
+best PSNR is the stopping point) and the final PSNR.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 launch with torch.distributed.run; every rank runs an independent
@@ -59,6 +68,7 @@ def _config_dict(n_patches=None, n_pix=None, slices=96):
             "stacks": "3 orthogonal + 1 oblique, 96 x 256^2 @ 0.75x0.75x2.5 mm",
             "patch": 64, "stride": 32, "psf": "gaussian kxy=1 kz=3 dz=0.75mm",
             "step": "pvr_reconstruct_iter: 2 NCC evals + pose update, 1 SR pass",
+            "pose": "affine, 12 parameters",
             "n_patches": n_patches, "n_patch_pixels": n_pix,
             "l2": "flushed between timed steps (256 MiB write)"}
 
@@ -225,8 +235,11 @@ def _oracle_sample(cfg, desc_all, y_all, n_sample, seed=0):
     return d, np.concatenate(ys), off
 
 
+N_PARAMS = 12   # affine patch poses (the workload's motion is affine)
+
+
 def _oracle_step(O, G, ps, ep, rp, x, y, d, npix, state, mask):
-    return O.reconstruct_iter(G, ps, ep, rp, x, y, d, np.zeros((d.shape[0], 6)), npix, state, mask, n_sr=1)
+    return O.reconstruct_iter(G, ps, ep, rp, x, y, d, np.zeros((d.shape[0], N_PARAMS)), npix, state, mask, n_sr=1)
 
 
 def run_oracle(cfg, desc_all, y_all, budget_s=15.0, steps=1, warmup=0, log=print):
@@ -234,18 +247,18 @@ def run_oracle(cfg, desc_all, y_all, budget_s=15.0, steps=1, warmup=0, log=print
     from oracle import pvr_oracle as O
     O.build()
     G, ps = O.geom(cfg["geom"]), O.psf(1.2, 1, 3, 0.75)
-    ep, rp = O.em_params(), O.reg_params(n_eval=2)
+    ep, rp = O.em_params(), O.reg_params(n_params=N_PARAMS, n_eval=2)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     # size the sample: time 4 patches, scale to the budget
     d, y, npix = _oracle_sample(cfg, desc_all, y_all, 4)
-    fix = O.pose_fixed(G, ps, d, np.zeros((d.shape[0], 6)))
+    fix = O.pose_fixed(G, ps, d, np.zeros((d.shape[0], N_PARAMS)), N_PARAMS)
     x = O.volume_init(G, ps, d, fix, y).astype(np.float32)
     t0 = time.perf_counter()
     _oracle_step(O, G, ps, ep, rp, x, y, d, npix, O.new_state(), np.ones(d.shape[0], np.uint8))
     per_patch = max((time.perf_counter() - t0) / 4, 1e-4)
     n = int(max(4, min(desc_all.shape[0], budget_s / per_patch)))
     d, y, npix = _oracle_sample(cfg, desc_all, y_all, n, seed=1)
-    fix = O.pose_fixed(G, ps, d, np.zeros((d.shape[0], 6)))
+    fix = O.pose_fixed(G, ps, d, np.zeros((d.shape[0], N_PARAMS)), N_PARAMS)
     x = O.volume_init(G, ps, d, fix, y).astype(np.float32)
     for _ in range(warmup):
         _oracle_step(O, G, ps, ep, rp, x, y, d, npix, O.new_state(), np.ones(d.shape[0], np.uint8))
@@ -256,14 +269,14 @@ def run_oracle(cfg, desc_all, y_all, budget_s=15.0, steps=1, warmup=0, log=print
         times.append(time.perf_counter() - t0)
     t = statistics.mean(times)
     info = {"kind": "oracle", "cores": cores, "sample": f"{d.shape[0]} of {desc_all.shape[0]} patches "
-            f"({npix} patch-pixels), full volume, one reconstruct_iter (2 NCC evals + 1 SR pass), "
+            f"({npix} patch-pixels), full volume, one reconstruct_iter (2 NCC evals + 1 SR pass, affine poses), "
             f"FP64 C oracle, OpenMP over patches", "step_s": t, "value": npix / t, "unit": UNIT}
     return npix / t, info
 
 
 # ----------------------------------------------------------------- setup --
 
-def _setup(device, slices=96):
+def _setup(device, slices=96, n_params=N_PARAMS):
     import torch
     from paper_1611_07289_b300 import pvr, synth
     t0 = time.perf_counter()
@@ -271,7 +284,7 @@ def _setup(device, slices=96):
     gen_s = time.perf_counter() - t0
     packed = torch.as_tensor(synth.pack_stacks(cfg["stacks"]), device=device)
     prm = pvr.default_params(psf_dz=0.75, max_patches=32768, max_pixels=1 << 27, max_patch_side=64,
-                             reg_evals=2, n_sr=1)
+                             reg_evals=2, n_sr=1, n_params=n_params)
     ctx = pvr.Context(cfg["geom"], prm)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -279,10 +292,47 @@ def _setup(device, slices=96):
     y = ctx.pvr_patches_gather(packed, pt)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
-    poses0 = torch.zeros((pt.n, 6), dtype=torch.float64, device=device)
+    poses0 = torch.zeros((pt.n, n_params), dtype=torch.float64, device=device)
     x0 = ctx.pvr_volume_init(y, pt, poses0)
     torch.cuda.synchronize()
     return cfg, ctx, pt, y, x0, poses0, gen_s, build_s
+
+
+def run_iterations(cfg, ctx_main, pt, y, x0, gt, dev, n_outer=10, reg_evals=40, n_sr=5, n_params=N_PARAMS):
+    """The method's whole outer iteration (registration to a step below 0.01
+    or reg_evals evaluations, then n_sr SR passes) repeated n_outer times
+    from the initial volume; per-iteration device time (CUDA events) and the
+    volume PSNR against the phantom after each."""
+    import torch
+    from paper_1611_07289_b300 import pvr
+    prm = pvr.default_params(psf_dz=0.75, max_patches=32768, max_pixels=1 << 27, max_patch_side=64,
+                             reg_evals=reg_evals, n_sr=n_sr, n_params=n_params)
+    ctx = pvr.Context(cfg["geom"], prm)
+    stream = torch.cuda.current_stream()
+    x, poses = x0.clone(), torch.zeros((pt.n, n_params), dtype=torch.float64, device=dev)
+    state, mask = pvr.new_state(dev), torch.ones(pt.n, dtype=torch.uint8, device=dev)
+    psnr = [float(ctx.pvr_metrics(gt, x)[0])]
+    ms = []
+    l0 = ctx.launches
+    for _ in range(n_outer):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.pvr_reconstruct_iter(x, y, pt, poses, state, mask)
+        b.record(stream)
+        psnr.append(float(ctx.pvr_metrics(gt, x)[0]))
+        ms.append(a.elapsed_time(b))
+    launches = ctx.launches - l0 - n_outer * 3   # the PSNR metric launches are not part of it
+    ctx.close()
+    best = int(np.argmax(psnr))
+    cum = np.cumsum([0.0] + ms) * 1e-3
+    return {"what": f"pvr_reconstruct_iter with reg_evals {reg_evals} (accept iff NCC rises, stop below step "
+                    f"0.01), n_sr {n_sr}, {'affine' if n_params == 12 else 'rigid'} poses, {n_outer} outer "
+                    "iterations from the initial volume A^T y / A^T 1",
+            "s_per_iteration": float(np.mean(ms)) * 1e-3, "ms_per_iteration": ms,
+            "psnr_db": psnr, "best_psnr_db": psnr[best], "best_at_iteration": best,
+            "s_to_best_psnr": float(cum[best]), "final_psnr_db": psnr[-1],
+            "gpu_launches_per_iteration": launches / n_outer,
+            "stopping_rule": "best PSNR (no regulariser: SIRT semi-converges and PSNR falls after it)"}
 
 
 def run_ours(args, ws, rank, local, dist):
@@ -411,6 +461,9 @@ def run_ours(args, ws, rank, local, dist):
     abytes = _algorithmic_bytes(dom, n_pix, n_vox)
     achieved = abytes / (dom_ms * 1e-3) / 1e9
     traffic = _profile_traffic(dom)
+    traffic_src = (f"dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed ncu summary "
+                   f"profiles/{dom}_uterus.md (cold-cache, serialised capture of the same kernel source)"
+                   if traffic is not None else "no ncu capture of the current kernel source")
     breakdown = {k: {"ms_per_launch": v[0] / max(v[1], 1), "share": v[0] / max(sum(p[0] for p in prof.values()), 1e-12),
                      "launch_groups": v[1]} for k, v in prof.items() if v[1]}
     res = {
@@ -424,6 +477,7 @@ def run_ours(args, ws, rank, local, dist):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "traffic_source": traffic_src,
                      "algorithmic_bytes": abytes, "ms_per_launch": dom_ms,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                      else "fallback 6.4 TB/s"},
@@ -433,6 +487,8 @@ def run_ours(args, ws, rank, local, dist):
         "s_per_iteration": t_ms * 1e-3, "psnr_db": {"before": psnr0, "after_timed_steps": psnr1},
         "setup_s": {"generate": gen_s, "patch_table": build_s},
     }
+    if not args.no_iteration:
+        res["iteration"] = run_iterations(cfg, ctx, pt, y, x0, gt, dev, n_outer=args.outer_full)
     if ws == 1 and not args.no_cpu_baseline:
         _, info = run_oracle(cfg, pt.desc.cpu().numpy(), y.cpu().numpy(), budget_s=args.cpu_budget)
         res["cpu_baseline"] = {"value": info["value"], "unit": UNIT, "cores": info["cores"],
@@ -586,7 +642,7 @@ def run_proposal(args, ws, rank, local):
     from paper_1611_07289_b300 import proposal, pvr
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
-    cfg, ctx, pt, y, x0, poses0, gen_s, build_s = _setup(dev, args.slices)
+    cfg, ctx, pt, y, x0, poses0, gen_s, build_s = _setup(dev, args.slices, n_params=6)
     gt = torch.as_tensor(cfg["gt"], device=dev)
     net = pvr.Net(batch_max=256, seed=7)
     net.reserve(pt.n, pt.n_pix)
@@ -669,6 +725,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-iteration", action="store_true", help="skip the whole-iteration field")
+    ap.add_argument("--outer-full", type=int, default=10, help="outer iterations of the whole-iteration field")
     ap.add_argument("--slices", type=int, default=96,
                     help="slices per stack (96 = the benchmark workload; fewer for profiling)")
     ap.add_argument("--workload", choices=["uterus", "uneven", "proposal"], default="uterus",

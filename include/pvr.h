@@ -301,9 +301,10 @@ PVR_API int pvr_simulate(pvr_ctx *ctx, const float *x, const pvr_patches *patche
  * the one array: calls that overlap on the GPU race, so serialise them.
  * The geometry and the PSF / pose settings pass the checks of
  * pvr_ctx_create (PVR_ERR_INVALID_ARG, nothing enqueued); n_params 6 or 12.
- * Malformed patch rows and non-finite poses are skipped (their pixels are
- * not written) and set the array's error word, which pvr_noalloc_status
- * reports; there is no context, so no error message. */
+ * A malformed patch row is skipped (its pixels are not written) and a pose
+ * whose sample map is not finite leaves its patch without valid pixels;
+ * both set the array's error word, which pvr_noalloc_status reports (there
+ * is no context, so no error message). */
 PVR_API int pvr_simulate_noalloc(const pvr_geometry *geom, const pvr_params *params, const float *x,
                                  const pvr_patches *patches, const double *poses, float *sim,
                                  uint8_t *valid, void *stream);
