@@ -493,6 +493,11 @@ PVR_API int pvr_net_train_step(pvr_net *net, const float *y, const float *s, con
                                const pvr_patches *patches, int32_t first, int32_t count,
                                const float *target, float lr, float *loss, void *stream);
 
+/* Synchronise `stream`, read and clear the network's device status: PVR_OK
+ * or PVR_ERR_TIMEOUT when a bounded wait of a tensor-core convolution gave
+ * up since the last read (its outputs are then not valid). */
+PVR_API int pvr_net_status(pvr_net *net, void *stream);
+
 /* Scratch of pvr_pose_propose for tables of up to max_patches patches and
  * max_pixels pixels (allocates; call once before proposing). */
 PVR_API int pvr_net_reserve(pvr_net *net, int32_t max_patches, int64_t max_pixels);

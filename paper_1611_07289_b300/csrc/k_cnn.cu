@@ -3,9 +3,9 @@
 // patch pose.  Activations and weights are bfloat16 (NHWC, channels a
 // multiple of 16), accumulation float32.
 //
-// Every 3x3 convolution pass is one implicit GEMM on the tensor cores
-// (mma.sync m16n8k16, bf16 x bf16 -> f32), with the im2col gather folded
-// into the tile loads:
+// Every 3x3 convolution pass is one implicit GEMM on the 5th-generation
+// tensor cores (tcgen05.mma kind::f16, bf16 x bf16 -> f32, accumulator in
+// tensor memory), with the im2col gather folded into the operand loads:
 //   forward      C[m = (n, oy, ox)][co]       = sum_k A[m][k = (ky, kx, ci)] B[co][k]
 //   input grad   C[m = (n, iy, ix)][ci]       = sum_k A[m][k = (ky, kx, co)] B[ci][k]
 //   weight grad  C[co][(ky, kx, ci)]          = sum_{m = (n, oy, ox)} A[co][m] B[(ky, kx, ci)][m]
@@ -16,9 +16,6 @@
 
 namespace pvr {
 namespace {
-
-constexpr int kBM = 64, kBN = 64, kBK = 16;
-constexpr int kRowStride = 24;   // bf16 per shared-memory tile row (16 used): conflict-free fragment reads
 
 struct ConvShape {
     int B, IH, IW, Cin, OH, OW, Cout, stride;   // padding 1, 3x3 taps
@@ -190,76 +187,173 @@ struct EpStore {
     }
 };
 
-// float32 accumulation of split-K partial sums (weight gradient)
-struct EpAdd {
+// float32 accumulation of split-K partial sums into the weight gradient
+// gw[co][k9], computed transposed: GEMM row m = k9, column n = co
+struct EpAddT {
     float *out;
-    int N;
+    int K9;
     __device__ void operator()(long long m, long long n, float v) const
     {
-        atomicAdd(out + (size_t)m * N + n, v);
+        atomicAdd(out + (size_t)n * K9 + m, v);
     }
 };
 
-__device__ __forceinline__ void mma_bf16(float c[4], const unsigned a[4], unsigned b0, unsigned b1)
+// ---- tcgen05 implicit GEMM ----
+//
+// One CTA (4 warps) computes a 128 x BN tile of C = A B^T (A: M x K, B:
+// N x K, both K-major, BN = N <= 64, a multiple of 16).  K advances in
+// stages of kTK = 32: all 128 threads gather the stage's A rows and B rows
+// through the loader functors (8 consecutive k per 16-byte chunk) into
+// shared memory in the tensor core's canonical no-swizzle K-major layout --
+// 8-row x 16-byte core matrices of 128 contiguous bytes, the 4 core
+// matrices of a row group side by side along K (leading-dimension offset
+// 128 B), row groups 512 B apart (stride-dimension offset) -- then one
+// thread issues the stage's two m128 x nBN x k16 MMAs, which accumulate in
+// tensor memory (128 lanes x BN float32 columns), and commits them to the
+// stage buffer's mbarrier.  Two buffers: the gather of stage s + 1 overlaps
+// the MMAs of stage s.  The epilogue reads the accumulator back with
+// tcgen05.ld (warp w owns rows 32w..32w+31) and hands each value to EP.
+// Every wait is bounded: on expiry the kernel records PVR_ERR_TIMEOUT in the
+// device word read by pvr_net_status, skips the rest and still frees its
+// tensor memory.
+constexpr int kTM = 128, kTK = 32;
+constexpr int kStageA = kTM * kTK * 2, kStageB = 64 * kTK * 2;   // bytes per stage buffer
+constexpr unsigned kWaitLimit = 1u << 24;                         // polls of one bounded wait
+
+__device__ unsigned g_tc_err;   // 1: a bounded wait of the tensor-core GEMM expired
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor (tcgen05 format): start address, leading-
+// and stride-dimension byte offsets (all >> 4), descriptor version 1, no
+// swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
 {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 
-// C[M][N] (+)= A[M][K] B[N][K]^T over the K range of this CTA (blockIdx.z
-// selects a slice of k_per_split); 128 threads, 64x64 tile, warp w owns
-// rows 16w..16w+15 and all 64 columns (8 m16n8 fragments).
-template <class LA, class LB, class EP>
-__global__ void __launch_bounds__(128) k_gemm_bf16(LA la, LB lb, EP ep, long long M, long long N, int K,
-                                                   int k_per_split)
+// Instruction descriptor of kind::f16: f32 accumulator, bf16 A and B, both
+// K-major, shape M x N.
+__host__ __device__ constexpr uint32_t umma_idesc(int M, int N)
 {
-    __shared__ __align__(16) __nv_bfloat16 As[kBM * kRowStride];
-    __shared__ __align__(16) __nv_bfloat16 Bs[kBN * kRowStride];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-    const long long m0 = (long long)blockIdx.x * kBM, n0 = (long long)blockIdx.y * kBN;
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (unsigned i = 0; i < kWaitLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Canonical K-major offset (bytes) of the 16-byte chunk of row r, k-chunk kc.
+__device__ __forceinline__ uint32_t canon_off(int r, int kc) { return (uint32_t)((r >> 3) * 512 + kc * 128 + (r & 7) * 16); }
+
+template <int BN, class LA, class LB, class EP>
+__global__ void __launch_bounds__(128) k_gemm_tc(LA la, LB lb, EP ep, long long M, long long N, int K,
+                                                 int k_per_split)
+{
+    __shared__ __align__(1024) unsigned char As[2][kStageA];
+    __shared__ __align__(1024) unsigned char Bs[2][kStageB];
+    __shared__ __align__(8) uint64_t mma_bar[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    constexpr int kCols = BN < 32 ? 32 : BN;   // tensor-memory columns (power of 2, >= 32)
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const long long m0 = (long long)blockIdx.x * kTM;
     const int kb = blockIdx.z * k_per_split;
     const int ke = min(K, kb + k_per_split);
-    float acc[8][4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    // each thread loads one 8-value chunk of each tile: row tid / 2, half tid % 2
-    const int lr = tid >> 1, lh = (tid & 1) * 8;
-    for (int k = kb; k < ke; k += kBK) {
-        const uint4 av = la(m0 + lr, k + lh, M, ke);
-        const uint4 bv = lb(n0 + lr, k + lh, N, ke);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mma_bar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mma_bar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    constexpr uint32_t idesc = umma_idesc(kTM, BN);
+    int stage = 0;
+    for (int k = kb; k < ke; k += kTK, ++stage) {
+        const int b = stage & 1;
+        // the MMAs that read this buffer two stages ago must be done
+        if (stage >= 2 && !mbar_wait(smem_u32(&mma_bar[b]), (uint32_t)(((stage >> 1) - 1) & 1))) abort_flag = 1;
+        for (int c = tid; c < kTM * (kTK / 8); c += 128) {
+            const int r = c & (kTM - 1), kc = c / kTM;
+            *reinterpret_cast<uint4 *>(As[b] + canon_off(r, kc)) = la(m0 + r, k + 8 * kc, M, ke);
+        }
+        for (int c = tid; c < BN * (kTK / 8); c += 128) {
+            const int r = c % BN, kc = c / BN;
+            *reinterpret_cast<uint4 *>(Bs[b] + canon_off(r, kc)) = lb(r, k + 8 * kc, N, ke);
+        }
+        // generic-proxy stores become visible to the tensor core (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        *reinterpret_cast<uint4 *>(As + lr * kRowStride + lh) = av;
-        *reinterpret_cast<uint4 *>(Bs + lr * kRowStride + lh) = bv;
-        __syncthreads();
-        const __nv_bfloat16 *ar = As + (warp * 16 + g) * kRowStride;
-        unsigned a[4];
-        a[0] = *reinterpret_cast<const unsigned *>(ar + 2 * t);
-        a[1] = *reinterpret_cast<const unsigned *>(ar + 8 * kRowStride + 2 * t);
-        a[2] = *reinterpret_cast<const unsigned *>(ar + 2 * t + 8);
-        a[3] = *reinterpret_cast<const unsigned *>(ar + 8 * kRowStride + 2 * t + 8);
+        if (abort_flag) break;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(As[b]), b0 = smem_u32(Bs[b]);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const __nv_bfloat16 *br = Bs + (j * 8 + g) * kRowStride;
-            const unsigned b0 = *reinterpret_cast<const unsigned *>(br + 2 * t);
-            const unsigned b1 = *reinterpret_cast<const unsigned *>(br + 2 * t + 8);
-            mma_bf16(acc[j], a, b0, b1);
+            for (int j = 0; j < kTK / 16; ++j) {
+                const uint64_t ad = umma_desc(a0 + 256 * j, 128, 512), bd = umma_desc(b0 + 256 * j, 128, 512);
+                const uint32_t acc = (k > kb || j > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&mma_bar[b]))
+                         : "memory");
         }
     }
-    const long long r0 = m0 + warp * 16 + g;
+    // the last stage's commit covers every MMA issued before it
+    if (stage > 0 && !abort_flag && !mbar_wait(smem_u32(&mma_bar[(stage - 1) & 1]), (uint32_t)(((stage - 1) >> 1) & 1)))
+        abort_flag = 1;
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (abort_flag) {
+        if (tid == 0) atomicOr(&g_tc_err, 1u);
+    } else if (stage > 0) {
+        const long long row = m0 + warp * 32 + (tid & 31);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const long long c0 = n0 + j * 8 + 2 * t;
-        if (r0 < M) {
-            if (c0 < N) ep(r0, c0, acc[j][0]);
-            if (c0 + 1 < N) ep(r0, c0 + 1, acc[j][1]);
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < M)
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    if (c0 + i < N) ep(row, (long long)(c0 + i), __uint_as_float(v[i]));
         }
-        if (r0 + 8 < M) {
-            if (c0 < N) ep(r0 + 8, c0, acc[j][2]);
-            if (c0 + 1 < N) ep(r0 + 8, c0 + 1, acc[j][3]);
-        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
     }
 }
 
@@ -432,15 +526,23 @@ __global__ void k_propose_select(const double *__restrict__ ncc0, const double *
     if (accepted) accepted[p] = take ? 1 : 0;
 }
 
+// C (+)= A B^T on the tensor cores; N <= 64.  split > 1 cuts K into slices
+// (blockIdx.z) whose partial sums the epilogue adds.
 template <class LA, class LB, class EP>
 cudaError_t gemm(LA la, LB lb, EP ep, long long M, long long N, int K, int split, cudaStream_t st)
 {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    if (N > 64) return cudaErrorInvalidValue;
     int kps = (K + split - 1) / split;
-    kps = (kps + kBK - 1) / kBK * kBK;
+    kps = (kps + kTK - 1) / kTK * kTK;
     const int nz = (K + kps - 1) / kps;
-    dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((N + kBN - 1) / kBN), (unsigned)nz);
-    k_gemm_bf16<LA, LB, EP><<<grid, 128, 0, st>>>(la, lb, ep, M, N, K, kps);
+    dim3 grid((unsigned)((M + kTM - 1) / kTM), 1, (unsigned)nz);
+    if (N <= 16)
+        k_gemm_tc<16, LA, LB, EP><<<grid, 128, 0, st>>>(la, lb, ep, M, N, K, kps);
+    else if (N <= 32)
+        k_gemm_tc<32, LA, LB, EP><<<grid, 128, 0, st>>>(la, lb, ep, M, N, K, kps);
+    else
+        k_gemm_tc<64, LA, LB, EP><<<grid, 128, 0, st>>>(la, lb, ep, M, N, K, kps);
     return cudaGetLastError();
 }
 
@@ -466,9 +568,11 @@ cudaError_t cnn_conv_backward(const __nv_bfloat16 *in, const __nv_bfloat16 *w, c
     cudaError_t e;
     if (gin && (e = gemm(BwdA{gout, out, sh}, BwdB{w, sh}, EpStore{gin, Cin}, Mi, Cin, 9 * Cout, 1, st)) != cudaSuccess)
         return e;
-    // weight gradient: K = all output positions, split for parallelism
+    // weight gradient, transposed so that the 128-row tile runs over the
+    // 9 Cin (tap, input channel) pairs: rows k9, columns co, K = all output
+    // positions, split for parallelism
     const int split = (int)((Mo + 4095) / 4096);
-    if ((e = gemm(WgA{gout, out, Cout}, WgB{in, sh}, EpAdd{gw, 9 * Cin}, Cout, 9 * Cin, (int)Mo,
+    if ((e = gemm(WgB{in, sh}, WgA{gout, out, Cout}, EpAddT{gw, 9 * Cin}, 9 * Cin, Cout, (int)Mo,
                   split > 0 ? split : 1, st)) != cudaSuccess)
         return e;
     dim3 grid(64, (unsigned)Cout);
@@ -529,6 +633,17 @@ cudaError_t cnn_to_bf16(const float *a, __nv_bfloat16 *b, long long n, cudaStrea
 {
     k_to_bf16<<<256, 256, 0, st>>>(a, b, n);
     return cudaGetLastError();
+}
+
+// Read and clear the timeout word of the tensor-core GEMM (stream-ordered
+// copy into *host_flag; the caller synchronises).
+cudaError_t cnn_read_timeout(unsigned *host_flag, cudaStream_t st)
+{
+    void *word = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&word, g_tc_err);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(host_flag, word, sizeof(unsigned), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    return cudaMemsetAsync(word, 0, sizeof(unsigned), st);
 }
 
 }  // namespace pvr

@@ -34,6 +34,7 @@ cudaError_t cnn_adam(float *w, const float *gw, float *m1, float *m2, long long 
 cudaError_t cnn_to_bf16(const float *a, __nv_bfloat16 *b, long long n, cudaStream_t st);
 cudaError_t cnn_propose_trial(const double *poses, const float *out, int n, const double scale[6], double *trial,
                               cudaStream_t st);
+cudaError_t cnn_read_timeout(unsigned *host_flag, cudaStream_t st);
 cudaError_t cnn_propose_select(const double *ncc0, const double *ncc1, const double *trial, int n, double *poses,
                                int32_t *accepted, cudaStream_t st);
 }  // namespace pvr
@@ -297,6 +298,15 @@ PVR_API int pvr_pose_propose(pvr_ctx *ctx, pvr_net *n, const float *x, const flo
     if (cnn_propose_select(n->ncc, n->ncc + pp->n, n->trial, pp->n, poses, accepted, st) != cudaSuccess)
         return PVR_ERR_CUDA;
     return PVR_OK;
+}
+
+PVR_API int pvr_net_status(pvr_net *n, void *stream)
+{
+    if (!n) return PVR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned h = 0;
+    if (cnn_read_timeout(&h, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return PVR_ERR_CUDA;
+    return h ? PVR_ERR_TIMEOUT : PVR_OK;
 }
 
 // Gradients of the last train step (float32, layout of pvr_net_get_params).

@@ -93,6 +93,7 @@ _SIGS = {
     "pvr_net_train_step": (C.c_int, [_VP, _VP, _VP, _VP, C.POINTER(Patches), C.c_int32, C.c_int32, _VP,
                                      C.c_float, _VP, _VP]),
     "pvr_net_reserve": (C.c_int, [_VP, C.c_int32, C.c_int64]),
+    "pvr_net_status": (C.c_int, [_VP, _VP]),
     "pvr_pose_propose": (C.c_int, [_VP, _VP, _VP, _VP, C.POINTER(Patches), _VP, _VP, _VP, _VP]),
     "pvr_patch_metrics": (C.c_int, [_VP, _VP, _VP, _VP, C.POINTER(Patches), C.c_int32, _VP, _VP, _VP]),
     "pvr_plan": (C.c_int, [_VP, C.POINTER(Patches), _VP, _VP, _VP, C.c_int32, C.c_int32, _VP]),
@@ -486,6 +487,10 @@ class Net:
         self._chk(lib.pvr_net_forward(self.h, _ptr(y), _ptr(s), _ptr(valid), C.byref(pt.c), int(first), int(count),
                                       _ptr(out), _stream(stream)), "pvr_net_forward")
         return out
+
+    def status(self, stream=None):
+        """Raise if a bounded wait of a tensor-core convolution gave up."""
+        self._chk(lib.pvr_net_status(self.h, _stream(stream)), "pvr_net_status")
 
     def reserve(self, max_patches, max_pixels):
         self._chk(lib.pvr_net_reserve(self.h, int(max_patches), int(max_pixels)), "pvr_net_reserve")
