@@ -8,8 +8,12 @@
 // tensor memory), with the im2col gather folded into the operand loads:
 //   forward      C[m = (n, oy, ox)][co]       = sum_k A[m][k = (ky, kx, ci)] B[co][k]
 //   input grad   C[m = (n, iy, ix)][ci]       = sum_k A[m][k = (ky, kx, co)] B[ci][k]
-//   weight grad  C[co][(ky, kx, ci)]          = sum_{m = (n, oy, ox)} A[co][m] B[(ky, kx, ci)][m]
-// The tile loader of each pass turns (row, k0) into 8 consecutive k values.
+//   weight grad  C[(ky, kx, ci)][co]          = sum_{m = (n, oy, ox)} act[m][(ky, kx, ci)] g[m][co]
+//                (transposed, with an extra row of ones whose result is
+//                the bias gradient sum_m g[m][co])
+// The tile loaders of the first two passes turn (row, k0) into 8
+// consecutive k values (K-major operands); those of the weight gradient
+// turn (row group, k) into 8 consecutive rows at one k (MN-major).
 #include <cuda_bf16.h>
 
 #include "pvr_internal.h"
@@ -108,58 +112,47 @@ struct BwdB {
     }
 };
 
-// weight-grad A: masked upstream gradient as A[co][m]: 8 consecutive m
-struct WgA {
-    const __nv_bfloat16 *g, *out;
-    int Cout;
-    __device__ uint4 operator()(long long co, int m0, long long N, int K) const
+// ---- MN-major loaders (weight gradient): 8 consecutive rows at one k ----
+
+// weight-grad A' (rows k9 = (ky, kx, ci), k = output position m): the 8
+// input channels ci..ci+7 under tap (ky, kx) of position m, one 16-byte
+// load; row 9 Cin is all ones (its GEMM row is the bias gradient), rows
+// beyond it are zero
+struct WgBmn {
+    const __nv_bfloat16 *in;
+    ConvShape sh;
+    __device__ uint4 operator()(long long k9, int m, long long N, int K) const
     {
-        unsigned u[4];
-        const __nv_bfloat16 zero = __float2bfloat16(0.f);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            __nv_bfloat16 v[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int m = m0 + 2 * j + h;
-                v[h] = zero;
-                if (co < N && m < K) {
-                    const size_t o = (size_t)m * Cout + co;
-                    if (__bfloat162float(out[o]) > 0.f) v[h] = g[o];
-                }
-            }
-            u[j] = pack2(v[0], v[1]);
-        }
-        return make_uint4(u[0], u[1], u[2], u[3]);
+        const int K9 = 9 * sh.Cin;
+        if (m >= K || k9 > K9) return zero4();
+        if (k9 == K9) return make_uint4(0x3F80u, 0u, 0u, 0u);   // bf16 1.0 in row K9
+        const int tap = (int)(k9 / sh.Cin), ci = (int)(k9 - (long long)tap * sh.Cin);
+        const int ky = tap / 3, kx = tap - ky * 3;
+        const int ox = m % sh.OW, r = m / sh.OW, oy = r % sh.OH, n = r / sh.OH;
+        const int iy = oy * sh.stride + ky - 1, ix = ox * sh.stride + kx - 1;
+        if (iy < 0 || ix < 0 || iy >= sh.IH || ix >= sh.IW) return zero4();
+        return *reinterpret_cast<const uint4 *>(in + (((size_t)n * sh.IH + iy) * sh.IW + ix) * sh.Cin + ci);
     }
 };
 
-// weight-grad B: activations as B[k9 = (ky, kx, ci)][m]: 8 consecutive m
-struct WgB {
-    const __nv_bfloat16 *in;
-    ConvShape sh;
-    __device__ uint4 operator()(long long k9, int m0, long long N, int K) const
+// weight-grad B' (rows co, k = output position m): the masked upstream
+// gradient of output channels co..co+7 at position m
+struct WgAmn {
+    const __nv_bfloat16 *g, *out;
+    int Cout;
+    __device__ uint4 operator()(long long co, int m, long long N, int K) const
     {
-        unsigned u[4];
+        if (co >= N || m >= K) return zero4();
+        const size_t o = (size_t)m * Cout + co;
+        const uint4 gv = *reinterpret_cast<const uint4 *>(g + o), ov = *reinterpret_cast<const uint4 *>(out + o);
+        const __nv_bfloat16 *gp = reinterpret_cast<const __nv_bfloat16 *>(&gv);
+        const __nv_bfloat16 *op = reinterpret_cast<const __nv_bfloat16 *>(&ov);
         const __nv_bfloat16 zero = __float2bfloat16(0.f);
-        const int tap = (int)(k9 / sh.Cin), ci = (int)(k9 - (long long)tap * sh.Cin);
-        const int ky = tap / 3, kx = tap - ky * 3;
+        unsigned u[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            __nv_bfloat16 v[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int m = m0 + 2 * j + h;
-                v[h] = zero;
-                if (k9 < N && m < K) {
-                    const int ox = m % sh.OW, r = m / sh.OW, oy = r % sh.OH, n = r / sh.OH;
-                    const int iy = oy * sh.stride + ky - 1, ix = ox * sh.stride + kx - 1;
-                    if (iy >= 0 && ix >= 0 && iy < sh.IH && ix < sh.IW)
-                        v[h] = in[(((size_t)n * sh.IH + iy) * sh.IW + ix) * sh.Cin + ci];
-                }
-            }
-            u[j] = pack2(v[0], v[1]);
-        }
+        for (int j = 0; j < 4; ++j)
+            u[j] = pack2(__bfloat162float(op[2 * j]) > 0.f ? gp[2 * j] : zero,
+                         __bfloat162float(op[2 * j + 1]) > 0.f ? gp[2 * j + 1] : zero);
         return make_uint4(u[0], u[1], u[2], u[3]);
     }
 };
@@ -188,20 +181,27 @@ struct EpStore {
 };
 
 // float32 accumulation of split-K partial sums into the weight gradient
-// gw[co][k9], computed transposed: GEMM row m = k9, column n = co
+// gw[co][k9], computed transposed (GEMM row m = k9, column n = co); GEMM
+// row K9 is the bias gradient gb[co]
 struct EpAddT {
-    float *out;
+    float *out, *bias;
     int K9;
     __device__ void operator()(long long m, long long n, float v) const
     {
-        atomicAdd(out + (size_t)n * K9 + m, v);
+        if (m < K9)
+            atomicAdd(out + (size_t)n * K9 + m, v);
+        else if (m == K9)
+            atomicAdd(bias + n, v);
     }
 };
 
 // ---- tcgen05 implicit GEMM ----
 //
 // One CTA (4 warps) computes a 128 x BN tile of C = A B^T (A: M x K, B:
-// N x K, both K-major, BN = N <= 64, a multiple of 16).  K advances in
+// N x K, BN = N <= 64, a multiple of 16), each operand K-major (16-byte
+// chunks of 8 consecutive k) or MN-major (chunks of 8 consecutive rows at
+// one k: the weight gradient, whose k -- the output position -- is not the
+// contiguous dimension of either operand).  K advances in
 // stages of kTK = 32: all 128 threads gather the stage's A rows and B rows
 // through the loader functors (8 consecutive k per 16-byte chunk) into
 // shared memory in the tensor core's canonical no-swizzle K-major layout --
@@ -233,11 +233,12 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 
-// Instruction descriptor of kind::f16: f32 accumulator, bf16 A and B, both
-// K-major, shape M x N.
-__host__ __device__ constexpr uint32_t umma_idesc(int M, int N)
+// Instruction descriptor of kind::f16: f32 accumulator, bf16 A and B,
+// each K-major or MN-major, shape M x N.
+__host__ __device__ constexpr uint32_t umma_idesc(int M, int N, bool mn_a, bool mn_b)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((mn_a ? 1u : 0u) << 15) | ((mn_b ? 1u : 0u) << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
@@ -257,7 +258,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 // Canonical K-major offset (bytes) of the 16-byte chunk of row r, k-chunk kc.
 __device__ __forceinline__ uint32_t canon_off(int r, int kc) { return (uint32_t)((r >> 3) * 512 + kc * 128 + (r & 7) * 16); }
 
-template <int BN, class LA, class LB, class EP>
+// Canonical MN-major offset (bytes) of the 16-byte chunk holding rows
+// 8g..8g+7 at k index p: core matrices of 8 k-rows x 8 elements, the 4
+// k-groups of a row group 128 B apart, row groups 512 B apart -- the same
+// extents as the K-major tiles.
+__device__ __forceinline__ uint32_t canon_off_mn(int g, int p) { return (uint32_t)(g * 512 + (p >> 3) * 128 + (p & 7) * 16); }
+
+template <int BN, bool MNA, bool MNB, class LA, class LB, class EP>
 __global__ void __launch_bounds__(128) k_gemm_tc(LA la, LB lb, EP ep, long long M, long long N, int K,
                                                  int k_per_split)
 {
@@ -287,19 +294,35 @@ __global__ void __launch_bounds__(128) k_gemm_tc(LA la, LB lb, EP ep, long long 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    constexpr uint32_t idesc = umma_idesc(kTM, BN);
+    constexpr uint32_t idesc = umma_idesc(kTM, BN, MNA, MNB);
     int stage = 0;
     for (int k = kb; k < ke; k += kTK, ++stage) {
         const int b = stage & 1;
         // the MMAs that read this buffer two stages ago must be done
         if (stage >= 2 && !mbar_wait(smem_u32(&mma_bar[b]), (uint32_t)(((stage >> 1) - 1) & 1))) abort_flag = 1;
-        for (int c = tid; c < kTM * (kTK / 8); c += 128) {
-            const int r = c & (kTM - 1), kc = c / kTM;
-            *reinterpret_cast<uint4 *>(As[b] + canon_off(r, kc)) = la(m0 + r, k + 8 * kc, M, ke);
+        if (MNA) {
+            // chunk = 8 consecutive rows (row group g) at one k: consecutive
+            // threads take consecutive k, one 16-byte core-matrix row each
+            for (int c = tid; c < kTM * (kTK / 8); c += 128) {
+                const int p = c % kTK, g = c / kTK;
+                *reinterpret_cast<uint4 *>(As[b] + canon_off_mn(g, p)) = la(m0 + 8 * g, k + p, M, ke);
+            }
+        } else {
+            for (int c = tid; c < kTM * (kTK / 8); c += 128) {
+                const int r = c & (kTM - 1), kc = c / kTM;
+                *reinterpret_cast<uint4 *>(As[b] + canon_off(r, kc)) = la(m0 + r, k + 8 * kc, M, ke);
+            }
         }
-        for (int c = tid; c < BN * (kTK / 8); c += 128) {
-            const int r = c % BN, kc = c / BN;
-            *reinterpret_cast<uint4 *>(Bs[b] + canon_off(r, kc)) = lb(r, k + 8 * kc, N, ke);
+        if (MNB) {
+            for (int c = tid; c < BN * (kTK / 8); c += 128) {
+                const int p = c % kTK, g = c / kTK;
+                *reinterpret_cast<uint4 *>(Bs[b] + canon_off_mn(g, p)) = lb(8 * g, k + p, N, ke);
+            }
+        } else {
+            for (int c = tid; c < BN * (kTK / 8); c += 128) {
+                const int r = c % BN, kc = c / BN;
+                *reinterpret_cast<uint4 *>(Bs[b] + canon_off(r, kc)) = lb(r, k + 8 * kc, N, ke);
+            }
         }
         // generic-proxy stores become visible to the tensor core (async proxy)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -463,21 +486,6 @@ __global__ void k_head_backward(const float *__restrict__ out, const float *__re
     }
 }
 
-// Bias gradient of a convolution: sum over m of the masked upstream gradient.
-__global__ void k_bias_grad(const __nv_bfloat16 *__restrict__ g, const __nv_bfloat16 *__restrict__ out,
-                            long long M, int C, float *__restrict__ gb)
-{
-    const int c = blockIdx.y;
-    float s = 0.f;
-    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < M; m += (long long)gridDim.x * blockDim.x) {
-        const size_t o = (size_t)m * C + c;
-        if (__bfloat162float(out[o]) > 0.f) s += __bfloat162float(g[o]);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(gb + c, s);
-}
-
 // Adam step on float32 master weights; refreshes the bf16 copy (may be null).
 __global__ void k_adam(float *__restrict__ w, const float *__restrict__ gw, float *__restrict__ m1,
                        float *__restrict__ m2, long long n, float lr, float b1, float b2, float eps,
@@ -528,7 +536,7 @@ __global__ void k_propose_select(const double *__restrict__ ncc0, const double *
 
 // C (+)= A B^T on the tensor cores; N <= 64.  split > 1 cuts K into slices
 // (blockIdx.z) whose partial sums the epilogue adds.
-template <class LA, class LB, class EP>
+template <bool MNA = false, bool MNB = false, class LA, class LB, class EP>
 cudaError_t gemm(LA la, LB lb, EP ep, long long M, long long N, int K, int split, cudaStream_t st)
 {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
@@ -538,11 +546,11 @@ cudaError_t gemm(LA la, LB lb, EP ep, long long M, long long N, int K, int split
     const int nz = (K + kps - 1) / kps;
     dim3 grid((unsigned)((M + kTM - 1) / kTM), 1, (unsigned)nz);
     if (N <= 16)
-        k_gemm_tc<16, LA, LB, EP><<<grid, 128, 0, st>>>(la, lb, ep, M, N, K, kps);
+        k_gemm_tc<16, MNA, MNB, LA, LB, EP><<<grid, 128, 0, st>>>(la, lb, ep, M, N, K, kps);
     else if (N <= 32)
-        k_gemm_tc<32, LA, LB, EP><<<grid, 128, 0, st>>>(la, lb, ep, M, N, K, kps);
+        k_gemm_tc<32, MNA, MNB, LA, LB, EP><<<grid, 128, 0, st>>>(la, lb, ep, M, N, K, kps);
     else
-        k_gemm_tc<64, LA, LB, EP><<<grid, 128, 0, st>>>(la, lb, ep, M, N, K, kps);
+        k_gemm_tc<64, MNA, MNB, LA, LB, EP><<<grid, 128, 0, st>>>(la, lb, ep, M, N, K, kps);
     return cudaGetLastError();
 }
 
@@ -568,16 +576,13 @@ cudaError_t cnn_conv_backward(const __nv_bfloat16 *in, const __nv_bfloat16 *w, c
     cudaError_t e;
     if (gin && (e = gemm(BwdA{gout, out, sh}, BwdB{w, sh}, EpStore{gin, Cin}, Mi, Cin, 9 * Cout, 1, st)) != cudaSuccess)
         return e;
-    // weight gradient, transposed so that the 128-row tile runs over the
-    // 9 Cin (tap, input channel) pairs: rows k9, columns co, K = all output
-    // positions, split for parallelism
+    // weight and bias gradient in one GEMM, transposed so that the 128-row
+    // tile runs over the 9 Cin (tap, input channel) pairs plus a row of ones
+    // (the bias): rows k9, columns co, K = all output positions (MN-major
+    // operands), split for parallelism
     const int split = (int)((Mo + 4095) / 4096);
-    if ((e = gemm(WgB{in, sh}, WgA{gout, out, Cout}, EpAddT{gw, 9 * Cin}, 9 * Cin, Cout, (int)Mo,
-                  split > 0 ? split : 1, st)) != cudaSuccess)
-        return e;
-    dim3 grid(64, (unsigned)Cout);
-    k_bias_grad<<<grid, 256, 0, st>>>(gout, out, Mo, Cout, gb);
-    return cudaGetLastError();
+    return gemm<true, true>(WgBmn{in, sh}, WgAmn{gout, out, Cout}, EpAddT{gw, gb, 9 * Cin}, 9 * Cin + 1, Cout,
+                            (int)Mo, split > 0 ? split : 1, st);
 }
 
 cudaError_t cnn_input(const float *y, const float *s, const uint8_t *valid, const int32_t *desc, int first,
