@@ -462,9 +462,12 @@ PVR_API int pvr_graph_launch(pvr_ctx *ctx, void *stream);
  * The network reads, per 64x64 patch, the acquired pixels y and the pixels
  * simulated at the current pose s (each normalised to zero mean and unit
  * deviation over the valid pixels) and predicts the 6 rigid parameters of
- * the correction; six 3x3 bf16 convolutions (tensor cores, float32
- * accumulation), global mean pooling, a float32 linear head.  Training is
- * mean squared error against given targets with Adam. */
+ * the correction in the frame of the patch's stack: translation along and
+ * rotation (degrees) about its unit column, row and slice-normal directions
+ * (the frame in which the image content of any stack moves alike); six 3x3
+ * bf16 convolutions (tensor cores, float32 accumulation), a float32 linear
+ * head on the flattened 4x4x64 last activation.  Training is mean squared
+ * error against given targets with Adam. */
 typedef struct pvr_net pvr_net;
 
 /* Allocates the network, its Adam state and activations for batches of up to
@@ -472,7 +475,8 @@ typedef struct pvr_net pvr_net;
 PVR_API int pvr_net_create(pvr_net **out, int32_t batch_max, uint64_t seed);
 PVR_API int pvr_net_destroy(pvr_net *net);
 /* Number of float32 parameters (conv weights [co][ky][kx][ci] and bias per
- * layer, then the head [6][64] and bias). */
+ * layer, then the head [6][1024] over the last activation in its (y, x,
+ * channel) order, and its bias). */
 PVR_API int64_t pvr_net_param_count(const pvr_net *net);
 /* Copy the float32 parameters to / from HOST memory (set resets Adam). */
 PVR_API int pvr_net_get_params(pvr_net *net, float *host_out);
@@ -504,8 +508,11 @@ PVR_API int pvr_net_reserve(pvr_net *net, int32_t max_patches, int64_t max_pixel
 
 /* Learned pose proposal with fallback: simulate every 64x64 patch at its
  * pose, let the network predict a correction (output k times scale[k], a
- * HOST double[6], in pose units: mm, degrees), evaluate NCC at the plain and
- * at the corrected pose, and keep the corrected pose only where NCC rises.
+ * HOST double[6], mm and degrees in the stack frame), map it to world pose
+ * increments with the stack's unit axes S (translation S t, angles S w:
+ * rotation about the stack axes to first order), evaluate NCC at the plain
+ * and at the corrected pose, and keep the corrected pose only where NCC
+ * rises.
  * The network predicts rigid corrections: the context must use rigid poses
  * (n_params 6; otherwise PVR_ERR_UNSUPPORTED).  poses: float64 [n][6]
  * in/out; accepted (device int32 [n], may be NULL):

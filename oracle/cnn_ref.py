@@ -7,11 +7,12 @@ input = the acquired and the simulated 64x64 patch, each normalised to zero
 mean and unit population deviation over the valid pixels (invalid pixels
 0), as 2 of 16 input channels; six 3x3 convolutions with padding 1, bias
 and ReLU (channels 32, 32, 64, 64, 64, 64; strides 1, 2, 2, 2, 2, 1);
-the mean over the 4x4 positions; a linear layer to 6 outputs.  Loss: the
+the 4x4x64 last activation flattened in (y, x, channel) order; a linear
+layer to 6 outputs.  Loss: the
 batch mean of sum_j (out_j - target_j)^2.
 
 Parameters come as one flat float32 vector: per layer the weights
-[co][ky][kx][ci] then the bias, then the head [6][64] and its bias.
+[co][ky][kx][ci] then the bias, then the head [6][1024] and its bias.
 With emulate_bf16, weights, the input image, every stored activation and
 every activation gradient are rounded to bfloat16 where the GPU stores them
 in that format.
@@ -23,6 +24,7 @@ import torch
 import torch.nn.functional as F
 
 LAYERS = [(16, 32, 1), (32, 32, 2), (32, 64, 2), (64, 64, 2), (64, 64, 2), (64, 64, 1)]
+FEAT = 4 * 4 * 64   # flattened last activation
 
 
 def _bf(t):
@@ -38,8 +40,8 @@ def unpack(flat):
         o += n
         bs.append(flat[o:o + cout].clone())
         o += cout
-    hw = flat[o:o + 6 * 64].reshape(6, 64).clone()
-    o += 6 * 64
+    hw = flat[o:o + 6 * FEAT].reshape(6, FEAT).clone()
+    o += 6 * FEAT
     hb = flat[o:o + 6].clone()
     return ws, bs, hw, hb
 
@@ -88,8 +90,8 @@ def forward(flat, img, emulate_bf16=True):
         if emulate_bf16:
             x = x + (_bf(x) - x).detach()
             x.register_hook(lambda g: _bf(g))
-    pooled = x.mean(dim=(2, 3))
-    out = pooled @ hw.t() + hb
+    feat = x.permute(0, 2, 3, 1).reshape(x.shape[0], FEAT)   # (y, x, channel) order
+    out = feat @ hw.t() + hb
     return out, (ws, bs, hw, hb)
 
 

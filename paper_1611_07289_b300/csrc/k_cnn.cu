@@ -435,54 +435,62 @@ __global__ void __launch_bounds__(256) k_cnn_input(const float *__restrict__ y, 
     }
 }
 
-// Head: global mean of the last activation (B x P x C, P positions), then
-// out[b][j] = bias[j] + sum_c wl[j][c] mean[b][c] (float32).  One CTA per
-// sample, C <= 128 threads.
-__global__ void k_head_forward(const __nv_bfloat16 *__restrict__ act, int P, int C,
-                               const float *__restrict__ wl, const float *__restrict__ bl, int J,
-                               float *__restrict__ pooled, float *__restrict__ out)
+// Head: out[b][j] = bias[j] + sum_f wl[j][f] feat[b][f] over the F = P C
+// features of the last activation (B x P x C, flattened in its NHWC order,
+// so the head sees where in the patch each feature lies), float32.  One CTA
+// of 128 threads per sample; feat receives the features as float32 for the
+// backward pass.  J <= 8.
+__global__ void __launch_bounds__(128) k_head_forward(const __nv_bfloat16 *__restrict__ act, int F,
+                                                      const float *__restrict__ wl, const float *__restrict__ bl,
+                                                      int J, float *__restrict__ feat, float *__restrict__ out)
 {
-    __shared__ float m[128];
-    const int b = blockIdx.x, c = threadIdx.x;
-    if (c < C) {
-        float s = 0.f;
-        for (int p = 0; p < P; ++p) s += __bfloat162float(act[((size_t)b * P + p) * C + c]);
-        m[c] = s / P;
-        pooled[(size_t)b * C + c] = m[c];
+    __shared__ float red[4][8];
+    const int b = blockIdx.x, t = threadIdx.x;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int f = t; f < F; f += blockDim.x) {
+        const float v = __bfloat162float(act[(size_t)b * F + f]);
+        feat[(size_t)b * F + f] = v;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < J) acc[j] = fmaf(wl[(size_t)j * F + f], v, acc[j]);
     }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+    if ((t & 31) == 0)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) red[t >> 5][j] = acc[j];
     __syncthreads();
-    if (c < J) {
-        float s = bl[c];
-        for (int k = 0; k < C; ++k) s = fmaf(wl[c * C + k], m[k], s);
-        out[(size_t)b * J + c] = s;
-    }
+    if (t < J) out[(size_t)b * J + t] = bl[t] + red[0][t] + red[1][t] + red[2][t] + red[3][t];
 }
 
 // Head backward for the loss mean_b sum_j (out - target)^2 / B: gradients
 // of the linear layer (accumulated into gwl, gbl) and of the last
-// activation (bf16, spread evenly over the P positions).
-__global__ void k_head_backward(const float *__restrict__ out, const float *__restrict__ target, int B,
-                                int J, const float *__restrict__ pooled, const float *__restrict__ wl,
-                                int C, int P, float *__restrict__ gwl, float *__restrict__ gbl,
-                                __nv_bfloat16 *__restrict__ gact, float *__restrict__ loss)
+// activation (bf16).  One CTA of 128 threads per sample.
+__global__ void __launch_bounds__(128) k_head_backward(const float *__restrict__ out,
+                                                       const float *__restrict__ target, int B, int J,
+                                                       const float *__restrict__ feat, const float *__restrict__ wl,
+                                                       int F, float *__restrict__ gwl, float *__restrict__ gbl,
+                                                       __nv_bfloat16 *__restrict__ gact, float *__restrict__ loss)
 {
-    __shared__ float go[16];
-    const int b = blockIdx.x, c = threadIdx.x;
-    if (c < J) {
-        const float e = out[(size_t)b * J + c] - target[(size_t)b * J + c];
-        go[c] = 2.f * e / B;
+    __shared__ float go[8];
+    const int b = blockIdx.x, t = threadIdx.x;
+    if (t < J) {
+        const float e = out[(size_t)b * J + t] - target[(size_t)b * J + t];
+        go[t] = 2.f * e / B;
         atomicAdd(loss, e * e / B);
-        atomicAdd(gbl + c, go[c]);
+        atomicAdd(gbl + t, go[t]);
     }
     __syncthreads();
-    if (c < C) {
-        float gm = 0.f;
+    for (int f = t; f < F; f += blockDim.x) {
+        const float v = feat[(size_t)b * F + f];
+        float ga = 0.f;
         for (int j = 0; j < J; ++j) {
-            gm = fmaf(wl[j * C + c], go[j], gm);
-            atomicAdd(gwl + j * C + c, go[j] * pooled[(size_t)b * C + c]);
+            ga = fmaf(wl[(size_t)j * F + f], go[j], ga);
+            atomicAdd(gwl + (size_t)j * F + f, go[j] * v);
         }
-        const __nv_bfloat16 gv = __float2bfloat16(gm / P);
-        for (int p = 0; p < P; ++p) gact[((size_t)b * P + p) * C + c] = gv;
+        gact[(size_t)b * F + f] = __float2bfloat16(ga);
     }
 }
 
@@ -508,17 +516,37 @@ __global__ void k_to_bf16(const float *__restrict__ a, __nv_bfloat16 *__restrict
         b[i] = __float2bfloat16(a[i]);
 }
 
-// trial[p][k] = poses[p][k] + scale[k] * out[p][k] (network correction in
-// pose units)
-__global__ void k_propose_trial(const double *__restrict__ poses, const float *__restrict__ out, int n,
+// trial = pose + (S t, S w): the network's correction of patch p is given
+// in the frame of its stack -- translation t and rotation angles w along /
+// about the column, row and slice-normal directions, out[p][k] times
+// scale[k] -- and S = the unit column, row and normal vectors of the
+// stack's pixel-to-world map maps both to world pose increments (mm, and
+// degrees about the world axes, to first order in the angles).
+__global__ void k_propose_trial(const DevGeom *__restrict__ g, const int32_t *__restrict__ desc,
+                                const double *__restrict__ poses, const float *__restrict__ out, int n,
                                 double s0, double s1, double s2, double s3, double s4, double s5,
                                 double *__restrict__ trial)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 6 * n) return;
-    const int k = i % 6;
-    const double sc = k == 0 ? s0 : k == 1 ? s1 : k == 2 ? s2 : k == 3 ? s3 : k == 4 ? s4 : s5;
-    trial[i] = poses[i] + sc * (double)out[i];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const double *P = g->p2w[desc[8 * (size_t)p]];
+    double S[3][3];   // S[r][c]: component r of unit axis c
+    for (int c = 0; c < 3; ++c) {
+        const double nr = sqrt(P[c] * P[c] + P[4 + c] * P[4 + c] + P[8 + c] * P[8 + c]);
+        for (int r = 0; r < 3; ++r) S[r][c] = nr > 0.0 ? P[4 * r + c] / nr : 0.0;
+    }
+    const double sc[6] = {s0, s1, s2, s3, s4, s5};
+    double loc[6];
+    for (int k = 0; k < 6; ++k) loc[k] = sc[k] * (double)out[6 * (size_t)p + k];
+    for (int r = 0; r < 3; ++r) {
+        double dt = 0.0, dw = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            dt += S[r][c] * loc[c];
+            dw += S[r][c] * loc[3 + c];
+        }
+        trial[6 * (size_t)p + r] = poses[6 * (size_t)p + r] + dt;
+        trial[6 * (size_t)p + 3 + r] = poses[6 * (size_t)p + 3 + r] + dw;
+    }
 }
 
 // Keep the proposal where it raises NCC, else the plain pose.
@@ -593,18 +621,20 @@ cudaError_t cnn_input(const float *y, const float *s, const uint8_t *valid, cons
     return cudaGetLastError();
 }
 
-cudaError_t cnn_head_forward(const __nv_bfloat16 *act, int B, int P, int C, const float *wl,
-                             const float *bl, int J, float *pooled, float *out, cudaStream_t st)
+cudaError_t cnn_head_forward(const __nv_bfloat16 *act, int B, int F, const float *wl, const float *bl, int J,
+                             float *feat, float *out, cudaStream_t st)
 {
-    k_head_forward<<<(unsigned)B, 128, 0, st>>>(act, P, C, wl, bl, J, pooled, out);
+    if (J > 8) return cudaErrorInvalidValue;
+    k_head_forward<<<(unsigned)B, 128, 0, st>>>(act, F, wl, bl, J, feat, out);
     return cudaGetLastError();
 }
 
-cudaError_t cnn_head_backward(const float *out, const float *target, int B, int J, const float *pooled,
-                              const float *wl, int C, int P, float *gwl, float *gbl, __nv_bfloat16 *gact,
-                              float *loss, cudaStream_t st)
+cudaError_t cnn_head_backward(const float *out, const float *target, int B, int J, const float *feat,
+                              const float *wl, int F, float *gwl, float *gbl, __nv_bfloat16 *gact, float *loss,
+                              cudaStream_t st)
 {
-    k_head_backward<<<(unsigned)B, 128, 0, st>>>(out, target, B, J, pooled, wl, C, P, gwl, gbl, gact, loss);
+    if (J > 8) return cudaErrorInvalidValue;
+    k_head_backward<<<(unsigned)B, 128, 0, st>>>(out, target, B, J, feat, wl, F, gwl, gbl, gact, loss);
     return cudaGetLastError();
 }
 
@@ -617,12 +647,12 @@ cudaError_t cnn_adam(float *w, const float *gw, float *m1, float *m2, long long 
     return cudaGetLastError();
 }
 
-cudaError_t cnn_propose_trial(const double *poses, const float *out, int n, const double scale[6], double *trial,
-                              cudaStream_t st)
+cudaError_t cnn_propose_trial(const DevGeom *g, const int32_t *desc, const double *poses, const float *out, int n,
+                              const double scale[6], double *trial, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    k_propose_trial<<<(6 * n + 255) / 256, 256, 0, st>>>(poses, out, n, scale[0], scale[1], scale[2], scale[3],
-                                                          scale[4], scale[5], trial);
+    k_propose_trial<<<(n + 127) / 128, 128, 0, st>>>(g, desc, poses, out, n, scale[0], scale[1], scale[2], scale[3],
+                                                      scale[4], scale[5], trial);
     return cudaGetLastError();
 }
 

@@ -330,6 +330,8 @@ const char *validate_setup(const pvr_geometry *g, const pvr_params *prm)
 
 int ctx_n_params(const pvr_ctx *c) { return c->prm.n_params; }
 
+const DevGeom *ctx_dev_geom(const pvr_ctx *c) { return c->d_geom; }
+
 }  // namespace pvr
 
 extern "C" {

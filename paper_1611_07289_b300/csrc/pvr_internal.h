@@ -39,8 +39,9 @@ void make_psf_tab(const pvr_geometry *g, const pvr_params *prm, PsfTab *tab);
 // context-free forward model: null when valid, else a one-line reason.
 const char *validate_setup(const pvr_geometry *g, const pvr_params *prm);
 
-// Pose parameter count (6 or 12) of a context.
+// Pose parameter count (6 or 12) and device geometry of a context.
 int ctx_n_params(const pvr_ctx *c);
+const DevGeom *ctx_dev_geom(const pvr_ctx *c);
 
 // Patch-tile decomposition shared by the per-patch kernels: tile side T
 // pixels, tiles_x * tiles_y tiles per patch (the largest patch's count);

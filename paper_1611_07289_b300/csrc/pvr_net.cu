@@ -1,9 +1,12 @@
 // pvr_net: the learned pose proposal.  A 2-D CNN reads a 64x64 acquired
 // patch and the patch simulated at the current pose estimate and predicts
-// the rigid correction (6 parameters) that registers them; NCC registration
+// the rigid correction (6 parameters, in the frame of the patch's stack:
+// along / about its column, row and normal directions) that registers them; NCC registration
 // starts from the proposal where it improves NCC and from the plain pose
 // otherwise.  Six 3x3 convolutions (ReLU; 32, 32, 64, 64, 64, 64 channels;
-// strides 1, 2, 2, 2, 2, 1), global mean pooling and a linear head.
+// strides 1, 2, 2, 2, 2, 1) and a linear head on the flattened 4x4x64
+// last activation (positions kept: a mean over them would discard where
+// the patch content lies, and with it the in-plane translation).
 // Weights: float32 master copies with Adam moments, bfloat16 working copies
 // for the tensor-core convolutions (csrc/k_cnn.cu).
 #include <cuda_bf16.h>
@@ -24,16 +27,16 @@ cudaError_t cnn_conv_backward(const __nv_bfloat16 *in, const __nv_bfloat16 *w, c
                               int IH, int IW, int Cin, int Cout, int stride, cudaStream_t st);
 cudaError_t cnn_input(const float *y, const float *s, const uint8_t *valid, const int32_t *desc, int first,
                       int count, int64_t n_pix, __nv_bfloat16 *img, cudaStream_t st);
-cudaError_t cnn_head_forward(const __nv_bfloat16 *act, int B, int P, int C, const float *wl,
-                             const float *bl, int J, float *pooled, float *out, cudaStream_t st);
-cudaError_t cnn_head_backward(const float *out, const float *target, int B, int J, const float *pooled,
-                              const float *wl, int C, int P, float *gwl, float *gbl, __nv_bfloat16 *gact,
+cudaError_t cnn_head_forward(const __nv_bfloat16 *act, int B, int F, const float *wl, const float *bl, int J,
+                             float *feat, float *out, cudaStream_t st);
+cudaError_t cnn_head_backward(const float *out, const float *target, int B, int J, const float *feat,
+                              const float *wl, int F, float *gwl, float *gbl, __nv_bfloat16 *gact,
                               float *loss, cudaStream_t st);
 cudaError_t cnn_adam(float *w, const float *gw, float *m1, float *m2, long long n, float lr, int step,
                      __nv_bfloat16 *wb, cudaStream_t st);
 cudaError_t cnn_to_bf16(const float *a, __nv_bfloat16 *b, long long n, cudaStream_t st);
-cudaError_t cnn_propose_trial(const double *poses, const float *out, int n, const double scale[6], double *trial,
-                              cudaStream_t st);
+cudaError_t cnn_propose_trial(const DevGeom *g, const int32_t *desc, const double *poses, const float *out, int n,
+                              const double scale[6], double *trial, cudaStream_t st);
 cudaError_t cnn_read_timeout(unsigned *host_flag, cudaStream_t st);
 cudaError_t cnn_propose_select(const double *ncc0, const double *ncc1, const double *trial, int n, double *poses,
                                int32_t *accepted, cudaStream_t st);
@@ -52,6 +55,7 @@ struct Layer {
 const Layer kLayers[] = {{16, 32, 1, 64}, {32, 32, 2, 64}, {32, 64, 2, 32},
                          {64, 64, 2, 16}, {64, 64, 2, 8},  {64, 64, 1, 4}};
 constexpr int kNL = 6, kSide = 64, kInC = 16, kOut = 6;
+constexpr int kFeat = 4 * 4 * 64;   // flattened last activation (OH x OW x Cout of the last layer)
 
 }  // namespace
 
@@ -62,7 +66,7 @@ struct pvr_net {
     float *w = nullptr, *gw = nullptr, *m1 = nullptr, *m2 = nullptr;
     __nv_bfloat16 *wb = nullptr;
     __nv_bfloat16 *img = nullptr, *act[kNL] = {}, *gact[kNL] = {};
-    float *pooled = nullptr, *out = nullptr, *loss = nullptr;
+    float *pooled = nullptr, *out = nullptr, *loss = nullptr;   // pooled: head features [batch][kFeat]
     int step = 0;
     // scratch of pvr_pose_propose (pvr_net_reserve)
     int64_t res_patches = 0, res_pixels = 0;
@@ -103,9 +107,8 @@ int forward(pvr_net *n, const float *y, const float *s, const uint8_t *valid, co
             return PVR_ERR_CUDA;
         in = n->act[l];
     }
-    const Layer &last = kLayers[kNL - 1];
-    if (cnn_head_forward(n->act[kNL - 1], count, last.OH() * last.OH(), last.Cout, n->w + n->head_w,
-                         n->w + n->head_b, kOut, n->pooled, n->out, st) != cudaSuccess)
+    if (cnn_head_forward(n->act[kNL - 1], count, kFeat, n->w + n->head_w, n->w + n->head_b, kOut, n->pooled,
+                         n->out, st) != cudaSuccess)
         return PVR_ERR_CUDA;
     return PVR_OK;
 }
@@ -128,7 +131,7 @@ PVR_API int pvr_net_create(pvr_net **out, int32_t batch_max, uint64_t seed)
         o += kLayers[l].Cout;
     }
     n->head_w = o;
-    o += (long long)kOut * kLayers[kNL - 1].Cout;
+    o += (long long)kOut * kFeat;
     n->head_b = o;
     o += kOut;
     n->n_params = o;
@@ -163,7 +166,7 @@ PVR_API int pvr_net_create(pvr_net **out, int32_t batch_max, uint64_t seed)
         alloc((void **)&n->act[l], sz);
         alloc((void **)&n->gact[l], sz);
     }
-    alloc((void **)&n->pooled, (size_t)batch_max * kLayers[kNL - 1].Cout * sizeof(float));
+    alloc((void **)&n->pooled, (size_t)batch_max * kFeat * sizeof(float));
     alloc((void **)&n->out, (size_t)batch_max * kOut * sizeof(float));
     alloc((void **)&n->loss, sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(n->w, h.data(), o * sizeof(float), cudaMemcpyHostToDevice);
@@ -233,10 +236,8 @@ PVR_API int pvr_net_train_step(pvr_net *n, const float *y, const float *s, const
     if (cudaMemsetAsync(n->loss, 0, sizeof(float), st) != cudaSuccess) return PVR_ERR_CUDA;
     int rc = forward(n, y, s, valid, pp, first, count, st);
     if (rc) return rc;
-    const Layer &last = kLayers[kNL - 1];
-    const int P = last.OH() * last.OH();
-    if (cnn_head_backward(n->out, target, count, kOut, n->pooled, n->w + n->head_w, last.Cout, P,
-                          n->gw + n->head_w, n->gw + n->head_b, n->gact[kNL - 1], n->loss, st) != cudaSuccess)
+    if (cnn_head_backward(n->out, target, count, kOut, n->pooled, n->w + n->head_w, kFeat, n->gw + n->head_w,
+                          n->gw + n->head_b, n->gact[kNL - 1], n->loss, st) != cudaSuccess)
         return PVR_ERR_CUDA;
     for (int l = kNL - 1; l >= 0; --l) {
         const Layer &L = kLayers[l];
@@ -291,7 +292,8 @@ PVR_API int pvr_pose_propose(pvr_ctx *ctx, pvr_net *n, const float *x, const flo
         if ((rc = pvr_net_forward(n, y, n->sim, n->valid, pp, first, cnt, n->props + (size_t)first * kOut, stream)))
             return rc;
     }
-    if (cnn_propose_trial(poses, n->props, pp->n, scale, n->trial, st) != cudaSuccess) return PVR_ERR_CUDA;
+    if (cnn_propose_trial(ctx_dev_geom(ctx), pp->desc, poses, n->props, pp->n, scale, n->trial, st) != cudaSuccess)
+        return PVR_ERR_CUDA;
     // NCC at the plain and at the proposed pose; keep the better
     if ((rc = pvr_ncc_grad(ctx, x, y, pp, poses, n->ncc, nullptr, stream))) return rc;
     if ((rc = pvr_ncc_grad(ctx, x, y, pp, n->trial, n->ncc + pp->n, nullptr, stream))) return rc;

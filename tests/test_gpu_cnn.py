@@ -44,7 +44,7 @@ def test_cnn_forward_and_gradients_match_reference(pvr):
     desc, npix, y, s, valid, target = _batch(rng, B)
     net = pvr.Net(batch_max=8, seed=3)
     flat = net.get_params()
-    assert flat.size == net.param_count() == sum(co * 9 * ci + co for ci, co, _ in cnn_ref.LAYERS) + 6 * 64 + 6
+    assert flat.size == net.param_count() == sum(co * 9 * ci + co for ci, co, _ in cnn_ref.LAYERS) + 6 * cnn_ref.FEAT + 6
     pt = pvr.PatchTable.from_numpy(desc, npix)
     dev = lambda a: torch.as_tensor(a, device="cuda")
     out = net.forward(dev(y), dev(s), dev(valid), pt).cpu().numpy()
