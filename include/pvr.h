@@ -151,6 +151,10 @@ typedef struct pvr_params {
      * PSF weight sum is not positive is invalid. */
     int32_t psf_kind;       /* default PVR_PSF_GAUSSIAN */
     double psf_sinc_eps;    /* default 1e-12 */
+    /* superpixel patch builder: the smallest superpixel size a the context
+     * serves (its scratch is sized for it at creation); 0 (default): no
+     * superpixel scratch, pvr_patches_build_slic is refused */
+    int32_t slic_a_min;
 } pvr_params;
 
 /* Patch table handed to every per-patch call (host struct, device table). */
@@ -252,9 +256,11 @@ PVR_API int pvr_patches_build_sizes(pvr_ctx *ctx, const float *stacks, const int
  * member_out (device uint8, capacity max_pixels) receives, per box pixel,
  * 1 if it belongs to the dilated superpixel: pass it as pvr_patches.member.
  * Centres start on a grid of max(1, round(W/a)) x max(1, round(H/a)) cells;
- * n_iter assignment/update rounds (intensity sums exact, see the design
- * notes).  a >= 2; gamma 0..32; n_iter 1..100.  Allocates and frees its own
- * scratch; synchronises `stream`; n_out, n_pix_out: HOST pointers. */
+ * n_iter assignment/update rounds (integer intensity sums, so the result
+ * does not depend on the summation order).  a >= pvr_params.slic_a_min
+ * (>= 2); gamma 0..32; n_iter 1..100.  Uses the context's superpixel scratch
+ * (allocates nothing); synchronises `stream`; n_out, n_pix_out: HOST
+ * pointers. */
 PVR_API int pvr_patches_build_slic(pvr_ctx *ctx, const float *stacks, int32_t a, double compactness,
                                    int32_t gamma, int32_t n_iter, double fg_frac, double keep_frac,
                                    int32_t *desc_out, uint8_t *member_out, int32_t max_out,

@@ -19,6 +19,8 @@
 
 #include <vector>
 
+#include <algorithm>
+
 #include "pvr_internal.h"
 
 namespace pvr {
@@ -302,11 +304,69 @@ __global__ void __launch_bounds__(256) k_slic_member(const SlicSlice *__restrict
 
 }  // namespace
 
+// Superpixel centres of every slice for superpixel size a: max(1, round(W/a))
+// x max(1, round(H/a)) per slice (never more for a larger a).
+int64_t slic_centres(const pvr_geometry &hg, int a)
+{
+    int64_t C = 0;
+    for (int s = 0; s < hg.n_stacks; ++s) {
+        const int64_t nx = std::max<int64_t>(1, lround((double)hg.stack_w[s] / a));
+        const int64_t ny = std::max<int64_t>(1, lround((double)hg.stack_h[s] / a));
+        C += (int64_t)hg.stack_k[s] * nx * ny;
+    }
+    return C;
+}
+
+namespace {
+
+// Carving of the superpixel scratch: 256-byte aligned pieces.
+struct SlicScratch {
+    SlicSlice *sl;
+    int *cs, *cnt, *box, *keep, *geo;
+    int32_t *label, *row_of;
+    float *cx, *cy, *ci;
+    unsigned long long *sums;
+};
+
+size_t carve(void *base, int n_slices, int64_t C, int64_t total, SlicScratch *out)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        void *p = base ? (void *)((char *)base + off) : nullptr;
+        off += (bytes + 255) / 256 * 256;
+        return p;
+    };
+    SlicScratch s;
+    s.sl = (SlicSlice *)take((size_t)n_slices * sizeof(SlicSlice));
+    s.cs = (int *)take((size_t)C * sizeof(int));
+    s.cnt = (int *)take((size_t)C * sizeof(int));
+    s.box = (int *)take((size_t)C * 4 * sizeof(int));
+    s.keep = (int *)take((size_t)C * sizeof(int));
+    s.geo = (int *)take((size_t)C * 4 * sizeof(int));
+    s.row_of = (int32_t *)take((size_t)C * sizeof(int32_t));
+    s.label = (int32_t *)take((size_t)total * sizeof(int32_t));
+    s.cx = (float *)take((size_t)C * sizeof(float));
+    s.cy = (float *)take((size_t)C * sizeof(float));
+    s.ci = (float *)take((size_t)C * sizeof(float));
+    s.sums = (unsigned long long *)take((size_t)C * 3 * sizeof(unsigned long long));
+    if (out) *out = s;
+    return off;
+}
+
+}  // namespace
+
+size_t slic_scratch_bytes(const pvr_geometry &hg, int a_min, int64_t total)
+{
+    int n_slices = 0;
+    for (int s = 0; s < hg.n_stacks; ++s) n_slices += hg.stack_k[s];
+    return carve(nullptr, n_slices, slic_centres(hg, a_min), total, nullptr);
+}
+
 cudaError_t launch_patches_build_slic(const DevGeom *g, const pvr_geometry &hg, const float *stacks, int64_t total,
                                       int a, double t, int gamma, int n_iter, double fg_frac, double keep_frac,
                                       int max_side, int32_t *desc_out, int max_out, uint8_t *member_out,
                                       int64_t max_pix, unsigned *imax_key, int32_t *counts, int64_t *n_centres_out,
-                                      cudaStream_t st)
+                                      void *scratch, cudaStream_t st)
 {
     (void)g;
     std::vector<SlicSlice> sl;
@@ -337,28 +397,15 @@ cudaError_t launch_patches_build_slic(const DevGeom *g, const pvr_geometry &hg, 
     }
     *n_centres_out = C;
     const int n_slices = (int)sl.size();
-    // scratch of this setup call
-    SlicSlice *d_sl = nullptr;
-    int *d_cs = nullptr, *cnt = nullptr, *box = nullptr, *keep = nullptr, *geo = nullptr;
-    int32_t *label = nullptr, *row_of = nullptr;
-    float *cx = nullptr, *cy = nullptr, *ci = nullptr;
-    unsigned long long *sums = nullptr;
+    // the context's superpixel scratch (sized for its smallest superpixel size)
+    SlicScratch sc;
+    carve(scratch, n_slices, C, total, &sc);
+    SlicSlice *d_sl = sc.sl;
+    int *d_cs = sc.cs, *cnt = sc.cnt, *box = sc.box, *keep = sc.keep, *geo = sc.geo;
+    int32_t *label = sc.label, *row_of = sc.row_of;
+    float *cx = sc.cx, *cy = sc.cy, *ci = sc.ci;
+    unsigned long long *sums = sc.sums;
     cudaError_t e = cudaSuccess;
-    auto alloc = [&](void **p, size_t b) {
-        if (e == cudaSuccess) e = cudaMalloc(p, b > 0 ? b : 1);
-    };
-    alloc((void **)&d_sl, sl.size() * sizeof(SlicSlice));
-    alloc((void **)&d_cs, (size_t)C * sizeof(int));
-    alloc((void **)&cnt, (size_t)C * sizeof(int));
-    alloc((void **)&box, (size_t)C * 4 * sizeof(int));
-    alloc((void **)&keep, (size_t)C * sizeof(int));
-    alloc((void **)&geo, (size_t)C * 4 * sizeof(int));
-    alloc((void **)&row_of, (size_t)C * sizeof(int32_t));
-    alloc((void **)&label, (size_t)total * sizeof(int32_t));
-    alloc((void **)&cx, (size_t)C * sizeof(float));
-    alloc((void **)&cy, (size_t)C * sizeof(float));
-    alloc((void **)&ci, (size_t)C * sizeof(float));
-    alloc((void **)&sums, (size_t)C * 3 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_sl, sl.data(), sl.size() * sizeof(SlicSlice), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_cs, c_slice.data(), c_slice.size() * sizeof(int), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, (size_t)C * sizeof(int), st);
@@ -389,12 +436,6 @@ cudaError_t launch_patches_build_slic(const DevGeom *g, const pvr_geometry &hg, 
             e = cudaGetLastError();
         }
     }
-    // the scratch goes once the work is done (this call synchronises anyway)
-    cudaError_t e2 = cudaStreamSynchronize(st);
-    if (e == cudaSuccess) e = e2;
-    void *ptrs[] = {d_sl, d_cs, cnt, box, keep, geo, row_of, label, cx, cy, ci, sums};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
     return e;
 }
 

@@ -34,7 +34,8 @@ cudaError_t launch_patches_build_slic(const DevGeom *g, const pvr_geometry &hg, 
                                       int a, double t, int gamma, int n_iter, double fg_frac, double keep_frac,
                                       int max_side, int32_t *desc_out, int max_out, uint8_t *member_out,
                                       int64_t max_pix, unsigned *imax_key, int32_t *counts, int64_t *n_centres_out,
-                                      cudaStream_t st);
+                                      void *scratch, cudaStream_t st);
+size_t slic_scratch_bytes(const pvr_geometry &hg, int a_min, int64_t total);
 }  // namespace pvr
 
 using namespace pvr;
@@ -78,6 +79,7 @@ struct pvr_ctx {
     unsigned *imax_key = nullptr;
     int32_t *counts = nullptr;
     void *slice_scr = nullptr;   // per-slice candidate table of the patch builder
+    void *slic_scr = nullptr;    // superpixel builder scratch (pvr_params.slic_a_min > 0)
     int n_slices = 0;
     // work plan of one patch table (pvr_plan): tiling, launch mode, tile list
     int tpp_alloc = 1;            // slots per patch the partial buffers hold
@@ -226,7 +228,7 @@ void free_all(pvr_ctx *c)
                     c->err, c->best, c->gbest, c->nbest, c->trial, c->delta, c->ncc_tmp,
                     c->grad_tmp, c->active, c->s_buf, c->e_buf, c->p_buf, c->v_buf,
                     c->valid_buf, c->mask_tmp, c->acc2, c->quad, c->gbuf, c->keep, c->imax_key,
-                    c->slice_scr, c->plan_items, c->plan_counter,
+                    c->slice_scr, c->slic_scr, c->plan_items, c->plan_counter,
                     c->counts, c->metric_scr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -384,6 +386,7 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
     if (prm->max_patch_side < 1 || prm->max_patch_side > kMaxSideLimit)
         return bad("max_patch_side outside 1..256");
     if (prm->patch_em_iters < 0 || prm->reg_evals < 0 || prm->n_sr < 0) return bad("negative count");
+    if (prm->slic_a_min != 0 && prm->slic_a_min < 2) return bad("slic_a_min must be 0 or >= 2");
     c->geom = *g;
     c->prm = *prm;
     cudaGetDevice(&c->device);
@@ -472,6 +475,7 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
     c->n_slices = 0;
     for (int s = 0; s < g->n_stacks; ++s) c->n_slices += g->stack_k[s];
     ALLOC((char *&)c->slice_scr, patches_slice_scratch_bytes(c->n_slices));
+    if (prm->slic_a_min > 0) ALLOC((char *&)c->slic_scr, slic_scratch_bytes(*g, prm->slic_a_min, off));
     ALLOC(c->metric_scr, kMetricScratch);
 #undef ALLOC
     if (e == cudaSuccess) e = cudaMemcpy(c->d_geom, &hg, sizeof hg, cudaMemcpyHostToDevice);
@@ -563,6 +567,8 @@ int pvr_patches_build_slic(pvr_ctx *c, const float *stacks, int32_t a, double co
     if (!c) return PVR_ERR_INVALID_ARG;
     REQUIRE(stacks && desc_out && member_out && n_out && n_pix_out, "NULL argument");
     REQUIRE(a >= 2 && gamma >= 0 && gamma <= 32 && n_iter >= 1 && n_iter <= 100, "a >= 2, gamma 0..32, n_iter 1..100");
+    REQUIRE(c->slic_scr != nullptr, "the context has no superpixel scratch (create it with slic_a_min > 0)");
+    REQUIRE(a >= c->prm.slic_a_min, "superpixel size %d below the context's slic_a_min %d", a, c->prm.slic_a_min);
     REQUIRE(compactness > 0.0 && isfinite(compactness), "compactness must be positive");
     REQUIRE(max_out >= 0, "max_out < 0");
     REQUIRE(isfinite(fg_frac) && isfinite(keep_frac), "non-finite level");
@@ -573,7 +579,7 @@ int pvr_patches_build_slic(pvr_ctx *c, const float *stacks, int32_t a, double co
     int64_t nc = 0;
     CUDA_TRY(launch_patches_build_slic(c->d_geom, c->geom, stacks, c->stack_total, a, compactness, gamma, n_iter,
                                        fg_frac, keep_frac, max_side, desc_out, max_out, member_out,
-                                       c->prm.max_pixels, c->imax_key, c->counts, &nc, st),
+                                       c->prm.max_pixels, c->imax_key, c->counts, &nc, c->slic_scr, st),
              "patches_build_slic");
     c->launches += 2 + 2 * (int64_t)n_iter + 4;
     int32_t h[4];

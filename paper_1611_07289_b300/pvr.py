@@ -49,7 +49,8 @@ class Params(C.Structure):
                 ("reg_delta_min", C.c_double), ("reg_grow", C.c_double),
                 ("reg_fixed_step", C.c_int32), ("reg_min_valid", C.c_int32), ("n_sr", C.c_int32),
                 ("max_patches", C.c_int32), ("max_pixels", C.c_int64),
-                ("max_patch_side", C.c_int32), ("psf_kind", C.c_int32), ("psf_sinc_eps", C.c_double)]
+                ("max_patch_side", C.c_int32), ("psf_kind", C.c_int32), ("psf_sinc_eps", C.c_double),
+                ("slic_a_min", C.c_int32)]
 
 
 class Patches(C.Structure):

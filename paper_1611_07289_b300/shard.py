@@ -10,8 +10,10 @@ problem splits over R ranks as follows:
   patch pixels start at offset 0 (``shard_table``);
 * the forward model, residuals, per-patch potentials and registration run on
   each rank's own rows with no exchange;
-* the exchanges per super-resolution pass are the global EM sums (Eq. for
-  sigma^2 and c: sum p e^2, sum p, pixel counts, and max / min of e for m),
+* the exchanges per super-resolution pass are the global EM sums: before
+  the E-step the pixel count, sum e^2 and max / min of e (the first call's
+  sigma^2 and the outlier density m, ``em_global_stats``), after it sum p and
+  sum p e^2 (the M-step's sigma^2 and c, ``em_mstep_sums``),
   the per-patch potentials p-bar for the patch mixture (an all-gather of one
   float per patch), and one sum over ranks of the adjoint volumes addon and
   conf before the SIRT update (``allreduce_sum_``).
@@ -92,6 +94,19 @@ def em_global_stats(e, valid, dist, group=None):
     dist.all_reduce(lo, op=dist.ReduceOp.MIN, group=group)
     dist.all_reduce(hi, op=dist.ReduceOp.MAX, group=group)
     return float(s[0]), float(s[1]), float(lo[0]), float(hi[0])
+
+
+def em_mstep_sums(p, e, valid, dist, group=None):
+    """Global M-step sums after the E-step (Sec. II, EM outlier model: the
+    new sigma^2 = sum p e^2 / sum p and c = sum p / N): returns (sum p,
+    sum p e^2) over the valid participating pixels of all ranks, float64."""
+    import torch
+    p = torch.as_tensor(p, dtype=torch.float64)
+    e = torch.as_tensor(e, dtype=torch.float64)
+    v = torch.as_tensor(valid).to(torch.bool)
+    s = torch.tensor([float(p[v].sum()), float((p[v] * e[v] * e[v]).sum())], dtype=torch.float64)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM, group=group)
+    return float(s[0]), float(s[1])
 
 
 def gather_patch_values(vals, bounds, dist, group=None):

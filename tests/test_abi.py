@@ -47,6 +47,7 @@ int main(void) {
   F(pvr_geometry, world_to_voxel); F(pvr_geometry, pixel_to_world); F(pvr_geometry, thickness);
   F(pvr_params, psf_dz); F(pvr_params, alpha); F(pvr_params, patch_rule); F(pvr_params, n_params);
   F(pvr_params, reg_grow); F(pvr_params, n_sr); F(pvr_params, max_pixels); F(pvr_params, max_patch_side);
+  F(pvr_params, psf_kind); F(pvr_params, psf_sinc_eps); F(pvr_params, slic_a_min);
   F(pvr_patches, n); F(pvr_patches, max_side); F(pvr_patches, n_pix);
   return 0;
 }

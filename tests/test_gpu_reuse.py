@@ -69,7 +69,8 @@ def test_reused_forward_model_with_superpixel_patches(pvr):
     the kept forward model honours the masks like the simulate kernel."""
     cfg = synth.config_tiny()
     geom = cfg["geom"]
-    prm = dict(reg_evals=3, reg_delta0=0.5, n_sr=1, max_patches=4096, max_pixels=1 << 22, max_patch_side=64)
+    prm = dict(reg_evals=3, reg_delta0=0.5, n_sr=1, max_patches=4096, max_pixels=1 << 22, max_patch_side=64,
+               slic_a_min=16)
     packed = _t(synth.pack_stacks(cfg["stacks"]))
     out = []
     for tile in (0, 32):

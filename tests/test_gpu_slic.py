@@ -40,7 +40,8 @@ def _case(seed):
 @pytest.mark.parametrize("a,t,gamma,keep", [(12, 10.0, 3, 0.0), (10, 4.0, 5, 0.5)])
 def test_slic_table_and_members_are_exact(pvr, a, t, gamma, keep):
     geom, stacks, rng = _case(1)
-    ctx = pvr.Context(geom, pvr.default_params(max_patches=4096, max_pixels=1 << 22, max_patch_side=128))
+    ctx = pvr.Context(geom, pvr.default_params(max_patches=4096, max_pixels=1 << 22, max_patch_side=128,
+                                               slic_a_min=8))
     pt, n = ctx.pvr_patches_build_slic(_t(synth.pack_stacks(stacks)), a, t, gamma, n_iter=6, fg_frac=0.3,
                                        keep_frac=keep)
     desc, member, npix = slic_ref.patches_build_slic(geom.stack_dims, stacks, a, t, gamma, n_iter=6, fg_frac=0.3,
@@ -53,7 +54,7 @@ def test_slic_table_and_members_are_exact(pvr, a, t, gamma, keep):
 def test_superpixel_patches_through_the_model(pvr):
     geom, stacks, rng = _case(2)
     ctx = pvr.Context(geom, pvr.default_params(psf_dz=0.8, max_patches=4096, max_pixels=1 << 22,
-                                               max_patch_side=128))
+                                               max_patch_side=128, slic_a_min=8))
     packed = _t(synth.pack_stacks(stacks))
     pt, n = ctx.pvr_patches_build_slic(packed, 12, 10.0, 3, n_iter=6)
     desc = pt.desc.cpu().numpy()

@@ -1,8 +1,11 @@
 """The patch-sharded form of a reconstruction pass, run as CPU ranks over
-gloo (world size 2).  Each rank computes its own rows with the oracle; the
-exchanges (adjoint sum, EM statistics, per-patch p-bar gather, slowest-rank
-time) go through paper_1611_07289_b300.shard and must reproduce the
-unsharded oracle results."""
+gloo (world size 2).  Each rank computes its own rows with the oracle (the
+forward model and adjoint) and runs the EM E-step on its own pixels; the
+exchanges (adjoint sum, the EM statistics before and the M-step sums after
+the E-step, the per-patch p-bar gather, slowest-rank time) go through
+paper_1611_07289_b300.shard and must reproduce the unsharded oracle's
+volumes, EM state, pixel weights and patch potentials."""
+import math
 import os
 import socket
 
@@ -94,11 +97,25 @@ def _rank_main(rank, ws, port):
         assert abs(se2 - float((ev * ev).sum())) <= 1e-12 * se2
         assert abs(1.0 / (emax - emin) - st[O.ST["M"]]) <= 1e-15 * st[O.ST["M"]]
 
-        # per-patch potentials from this rank's pixels, gathered in table order
+        # the first call's state from the global statistics, the E-step on
+        # this rank's pixels, the M-step from the all-reduced sums
+        ep = O.em_params()
+        rng_e = emax - emin
+        sfloor = max((ep.sigma_floor_rel * rng_e) ** 2, 1e-12)
+        sigma2, c, m = max(se2 / n, sfloor), ep.c0, 1.0 / rng_e
+        e = (y[lo:hi].astype(np.float64) - s)
+        G = np.exp(-e * e / (2.0 * sigma2)) / (math.sqrt(2.0 * math.pi) * math.sqrt(sigma2))
+        p = np.where(v > 0, G * c / (G * c + m * (1.0 - c)), 0.0)
+        assert np.allclose(p, p_full[lo:hi], rtol=1e-12, atol=1e-300)
+        sp, spe2 = shard.em_mstep_sums(p, e, v, dist)
+        assert abs(max(spe2 / sp, sfloor) - st[O.ST["SIGMA2"]]) <= 1e-12 * st[O.ST["SIGMA2"]]
+        assert abs(min(max(sp / n, 1e-3), 1 - 1e-3) - st[O.ST["C"]]) <= 1e-12
+
+        # per-patch potentials from this rank's own E-step, gathered in table order
         pb = []
         for row in d:
             o, k = int(row[6]), int(row[4] * row[5])
-            pv, vv = p_full[lo + o:lo + o + k], v[o:o + k].astype(bool)
+            pv, vv = p[o:o + k], v[o:o + k].astype(bool)
             pb.append(np.sqrt(np.sum(pv[vv] ** 2) / vv.sum()) if vv.sum() else 0.0)
         allpb = shard.gather_patch_values(np.array(pb), b, dist)
         keep = np.array([v_full[int(q[6]):int(q[6] + q[4] * q[5])].sum() > 0 for q in desc])
