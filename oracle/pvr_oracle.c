@@ -17,6 +17,8 @@
  *   or_em_weights      voxel/pixel EM robust statistics + patch   (Eqs. for m, p and p-bar, Sec. II "EM-Based
  *                      potentials and patch classification         Outlier Removal")
  *   or_volume_update   weighted SIRT step                         (super-resolution by gradient descent, Sec. II)
+ *   or_sr_update       the SIRT step followed by an edge-preserving  (the regularised super-resolution PVR builds
+ *                      anisotropic-diffusion step                   on, Sec. I related work, Sec. II)
  *   or_ncc_grad        NCC of a patch and d NCC / d pose          (Sec. II registration with CC; Eq. cross_corr)
  *   or_sim_pose_vjp    d (sum r * sim) / d pose of one patch      (Eq. 1 differentiated through the sample positions)
  *   or_register        per-patch gradient ascent on NCC           (Sec. III "patch-wise gradient descent")
@@ -662,6 +664,53 @@ void or_volume_update(double *x, const double *addon, const double *conf, size_t
             x[v] = nv > 0.0 ? nv : 0.0;
         }
     }
+}
+
+/* Regularised super-resolution update (reading of the edge-preserving
+ * regularisation by anisotropic diffusion of the SR framework PVR builds
+ * on; the paper prints no formula).  First the SIRT step of
+ * or_volume_update gives u.  Then every voxel v reached by the data
+ * (conf > conf_eps) takes one explicit diffusion step over its 26
+ * neighbours d inside the volume:
+ *   x(v) = max(u(v) + lambda * sum_d w_d psi(u(v + d) - u(v)), 0),
+ *   psi(D) = D / sqrt(1 + (D / delta)^2)   (edge-stopping flux: about D for
+ *            differences well below delta, bounded by delta above it),
+ *   w_d = (1 / |d|^2) / W,  W = 6 + 12 / 2 + 8 / 3 = 44 / 3,
+ * |d| in voxel steps, so the weights of a full neighbourhood sum to one and
+ * 0 <= lambda <= 1 keeps the step a convex combination for small
+ * differences.  Voxels the data did not reach keep u.  x: [nz][ny][nx]. */
+void or_sr_update(double *x, const double *addon, const double *conf, int nx, int ny, int nz, double alpha,
+                  double conf_eps, double lambda, double delta)
+{
+    size_t n = (size_t)nx * ny * nz;
+    double *u = (double *)malloc(n * sizeof(double));
+    memcpy(u, x, n * sizeof(double));
+    or_volume_update(u, addon, conf, n, alpha, conf_eps);
+    const double W = 6.0 + 12.0 / 2.0 + 8.0 / 3.0;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int xx = 0; xx < nx; ++xx) {
+                size_t v = ((size_t)z * ny + y) * nx + xx;
+                if (!(conf[v] > conf_eps)) {
+                    x[v] = u[v];
+                    continue;
+                }
+                double flux = 0.0;
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            int r2 = dx * dx + dy * dy + dz * dz;
+                            if (r2 == 0) continue;
+                            int qx = xx + dx, qy = y + dy, qz = z + dz;
+                            if (qx < 0 || qy < 0 || qz < 0 || qx >= nx || qy >= ny || qz >= nz) continue;
+                            double D = u[((size_t)qz * ny + qy) * nx + qx] - u[v];
+                            double psi = D / sqrt(1.0 + (D / delta) * (D / delta));
+                            flux += (1.0 / (double)r2) / W * psi;
+                        }
+                double nv = u[v] + lambda * flux;
+                x[v] = nv > 0.0 ? nv : 0.0;
+            }
+    free(u);
 }
 
 /* -------------------------------------------------------- registration -- */

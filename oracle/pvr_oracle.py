@@ -85,6 +85,8 @@ def lib():
         L.or_em_weights.argtypes = [P(C.c_float), P(C.c_double), P(C.c_uint8), P(C.c_int), C.c_int,
                                     P(_EmParams), P(C.c_double), P(C.c_uint8), P(C.c_uint8),
                                     P(C.c_double), P(C.c_double), P(C.c_double)]
+        L.or_sr_update.argtypes = [P(C.c_double), P(C.c_double), P(C.c_double), C.c_int, C.c_int, C.c_int,
+                                   C.c_double, C.c_double, C.c_double, C.c_double]
         L.or_volume_update.argtypes = [P(C.c_double), P(C.c_double), P(C.c_double), C.c_size_t,
                                        C.c_double, C.c_double]
         L.or_ncc_grad.argtypes = [P(_Geom), P(_Psf), P(C.c_float), P(C.c_float), P(C.c_int),
@@ -238,6 +240,18 @@ def volume_update(x, addon, conf, alpha=1.0, conf_eps=1e-6):
     return xo
 
 
+def sr_update(x, addon, conf, dims, alpha=1.0, conf_eps=1e-6, lam=0.0, delta=100.0):
+    """SIRT step then the edge-preserving diffusion step (or_sr_update);
+    dims = (nx, ny, nz); returns the new volume (f64, flat)."""
+    xo = np.array(x, dtype=np.float64, copy=True).reshape(-1)
+    addon = _c(addon, np.float64).reshape(-1)
+    conf = _c(conf, np.float64).reshape(-1)
+    nx, ny, nz = (int(v) for v in dims)
+    lib().or_sr_update(_ptr(xo, C.c_double), _ptr(addon, C.c_double), _ptr(conf, C.c_double), nx, ny, nz,
+                       float(alpha), float(conf_eps), float(lam), float(delta))
+    return xo
+
+
 def ncc_grad(G, ps, x, y, drow, theta, n_params=6, min_valid=16, exact=True, member=None):
     """NCC of one patch and its pose gradient; returns (ncc, grad).  member:
     uint8 per patch pixel (indexed like y) or None."""
@@ -314,9 +328,10 @@ def volume_init(G, ps, desc, fix, y, conf_eps=1e-6):
     return x
 
 
-def sr_pass(G, ps, ep, x, y, desc, fix, npix, state, mask_in, alpha=1.0, conf_eps=1e-6):
+def sr_pass(G, ps, ep, x, y, desc, fix, npix, state, mask_in, alpha=1.0, conf_eps=1e-6, lam=0.0, delta=100.0):
     """One super-resolution pass: simulate, EM weights, weighted adjoint of the
-    residual, SIRT update.  Pixel weight = patch mask * p (an excluded patch
+    residual, SIRT update (followed by the edge-preserving diffusion step
+    when lam > 0).  Pixel weight = patch mask * p (an excluded patch
     contributes nothing).  Returns (x_new, aux dict)."""
     sim, valid, _ = simulate(G, ps, np.asarray(x, dtype=np.float32), desc, fix, npix)
     p, wp, pbar, mask = em_weights(y, sim, valid, desc, ep, state, mask_in)
@@ -327,13 +342,16 @@ def sr_pass(G, ps, ep, x, y, desc, fix, npix, state, mask_in, alpha=1.0, conf_ep
     e = np.where(valid > 0, np.asarray(y, dtype=np.float64) - sim, 0.0)
     wgt = pix_mask * p
     addon, conf = adjoint(G, ps, desc, fix, r=e, w=wgt)
-    xn = volume_update(np.asarray(x, dtype=np.float64), addon, conf, alpha, conf_eps)
+    if lam > 0.0:
+        xn = sr_update(np.asarray(x, dtype=np.float64), addon, conf, (G.nx, G.ny, G.nz), alpha, conf_eps, lam, delta)
+    else:
+        xn = volume_update(np.asarray(x, dtype=np.float64), addon, conf, alpha, conf_eps)
     return xn, dict(sim=sim, valid=valid, p=p, w_patch=wp, pbar=pbar, mask=mask, addon=addon,
                     conf=conf)
 
 
 def reconstruct_iter(G, ps, ep, rp, x, y, desc, poses, npix, state, mask, n_sr=1, alpha=1.0,
-                     conf_eps=1e-6):
+                     conf_eps=1e-6, lam=0.0, delta=100.0):
     """One outer PVR iteration (Sec. II): register every patch to the current
     volume, then n_sr super-resolution passes with EM outlier weights.
     Returns (x, poses, mask, ncc)."""
@@ -342,7 +360,7 @@ def reconstruct_iter(G, ps, ep, rp, x, y, desc, poses, npix, state, mask, n_sr=1
     x = np.asarray(x, dtype=np.float64)
     for _ in range(n_sr):
         x, aux = sr_pass(G, ps, ep, x.astype(np.float32), y, desc, fix, npix, state, mask, alpha,
-                         conf_eps)
+                         conf_eps, lam, delta)
         mask = aux["mask"]
     return x, poses, mask, ncc
 

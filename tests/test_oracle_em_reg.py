@@ -9,6 +9,11 @@ against facts fixed by statistics and algebra (not by re-typing formulas):
   planted outlier patches (a heavy-tailed residual population) are masked;
 * SIRT on a consistent system (y = A x*) reduces the data residual
   monotonically and keeps x >= 0;
+* the edge-preserving diffusion step after it: the identity for lambda = 0,
+  a constant and a linear ramp are fixed points, total intensity is
+  conserved, for a large edge threshold it is the linear 26-neighbour
+  diffusion (scipy correlate with the same weights), and a large step edge
+  is smoothed far less than a small one;
 * NCC: self-similarity 1, invariance to positive affine intensity changes,
   sign flip for negative scaling; gradient = central finite differences;
 * noiseless registration recovers a known rigid transform, and a known
@@ -175,6 +180,68 @@ def _reg_case(seed=0):
         r[6] = off
         off += int(r[4] * r[5])
     return geom, x, d, off
+
+
+def _sr(u, lam, delta, conf=None, addon=None):
+    nz, ny, nx = u.shape
+    conf = np.ones(u.size) if conf is None else conf
+    addon = np.zeros(u.size) if addon is None else addon
+    return O.sr_update(u.reshape(-1), addon, conf, (nx, ny, nz), 1.0, 1e-6, lam, delta).reshape(u.shape)
+
+
+def test_sr_update_fixed_points_and_identity():
+    rng = np.random.default_rng(0)
+    u = rng.uniform(100, 900, (6, 7, 8))
+    addon = rng.normal(0, 30, u.size)
+    conf = rng.uniform(0.0, 2.0, u.size)
+    conf[::7] = 0.0
+    # lambda = 0: exactly the SIRT step
+    assert np.array_equal(O.sr_update(u.reshape(-1), addon, conf, (8, 7, 6), 1.0, 1e-6, 0.0, 50.0),
+                          O.volume_update(u.reshape(-1), addon, conf))
+    # a constant volume is a fixed point
+    c = np.full((6, 7, 8), 321.0)
+    assert np.array_equal(_sr(c, 0.8, 20.0), c)
+    # a linear ramp is a fixed point away from the border (fluxes of opposite
+    # neighbours cancel), for any edge threshold
+    z, y, x = np.meshgrid(np.arange(6), np.arange(7), np.arange(8), indexing="ij")
+    ramp = 200.0 + 13.0 * x - 7.0 * y + 5.0 * z
+    for delta in (3.0, 1e6):
+        out = _sr(ramp, 0.7, delta)
+        assert np.allclose(out[1:-1, 1:-1, 1:-1], ramp[1:-1, 1:-1, 1:-1], rtol=0, atol=1e-10)
+        assert not np.allclose(out, ramp, rtol=0, atol=1e-6)   # the border does move
+
+
+def test_sr_update_conserves_intensity_and_is_linear_diffusion_for_large_delta():
+    from scipy.ndimage import correlate
+    rng = np.random.default_rng(1)
+    u = rng.uniform(400, 600, (9, 10, 11))
+    out = _sr(u, 0.5, 25.0)
+    assert abs(out.sum() - u.sum()) <= 1e-12 * u.sum()
+    # edge threshold far above every difference: psi(D) = D exactly, the
+    # step is (1 - lambda) u + lambda * (26-neighbour weighted mean)
+    k = np.zeros((3, 3, 3))
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                r2 = dx * dx + dy * dy + dz * dz
+                if r2:
+                    k[dz + 1, dy + 1, dx + 1] = (1.0 / r2) / (6 + 12 / 2 + 8 / 3)
+    lam = 0.6
+    lin = _sr(u, lam, 1e30)
+    ref = (1 - lam) * u + lam * correlate(u, k, mode="constant")
+    assert np.allclose(lin[1:-1, 1:-1, 1:-1], ref[1:-1, 1:-1, 1:-1], rtol=1e-13, atol=0)
+
+
+def test_sr_update_preserves_large_edges():
+    """Edge-stopping flux: a step of 10 delta moves by a few per cent of what
+    a step of delta / 10 moves, relative to its height."""
+    def edge_change(h):
+        u = np.full((4, 6, 8), 500.0)
+        u[:, :, 4:] += h
+        out = _sr(u, 0.8, 10.0)
+        return np.max(np.abs(out - u)) / h
+    small, large = edge_change(1.0), edge_change(100.0)
+    assert large < 0.15 * small, (small, large)
 
 
 def test_ncc_identities():
