@@ -73,7 +73,7 @@ typedef enum pvr_status {
     PVR_ERR_CUDA = -2,        /* a CUDA runtime call failed */
     PVR_ERR_NUMERIC = -3,     /* non-finite pose or state seen on the device */
     PVR_ERR_BOUNDS = -4,      /* a patch row outside its stack / pixel range */
-    PVR_ERR_TIMEOUT = -5,     /* reserved: a bounded device wait gave up */
+    PVR_ERR_TIMEOUT = -5,     /* a bounded device wait gave up */
     PVR_ERR_UNSUPPORTED = -6  /* valid request this build does not implement */
 } pvr_status;
 
@@ -155,6 +155,15 @@ typedef struct pvr_params {
      * serves (its scratch is sized for it at creation); 0 (default): no
      * superpixel scratch, pvr_patches_build_slic is refused */
     int32_t slic_a_min;
+    /* regularised super-resolution update: after the SIRT step every voxel
+     * the data reached takes one edge-preserving diffusion step over its 26
+     * neighbours, x += sr_lambda * sum_d w_d psi(x_d - x), psi(D) =
+     * D / sqrt(1 + (D / sr_edge_delta)^2), w_d = (1/|d|^2) / (44/3) (the
+     * anisotropic-diffusion regularisation of the SR framework PVR follows,
+     * Sec. I and II), then x = max(x, 0).  sr_lambda 0 (default): plain
+     * SIRT; 0..1.  sr_edge_delta > 0, intensity units (default 100). */
+    double sr_lambda;
+    double sr_edge_delta;
 } pvr_params;
 
 /* Patch table handed to every per-patch call (host struct, device table). */
@@ -188,7 +197,8 @@ PVR_API int pvr_ctx_destroy(pvr_ctx *ctx);
 PVR_API const char *pvr_last_error(const pvr_ctx *ctx);
 
 /* Synchronise `stream`, read and clear the device error word: PVR_OK,
- * PVR_ERR_BOUNDS or PVR_ERR_NUMERIC. */
+ * PVR_ERR_BOUNDS, PVR_ERR_NUMERIC or PVR_ERR_TIMEOUT (a bounded device wait
+ * gave up; the affected output is not valid). */
 PVR_API int pvr_device_status(pvr_ctx *ctx, void *stream);
 
 /* Number of kernel launches this context has enqueued since creation
@@ -352,8 +362,9 @@ PVR_API int pvr_em_weights(pvr_ctx *ctx, const float *y, const float *sim, const
                    uint8_t *mask_out, float *p, float *w_patch, float *pbar, void *stream);
 
 /* Weighted SIRT step of the super-resolution update (rows of A sum to one):
- * where conf > conf_eps, x = max(x + alpha * addon / conf, 0).  If
- * clear_accumulators, addon and conf are zeroed in the same pass. */
+ * where conf > conf_eps, x = max(x + alpha * addon / conf, 0); with
+ * sr_lambda > 0 followed by the edge-preserving diffusion step on those
+ * voxels (pvr_params).  If clear_accumulators, addon and conf are zeroed. */
 PVR_API int pvr_volume_update(pvr_ctx *ctx, float *x, float *addon, float *conf, int32_t clear_accumulators,
                       void *stream);
 
@@ -421,7 +432,8 @@ PVR_API int pvr_register(pvr_ctx *ctx, const float *x, const float *y, const pvr
 /* One outer PVR iteration (Sec. II loop): pvr_register with reg_evals
  * evaluations, then n_sr super-resolution passes, each: simulate, residual
  * e = y - sim, EM weights (mask carried from pass to pass), weighted adjoint
- * of e with pixel weight mask_patch * p, SIRT update of x.  x: in/out;
+ * of e with pixel weight mask_patch * p, SIRT update of x (with the
+ * edge-preserving diffusion step when sr_lambda > 0).  x: in/out;
  * poses: in/out; state: EM state in/out; mask: uint8 [n] in/out (set to 1
  * before the first call); p (float32 [n_pix]) and w_patch (float32 [n])
  * receive the last pass's weights (either may be NULL).  When every patch

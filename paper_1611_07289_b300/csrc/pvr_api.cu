@@ -72,6 +72,7 @@ struct pvr_ctx {
     uint8_t *v_buf = nullptr, *valid_buf = nullptr, *mask_tmp = nullptr;
     float2 *acc2 = nullptr;   // interleaved (addon, conf) accumulator, one pair per voxel
     float4 *quad = nullptr;   // quad copy of the volume read by the gathers
+    float *x_next = nullptr;  // regularised update's output volume (sr_lambda > 0)
     float *gbuf = nullptr;    // NCC gradient scratch (per-lattice-point gradient sums)
     long long gbuf_tiles = 0;
     int32_t *keep = nullptr;
@@ -227,7 +228,7 @@ void free_all(pvr_ctx *c)
     void *ptrs[] = {c->d_geom, c->fix, c->part, c->epart, c->gpart, c->pstat, c->pbar, c->wsc, c->emblk, c->emcount, c->ncc_counter, c->elig,
                     c->err, c->best, c->gbest, c->nbest, c->trial, c->delta, c->ncc_tmp,
                     c->grad_tmp, c->active, c->s_buf, c->e_buf, c->p_buf, c->v_buf,
-                    c->valid_buf, c->mask_tmp, c->acc2, c->quad, c->gbuf, c->keep, c->imax_key,
+                    c->valid_buf, c->mask_tmp, c->acc2, c->quad, c->x_next, c->gbuf, c->keep, c->imax_key,
                     c->slice_scr, c->slic_scr, c->plan_items, c->plan_counter,
                     c->counts, c->metric_scr};
     for (void *p : ptrs)
@@ -250,6 +251,29 @@ int pose_fixed(pvr_ctx *c, const pvr_patches *pp, int max_side, const double *po
                                                 max_side, c->psf.kxy, c->psf.kz, c->fix, c->err, st),
              "pose_to_fixed");
     c->launches += pp->n > 0;
+    return PVR_OK;
+}
+
+// The super-resolution update of x from the interleaved accumulator: the
+// SIRT step, and with sr_lambda > 0 the edge-preserving diffusion step
+// (into x_next, copied back); the accumulator ends cleared.  Returns the
+// number of kernels launched through *launched.
+int sr_update_pairs(pvr_ctx *c, float *x, cudaStream_t st, int *launched)
+{
+    const float alpha = (float)c->prm.alpha, eps = (float)c->prm.conf_eps;
+    if (c->prm.sr_lambda <= 0.0) {
+        CUDA_TRY_T(PVR_K_UPDATE, launch_volume_update_pairs(x, c->acc2, c->nvox, alpha, eps, 1, 0, st), "volume_update");
+        *launched = 1;
+        return PVR_OK;
+    }
+    CUDA_TRY_T(PVR_K_UPDATE, launch_volume_update_pairs(x, c->acc2, c->nvox, alpha, eps, 0, 0, st), "volume_update");
+    CUDA_TRY_T(PVR_K_UPDATE, launch_sr_diffuse_pairs(x, c->acc2, c->x_next, c->geom.nx, c->geom.ny, c->geom.nz,
+                                                     (float)c->prm.sr_lambda, (float)c->prm.sr_edge_delta, eps,
+                                                     c->err, st),
+               "sr_diffuse");
+    CUDA_TRY(cudaMemcpyAsync(x, c->x_next, (size_t)c->nvox * sizeof(float), cudaMemcpyDeviceToDevice, st),
+             "copy regularised volume");
+    *launched = 2;
     return PVR_OK;
 }
 
@@ -327,6 +351,9 @@ const char *validate_setup(const pvr_geometry *g, const pvr_params *prm)
     if (prm->psf_kind == PVR_PSF_TAYLOR_SINC && !(prm->psf_sinc_eps > 0.0 && prm->psf_sinc_eps < 1.0))
         return "psf_sinc_eps outside (0, 1)";
     if (prm->n_params != 6 && prm->n_params != 12) return "n_params must be 6 (rigid) or 12 (affine)";
+    if (!(prm->sr_lambda >= 0.0 && prm->sr_lambda <= 1.0)) return "sr_lambda outside 0..1";
+    if (prm->sr_lambda > 0.0 && !(prm->sr_edge_delta > 0.0 && isfinite(prm->sr_edge_delta)))
+        return "sr_edge_delta must be positive";
     return nullptr;
 }
 
@@ -368,6 +395,9 @@ void pvr_params_default(pvr_params *p)
     p->max_patch_side = 128;
     p->psf_kind = PVR_PSF_GAUSSIAN;
     p->psf_sinc_eps = 1e-12;
+    p->slic_a_min = 0;
+    p->sr_lambda = 0.0;
+    p->sr_edge_delta = 100.0;
 }
 
 int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
@@ -461,6 +491,7 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
     ALLOC(c->mask_tmp, P);
     ALLOC(c->acc2, (size_t)c->nvox);
     ALLOC(c->quad, (size_t)c->nvox);
+    if (prm->sr_lambda > 0.0) ALLOC(c->x_next, (size_t)c->nvox);
     {
         // gradient scratch: all tiles if they fit in 2.5 GB, else chunks of whole patches
         size_t per = ncc_gbuf_floats_per_tile(tl, prm->psf_kxy) * sizeof(float);
@@ -517,6 +548,7 @@ int pvr_device_status(pvr_ctx *c, void *stream)
     CUDA_TRY(cudaMemsetAsync(c->err, 0, sizeof h, st), "clear error word");
     if (h & 1) return fail(c, PVR_ERR_BOUNDS, "a patch row lies outside its stack or pixel range");
     if (h & 2) return fail(c, PVR_ERR_NUMERIC, "a pose produced a non-finite sample map");
+    if (h & 4) return fail(c, PVR_ERR_TIMEOUT, "a bounded device wait gave up (tile staging)");
     return PVR_OK;
 }
 
@@ -705,10 +737,20 @@ int pvr_volume_update(pvr_ctx *c, float *x, float *addon, float *conf, int32_t c
 {
     if (!c) return PVR_ERR_INVALID_ARG;
     REQUIRE(x && addon && conf, "NULL argument");
-    CUDA_TRY(launch_volume_update(x, addon, conf, c->nvox, (float)c->prm.alpha,
-                                  (float)c->prm.conf_eps, clear, 0, (cudaStream_t)stream),
-             "volume_update");
-    c->launches += 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    const float alpha = (float)c->prm.alpha, eps = (float)c->prm.conf_eps;
+    if (c->prm.sr_lambda <= 0.0) {
+        CUDA_TRY(launch_volume_update(x, addon, conf, c->nvox, alpha, eps, clear, 0, st), "volume_update");
+        c->launches += 1;
+        return PVR_OK;
+    }
+    CUDA_TRY(launch_volume_update(x, addon, conf, c->nvox, alpha, eps, 0, 0, st), "volume_update");
+    CUDA_TRY(launch_sr_diffuse_split(x, addon, conf, clear, c->x_next, c->geom.nx, c->geom.ny, c->geom.nz,
+                                     (float)c->prm.sr_lambda, (float)c->prm.sr_edge_delta, eps, c->err, st),
+             "sr_diffuse");
+    CUDA_TRY(cudaMemcpyAsync(x, c->x_next, (size_t)c->nvox * sizeof(float), cudaMemcpyDeviceToDevice, st),
+             "copy regularised volume");
+    c->launches += 2;
     return PVR_OK;
 }
 
@@ -936,10 +978,9 @@ int pvr_reconstruct_iter(pvr_ctx *c, float *x, const float *y, const pvr_patches
         CUDA_TRY_T(PVR_K_ADJOINT, launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix,
                                 pp->n, c->e_buf, c->p_buf, mask, (float *)c->acc2, nullptr, 1, st, wq),
                  "adjoint");
-        CUDA_TRY_T(PVR_K_UPDATE, launch_volume_update_pairs(x, c->acc2, c->nvox, (float)c->prm.alpha,
-                                      (float)c->prm.conf_eps, 1, 0, st),
-                 "volume_update");
-        c->launches += (pp->n > 0 ? (reuse ? 2 : 3) : 1) + em_launch_count(pp->n, c->prm);
+        int upd = 0;
+        if ((rc = sr_update_pairs(c, x, st, &upd))) return rc;
+        c->launches += (pp->n > 0 ? (reuse ? 1 : 2) : 0) + upd + em_launch_count(pp->n, c->prm);
     }
     if (p && pp->n_pix > 0)
         CUDA_TRY(cudaMemcpyAsync(p, c->p_buf, (size_t)pp->n_pix * sizeof(float),

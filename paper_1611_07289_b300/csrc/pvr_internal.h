@@ -113,6 +113,17 @@ cudaError_t launch_split_pairs(const float2 *acc, int64_t nvox, float *addon, fl
 cudaError_t launch_volume_update(float *x, float *addon, float *conf, int64_t nvox, float alpha,
                                  float conf_eps, int clear, int init_mode, cudaStream_t st);
 
+// Edge-preserving diffusion step after the SIRT step (u = the SIRT result):
+// xo = the regularised volume; the accumulator (interleaved pairs, or
+// separate arrays cleared when `clear`) is read and cleared voxel by voxel.
+// A bounded wait that expires sets bit 4 of the device error word.
+cudaError_t launch_sr_diffuse_pairs(const float *u, float2 *acc, float *xo, int nx, int ny, int nz, float lambda,
+                                    float delta, float conf_eps, int32_t *err, cudaStream_t st);
+cudaError_t launch_sr_diffuse_split(const float *u, float *addon, float *conf, int clear, float *xo, int nx, int ny,
+                                    int nz, float lambda, float delta, float conf_eps, int32_t *err, cudaStream_t st);
+// True when the diffusion step stages its tiles by TMA for this volume.
+bool sr_diffuse_uses_tma(const float *u, int nx, int ny, int nz);
+
 
 // NCC moments (+ gradient when gpart != null) of every patch, gathering
 // from the quad copy of the volume.  One-tile patches run one fused

@@ -50,7 +50,7 @@ class Params(C.Structure):
                 ("reg_fixed_step", C.c_int32), ("reg_min_valid", C.c_int32), ("n_sr", C.c_int32),
                 ("max_patches", C.c_int32), ("max_pixels", C.c_int64),
                 ("max_patch_side", C.c_int32), ("psf_kind", C.c_int32), ("psf_sinc_eps", C.c_double),
-                ("slic_a_min", C.c_int32)]
+                ("slic_a_min", C.c_int32), ("sr_lambda", C.c_double), ("sr_edge_delta", C.c_double)]
 
 
 class Patches(C.Structure):

@@ -48,6 +48,7 @@ int main(void) {
   F(pvr_params, psf_dz); F(pvr_params, alpha); F(pvr_params, patch_rule); F(pvr_params, n_params);
   F(pvr_params, reg_grow); F(pvr_params, n_sr); F(pvr_params, max_pixels); F(pvr_params, max_patch_side);
   F(pvr_params, psf_kind); F(pvr_params, psf_sinc_eps); F(pvr_params, slic_a_min);
+  F(pvr_params, sr_lambda); F(pvr_params, sr_edge_delta);
   F(pvr_patches, n); F(pvr_patches, max_side); F(pvr_patches, n_pix);
   return 0;
 }

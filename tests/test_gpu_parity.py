@@ -195,6 +195,65 @@ def test_volume_update_and_init_match_oracle(pvr):
     assert rel_l2(x0, O.volume_init(G, ps, desc, fix, y)) < 1e-5
 
 
+@pytest.mark.parametrize("dims,lam,delta", [((64, 64, 64), 0.5, 40.0), ((21, 17, 13), 0.9, 5.0),
+                                            ((40, 24, 9), 0.3, 1e4)])
+def test_regularised_update_matches_oracle(pvr, dims, lam, delta):
+    """SIRT step followed by the edge-preserving diffusion step: 64^3 and
+    40 x 24 x 9 stage their tiles by TMA (row pitch a multiple of 16 bytes),
+    21 x 17 x 13 by plain loads; ragged edge blocks in every case."""
+    nx, ny, nz = dims
+    w2v, v2w = synth.volume_geometry(dims, 1.0)
+    P = synth.stack_matrix((1, 0, 0), (0, 1, 0), (0, 0, 1), 8, 8, 2, 1.0, 2.0)
+    geom = synth.Geometry(dims, w2v, v2w, [(8, 8, 2)], [P], [2.0])
+    rng = np.random.default_rng(17)
+    n = nx * ny * nz
+    x = rng.uniform(0, 1000, n).astype(np.float32)
+    x[: n // 3] = 500.0   # a flat region next to a noisy one: both flux regimes
+    a = rng.normal(0, 30, n).astype(np.float32)
+    c = np.where(rng.uniform(size=n) < 0.15, 0.0, rng.uniform(0.1, 3, n)).astype(np.float32)
+    ctx = pvr.Context(geom, pvr.default_params(max_patches=16, max_pixels=1 << 12, max_patch_side=8,
+                                               sr_lambda=lam, sr_edge_delta=delta))
+    for clear in (False, True):
+        xg, ag, cg = _t(x), _t(a), _t(c)
+        ctx.pvr_volume_update(xg, ag, cg, clear=clear)
+        ctx.pvr_device_status()
+        ref = O.sr_update(x, a, c, dims, 1.0, 1e-6, lam, delta)
+        assert rel_l2(xg.cpu().numpy(), ref) < 1e-6
+        if clear:
+            assert float(ag.abs().sum()) == 0.0 and float(cg.abs().sum()) == 0.0
+        else:
+            assert np.array_equal(cg.cpu().numpy(), c)
+    # lambda = 0 is the plain SIRT step
+    ctx0 = pvr.Context(geom, pvr.default_params(max_patches=16, max_pixels=1 << 12, max_patch_side=8))
+    xg = _t(x)
+    ctx0.pvr_volume_update(xg, _t(a), _t(c), clear=True)
+    assert rel_l2(xg.cpu().numpy(), O.volume_update(x, a, c, 1.0, 1e-6)) < 1e-6
+
+
+def test_reconstruct_iter_with_regulariser_matches_oracle(pvr):
+    cfg = synth.config_tiny()
+    geom = cfg["geom"]
+    G, ps = O.geom(geom), O.psf(1.2, 1, 3, 1.0)
+    desc, npix = O.patches_build(G, synth.pack_stacks(cfg["stacks"]), 32, 16)
+    y = synth.pack_patch_pixels(cfg["stacks"], desc)
+    poses = np.zeros((desc.shape[0], 6))
+    x0 = O.volume_init(G, ps, desc, O.pose_fixed(G, ps, desc, poses), y).astype(np.float32)
+    ctx = _ctx(pvr, geom, reg_fixed_step=1, reg_delta0=0.25, reg_evals=3, n_sr=2, sr_lambda=0.4,
+               sr_edge_delta=60.0)
+    pt = pvr.PatchTable.from_numpy(desc, npix)
+    xg, pg = _t(x0.reshape(64, 64, 64)), _t(poses)
+    st = pvr.new_state()
+    mask = torch.ones(desc.shape[0], dtype=torch.uint8, device="cuda")
+    ctx.pvr_reconstruct_iter(xg, _t(y), pt, pg, st, mask)
+    ctx.pvr_device_status()
+    xo, po, mo, _ = O.reconstruct_iter(G, ps, O.em_params(), O.reg_params(n_eval=3, fixed_step=1, delta0=0.25),
+                                       x0, y, desc, poses, npix, O.new_state(), np.ones(desc.shape[0], np.uint8),
+                                       n_sr=2, lam=0.4, delta=60.0)
+    assert np.max(np.abs(pg.cpu().numpy() - po)) < 1e-3
+    assert rel_l2(xg.cpu().numpy(), xo) < 1e-4
+    assert np.array_equal(mask.cpu().numpy(), mo)
+
+
 def test_ncc_and_gradient_match_oracle(pvr):
     cfg = synth.config_tiny(noise=True)
     geom = cfg["geom"]
