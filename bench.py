@@ -277,11 +277,12 @@ def run_oracle(cfg, desc_all, y_all, budget_s=15.0, steps=1, warmup=0, log=print
 
 # ----------------------------------------------------------------- setup --
 
-def _setup(device, slices=96, n_params=N_PARAMS):
+def _setup(device, slices=96, n_params=N_PARAMS, cfg=None):
     import torch
     from paper_1611_07289_b300 import pvr, synth
     t0 = time.perf_counter()
-    cfg = synth.config_uterus(device=device, slices=slices)
+    if cfg is None:
+        cfg = synth.config_uterus(device=device, slices=slices)
     gen_s = time.perf_counter() - t0
     packed = torch.as_tensor(synth.pack_stacks(cfg["stacks"]), device=device)
     prm = pvr.default_params(psf_dz=0.75, max_patches=32768, max_pixels=1 << 27, max_patch_side=64,
@@ -507,6 +508,18 @@ def run_ours(args, ws, rank, local, dist):
         res["iteration"] = run_iterations(cfg, ctx, pt, y, x0, gt, dev, n_outer=args.outer_full,
                                           target=plain["best_psnr_db"])
         res["iteration_unregularised"] = plain
+    if ws == 1 and not args.no_extras:
+        # the batched uneven-patch form (NEXT-1) and the learned pose
+        # proposal (NEXT-3) on the same volume and stacks, summarised
+        ctx.close()
+        u = run_uneven(args, ws, rank, local, cfg)
+        res["batched_uneven"] = {k: u[k] for k in ("value", "unit", "ms_per_step", "simulate_adjoint_ms",
+                                                   "iteration_ms", "roofline")}
+        res["batched_uneven"]["config"] = u["config"]
+        p = run_proposal(args, ws, rank, local, cfg)
+        res["learned_proposal"] = {k: p[k] for k in ("metric", "value", "unit", "plain_s_to_psnr",
+                                                     "plain_best_psnr_db", "learned_best_psnr_db",
+                                                     "s_to_psnr_per_run", "training", "config")}
     if ws == 1 and not args.no_cpu_baseline:
         _, info = run_oracle(cfg, pt.desc.cpu().numpy(), y.cpu().numpy(), budget_s=args.cpu_budget)
         res["cpu_baseline"] = {"value": info["value"], "unit": UNIT, "cores": info["cores"],
@@ -531,7 +544,7 @@ def _onchip(dom, prof, pt, clocks):
             "peak_source": f"nominal {L1_BYTES_PER_CLK_SM} B/clock/SM x {n_sm} SMs x {mhz:.0f} MHz"}
 
 
-def run_uneven(args, ws, rank, local):
+def run_uneven(args, ws, rank, local, cfg=None):
     """Batched patches of uneven sizes (sides 32..128 drawn per slice, stride
     side / 2) on the uterus volume: simulate + adjoint as one launch per
     patch size against one planned (tuned) launch over all sizes, and the
@@ -541,7 +554,7 @@ def run_uneven(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
     t0 = time.perf_counter()
-    cfg = synth.config_uneven(device=dev, slices=args.slices)
+    cfg = synth.config_uneven(device=dev, slices=args.slices) if cfg is None else synth.uneven_sides(cfg)
     gen_s = time.perf_counter() - t0
     packed = torch.as_tensor(synth.pack_stacks(cfg["stacks"]), device=dev)
     prm = pvr.default_params(psf_dz=0.75, max_patches=65536, max_pixels=1 << 27, max_patch_side=128,
@@ -627,6 +640,7 @@ def run_uneven(args, ws, rank, local):
         g_ms.append(a.elapsed_time(b))
     clocks = sampler.stop()
     ms_graph = float(np.median(g_ms))
+    ctx.close()
     peaks, peak_kind = _peaks()
     abytes = _algorithmic_bytes("simulate", n_pix, n_vox) + _algorithmic_bytes("adjoint", n_pix, n_vox)
     achieved = abytes / (ms_plan * 1e-3) / 1e9
@@ -651,7 +665,7 @@ def run_uneven(args, ws, rank, local):
     }
 
 
-def run_proposal(args, ws, rank, local):
+def run_proposal(args, ws, rank, local, cfg=None):
     """Learned pose proposal on the uterus workload: train the CNN on pairs
     the forward model makes from random uterus phantoms, then reconstruct
     from the acquired positions with and without the proposal (+ NCC
@@ -660,7 +674,7 @@ def run_proposal(args, ws, rank, local):
     from paper_1611_07289_b300 import proposal, pvr
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
-    cfg, ctx, pt, y, x0, poses0, gen_s, build_s = _setup(dev, args.slices, n_params=6)
+    cfg, ctx, pt, y, x0, poses0, gen_s, build_s = _setup(dev, args.slices, n_params=6, cfg=cfg)
     gt = torch.as_tensor(cfg["gt"], device=dev)
     net = pvr.Net(batch_max=256, seed=7)
     net.reserve(pt.n, pt.n_pix)
@@ -754,6 +768,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-iteration", action="store_true", help="skip the whole-iteration field")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched uneven-patch and learned-proposal fields")
     ap.add_argument("--outer-full", type=int, default=10, help="outer iterations of the whole-iteration field")
     ap.add_argument("--slices", type=int, default=96,
                     help="slices per stack (96 = the benchmark workload; fewer for profiling)")

@@ -389,16 +389,23 @@ def config_uterus(seed=7289, device="cpu", slices=96, size=256):
                 fwhm_xy=1.2, dz=sp, n_outer=10)
 
 
+def uneven_sides(cfg, seed=7289, sides=(32, 48, 64, 96, 128)):
+    """A copy of a workload dictionary with a patch side per slice drawn from
+    `sides` and stride side / 2 (slice_a, slice_stride: one entry per slice
+    of every stack, in order)."""
+    rng = np.random.default_rng(seed + 1)
+    nk = sum(k for (_, _, k) in cfg["geom"].stack_dims)
+    sa = rng.choice(np.asarray(sides, dtype=np.int32), nk).astype(np.int32)
+    out = dict(cfg)
+    out.update(name=cfg["name"] + "-uneven", slice_a=sa, slice_stride=(sa // 2).astype(np.int32))
+    return out
+
+
 def config_uneven(seed=7289, device="cpu", slices=96, size=256, sides=(32, 48, 64, 96, 128)):
     """Uterus workload with a patch side per slice (module docstring): the
     config_uterus dictionary plus slice_a, slice_stride (one entry per slice
     of every stack, in order)."""
-    cfg = config_uterus(seed=seed, device=device, slices=slices, size=size)
-    rng = np.random.default_rng(seed + 1)
-    nk = sum(k for (_, _, k) in cfg["geom"].stack_dims)
-    sa = rng.choice(np.asarray(sides, dtype=np.int32), nk).astype(np.int32)
-    cfg.update(name=cfg["name"] + "-uneven", slice_a=sa, slice_stride=(sa // 2).astype(np.int32))
-    return cfg
+    return uneven_sides(config_uterus(seed=seed, device=device, slices=slices, size=size), seed, sides)
 
 
 def skew_matrix(theta_deg):
