@@ -358,8 +358,14 @@ def run_ours(args, ws, rank, local, dist):
     dev = f"cuda:{local}"
     cfg, ctx, pt, y, x0, poses0, gen_s, build_s = _setup(dev, args.slices)
     n_pix, n_vox = pt.n_pix, cfg["geom"].n_vox
-    # launch plan for simulate / adjoint tuned on this table (setup, untimed)
-    plan = ctx.pvr_plan(pt, x0, y, poses0)
+    # launch plan for simulate / adjoint tuned on this table (setup, untimed),
+    # or the one given (profiling runs: the tuner's timings are distorted
+    # under a profiler)
+    if args.plan:
+        tile, mode = (int(v) for v in args.plan.split(","))
+        plan = ctx.pvr_plan(pt, x0, y, poses0, tile=tile, mode=mode)
+    else:
+        plan = ctx.pvr_plan(pt, x0, y, poses0)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     gt = torch.as_tensor(cfg["gt"], device=dev)
@@ -768,6 +774,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-iteration", action="store_true", help="skip the whole-iteration field")
+    ap.add_argument("--plan", default="", help="force the simulate / adjoint launch plan: 'tile,mode' "
+                    "(tile 32 or 64; mode 0 = one CTA per tile, 1 = work queue) instead of tuning it")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched uneven-patch and learned-proposal fields")
     ap.add_argument("--outer-full", type=int, default=10, help="outer iterations of the whole-iteration field")

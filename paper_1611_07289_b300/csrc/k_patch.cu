@@ -1245,14 +1245,44 @@ __device__ __forceinline__ void walk_grad(const SRC &src, const VolDims &vd, con
     }
 }
 
+// L2 policies of the gradient scratch.  The persistent kernels' slots (one
+// per resident CTA, about 60 MB) are evict-last, so that the streamed patch
+// pixels and kept residuals (evict-first) leave L2 before them and a slot is
+// read back and discarded before it reaches DRAM; the chunked multi-tile
+// path, whose scratch holds every tile of a chunk, stays evict-normal.
+__device__ __forceinline__ uint64_t scratch_policy(bool keep)
+{
+    uint64_t pol;
+    if (keep)
+        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    else
+        asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// Store / load of one gradient plane entry of the global scratch: kept in L2
+// only (.cg), under the evict-last policy.
+__device__ __forceinline__ void g_store(float *p, float v, uint64_t pol)
+{
+    asm volatile("st.global.cg.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+
+__device__ __forceinline__ float g_load(const float *p, uint64_t pol)
+{
+    float v;
+    asm volatile("ld.global.cg.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol) : "memory");
+    return v;
+}
+
 // Gather pass of the NCC moments kernel: A, B into shared memory and the
 // gradient sums GA, GB into G (FAST: interior tile).
-template <int KZ, bool FAST, class SRC>
+template <int KZ, bool FAST, class SRC, bool KEEP_L2 = true>
 __device__ __forceinline__ void moments_gather(const SRC src, const VolDims &vd,
                                                const TileInfo &ti, int kxy, int kz, int order,
                                                const float *__restrict__ gz, float *A, float *B,
                                                float *G, int Lmax)
 {
+    const uint64_t pol = scratch_policy(KEEP_L2);
     if (order != kAlongZeta) {
         for (int it = threadIdx.x; it < ti.L; it += blockDim.x) {
             int li, lj;
@@ -1272,8 +1302,8 @@ __device__ __forceinline__ void moments_gather(const SRC src, const VolDims &vd,
             B[si] = b;
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
-                __stcg(G + r * Lmax + si, ga[r]);
-                __stcg(G + (3 + r) * Lmax + si, gb[r]);
+                g_store(G + r * Lmax + si, ga[r], pol);
+                g_store(G + (3 + r) * Lmax + si, gb[r], pol);
             }
         }
     } else {
@@ -1316,7 +1346,7 @@ __device__ __forceinline__ void moments_gather(const SRC src, const VolDims &vd,
             if (lp < ti.L) {
                 if (zl == 0) A[lp] = t;
                 else if (zl == 1) B[lp] = t;
-                else __stcg(G + (zl - 2) * Lmax + lp, t);
+                else g_store(G + (zl - 2) * Lmax + lp, t, pol);
             }
         }
     }
@@ -1370,9 +1400,9 @@ __global__ void __launch_bounds__(256, 4) k_ncc_moments(const SRC x, VolDims vd,
             for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) A[lp] = B[lp] = 0.f;
         }
     } else if (tile_interior(ti, vd, kxy, kz)) {
-        moments_gather<KZ, true, SRC>(x, vd, ti, kxy, kz, order, gz, A, B, G, Lmax);
+        moments_gather<KZ, true, SRC, false>(x, vd, ti, kxy, kz, order, gz, A, B, G, Lmax);
     } else {
-        moments_gather<KZ, false, SRC>(x, vd, ti, kxy, kz, order, gz, A, B, G, Lmax);
+        moments_gather<KZ, false, SRC, false>(x, vd, ti, kxy, kz, order, gz, A, B, G, Lmax);
     }
     __syncthreads();
     FFSum f1, f2, f3, f4, f5;
@@ -1544,7 +1574,7 @@ __device__ void pose_jacobian_col(const DevGeom *__restrict__ g, const int32_t *
 // (float32 per thread over its few lattice points).  The zero padding adds
 // exact zeros where a tap falls outside the tile, so the sums equal those of
 // a loop that skips them.
-template <int KXY>
+template <int KXY, bool KEEP_L2 = true>
 __device__ __forceinline__ void grad_lattice_moments(const TileInfo &ti, int kxy_rt, const float *gxy,
                                                      const float *Cp, const float *G, int Lmax,
                                                      float mo[12])
@@ -1552,6 +1582,7 @@ __device__ __forceinline__ void grad_lattice_moments(const TileInfo &ti, int kxy
     const int kxy = KXY >= 0 ? KXY : kxy_rt;
     const float cu = 0.5f * (float)(ti.w - 1), cv = 0.5f * (float)(ti.h - 1);
     const int cw = cpad_w(ti, kxy);
+    const uint64_t pol = scratch_policy(KEEP_L2);
 #pragma unroll
     for (int k = 0; k < 12; ++k) mo[k] = 0.f;
     for (int lp = threadIdx.x; lp < ti.L; lp += blockDim.x) {
@@ -1569,10 +1600,10 @@ __device__ __forceinline__ void grad_lattice_moments(const TileInfo &ti, int kxy
         const float di = (float)(ti.i0 - kxy + li) - cu, dj = (float)(ti.j0 - kxy + lj) - cv;
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-            const float s0 = u * __ldcg(G + r * Lmax + lp);
+            const float s0 = u * g_load(G + r * Lmax + lp, pol);
             mo[r] = fmaf(s0, di, mo[r]);
             mo[3 + r] = fmaf(s0, dj, mo[3 + r]);
-            mo[6 + r] = fmaf(u, __ldcg(G + (3 + r) * Lmax + lp), mo[6 + r]);
+            mo[6 + r] = fmaf(u, g_load(G + (3 + r) * Lmax + lp, pol), mo[6 + r]);
             mo[9 + r] += s0;
         }
     }
@@ -1667,7 +1698,7 @@ __global__ void __launch_bounds__(256) k_ncc_grad(VolDims vd, const DevGeom *__r
     }
     __syncthreads();
     float mo[12];
-    grad_lattice_moments<KXY>(ti, kxy, psf.gxy, C, gbuf + (size_t)blockIdx.x * 6 * Lmax, Lmax, mo);
+    grad_lattice_moments<KXY, false>(ti, kxy, psf.gxy, C, gbuf + (size_t)blockIdx.x * 6 * Lmax, Lmax, mo);
     double mom[12];
     block_sum_fd<12>(mo, mom, red);
     if (threadIdx.x == 0) {

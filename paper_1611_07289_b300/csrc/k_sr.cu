@@ -74,6 +74,37 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity)
     return false;
 }
 
+// Flux sum of one voxel from the staged box; INNER: every neighbour is
+// inside the volume (no bounds tests).
+template <bool INNER>
+__device__ __forceinline__ float box_flux(const float (&box)[kSZ][kSY][kSX], int cx, int cy, int cz, int gx, int gy,
+                                          int gz, int nx, int ny, int nz, float c, float inv_delta)
+{
+    const float W = 6.f + 12.f / 2.f + 8.f / 3.f;
+    const float w1 = 1.f / W, w2 = (1.f / 2.f) / W, w3 = (1.f / 3.f) / W;
+    float flux = 0.f;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 == 0) continue;
+                if (!INNER) {
+                    const int qx = gx + dx, qy = gy + dy, qz = gz + dz;
+                    if (qx < 0 || qy < 0 || qz < 0 || qx >= nx || qy >= ny || qz >= nz) continue;
+                }
+                const float D = box[cz + 1 + dz][cy + 1 + dy][cx + kHX + dx] - c;
+                const float t = D * inv_delta;
+                const float psi = D * rsqrtf(fmaf(t, t, 1.f));
+                flux = fmaf(r2 == 1 ? w1 : (r2 == 2 ? w2 : w3), psi, flux);
+            }
+    return flux;
+}
+
+constexpr int kPerThread = kBX * kBY * kBZ / 256;   // voxels per thread (blocks of 256 threads)
+
 template <bool TMA, class ACC>
 __global__ void __launch_bounds__(256) k_sr_diffuse(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ u,
                                                     ACC acc, float *__restrict__ xo, int nx, int ny, int nz,
@@ -83,18 +114,27 @@ __global__ void __launch_bounds__(256) k_sr_diffuse(const __grid_constant__ CUte
     __shared__ __align__(128) float box[kSZ][kSY][kSX];
     __shared__ __align__(8) uint64_t bar;
     const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY, z0 = blockIdx.z * kBZ;
+    if (TMA && threadIdx.x == 0) {
+        const uint32_t b = smem_u32(&bar);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(kBoxBytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+            "%4}], [%5];" ::"r"(smem_u32(&box[0][0][0])),
+            "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x0 - kHX), "r"(y0 - 1), "r"(z0 - 1), "r"(b)
+            : "memory");
+    }
+    // each thread's voxels and their accumulator entries, read (and
+    // cleared) while the tile is in flight
+    float conf[kPerThread];
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        const int k = threadIdx.x + 256 * j;
+        const int gx = x0 + k % kBX, gy = y0 + (k / kBX) % kBY, gz = z0 + k / (kBX * kBY);
+        conf[j] = (gx < nx && gy < ny && gz < nz) ? acc.take(((size_t)gz * ny + gy) * nx + gx) : 0.f;
+    }
     if (TMA) {
-        if (threadIdx.x == 0) {
-            const uint32_t b = smem_u32(&bar);
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(kBoxBytes) : "memory");
-            asm volatile(
-                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
-                "%4}], [%5];" ::"r"(smem_u32(&box[0][0][0])),
-                "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x0 - kHX), "r"(y0 - 1), "r"(z0 - 1), "r"(b)
-                : "memory");
-        }
         __syncthreads();   // the barrier is initialised before anyone waits on it
         if (!bar_wait(smem_u32(&bar), 0)) {
             // give up: report, then wait once more (bounded) for the copy in flight
@@ -111,34 +151,22 @@ __global__ void __launch_bounds__(256) k_sr_diffuse(const __grid_constant__ CUte
         }
         __syncthreads();
     }
-    const float W = 6.f + 12.f / 2.f + 8.f / 3.f;
-    const float w1 = 1.f / W, w2 = (1.f / 2.f) / W, w3 = (1.f / 3.f) / W;
-    for (int k = threadIdx.x; k < kBX * kBY * kBZ; k += blockDim.x) {
+    // blocks whose one-voxel shell lies inside the volume need no bounds tests
+    const bool inner = x0 >= 1 && y0 >= 1 && z0 >= 1 && x0 + kBX < nx && y0 + kBY < ny && z0 + kBZ < nz;
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        const int k = threadIdx.x + 256 * j;
         const int cx = k % kBX, cy = (k / kBX) % kBY, cz = k / (kBX * kBY);
         const int gx = x0 + cx, gy = y0 + cy, gz = z0 + cz;
         if (gx >= nx || gy >= ny || gz >= nz) continue;
-        const size_t v = ((size_t)gz * ny + gy) * nx + gx;
         const float c = box[cz + 1][cy + 1][cx + kHX];
-        const float conf = acc.take(v);
         float out = c;
-        if (conf > conf_eps) {
-            float flux = 0.f;
-            for (int dz = -1; dz <= 1; ++dz)
-                for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        const int r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 == 0) continue;
-                        const int qx = gx + dx, qy = gy + dy, qz = gz + dz;
-                        if (qx < 0 || qy < 0 || qz < 0 || qx >= nx || qy >= ny || qz >= nz) continue;
-                        const float D = box[cz + 1 + dz][cy + 1 + dy][cx + kHX + dx] - c;
-                        const float t = D * inv_delta;
-                        const float psi = D / sqrtf(1.f + t * t);
-                        flux = fmaf(r2 == 1 ? w1 : (r2 == 2 ? w2 : w3), psi, flux);
-                    }
+        if (conf[j] > conf_eps) {
+            const float flux = inner ? box_flux<true>(box, cx, cy, cz, gx, gy, gz, nx, ny, nz, c, inv_delta)
+                                     : box_flux<false>(box, cx, cy, cz, gx, gy, gz, nx, ny, nz, c, inv_delta);
             out = fmaxf(c + lambda * flux, 0.f);
         }
-        xo[v] = out;
+        xo[((size_t)gz * ny + gy) * nx + gx] = out;
     }
 }
 
