@@ -1817,7 +1817,11 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
                 sh_coef[3] = (float)ms;
             }
             // the registration's acceptance test on the NCC k_ncc_finish reports
-            sh_best = bs.mode == 2 && (bs.fixed || (ok ? ncc : 0.0) > bs.nbest[ti.p]);
+            const bool decide = bs.mode == 2 || bs.grad_if_accepted;   // bs.nbest is set then
+            const bool accepted = decide && (bs.fixed || (ok ? ncc : 0.0) > bs.nbest[ti.p]);
+            sh_best = bs.mode == 2 && accepted;
+            // a rejected trial's gradient is never used
+            if (bs.grad_if_accepted && !accepted) sh_ok = 0;
         }
         __syncthreads();
         if (sh_best)

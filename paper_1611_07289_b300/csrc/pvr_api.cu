@@ -876,13 +876,13 @@ static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_p
     Tiling tl = make_tiling(ms, pp);
     keep_best = keep_best && tl.tpp == 1;
     BestSim bs;
+    bs.nbest = c->nbest;
+    bs.fixed = c->prm.reg_fixed_step != 0;
     if (keep_best) {
         bs.mode = 1;
         bs.e = c->e_buf;
         bs.valid = c->valid_buf;
         bs.part = c->epart;
-        bs.nbest = c->nbest;
-        bs.fixed = c->prm.reg_fixed_step != 0;
     }
     CUDA_TRY(launch_reg_init(poses, c->prm.n_params, n, c->best, c->trial, c->delta, c->active,
                              c->prm.reg_delta0, st),
@@ -901,6 +901,7 @@ static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_p
                                  c->ncc_counter, st, bs),
                  "ncc_grad");
         if (keep_best) bs.mode = 2;   // after the first evaluation: accepted trials only
+        bs.grad_if_accepted = 1;      // later evaluations: gradients of accepted trials only
         CUDA_TRY_T(PVR_K_NCC_FINISH, launch_ncc_finish(c->d_geom, pp->desc, c->trial, c->prm.n_params, n, tl, c->part,
                                                        gpart, c->prm.reg_min_valid, c->ncc_tmp, grad, st),
                  "ncc_finish");

@@ -75,6 +75,11 @@ struct BestSim {
     const double *nbest = nullptr;
     int mode = 0;
     int fixed = 0;
+    // a registration evaluation after the first: the gradient is needed
+    // only where the trial is accepted (a rejected trial's next step uses
+    // the gradient at the best pose), so one-tile patches skip the gradient
+    // pass elsewhere (their gradient slots read as zero)
+    int grad_if_accepted = 0;
 };
 
 // Launchers (each returns cudaGetLastError() of its launches).
