@@ -304,19 +304,23 @@ SR_LAMBDA, SR_EDGE_DELTA = 0.5, 150.0   # regularised SR update of the whole-ite
 
 
 def run_iterations(cfg, ctx_main, pt, y, x0, gt, dev, n_outer=10, reg_evals=40, n_sr=5, n_params=N_PARAMS,
-                   lam=SR_LAMBDA, delta=SR_EDGE_DELTA, target=None):
+                   lam=SR_LAMBDA, delta=SR_EDGE_DELTA, target=None, plan=None):
     """The method's whole outer iteration (registration to a step below 0.01
     or reg_evals evaluations, then n_sr SR passes, each a SIRT step followed
     -- lam > 0 -- by the edge-preserving diffusion step) repeated n_outer
     times from the initial volume; per-iteration device time (CUDA events)
     and the volume PSNR against the phantom after each; with `target`, the
-    time at which PSNR first reaches it."""
+    time at which PSNR first reaches it.  plan: (tile, mode) of the launch
+    plan to make for the table (setup, untimed), which also fixes the
+    spatial patch launch order."""
     import torch
     from paper_1611_07289_b300 import pvr
     prm = pvr.default_params(psf_dz=0.75, max_patches=32768, max_pixels=1 << 27, max_patch_side=64,
                              reg_evals=reg_evals, n_sr=n_sr, n_params=n_params, sr_lambda=lam,
                              sr_edge_delta=delta)
     ctx = pvr.Context(cfg["geom"], prm)
+    if plan is not None:
+        ctx.pvr_plan(pt, tile=plan[0], mode=plan[1])
     stream = torch.cuda.current_stream()
     x, poses = x0.clone(), torch.zeros((pt.n, n_params), dtype=torch.float64, device=dev)
     state, mask = pvr.new_state(dev), torch.ones(pt.n, dtype=torch.uint8, device=dev)
@@ -510,9 +514,9 @@ def run_ours(args, ws, rank, local, dist):
         "setup_s": {"generate": gen_s, "patch_table": build_s},
     }
     if not args.no_iteration:
-        plain = run_iterations(cfg, ctx, pt, y, x0, gt, dev, n_outer=args.outer_full, lam=0.0)
+        plain = run_iterations(cfg, ctx, pt, y, x0, gt, dev, n_outer=args.outer_full, lam=0.0, plan=plan[:2])
         res["iteration"] = run_iterations(cfg, ctx, pt, y, x0, gt, dev, n_outer=args.outer_full,
-                                          target=plain["best_psnr_db"])
+                                          target=plain["best_psnr_db"], plan=plan[:2])
         res["iteration_unregularised"] = plain
     if ws == 1 and not args.no_extras:
         # the batched uneven-patch form (NEXT-1) and the learned pose

@@ -454,7 +454,14 @@ PVR_API int pvr_reconstruct_iter(pvr_ctx *ctx, float *x, const float *y, const p
  * x, y, poses and keeps the fastest; it synchronises `stream`.  The plan
  * applies to later pvr_simulate, pvr_adjoint and pvr_reconstruct_iter calls
  * with this same table (device pointer, n, n_pix); NCC and registration keep
- * their own tiling.  Reads the table to the host and synchronises. */
+ * their own tiling.  The plan also fixes a launch order of the table's
+ * patches for every per-tile kernel (simulate, adjoint, NCC with and without
+ * gradient, pose gradient; the work queue's items within each tile size):
+ * patches sorted by the block of 32^3 voxels holding their centre at the
+ * identity pose (z block, then y, then x), so that the CTAs running at one
+ * time read a compact part of the volume.  Results do not depend on it
+ * except for the float32 summation order of the adjoint's reductions.
+ * Reads the table to the host and synchronises. */
 PVR_API int pvr_plan(pvr_ctx *ctx, const pvr_patches *patches, const float *x, const float *y,
                      const double *poses, int32_t tile, int32_t mode, void *stream);
 

@@ -50,6 +50,17 @@ __device__ __forceinline__ bool member_ok(const Tiling &tl, size_t o)
     return !tl.member || tl.member[o];
 }
 
+// Tile slot processed at launch position k: with a patch launch order
+// (Tiling::order) the patches' slots in that order, each patch's tiles
+// together.  Results do not depend on the order: every tile writes its own
+// partial sums.
+__device__ __forceinline__ long long tile_at(const Tiling &tl, long long k)
+{
+    if (!tl.order) return k;
+    const int q = (int)k / tl.tpp;   // slots < 2^31 (max_patches x tiles per patch)
+    return (long long)__ldg(tl.order + q) * tl.tpp + ((int)k - q * tl.tpp);
+}
+
 // Decode block -> (patch, tile); returns false for an empty tile or a
 // patch whose descriptor row failed validation in the pose kernel.
 __device__ __forceinline__ bool tile_setup_at(long long gid, const int32_t *__restrict__ desc,
@@ -776,7 +787,7 @@ __global__ void __launch_bounds__(256) k_simulate(const SRC x, VolDims vd,
                                                   double *__restrict__ part)
 {
     extern __shared__ float sm[];
-    simulate_tile<KXY, KZ, SRC>(blockIdx.x, x, vd, desc, fix, psf, tl, y, out, valid, part, sm);
+    simulate_tile<KXY, KZ, SRC>(tile_at(tl, blockIdx.x), x, vd, desc, fix, psf, tl, y, out, valid, part, sm);
 }
 
 // Next work item of a persistent CTA from the queue counter (thread 0 takes
@@ -1071,7 +1082,7 @@ __global__ void __launch_bounds__(256, 3) k_adjoint(VolDims vd, const int32_t *_
                                                  float *__restrict__ conf)
 {
     extern __shared__ float sm[];
-    adjoint_tile<KXY, KZ, PAIR>(blockIdx.x, vd, desc, fix, psf, tl, r, w, pmask, pweight, addon, conf, sm);
+    adjoint_tile<KXY, KZ, PAIR>(tile_at(tl, blockIdx.x), vd, desc, fix, psf, tl, r, w, pmask, pweight, addon, conf, sm);
 }
 
 // The adjoint as a persistent work queue over listed (patch, tile) slots.
@@ -1377,7 +1388,7 @@ __global__ void __launch_bounds__(256, 4) k_ncc_moments(const SRC x, VolDims vd,
     __shared__ int sh_best;
     const int kxy = KXY >= 0 ? KXY : psf.kxy;
     const int kz = KZ >= 0 ? KZ : psf.kz;
-    const long long gid = tile_base + blockIdx.x;
+    const long long gid = tile_at(tl, tile_base + blockIdx.x);
     TileInfo ti;
     bool has = tile_setup_at(gid, desc, fix, tl, kxy, ti);
     double *pt = part + (size_t)gid * kPartStride;
@@ -1656,7 +1667,7 @@ __global__ void __launch_bounds__(256) k_ncc_grad(VolDims vd, const DevGeom *__r
     __shared__ int sh_ok;
     const int kxy = KXY >= 0 ? KXY : psf.kxy;
     const int kz = KZ >= 0 ? KZ : psf.kz;
-    const long long gid = tile_base + blockIdx.x;
+    const long long gid = tile_at(tl, tile_base + blockIdx.x);
     TileInfo ti;
     bool has = tile_setup_at(gid, desc, fix, tl, kxy, ti);
     double *gp = gpart + (size_t)gid * kGradStride;
@@ -1743,8 +1754,8 @@ __global__ void __launch_bounds__(256, 4) k_ncc_fused(const SRC x, VolDims vd,
         __syncthreads();
         if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
         __syncthreads();
-        const long long gid = cur;
-        if (gid >= n_tiles) break;
+        if (cur >= n_tiles) break;
+        const long long gid = tile_at(tl, cur);
         TileInfo ti;
         const bool has = tile_setup_at(gid, desc, fix, tl, kxy, ti);
         double *pt = part + (size_t)gid * kPartStride;
@@ -1886,8 +1897,8 @@ __global__ void __launch_bounds__(256, 4) k_pose_vjp(const SRC x, VolDims vd,
         __syncthreads();
         if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
         __syncthreads();
-        const long long gid = cur;
-        if (gid >= n_tiles) break;
+        if (cur >= n_tiles) break;
+        const long long gid = tile_at(tl, cur);
         TileInfo ti;
         const bool has = tile_setup_at(gid, desc, fix, tl, kxy, ti);
         double *gp = gpart + (size_t)gid * kGradStride;

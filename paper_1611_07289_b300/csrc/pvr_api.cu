@@ -92,6 +92,7 @@ struct pvr_ctx {
     Tiling plan_tl{};
     int plan_mode = 0;            // 0: one CTA per slot, 1: persistent work queue
     int plan_n_items = 0;
+    int32_t *plan_order = nullptr;   // patch launch order of the planned table (Tiling::order)
     // captured reconstruct_iter (pvr_graph_capture)
     cudaGraphExec_t graph_exec = nullptr;
     int64_t graph_launches = 0;
@@ -157,11 +158,22 @@ const WorkQueue *plan_for(pvr_ctx *c, const pvr_patches *pp, int max_side, Tilin
         return nullptr;
     *tl = c->plan_tl;
     tl->member = pp->member;
+    tl->order = c->plan_order;
     if (c->plan_mode != 1) return nullptr;
     wq->items = c->plan_items;
     wq->n_items = c->plan_n_items;
     wq->counter = c->plan_counter;
     return wq;
+}
+
+// The default tiling of a table, with the planned launch order when pvr_plan
+// was called on this exact table.
+Tiling tiling_for(const pvr_ctx *c, int max_side, const pvr_patches *pp)
+{
+    Tiling t = make_tiling(max_side, pp);
+    if (c->plan_n >= 0 && pp->desc == c->plan_desc && pp->n == c->plan_n && pp->n_pix == c->plan_npix)
+        t.order = c->plan_order;
+    return t;
 }
 
 int check_patches(pvr_ctx *c, const pvr_patches *pp, int *max_side)
@@ -229,7 +241,7 @@ void free_all(pvr_ctx *c)
                     c->err, c->best, c->gbest, c->nbest, c->trial, c->delta, c->ncc_tmp,
                     c->grad_tmp, c->active, c->s_buf, c->e_buf, c->p_buf, c->v_buf,
                     c->valid_buf, c->mask_tmp, c->acc2, c->quad, c->x_next, c->gbuf, c->keep, c->imax_key,
-                    c->slice_scr, c->slic_scr, c->plan_items, c->plan_counter,
+                    c->slice_scr, c->slic_scr, c->plan_items, c->plan_counter, c->plan_order,
                     c->counts, c->metric_scr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -467,6 +479,7 @@ int pvr_ctx_create(pvr_ctx **out, const pvr_geometry *g, const pvr_params *prm)
     ALLOC(c->gpart, P * (size_t)c->tpp_alloc * kGradStride);
     ALLOC(c->plan_items, P * (size_t)c->tpp_alloc);
     ALLOC(c->plan_counter, 4);
+    ALLOC(c->plan_order, P);
     ALLOC(c->pstat, 8);
     ALLOC(c->pbar, P);
     ALLOC(c->wsc, P);
@@ -675,7 +688,7 @@ int pvr_simulate(pvr_ctx *c, const float *x, const pvr_patches *pp, const double
     if (pp->n == 0) return PVR_OK;
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     if ((rc = build_quad(c, x, st))) return rc;
-    Tiling tl = make_tiling(ms, pp);
+    Tiling tl = tiling_for(c, ms, pp);
     WorkQueue wqs;
     const WorkQueue *wq = plan_for(c, pp, ms, &tl, &wqs);
     CUDA_TRY_T(PVR_K_SIMULATE, launch_simulate(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x,
@@ -700,7 +713,7 @@ int pvr_adjoint(pvr_ctx *c, const pvr_patches *pp, const double *poses, const fl
     // reduction per voxel corner), then copy / add into the caller's arrays
     CUDA_TRY(cudaMemsetAsync(c->acc2, 0, (size_t)c->nvox * sizeof(float2), st), "clear");
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
-    Tiling tl = make_tiling(ms, pp);
+    Tiling tl = tiling_for(c, ms, pp);
     WorkQueue wqs;
     const WorkQueue *wq = plan_for(c, pp, ms, &tl, &wqs);
     CUDA_TRY_T(PVR_K_ADJOINT, launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix, pp->n,
@@ -722,7 +735,7 @@ int pvr_em_weights(pvr_ctx *c, const float *y, const float *sim, const uint8_t *
     REQUIRE(y && valid && state && mask_out && p, "NULL argument");
     REQUIRE(mask_in != mask_out, "mask_in and mask_out must not alias");
     cudaStream_t st = (cudaStream_t)stream;
-    Tiling tl = make_tiling(ms, pp);
+    Tiling tl = tiling_for(c, ms, pp);
     CUDA_TRY_T(PVR_K_EM, launch_em_stats(y, sim, valid, pp->desc, pp->n, pp->n_pix, tl, c->err, c->part, st),
              "em_stats");
     CUDA_TRY_T(PVR_K_EM, launch_em(y, sim, valid, pp->desc, pp->n, pp->n_pix, tl, c->err, state, mask_in,
@@ -765,7 +778,7 @@ int pvr_volume_init(pvr_ctx *c, float *x, const float *y, const pvr_patches *pp,
     cudaStream_t st = (cudaStream_t)stream;
     CUDA_TRY(cudaMemsetAsync(c->acc2, 0, (size_t)c->nvox * sizeof(float2), st), "clear");
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
-    Tiling tl = make_tiling(ms, pp);
+    Tiling tl = tiling_for(c, ms, pp);
     CUDA_TRY_T(PVR_K_ADJOINT, launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix, pp->n,
                             y, nullptr, nullptr, (float *)c->acc2, nullptr, 1, st),
              "adjoint");
@@ -802,7 +815,7 @@ int pvr_rigidity_map(pvr_ctx *c, const pvr_patches *pp, const double *poses, con
     cudaStream_t st = (cudaStream_t)stream;
     CUDA_TRY(cudaMemsetAsync(c->acc2, 0, (size_t)c->nvox * sizeof(float2), st), "clear");
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
-    Tiling tl = make_tiling(ms, pp);
+    Tiling tl = tiling_for(c, ms, pp);
     CUDA_TRY_T(PVR_K_ADJOINT, launch_adjoint(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, pp->desc, c->fix,
                                              pp->n, p, nullptr, nullptr, (float *)c->acc2, nullptr, 1, st,
                                              nullptr, pbar),
@@ -826,7 +839,7 @@ int pvr_ncc_grad(pvr_ctx *c, const float *x, const float *y, const pvr_patches *
     if (pp->n == 0) return PVR_OK;
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     if ((rc = build_quad(c, x, st))) return rc;
-    Tiling tl = make_tiling(ms, pp);
+    Tiling tl = tiling_for(c, ms, pp);
     CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, c->quad, y,
                              pp->desc, c->fix, poses, pp->n, c->s_buf, c->v_buf, c->part,
                              grad ? c->gpart : nullptr, nullptr, c->prm.reg_min_valid, c->gbuf,
@@ -850,7 +863,7 @@ int pvr_pose_grad(pvr_ctx *c, const float *x, const float *r, const pvr_patches 
     cudaStream_t st = (cudaStream_t)stream;
     if (pp->n == 0) return PVR_OK;
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
-    Tiling tl = make_tiling(ms, pp);
+    Tiling tl = tiling_for(c, ms, pp);
     CUDA_TRY_T(PVR_K_NCC, launch_pose_vjp(c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, r,
                                           pp->desc, c->fix, pp->n, c->gpart, c->gbuf, c->gbuf_tiles,
                                           c->ncc_counter, st),
@@ -873,7 +886,7 @@ static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_p
     int n = pp->n;
     if (kept) *kept = false;
     if (n == 0 || n_evals <= 0) return PVR_OK;
-    Tiling tl = make_tiling(ms, pp);
+    Tiling tl = tiling_for(c, ms, pp);
     keep_best = keep_best && tl.tpp == 1;
     BestSim bs;
     bs.nbest = c->nbest;
@@ -944,7 +957,7 @@ int pvr_reconstruct_iter(pvr_ctx *c, float *x, const float *y, const pvr_patches
     // one-tile patches under the super-resolution tiling too: the
     // registration's NCC kernels keep the forward model at the final poses,
     // and the first pass below reuses it instead of simulating again
-    Tiling tl = make_tiling(ms, pp);
+    Tiling tl = tiling_for(c, ms, pp);
     WorkQueue wqs;
     const WorkQueue *wq = plan_for(c, pp, ms, &tl, &wqs);
     bool kept = false;
@@ -994,13 +1007,49 @@ int pvr_reconstruct_iter(pvr_ctx *c, float *x, const float *y, const pvr_patches
 
 namespace {
 
+// Launch order of a patch table: the patches sorted (stably) by the block of
+// 32^3 voxels that holds their centre at the identity pose, z block first,
+// then y, then x.  The CTAs running at one time then gather from (and
+// scatter to) a compact part of the volume whatever the stack order of the
+// table; in table order the patches of each stack sweep the whole volume,
+// and the volume data is fetched from DRAM again for every stack.  Rows with
+// an invalid stack index keep key 0 (the kernels skip them anyway).
+std::vector<int32_t> spatial_patch_order(const pvr_geometry &g, const std::vector<int32_t> &desc, int n)
+{
+    std::vector<std::pair<int64_t, int32_t>> v((size_t)n);
+    const double *W = g.world_to_voxel;
+    for (int p = 0; p < n; ++p) {
+        const int32_t *d = &desc[8 * (size_t)p];
+        int64_t key = 0;
+        if (d[0] >= 0 && d[0] < g.n_stacks) {
+            const double *M = g.pixel_to_world[d[0]];
+            const double ci = d[2] + 0.5 * d[4] - 0.5, cj = d[3] + 0.5 * d[5] - 0.5, k = d[1];
+            double w[3];
+            for (int r = 0; r < 3; ++r) w[r] = M[4 * r] * ci + M[4 * r + 1] * cj + M[4 * r + 2] * k + M[4 * r + 3];
+            int64_t b[3];
+            for (int r = 0; r < 3; ++r) {
+                const double v_ = W[4 * r] * w[0] + W[4 * r + 1] * w[1] + W[4 * r + 2] * w[2] + W[4 * r + 3];
+                b[r] = v_ >= 0.0 ? (v_ < 32.0 * 1023.0 ? (int64_t)(v_ / 32.0) : 1023) : 0;   // NaN -> 0
+            }
+            key = (b[2] * 1024 + b[1]) * 1024 + b[0];
+        }
+        v[(size_t)p] = {key, (int32_t)p};
+    }
+    std::stable_sort(v.begin(), v.end(), [](const std::pair<int64_t, int32_t> &a,
+                                            const std::pair<int64_t, int32_t> &b) { return a.first < b.first; });
+    std::vector<int32_t> order((size_t)n);
+    for (int i = 0; i < n; ++i) order[(size_t)i] = v[(size_t)i].second;
+    return order;
+}
+
 // Non-empty (patch, tile) slots of the table under tiling tl, largest tiles
-// first (stable, so equal tiles keep table order).
-std::vector<int32_t> tile_items(const std::vector<int32_t> &desc, int n, const Tiling &tl)
+// first (stable, so equal tiles keep the patch order given).
+std::vector<int32_t> tile_items(const std::vector<int32_t> &desc, const std::vector<int32_t> &porder,
+                                const Tiling &tl)
 {
     std::vector<std::pair<int, int32_t>> v;
-    v.reserve((size_t)n * tl.tpp);
-    for (int p = 0; p < n; ++p) {
+    v.reserve(porder.size() * tl.tpp);
+    for (const int32_t p : porder) {
         const int w = desc[8 * (size_t)p + 4], h = desc[8 * (size_t)p + 5];
         for (int t = 0; t < tl.tpp; ++t) {
             const int i0 = (t % tl.tiles_x) * tl.T, j0 = (t / tl.tiles_x) * tl.T;
@@ -1036,6 +1085,10 @@ int pvr_plan(pvr_ctx *c, const pvr_patches *pp, const float *x, const float *y, 
     CUDA_TRY(cudaMemcpyAsync(desc.data(), pp->desc, desc.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st),
              "read table");
     CUDA_TRY(cudaStreamSynchronize(st), "synchronise");
+    const std::vector<int32_t> porder = spatial_patch_order(c->geom, desc, pp->n);
+    CUDA_TRY(cudaMemcpyAsync(c->plan_order, porder.data(), porder.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             st),
+             "upload order");
     // candidates: tile side 64 (or the largest side below it), and 32 where
     // the partial buffers hold its slots; each as one CTA per slot or as a
     // persistent work queue
@@ -1052,7 +1105,8 @@ int pvr_plan(pvr_ctx *c, const pvr_patches *pp, const float *x, const float *y, 
     for (int T : sides) {
         Tiling tl = make_tiling_t(ms, T);
         tl.member = pp->member;
-        if (mode != 0) cands.push_back({tl, 1, tile_items(desc, pp->n, tl)});
+        tl.order = c->plan_order;
+        if (mode != 0) cands.push_back({tl, 1, tile_items(desc, porder, tl)});
         if (mode != 1) cands.push_back({tl, 0, {}});
     }
     int best = 0;

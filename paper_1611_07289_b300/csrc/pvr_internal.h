@@ -50,6 +50,10 @@ struct Tiling {
     int T;
     int tiles_x, tiles_y, tpp;
     const uint8_t *member = nullptr;   // per patch pixel: 1 = part of the patch (null: all)
+    // patch launch order (a permutation of 0 .. n - 1): launch position k
+    // (the k-th CTA, or the k-th tile a persistent kernel takes) processes
+    // tile k % tpp of patch order[k / tpp] (null: slot order)
+    const int32_t *order = nullptr;
 };
 
 // Persistent work queue over the non-empty (patch, tile) slots of a patch

@@ -94,6 +94,31 @@ def test_planned_launches_match_unplanned_and_oracle(pvr, planned):
     assert ctx.pvr_plan_info() == (0, -1, 0)
 
 
+def test_planned_patch_order_leaves_ncc_and_gradient_unchanged(pvr, planned):
+    """pvr_plan also fixes the launch order of the table's patches (sorted by
+    the 32^3-voxel block of their centre).  The NCC kernels write one sum per
+    tile, so NCC and gradient are bit-identical with and without that order:
+    for the whole table (multi-tile patches: the chunked kernels) and for its
+    patches of at most 64 pixels (one tile each: the persistent fused
+    kernel, which takes tiles from a counter in that order)."""
+    ctx, pt, y = planned["ctx"], planned["pt"], planned["y"]
+    X, P = _t(planned["x"]), _t(planned["poses"])
+    desc = pt.desc.cpu().numpy()
+    small = np.flatnonzero(desc[:, 4] <= 64)
+    sub = pvr.PatchTable(pt.desc[_t(small)].contiguous(), pt.n_pix)
+    assert pt.max_side > 64 and 0 < small.size < pt.n and sub.max_side <= 64
+    for table, poses in ((pt, P), (sub, P[_t(small)].contiguous())):
+        ctx.pvr_plan_clear()
+        n0, g0 = ctx.pvr_ncc_grad(X, y, table, poses)
+        m0, _ = ctx.pvr_ncc_grad(X, y, table, poses, want_grad=False)
+        ctx.pvr_plan(table, tile=64, mode=0)
+        n1, g1 = ctx.pvr_ncc_grad(X, y, table, poses)
+        m1, _ = ctx.pvr_ncc_grad(X, y, table, poses, want_grad=False)
+        assert torch.equal(n0, n1) and torch.equal(g0, g1) and torch.equal(m0, m1)
+        assert torch.isfinite(g0).all() and (n0 != 0).any()
+    ctx.pvr_plan_clear()
+
+
 def test_iteration_plan_and_graph_match_direct_call(pvr, planned):
     ctx, pt = planned["ctx"], planned["pt"]
     y = planned["y"]
