@@ -2126,7 +2126,7 @@ cudaError_t launch_adjoint(const PsfTab &psf, const Tiling &tl, int nx, int ny, 
 }
 
 cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &tl, int nx, int ny,
-                            int nz, const float4 *quad, const float *y,
+                            int nz, const float *xplain, const float4 *quad, const float *y,
                             const int32_t *desc, const int32_t *fix, const double *poses, int n,
                             float *s_buf,
                             uint8_t *v_buf, double *part, double *gpart, const int32_t *active,
@@ -2149,21 +2149,20 @@ cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &t
     cudaError_t e;
     if (gpart && tl.tpp == 1) {
         // one-tile patches: the fused persistent kernel, one scratch slot per
-        // CTA, gathering from the quad copy (two 16-byte loads per sample).
-        // Under the spatial launch order the quad data of the tiles in flight
-        // is a small part of L2; in table order the 200 MB quad copy pushed
-        // the scratch slots (about 60 MB in flight) out of L2 and the plain
-        // volume was the faster source.
+        // CTA.  It gathers from the plain volume: the scratch slots in flight
+        // (about 60 MB) then share L2 with 50 MB of volume instead of the
+        // 200 MB quad copy, and stay on chip.
+        const PlainVol xp{xplain};
         size_t smem3 = (size_t)(2 * Lmax + Cmax) * sizeof(float);
         int dev = 0, nsm = 0, per_sm = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         if (fast) {
-            if ((e = prep(k_ncc_fused<1, 3, QuadVol>, smem3)) != cudaSuccess) return e;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ncc_fused<1, 3, QuadVol>, 256, smem3);
+            if ((e = prep(k_ncc_fused<1, 3, PlainVol>, smem3)) != cudaSuccess) return e;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ncc_fused<1, 3, PlainVol>, 256, smem3);
         } else {
-            if ((e = prep(k_ncc_fused<-1, -1, QuadVol>, smem3)) != cudaSuccess) return e;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ncc_fused<-1, -1, QuadVol>, 256, smem3);
+            if ((e = prep(k_ncc_fused<-1, -1, PlainVol>, smem3)) != cudaSuccess) return e;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ncc_fused<-1, -1, PlainVol>, 256, smem3);
         }
         if (e != cudaSuccess) return e;
         long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
@@ -2173,10 +2172,10 @@ cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &t
         if (grid <= 0) return cudaErrorInvalidValue;
         if ((e = cudaMemsetAsync(counter, 0, sizeof(int), st)) != cudaSuccess) return e;
         if (fast)
-            k_ncc_fused<1, 3, QuadVol><<<(unsigned)grid, 256, smem3, st>>>(x, vd, desc, fix, psf, tl, total, y, active,
+            k_ncc_fused<1, 3, PlainVol><<<(unsigned)grid, 256, smem3, st>>>(xp, vd, desc, fix, psf, tl, total, y, active,
                                                                   part, gpart, gbuf, Lmax, min_valid, bs, counter);
         else
-            k_ncc_fused<-1, -1, QuadVol><<<(unsigned)grid, 256, smem3, st>>>(x, vd, desc, fix, psf, tl, total, y,
+            k_ncc_fused<-1, -1, PlainVol><<<(unsigned)grid, 256, smem3, st>>>(xp, vd, desc, fix, psf, tl, total, y,
                                                                     active, part, gpart, gbuf, Lmax,
                                                                     min_valid, bs, counter);
         return cudaGetLastError();

@@ -840,7 +840,7 @@ int pvr_ncc_grad(pvr_ctx *c, const float *x, const float *y, const pvr_patches *
     if ((rc = pose_fixed(c, pp, ms, poses, st))) return rc;
     if ((rc = build_quad(c, x, st))) return rc;
     Tiling tl = tiling_for(c, ms, pp);
-    CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, c->quad, y,
+    CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, c->quad, y,
                              pp->desc, c->fix, poses, pp->n, c->s_buf, c->v_buf, c->part,
                              grad ? c->gpart : nullptr, nullptr, c->prm.reg_min_valid, c->gbuf,
                              c->gbuf_tiles, c->ncc_counter, st),
@@ -908,7 +908,7 @@ static int register_impl(pvr_ctx *c, const float *x, const float *y, const pvr_p
         // never be used, so it computes the NCC alone
         const bool need_grad = ev < n_evals - 1;
         double *gpart = need_grad ? c->gpart : nullptr, *grad = need_grad ? c->grad_tmp : nullptr;
-        CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, c->quad, y,
+        CUDA_TRY_T(PVR_K_NCC, launch_ncc_grad(c->d_geom, c->psf, tl, c->geom.nx, c->geom.ny, c->geom.nz, x, c->quad, y,
                                  pp->desc, c->fix, c->trial, n, c->s_buf, c->v_buf, c->part,
                                  gpart, c->active, c->prm.reg_min_valid, c->gbuf, c->gbuf_tiles,
                                  c->ncc_counter, st, bs),

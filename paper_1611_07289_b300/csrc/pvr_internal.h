@@ -140,7 +140,7 @@ bool sr_diffuse_uses_tma(const float *u, int nx, int ny, int nz);
 // streams per-lattice-point gradient sums through gbuf, in chunks of whole
 // patches of at most gbuf_tiles tiles.
 cudaError_t launch_ncc_grad(const DevGeom *g, const PsfTab &psf, const Tiling &tl, int nx, int ny,
-                            int nz, const float4 *quad, const float *y,
+                            int nz, const float *xplain, const float4 *quad, const float *y,
                             const int32_t *desc, const int32_t *fix, const double *poses, int n,
                             float *s_buf,
                             uint8_t *v_buf, double *part, double *gpart, const int32_t *active,
