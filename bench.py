@@ -66,7 +66,7 @@ def _dist():
 def _config_dict(n_patches=None, n_pix=None, slices=96):
     wl = WORKLOAD if slices == 96 else WORKLOAD.replace("4x96", f"4x{slices}")
     return {"workload": wl, "volume": [256, 256, 192], "voxel_mm": 0.75,
-            "stacks": "3 orthogonal + 1 oblique, 96 x 256^2 @ 0.75x0.75x2.5 mm",
+            "stacks": f"3 orthogonal + 1 oblique, {slices} x 256^2 @ 0.75x0.75x2.5 mm",
             "patch": 64, "stride": 32, "psf": "gaussian kxy=1 kz=3 dz=0.75mm",
             "step": "pvr_reconstruct_iter: 2 NCC evals + pose update, 1 SR pass",
             "pose": "affine, 12 parameters",
