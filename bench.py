@@ -526,6 +526,13 @@ def run_ours(args, ws, rank, local, dist):
         res["batched_uneven"] = {k: u[k] for k in ("value", "unit", "ms_per_step", "simulate_adjoint_ms",
                                                    "iteration_ms", "roofline")}
         res["batched_uneven"]["config"] = u["config"]
+        d = run_diff(args, ws, rank, local)
+        res["differentiable"] = {k: d[k] for k in ("metric", "value", "unit", "ms_per_step",
+                                                   "kernels_ms_per_step", "gpu_launches_per_step",
+                                                   "descends", "config")}
+        res["differentiable"]["loss_first_last"] = [d["loss"][0], d["loss"][-1]]
+        res["differentiable"]["pose_error_first_last"] = [d["pose_mean_abs_error"][0],
+                                                          d["pose_mean_abs_error"][-1]]
         p = run_proposal(args, ws, rank, local, cfg)
         res["learned_proposal"] = {k: p[k] for k in ("metric", "value", "unit", "plain_s_to_psnr",
                                                      "plain_best_psnr_db", "learned_best_psnr_db",
@@ -745,6 +752,92 @@ def run_proposal(args, ws, rank, local, cfg=None):
     }
 
 
+def run_diff(args, ws, rank, local, steps=10, warmup=3):
+    """Differentiable forward model: 128^3 nested-ellipsoid volume at 1 mm,
+    3 orthogonal stacks of 86 slices of 128^2 at 1 x 1 x 1.5 mm, every 48 x 48
+    patch at stride 24.  One step is one L2 gradient-descent step on the
+    volume and the rigid poses through autograd.simulate_patches (forward
+    pvr_simulate; backward pvr_adjoint for the volume, pvr_pose_grad for the
+    poses) plus the loss and the update in torch; device-timed with CUDA
+    events, L2 flushed between steps.  The data are simulated from the true
+    volume at the true poses; the start is 0.8 x the volume and poses
+    perturbed by up to 1 mm / 1 degree, so the loss and the pose error must
+    fall at every step."""
+    import torch
+    from paper_1611_07289_b300 import pvr, synth
+    from paper_1611_07289_b300.autograd import simulate_patches
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    cfg = synth.config_diff(device=dev)
+    geom, desc, npix = cfg["geom"], cfg["desc"], cfg["n_pix"]
+    ctx = pvr.Context(geom, pvr.default_params(psf_dz=1.0, max_patches=len(desc), max_pixels=npix,
+                                               max_patch_side=48))
+    pt = pvr.PatchTable.from_numpy(desc, npix, device=dev)
+    x_true = torch.as_tensor(cfg["gt"].astype(np.float32), device=dev).reshape(ctx.vol_shape).contiguous()
+    th_true = torch.zeros((pt.n, 6), dtype=torch.float64, device=dev)
+    y, _ = ctx.pvr_simulate(x_true, pt, th_true)
+    rng = np.random.default_rng(4)
+    th0 = th_true + torch.as_tensor(synth.random_poses(rng, pt.n, rot=1.0, trans=1.0), device=dev)
+    x0 = (x_true * 0.8).contiguous()
+    plan = ctx.pvr_plan(pt, x0, y, th0)
+    _, conf = ctx.pvr_adjoint(pt, th_true)
+    ax = 1.0 / float(conf.max())      # below 2 / ||A^T A|| (rows of A sum to one)
+
+    def step(x, th):
+        sim, valid = simulate_patches(x, th, ctx, pt)
+        r = (sim - y) * valid.float()
+        loss = 0.5 * (r * r).sum()
+        x.grad = th.grad = None
+        loss.backward()
+        with torch.no_grad():
+            x -= ax * x.grad
+            g = th.grad
+            th -= 0.05 * g / g.norm(dim=1, keepdim=True).clamp_min(1e-30)
+        return loss.detach()
+
+    x, th = x0.clone().requires_grad_(True), th0.clone().requires_grad_(True)
+    for _ in range(warmup):
+        step(x, th)
+    torch.cuda.synchronize()
+    x, th = x0.clone().requires_grad_(True), th0.clone().requires_grad_(True)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    losses, perr = [], [(th.detach() - th_true).abs().mean()]
+    l0 = ctx.launches
+    ctx.pvr_profile_enable(True)
+    ctx.pvr_profile_read()
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        losses.append(step(x, th))
+        ev[k][1].record(stream)
+        perr.append((th.detach() - th_true).abs().mean())
+    torch.cuda.synchronize()
+    prof = ctx.pvr_profile_read()
+    ctx.pvr_profile_enable(False)
+    launches = ctx.launches - l0
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    losses = [float(v) for v in losses]
+    perr = [float(v) for v in perr]
+    ctx.pvr_device_status()
+    ctx.close()
+    return {
+        "metric": "patch-pixels/s of one autograd step (forward model, volume and pose gradients, update)",
+        "value": npix / (ms * 1e-3), "unit": "patch-pixels/s", "ms_per_step": ms, "steps": steps,
+        "warmup": warmup,
+        "kernels_ms_per_step": {k: v[0] / steps for k, v in prof.items() if v[1]},
+        "gpu_launches_per_step": launches / steps,
+        "loss": losses, "pose_mean_abs_error": perr,
+        "descends": all(b < a for a, b in zip(losses, losses[1:])) and perr[-1] < perr[0],
+        "config": {"workload": "diff-128: 128^3 at 1 mm, 3 x 86 slices of 128^2, 48x48 patches stride 24",
+                   "n_patches": pt.n, "n_patch_pixels": npix, "pose": "rigid, 6 parameters",
+                   "launch_plan": {"tile": plan[0], "mode": plan[1]},
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "data": "synthetic", "dtype": "f32",
+    }
+
+
 def run_reference(args, ws, rank):
     """The FP64 oracle as the reference arm: rank 0 only, on the host cores."""
     if rank != 0:
@@ -785,9 +878,10 @@ def main():
     ap.add_argument("--outer-full", type=int, default=10, help="outer iterations of the whole-iteration field")
     ap.add_argument("--slices", type=int, default=96,
                     help="slices per stack (96 = the benchmark workload; fewer for profiling)")
-    ap.add_argument("--workload", choices=["uterus", "uneven", "proposal"], default="uterus",
+    ap.add_argument("--workload", choices=["uterus", "uneven", "proposal", "diff"], default="uterus",
                     help="uneven: patch sides 32..128 per slice (batched-launch comparison, 1 GPU); "
-                         "proposal: learned pose proposal, time to PSNR against plain registration")
+                         "proposal: learned pose proposal, time to PSNR against plain registration; "
+                         "diff: autograd step of the differentiable forward model (128^3)")
     ap.add_argument("--pairs", type=int, default=200000, help="training pairs (proposal workload)")
     ap.add_argument("--outer", type=int, default=8, help="outer iterations (proposal workload)")
     ap.add_argument("--propose-iters", type=int, default=2, help="iterations that start with the proposal")
@@ -801,6 +895,8 @@ def main():
         res = run_uneven(args, ws, rank, local) if rank == 0 else None
     elif args.workload == "proposal":
         res = run_proposal(args, ws, rank, local) if rank == 0 else None
+    elif args.workload == "diff":
+        res = run_diff(args, ws, rank, local, steps=args.steps, warmup=args.warmup) if rank == 0 else None
     else:
         if ws > 1:
             import torch.distributed as dist
