@@ -838,6 +838,120 @@ def run_diff(args, ws, rank, local, steps=10, warmup=3):
     }
 
 
+def _event_ms(fn, reps=5, warmup=2, flush=None):
+    """Median device time (ms) of fn() over reps runs after warmup runs,
+    CUDA events on the current stream, L2 flushed before each run."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    ts = []
+    s = torch.cuda.current_stream()
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def run_variants(args, ws, rank, local, cfg=None):
+    """The paper's variants on the uterus workload, each timed through its
+    library call (CUDA events, L2 flushed): the benchmark step with the
+    Taylor-sinc in-plane PSF against the Gaussian one, the rigidity map, the
+    per-patch metrics with local DSSIM maps, the superpixel patch table; and
+    on the skew-motion workload (the paper's adult-brain motion model on a
+    phantom) patches under rigid and affine poses and whole slices under
+    rigid poses, PSNR after each outer iteration."""
+    import torch
+    from paper_1611_07289_b300 import pvr, synth
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    if cfg is None:
+        cfg = synth.config_uterus(device=dev, slices=args.slices)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    packed = torch.as_tensor(synth.pack_stacks(cfg["stacks"]), device=dev)
+    out = {}
+    steps = {}
+    for kind, name in ((0, "gaussian"), (1, "taylor_sinc")):
+        prm = pvr.default_params(psf_dz=0.75, max_patches=32768, max_pixels=1 << 27, max_patch_side=64,
+                                 reg_evals=2, n_sr=1, n_params=N_PARAMS, psf_kind=kind, slic_a_min=32)
+        ctx = pvr.Context(cfg["geom"], prm)
+        pt, n = ctx.pvr_patches_build(packed, 64, 32, 0.01, 0.5)
+        y = ctx.pvr_patches_gather(packed, pt)
+        P0 = torch.zeros((pt.n, N_PARAMS), dtype=torch.float64, device=dev)
+        x0 = ctx.pvr_volume_init(y, pt, P0)
+        ctx.pvr_plan(pt, x0, y, P0)
+        x, P, st = x0.clone(), P0.clone(), pvr.new_state(dev)
+        m = torch.ones(pt.n, dtype=torch.uint8, device=dev)
+        steps[name] = _event_ms(lambda: ctx.pvr_reconstruct_iter(x, y, pt, P, st, m), flush=flush)
+        if kind == 0:
+            sim, valid = ctx.pvr_simulate(x0, pt, P0)
+            st2 = pvr.new_state(dev)
+            p, w, pbar, mk = ctx.pvr_em_weights(y, sim, valid, pt, st2)
+            out["rigidity_map_ms"] = _event_ms(lambda: ctx.pvr_rigidity_map(pt, P0, p, pbar), flush=flush)
+            out["patch_metrics_ms"] = _event_ms(lambda: ctx.pvr_patch_metrics(y, sim, valid, pt, w=3),
+                                                flush=flush)
+            res = {}
+
+            def slic():
+                res["t"] = ctx.pvr_patches_build_slic(packed, 32, 10.0, 2, n_iter=10)
+            out["slic_patch_table_ms"] = _event_ms(slic, reps=3, warmup=1, flush=flush)
+            spt, sn = res["t"]
+            out["slic_patches"] = int(sn)
+            out["slic_patch_pixels"] = int(spt.n_pix)
+            out["n_patches"] = int(pt.n)
+            out["n_patch_pixels"] = int(pt.n_pix)
+        ctx.pvr_device_status()
+        ctx.close()
+    out["step_ms"] = steps
+    # skew motion: patches under rigid (6) and affine (12) poses, and whole
+    # slices under rigid poses (slice-to-volume registration), 4 outer
+    # iterations with the regularised update
+    sk = synth.config_skew(theta_deg=5.0, device=dev)
+    gt = torch.as_tensor(sk["gt"], device=dev)
+    spacked = torch.as_tensor(synth.pack_stacks(sk["stacks"]), device=dev)
+    skew = {}
+    for name, a, stride, npar in (("patches_rigid", 32, 16, 6), ("patches_affine", 32, 16, 12),
+                                  ("slices_rigid", 96, 96, 6)):
+        prm = pvr.default_params(psf_dz=sk["dz"], max_patches=32768, max_pixels=1 << 26, max_patch_side=96,
+                                 reg_evals=20, n_sr=3, n_params=npar, sr_lambda=SR_LAMBDA,
+                                 sr_edge_delta=SR_EDGE_DELTA)
+        ctx = pvr.Context(sk["geom"], prm)
+        pt, n = ctx.pvr_patches_build(spacked, a, stride, sk["fg_frac"], sk["keep_frac"] if a < 96 else 0.0)
+        y = ctx.pvr_patches_gather(spacked, pt)
+        P = torch.zeros((pt.n, npar), dtype=torch.float64, device=dev)
+        x = ctx.pvr_volume_init(y, pt, P)
+        ctx.pvr_plan(pt, tile=64, mode=0)
+        st, m = pvr.new_state(dev), torch.ones(pt.n, dtype=torch.uint8, device=dev)
+        psnr, ms = [float(ctx.pvr_metrics(gt, x)[0])], []
+        for _ in range(4):
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record()
+            ctx.pvr_reconstruct_iter(x, y, pt, P, st, m)
+            b_.record()
+            torch.cuda.synchronize()
+            ms.append(a_.elapsed_time(b_))
+            psnr.append(float(ctx.pvr_metrics(gt, x)[0]))
+        skew[name] = {"n_patches": int(pt.n), "psnr_db": psnr, "ms_per_iteration": ms}
+        ctx.pvr_device_status()
+        ctx.close()
+    skew["config"] = {"workload": "skew-5deg: 96^3 nested ellipsoids at 1.25 mm, 3 orthogonal stacks of 48 "
+                                  "slices of 96^2, odd slices skewed (tan 5 deg); patches 32x32 stride 16 or "
+                                  "whole slices",
+                      "reg_evals": 20, "n_sr": 3, "outer_iterations": 4,
+                      "sr_update": f"SIRT + diffusion (lambda {SR_LAMBDA}, delta {SR_EDGE_DELTA})"}
+    out["skew_motion"] = skew
+    out["config"] = {"workload": WORKLOAD, "step": "pvr_reconstruct_iter: 2 NCC evals + pose update, 1 SR pass",
+                     "slic": "a = 32, compactness 10, dilation 2 px, 10 iterations (boxes above 64 px dropped)",
+                     "l2": "flushed before each timed call (256 MiB write)"}
+    out["data"] = "synthetic"
+    return out
+
+
 def run_reference(args, ws, rank):
     """The FP64 oracle as the reference arm: rank 0 only, on the host cores."""
     if rank != 0:
@@ -878,10 +992,13 @@ def main():
     ap.add_argument("--outer-full", type=int, default=10, help="outer iterations of the whole-iteration field")
     ap.add_argument("--slices", type=int, default=96,
                     help="slices per stack (96 = the benchmark workload; fewer for profiling)")
-    ap.add_argument("--workload", choices=["uterus", "uneven", "proposal", "diff"], default="uterus",
+    ap.add_argument("--workload", choices=["uterus", "uneven", "proposal", "diff", "variants"],
+                    default="uterus",
                     help="uneven: patch sides 32..128 per slice (batched-launch comparison, 1 GPU); "
                          "proposal: learned pose proposal, time to PSNR against plain registration; "
-                         "diff: autograd step of the differentiable forward model (128^3)")
+                         "diff: autograd step of the differentiable forward model (128^3); "
+                         "variants: the paper's variants (Taylor-sinc PSF, rigidity map, metrics, "
+                         "superpixels, skew motion)")
     ap.add_argument("--pairs", type=int, default=200000, help="training pairs (proposal workload)")
     ap.add_argument("--outer", type=int, default=8, help="outer iterations (proposal workload)")
     ap.add_argument("--propose-iters", type=int, default=2, help="iterations that start with the proposal")
@@ -895,6 +1012,8 @@ def main():
         res = run_uneven(args, ws, rank, local) if rank == 0 else None
     elif args.workload == "proposal":
         res = run_proposal(args, ws, rank, local) if rank == 0 else None
+    elif args.workload == "variants":
+        res = run_variants(args, ws, rank, local) if rank == 0 else None
     elif args.workload == "diff":
         res = run_diff(args, ws, rank, local, steps=args.steps, warmup=args.warmup) if rank == 0 else None
     else:
