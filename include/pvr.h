@@ -468,6 +468,11 @@ PVR_API int pvr_plan(pvr_ctx *ctx, const pvr_patches *patches, const float *x, c
 /* The current plan: tile side (0 if none), mode (-1 if none), listed tiles. */
 PVR_API int pvr_plan_info(const pvr_ctx *ctx, int32_t *tile, int32_t *mode, int32_t *n_items);
 
+/* The plan's patch launch order (a permutation of 0 .. n-1; n = the planned
+ * table's patch count) copied to HOST memory host_out[n].  PVR_ERR_INVALID_ARG
+ * without a plan or for another n.  Synchronises `stream`. */
+PVR_API int pvr_plan_order(pvr_ctx *ctx, int32_t *host_out, int32_t n, void *stream);
+
 /* Drop the plan (later calls use one CTA per 64-pixel tile slot). */
 PVR_API int pvr_plan_clear(pvr_ctx *ctx);
 

@@ -1181,6 +1181,19 @@ int pvr_plan_info(const pvr_ctx *c, int32_t *tile, int32_t *mode, int32_t *n_ite
     return PVR_OK;
 }
 
+int pvr_plan_order(pvr_ctx *c, int32_t *host_out, int32_t n, void *stream)
+{
+    if (!c) return PVR_ERR_INVALID_ARG;
+    REQUIRE(c->plan_n >= 0, "no plan is held");
+    REQUIRE(n == c->plan_n && (n == 0 || host_out), "n must be the planned table's patch count");
+    if (n == 0) return PVR_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(host_out, c->plan_order, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, st),
+             "read order");
+    CUDA_TRY(cudaStreamSynchronize(st), "synchronise");
+    return PVR_OK;
+}
+
 int pvr_plan_clear(pvr_ctx *c)
 {
     if (!c) return PVR_ERR_INVALID_ARG;

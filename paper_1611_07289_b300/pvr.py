@@ -100,6 +100,7 @@ _SIGS = {
     "pvr_plan": (C.c_int, [_VP, C.POINTER(Patches), _VP, _VP, _VP, C.c_int32, C.c_int32, _VP]),
     "pvr_plan_info": (C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pvr_plan_clear": (C.c_int, [_VP]),
+    "pvr_plan_order": (C.c_int, [_VP, _VP, C.c_int32, _VP]),
     "pvr_graph_capture": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, _VP, _VP, _VP, _VP, _VP]),
     "pvr_graph_launch": (C.c_int, [_VP, _VP]),
     "pvr_register": (C.c_int, [_VP, _VP, _VP, C.POINTER(Patches), _VP, C.c_int32, _VP, _VP]),
@@ -398,6 +399,12 @@ class Context:
         t, m, n = C.c_int32(0), C.c_int32(0), C.c_int32(0)
         self._chk(lib.pvr_plan_info(self.h, C.byref(t), C.byref(m), C.byref(n)))
         return int(t.value), int(m.value), int(n.value)
+
+    def pvr_plan_order(self, n, stream=None):
+        """The plan's patch launch order (numpy int32 [n])."""
+        out = np.zeros(max(int(n), 1), dtype=np.int32)
+        self._chk(lib.pvr_plan_order(self.h, out.ctypes.data_as(C.c_void_p), int(n), _stream(stream)))
+        return out[:int(n)]
 
     def pvr_plan_clear(self):
         self._chk(lib.pvr_plan_clear(self.h))

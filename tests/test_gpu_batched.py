@@ -119,6 +119,45 @@ def test_planned_patch_order_leaves_ncc_and_gradient_unchanged(pvr, planned):
     ctx.pvr_plan_clear()
 
 
+def _spatial_order(geom, desc):
+    """The documented launch order: patches stably sorted by the 32^3-voxel
+    block (z, then y, then x) holding their centre at the identity pose."""
+    d = np.asarray(desc, dtype=np.int64)
+    W = np.asarray(geom.w2v, dtype=np.float64)
+    keys = np.zeros(len(d), dtype=np.int64)
+    for i, row in enumerate(d):
+        P = np.asarray(geom.p2w[row[0]], dtype=np.float64)
+        ci, cj, k = row[2] + 0.5 * row[4] - 0.5, row[3] + 0.5 * row[5] - 0.5, float(row[1])
+        w = [P[r, 0] * ci + P[r, 1] * cj + P[r, 2] * k + P[r, 3] for r in range(3)]
+        b = []
+        for r in range(3):
+            v = W[r, 0] * w[0] + W[r, 1] * w[1] + W[r, 2] * w[2] + W[r, 3]
+            b.append(int(v / 32.0) if 0.0 <= v < 32.0 * 1023.0 else (1023 if v >= 0.0 else 0))
+        keys[i] = (b[2] * 1024 + b[1]) * 1024 + b[0]
+    return np.argsort(keys, kind="stable").astype(np.int32), keys
+
+
+def test_plan_order_is_the_spatial_sort(pvr):
+    """pvr_plan_order returns a permutation equal to the documented sort of
+    the 128^3 workload's 4,128 patches (three stacks, many 32^3 blocks)."""
+    cfg = synth.config_diff()
+    geom, desc, npix = cfg["geom"], cfg["desc"], cfg["n_pix"]
+    ctx = pvr.Context(geom, pvr.default_params(max_patches=len(desc), max_pixels=npix, max_patch_side=48))
+    pt = pvr.PatchTable.from_numpy(desc, npix)
+    with pytest.raises(pvr.PvrError):
+        ctx.pvr_plan_order(pt.n)                      # no plan yet
+    ctx.pvr_plan(pt, tile=64, mode=0)
+    order = ctx.pvr_plan_order(pt.n)
+    ref, keys = _spatial_order(geom, desc)
+    assert len(np.unique(keys)) > 20
+    assert np.array_equal(np.sort(order), np.arange(pt.n))
+    assert np.array_equal(order, ref)
+    with pytest.raises(pvr.PvrError):
+        ctx.pvr_plan_order(pt.n - 1)                  # another count
+    ctx.pvr_plan_clear()
+    ctx.close()
+
+
 def test_iteration_plan_and_graph_match_direct_call(pvr, planned):
     ctx, pt = planned["ctx"], planned["pt"]
     y = planned["y"]
