@@ -197,6 +197,44 @@ def _profile_traffic(cls):
     return float(m.group(1))
 
 
+_CLASS_KERNELS = {"ncc": ("k_ncc_fused", "k_ncc_moments"), "adjoint": ("k_adjoint",)}
+
+
+def _profile_issue(cls):
+    """Issue utilisation of the kernels of `cls` from the committed ncu
+    counters (profiles/kernels_uterus24.md: smsp__issue_active, warp
+    instructions, duration), if the kernel source is unchanged: the fraction
+    of the SM schedulers' issue slots used while the kernel ran.  These
+    kernels are gathers bound by instruction issue and load latency, so this
+    is the bound that their HBM fraction does not show."""
+    path = os.path.join(ROOT, "profiles", "kernels_uterus24.md")
+    if cls not in _CLASS_KERNELS or not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    h = re.search(r"source_sha256 of csrc/k_patch.cu:\s*([0-9a-f]+)", txt)
+    src = open(os.path.join(ROOT, "paper_1611_07289_b300", "csrc", "k_patch.cu"), "rb").read()
+    if not h or hashlib.sha256(src).hexdigest()[:16] != h.group(1)[:16]:
+        return None
+    out = {}
+    for k in _CLASS_KERNELS[cls]:
+        m = re.search(r"## `" + k + r"`(.*?)(?=\n## |\Z)", txt, re.S)
+        if not m:
+            continue
+        sec = m.group(1)
+        ia = re.search(r"issue active % \(`smsp__issue_active[^`]*`\) \| ([0-9.]+)", sec)
+        ls = re.search(r"stall long scoreboard / issue \([^)]*\) \| ([0-9.]+)", sec)
+        bs = re.search(r"stall barrier / issue \([^)]*\) \| ([0-9.]+)", sec)
+        if ia:
+            out[k] = {"issue_active_frac": float(ia.group(1)) / 100.0,
+                      "stall_long_scoreboard_per_issue": float(ls.group(1)) if ls else None,
+                      "stall_barrier_per_issue": float(bs.group(1)) if bs else None}
+    if not out:
+        return None
+    return {"bound": "issue", "kernels": out,
+            "source": "ncu counters of the same kernel source, uterus geometry at 24 slices per stack "
+                      "(profiles/kernels_uterus24.md)"}
+
+
 L1_BYTES_PER_CLK_SM = 128   # nominal L1 load bandwidth of an SM
 
 
@@ -508,6 +546,7 @@ def run_ours(args, ws, rank, local, dist):
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                      else "fallback 6.4 TB/s"},
         "onchip": _onchip(dom, prof, pt, clocks),
+        "issue": {c: _profile_issue(c) for c in ("ncc", "adjoint")},
         "kernels": breakdown,
         "clocks": clocks,
         "s_per_iteration": t_ms * 1e-3, "psnr_db": {"before": psnr0, "after_timed_steps": psnr1},
