@@ -340,13 +340,93 @@ __global__ void k_metrics3(const double *__restrict__ scr1, const double *__rest
 // the local SSIM of every valid pixel over the valid pixels of its
 // (2w+1)^2 window clipped to the patch (same c1, c2), written as the DSSIM
 // heat map, and the mean local SSIM.
+// Local SSIM of pixel (i, j) from its window sums {k, sum a, sum b, sum a^2,
+// sum b^2, sum ab} over the valid pixels of the window.
+__device__ __forceinline__ double local_ssim(const double S[6], double c1, double c2)
+{
+    const double rk = 1.0 / S[0], ma = S[1] * rk, mb = S[2] * rk;   // one float64 division
+    const double va = fmax(S[3] * rk - ma * ma, 0.0), vb = fmax(S[4] * rk - mb * mb, 0.0);
+    const double cab = S[5] * rk - ma * mb;
+    return ((2.0 * ma * mb + c1) * (2.0 * cab + c2)) / ((ma * ma + mb * mb + c1) * (va + vb + c2));
+}
+
+// Pass 3 with the window sums built row by row: row r of the patch is staged
+// in shared memory, thread i forms its column's horizontal window sums R(i, r)
+// (6 channels) into a ring of the 2w+1 rows of the current window, and the
+// window sums of output row j are the ring's rows added in row order.  Every
+// float64 product is formed once per (pixel, column of its window) instead of
+// once per (pixel, window pixel).  wmax: patch width the ring is sized for.
+__device__ void local_ssim_rows(const float *__restrict__ y, const float *__restrict__ sim,
+                                const uint8_t *__restrict__ valid, size_t off, int W, int H, int w,
+                                int wmax, double c1, double c2, float *__restrict__ map, double ls[2],
+                                double *ring)
+{
+    const int nslot = 2 * w + 1;
+    float *ry = reinterpret_cast<float *>(ring + (size_t)nslot * wmax * 6);
+    float *rs = ry + wmax;
+    uint8_t *rv = reinterpret_cast<uint8_t *>(rs + wmax);
+    const int i = threadIdx.x;
+    auto add_row = [&](int r) {   // stage row r and store its horizontal sums in slot r mod nslot
+        __syncthreads();          // the previous row's staging is no longer read
+        for (int t = threadIdx.x; t < W; t += blockDim.x) {
+            const size_t q = off + (size_t)r * W + t;
+            ry[t] = y[q];
+            rs[t] = sim[q];
+            rv[t] = valid[q];
+        }
+        __syncthreads();
+        if (i < W) {
+            double R[6] = {0, 0, 0, 0, 0, 0};
+            for (int ii = max(i - w, 0); ii <= min(i + w, W - 1); ++ii) {
+                if (!rv[ii]) continue;
+                const double a = ry[ii], b = rs[ii];
+                R[0] += 1.0;
+                R[1] += a;
+                R[2] += b;
+                R[3] += a * a;
+                R[4] += b * b;
+                R[5] += a * b;
+            }
+            double *slot = ring + ((size_t)(r % nslot) * wmax + i) * 6;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) slot[c] = R[c];
+        }
+    };
+    for (int r = 0; r < min(w, H); ++r) add_row(r);
+    for (int j = 0; j < H; ++j) {
+        if (j + w < H) add_row(j + w);
+        // the ring rows are this thread's own column: no barrier needed to read them
+        if (i < W) {
+            const size_t o = off + (size_t)j * W + i;
+            if (!valid[o]) {
+                if (map) map[o] = 0.f;
+                continue;
+            }
+            double S[6] = {0, 0, 0, 0, 0, 0};
+            for (int jj = max(j - w, 0); jj <= min(j + w, H - 1); ++jj) {
+                const double *slot = ring + ((size_t)(jj % nslot) * wmax + i) * 6;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) S[c] += slot[c];
+            }
+            const double ss = local_ssim(S, c1, c2);
+            if (map) map[o] = (float)((1.0 - ss) / 2.0);
+            ls[0] += ss;
+            ls[1] += 1.0;
+        }
+    }
+}
+
+// wmax > 0: the ring of local_ssim_rows (dynamic shared memory) serves
+// patches up to wmax pixels wide; wider ones, and wmax = 0, take the direct
+// window loop.
 __global__ void __launch_bounds__(256) k_patch_metrics(const float *__restrict__ y,
                                                        const float *__restrict__ sim,
                                                        const uint8_t *__restrict__ valid,
                                                        const int32_t *__restrict__ desc, int w,
                                                        double *__restrict__ out,
-                                                       float *__restrict__ map)
+                                                       float *__restrict__ map, int wmax)
 {
+    extern __shared__ double ring[];
     __shared__ double sh[32 * 8];
     __shared__ double glob[8];
     const int32_t *d = desc + 8 * (size_t)blockIdx.x;
@@ -406,6 +486,12 @@ __global__ void __launch_bounds__(256) k_patch_metrics(const float *__restrict__
     }
     // pass 3: local SSIM map
     double ls[2] = {0.0, 0.0};
+    if (W <= wmax && W <= (int)blockDim.x) {
+        local_ssim_rows(y, sim, valid, off, W, H, w, wmax, c1, c2, map, ls, ring);
+        block_sums<2>(ls, sh);
+        if (threadIdx.x == 0) o[4] = ls[1] > 0.0 ? ls[0] / ls[1] : 0.0;
+        return;
+    }
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
         const int j = t / W, i = t - j * W;
         if (!valid[off + t]) {
@@ -506,10 +592,23 @@ cudaError_t launch_patches_gather(const DevGeom *g, const float *stacks, const i
 }
 
 cudaError_t launch_patch_metrics(const float *y, const float *sim, const uint8_t *valid, const int32_t *desc,
-                                 int n, int w, double *out, float *map, cudaStream_t st)
+                                 int n, int w, int max_side, double *out, float *map, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    k_patch_metrics<<<(unsigned)n, 256, 0, st>>>(y, sim, valid, desc, w, out, map);
+    // the row ring (2w+1 rows of 6 float64 per column, plus one staged row)
+    // when it fits 100 KB of shared memory; else the direct window loop
+    int wmax = max_side <= 256 ? max_side : 0;
+    size_t smem = wmax > 0 ? (size_t)(2 * w + 1) * wmax * 6 * sizeof(double) + (size_t)wmax * 9 + 16 : 0;
+    if (smem > 100 * 1024) {
+        wmax = 0;
+        smem = 0;
+    }
+    cudaError_t e;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(k_patch_metrics, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+        return e;
+    k_patch_metrics<<<(unsigned)n, 256, smem, st>>>(y, sim, valid, desc, w, out, map, wmax);
     return cudaGetLastError();
 }
 

@@ -798,7 +798,7 @@ int pvr_patch_metrics(pvr_ctx *c, const float *y, const float *sim, const uint8_
     if (rc) return rc;
     REQUIRE(w >= 0 && w <= 16, "window half-width must be 0..16");
     REQUIRE(pp->n == 0 || (y && sim && valid && out), "NULL argument");
-    CUDA_TRY(launch_patch_metrics(y, sim, valid, pp->desc, pp->n, w, out, map, (cudaStream_t)stream),
+    CUDA_TRY(launch_patch_metrics(y, sim, valid, pp->desc, pp->n, w, ms, out, map, (cudaStream_t)stream),
              "patch_metrics");
     c->launches += pp->n > 0;
     return PVR_OK;

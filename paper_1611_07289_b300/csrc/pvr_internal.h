@@ -181,7 +181,7 @@ cudaError_t launch_patches_gather(const DevGeom *g, const float *stacks, const i
                                   int n, int64_t n_pix, int32_t *err, float *y, cudaStream_t st);
 
 cudaError_t launch_patch_metrics(const float *y, const float *sim, const uint8_t *valid, const int32_t *desc,
-                                 int n, int w, double *out, float *map, cudaStream_t st);
+                                 int n, int w, int max_side, double *out, float *map, cudaStream_t st);
 
 cudaError_t launch_metrics(const float *ref, const float *img, const uint8_t *mask, int64_t n,
                            double *scratch, double *out, cudaStream_t st);
