@@ -574,7 +574,7 @@ __global__ void k_reg_init(const double *__restrict__ poses, int n_params, int n
     active[p] = 1;
 }
 
-// Judge evaluation `eval` (NCC and gradient at the trial pose) and propose
+// Assess evaluation `eval` (NCC and gradient at the trial pose) and propose
 // the next trial: best + delta (g/s) / |g/s| / s, s = per-parameter scale
 // (translations 1 mm; rigid angles the patch half-diagonal times pi/180,
 // affine entries the half-diagonal, so that one scaled unit moves the patch
