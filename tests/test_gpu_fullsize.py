@@ -1,7 +1,9 @@
 """Parity at the benchmark's full size (uterus workload: 256x256x192 volume,
 4 x 96 x 256^2 stacks, patches 64 / stride 32, about 18k patches and 74M
 patch-pixels) in the launch configuration bench.py times (context with
-max_patch_side 64: one 64x64 tile per CTA).
+max_patch_side 64: one 64x64 tile per CTA; the launch plan the benchmark's
+tuner picks for this table, 64-pixel tiles with one CTA per tile, which also
+fixes the spatial patch launch order).
 
 The oracle cannot process 74M patch-pixels in seconds, so it is compared on
 sampled patches of the full-size GPU outputs (forward model, NCC and its
@@ -33,6 +35,7 @@ def full():
     ctx = pvr.Context(geom, prm)
     pt, n = ctx.pvr_patches_build(packed, 64, 32, 0.01, 0.5)
     y = ctx.pvr_patches_gather(packed, pt)
+    assert ctx.pvr_plan(pt, tile=64, mode=0)[:2] == (64, 0)
     rng = np.random.default_rng(7289)
     poses = synth.random_poses(rng, pt.n, rot=5.0, trans=3.0)
     return dict(pvr=pvr, cfg=cfg, geom=geom, packed_np=packed_np, ctx=ctx, pt=pt, n=n, y=y,
