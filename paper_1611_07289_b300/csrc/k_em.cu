@@ -206,13 +206,9 @@ __global__ void __launch_bounds__(256) k_em_estep(const float *__restrict__ y,
     const float inv2s2 = (float)pstat[3], K = (float)pstat[4];
     const bool part_in = !mask_in || mask_in[r.p];
     float sp = 0.f, spe2 = 0.f, sp2 = 0.f, nv = 0.f;
-    const float rtw = 1.0f / (float)r.tw;
-    for (int pp = threadIdx.x; pp < r.tw * r.th; pp += blockDim.x) {
-        const int row = tile_row(pp, rtw);
-        size_t o = (size_t)r.off + (size_t)(r.j0 + row) * r.w + r.i0 + (pp - row * r.tw);
+    auto pixel = [&](bool v, float e) {
         float pv = 0.f;
-        if (valid[o]) {
-            float e = sim ? y[o] - sim[o] : y[o];
+        if (v) {
             pv = m_zero ? 1.f : 1.f / (1.f + K * expf(e * e * inv2s2));
             if (part_in) {
                 sp += pv;
@@ -221,7 +217,39 @@ __global__ void __launch_bounds__(256) k_em_estep(const float *__restrict__ y,
             sp2 = fmaf(pv, pv, sp2);
             nv += 1.f;
         }
-        p_out[o] = pv;
+        return pv;
+    };
+    if (((r.off | r.w | r.i0 | r.tw) & 3) == 0) {
+        // rows of whole 16-byte groups: four pixels per 16-byte load and store
+        const int qw = r.tw >> 2;
+        const float rqw = 1.0f / (float)qw;
+        for (int qq = threadIdx.x; qq < qw * r.th; qq += blockDim.x) {
+            const int row = tile_row(qq, rqw);
+            const size_t o = (size_t)r.off + (size_t)(r.j0 + row) * r.w + r.i0 + 4 * (qq - row * qw);
+            const uchar4 v = *reinterpret_cast<const uchar4 *>(valid + o);
+            float4 e = *reinterpret_cast<const float4 *>(y + o);
+            if (sim) {
+                const float4 s4 = *reinterpret_cast<const float4 *>(sim + o);
+                e.x -= s4.x;
+                e.y -= s4.y;
+                e.z -= s4.z;
+                e.w -= s4.w;
+            }
+            float4 pv;
+            pv.x = pixel(v.x, e.x);
+            pv.y = pixel(v.y, e.y);
+            pv.z = pixel(v.z, e.z);
+            pv.w = pixel(v.w, e.w);
+            *reinterpret_cast<float4 *>(p_out + o) = pv;
+        }
+    } else {
+        const float rtw = 1.0f / (float)r.tw;
+        for (int pp = threadIdx.x; pp < r.tw * r.th; pp += blockDim.x) {
+            const int row = tile_row(pp, rtw);
+            size_t o = (size_t)r.off + (size_t)(r.j0 + row) * r.w + r.i0 + (pp - row * r.tw);
+            const bool v = valid[o];
+            p_out[o] = pixel(v, v ? (sim ? y[o] - sim[o] : y[o]) : 0.f);
+        }
     }
     // float32 tile sums (at most a 64 x 64 tile: counts exact, sums to ~1e-7)
     float a[4] = {sp, spe2, sp2, nv};
