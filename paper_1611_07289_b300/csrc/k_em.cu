@@ -142,14 +142,16 @@ __global__ void __launch_bounds__(kRedThreads) k_em_prepare(int n, int tpp,
     __shared__ double sh[32 * 2];
     double a[2] = {0.0, 0.0}, mn[1] = {INFINITY}, mx[1] = {-INFINITY};
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        if (mask_in && !mask_in[p]) continue;
+        // the mask and the partials are loaded together (16-byte loads)
+        const bool in = !mask_in || mask_in[p];
         for (int t = 0; t < tpp; ++t) {
-            const double *pt = part + ((size_t)p * tpp + t) * kPartStride;
-            if (pt[0] > 0.0) {
-                a[0] += pt[0];
-                a[1] += pt[1];
-                mn[0] = fmin(mn[0], pt[2]);
-                mx[0] = fmax(mx[0], pt[3]);
+            const double2 *pt = reinterpret_cast<const double2 *>(part + ((size_t)p * tpp + t) * kPartStride);
+            const double2 u = pt[0], v = pt[1];   // {N, sum e^2}, {min e, max e}
+            if (in && u.x > 0.0) {
+                a[0] += u.x;
+                a[1] += u.y;
+                mn[0] = fmin(mn[0], v.x);
+                mx[0] = fmax(mx[0], v.y);
             }
         }
     }
@@ -303,22 +305,37 @@ __device__ __forceinline__ void store_block(double *bpart, const double *v, int 
         for (int k = 0; k < nv; ++k) bpart[(size_t)blockIdx.x * 8 + k] = v[k];
 }
 
-// Fold of k_em_patch_pot: pixel-level M-step, patch outlier density, first-
-// call initialisation of the patch-level model.
+// Field k of the nb block partials folded by the 32 lanes of one warp in a
+// fixed order (lane l takes blocks l, l + 32, ..., then a butterfly of
+// shuffles, whose pairwise operations are commutative, so every lane holds
+// the same value): the loads are issued together instead of one after the
+// other by a single thread.  op: 0 sum, 1 min, 2 max.
+__device__ __forceinline__ double warp_fold(int nb, const double *__restrict__ bpart, int k, int op)
+{
+    double s = op == 0 ? 0.0 : (op == 1 ? INFINITY : -INFINITY);
+    for (int b = threadIdx.x & 31; b < nb; b += 32) {
+        const double v = bpart[8 * (size_t)b + k];
+        s = op == 0 ? s + v : (op == 1 ? fmin(s, v) : fmax(s, v));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double t = __shfl_xor_sync(0xffffffffu, s, o);
+        s = op == 0 ? s + t : (op == 1 ? fmin(s, t) : fmax(s, t));
+    }
+    return s;
+}
+
+// Fold of k_em_patch_pot (called by the 32 lanes of warp 0 of the last
+// block): pixel-level M-step, patch outlier density, first-call
+// initialisation of the patch-level model.
 __device__ void em_patch_head(int nb, const double *__restrict__ bpart, double *__restrict__ state,
                               double *__restrict__ pstat, double c0, int rule)
 {
-    double sp = 0, spe2 = 0, ps = 0, ps2 = 0, ne = 0, mn = INFINITY, mx = -INFINITY;
-    for (int b = 0; b < nb; ++b) {
-        const double *v = bpart + 8 * (size_t)b;
-        sp += v[0];
-        spe2 += v[1];
-        ps += v[2];
-        ps2 += v[3];
-        ne += v[4];
-        mn = fmin(mn, v[5]);
-        mx = fmax(mx, v[6]);
-    }
+    const double sp = warp_fold(nb, bpart, 0, 0), spe2 = warp_fold(nb, bpart, 1, 0);
+    const double ps = warp_fold(nb, bpart, 2, 0), ps2 = warp_fold(nb, bpart, 3, 0);
+    const double ne = warp_fold(nb, bpart, 4, 0);
+    const double mn = warp_fold(nb, bpart, 5, 1), mx = warp_fold(nb, bpart, 6, 2);
+    if ((threadIdx.x & 31) != 0) return;
     double sfloor = pstat[0], npart = state[PVR_ST_N_PART];
     if (sp > 0.0) {
         double s2 = spe2 / sp;
@@ -385,24 +402,25 @@ __global__ void __launch_bounds__(256) k_em_patch_pot(const int32_t *__restrict_
     block_reduce<1>(mx, sh, 2);
     double v[7] = {a[0], a[1], a[2], a[3], a[4], mn[0], mx[0]};
     store_block(bpart, v, 7);
-    if (last_block(counter) && threadIdx.x == 0) em_patch_head(gridDim.x, bpart, state, pstat, c0, rule);
+    if (last_block(counter) && threadIdx.x < 32) em_patch_head(gridDim.x, bpart, state, pstat, c0, rule);
 }
 
-// M-step of the patch-level model; stops the loop when m_p = 0 or no weight.
+// M-step of the patch-level model (called by the 32 lanes of warp 0 of the
+// last block); stops the loop when m_p = 0 or no weight.
 __device__ void em_patch_mstep(int nb, const double *__restrict__ bpart, double *__restrict__ state,
                                double *__restrict__ pstat)
 {
-    if (pstat[6] != 0.0) return;
-    if (pstat[5] == 0.0) {
-        pstat[6] = 1.0;
+    const bool lead = (threadIdx.x & 31) == 0;
+    const double stop = pstat[6], mp = pstat[5];
+    __syncwarp();   // every lane has read the flags before lane 0 may write them
+    if (stop != 0.0) return;
+    if (mp == 0.0) {
+        if (lead) pstat[6] = 1.0;
         return;
     }
-    double sw = 0, swp = 0, swp2 = 0;
-    for (int b = 0; b < nb; ++b) {
-        sw += bpart[8 * (size_t)b];
-        swp += bpart[8 * (size_t)b + 1];
-        swp2 += bpart[8 * (size_t)b + 2];
-    }
+    const double sw = warp_fold(nb, bpart, 0, 0), swp = warp_fold(nb, bpart, 1, 0);
+    const double swp2 = warp_fold(nb, bpart, 2, 0);
+    if (!lead) return;
     if (!(sw > 0.0)) {
         pstat[6] = 1.0;
         return;
@@ -459,15 +477,16 @@ __global__ void __launch_bounds__(256) k_em_patch_estep(int n, const uint8_t *__
     __shared__ double sh[32 * 3];
     // the loop has stopped: keep the last weights (every block still counts in)
     if (pstat[6] == 0.0) em_patch_estep_block(n, elig, pbar, state, pstat, wsc, bpart, sh);
-    if (last_block(counter) && mstep && threadIdx.x == 0) em_patch_mstep(gridDim.x, bpart, state, pstat);
+    if (last_block(counter) && mstep && threadIdx.x < 32) em_patch_mstep(gridDim.x, bpart, state, pstat);
 }
 
-// Fold of k_em_patch_final: patch counts into the EM state.
+// Fold of k_em_patch_final (the 32 lanes of warp 0 of the last block):
+// patch counts into the EM state.
 __device__ void em_patch_tail(int nb, const double *__restrict__ bpart, double *__restrict__ state,
                               const double *__restrict__ pstat, int rule)
 {
-    double nin = 0.0;
-    for (int b = 0; b < nb; ++b) nin += bpart[8 * (size_t)b];
+    const double nin = warp_fold(nb, bpart, 0, 0);
+    if ((threadIdx.x & 31) != 0) return;
     state[PVR_ST_N_ELIG] = pstat[7];
     state[PVR_ST_N_IN] = nin;
     if (rule == 0) state[PVR_ST_M_P] = pstat[5];
@@ -498,7 +517,7 @@ __global__ void __launch_bounds__(256) k_em_patch_final(int n, const uint8_t *__
     }
     block_reduce<1>(cnt, sh, 0);
     store_block(bpart, cnt, 1);
-    if (last_block(counter) && threadIdx.x == 0) em_patch_tail(gridDim.x, bpart, state, pstat, rule);
+    if (last_block(counter) && threadIdx.x < 32) em_patch_tail(gridDim.x, bpart, state, pstat, rule);
 }
 
 
