@@ -1965,6 +1965,38 @@ __global__ void k_ncc_finish(const DevGeom *__restrict__ g, int n_params, int n,
         mom[k] = s;
     }
     const int32_t *d = desc + 8 * (size_t)p;
+    if (n_params == 12) {
+        // affine: the derivative of the linear part by entry (a, b) is the
+        // unit matrix E_ab, so column k = 3 + 3a + b of the Jacobian is
+        // W[:, a] S[b, :] (the values pose_jacobian_col forms from E_ab,
+        // whose other products are exact zeros)
+        const double *S = g->p2w[d[0]];
+        const double *W = g->w2v;
+        const double zs = g->dz / sqrt(S[2] * S[2] + S[6] * S[6] + S[10] * S[10]);
+        for (int k = 0; k < 12; ++k) {
+            double jc[12];
+            if (k < 3) {
+                for (int r = 0; r < 3; ++r) {
+                    jc[r] = jc[3 + r] = jc[6 + r] = 0.0;
+                    jc[9 + r] = W[4 * r + k];
+                }
+            } else {
+                const int ea = (k - 3) / 3, eb = (k - 3) % 3;
+                for (int r = 0; r < 3; ++r) {
+                    for (int c = 0; c < 3; ++c) {
+                        const double q = W[4 * r + ea] * S[4 * eb + c];
+                        jc[3 * c + r] = c == 2 ? q * zs : q;
+                    }
+                    jc[9 + r] = 0.0;
+                }
+            }
+            double gsum = 0.0;
+            for (int r = 0; r < 3; ++r)
+                gsum += jc[r] * mom[r] + jc[3 + r] * mom[3 + r] + jc[6 + r] * mom[6 + r] + jc[9 + r] * mom[9 + r];
+            gr[k] = gsum;
+        }
+        return;
+    }
     double dL[9][9];
     linear_derivs(poses + (size_t)n_params * p, n_params, dL);
     for (int k = 0; k < n_params; ++k) {
