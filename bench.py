@@ -1027,7 +1027,7 @@ def main():
     ap.add_argument("--plan", default="", help="force the simulate / adjoint launch plan: 'tile,mode' "
                     "(tile 32 or 64; mode 0 = one CTA per tile, 1 = work queue) instead of tuning it")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched uneven-patch and learned-proposal fields")
+                    help="skip the batched uneven-patch, differentiable and learned-proposal fields")
     ap.add_argument("--outer-full", type=int, default=10, help="outer iterations of the whole-iteration field")
     ap.add_argument("--slices", type=int, default=96,
                     help="slices per stack (96 = the benchmark workload; fewer for profiling)")
